@@ -1,0 +1,476 @@
+"""Plain FP64 CPU oracle of the TILD timestep (MATILDA.FT, arXiv 2302.02474).
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module. It shares no code with the CUDA path and imports nothing from it;
+both sides receive the same seeded arrays from the input generator.
+
+What it computes, in the paper's notation (Sec. "Structure of
+theoretically-informed coarse-grained and field-theoretic models" and
+Sec. "Long-range interactions"):
+
+* microscopic densities rho_K (Eq. rhohat) assigned to a periodic grid with
+  the Deserno-Holm / cardinal B-spline weights of order P = pmeorder + 1
+  (Sec. "Long-range interactions"; the same weights interpolate forces back,
+  caption of Fig. pmm);
+* the Gaussian-smeared Flory (Eq. fh) and Helfand (Eq. HelfandP) energies,
+  with u_G a unit Gaussian of width sigma, sigma^2 = 2 a^2 (Eqs. smearRho,
+  fhF, HelfandF), evaluated by FFT convolution (Eq. PMM);
+* the harmonic bond energy with spring constant 3/b^2 (Eq. bonds);
+* the Gronbech-Jensen-Farago Langevin integrator (named in the Integrator
+  Class list and used by Listing infile), with Philox4x32-10 random numbers
+  and Box-Muller normals.
+
+Readings where the paper is silent are listed with each function.
+Everything here is FP64; the only library primitives are numpy's FFT and
+``bincount``.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, Optional
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Periodic box
+# ---------------------------------------------------------------------------
+
+
+def wrap(x: np.ndarray, L: float) -> np.ndarray:
+    """Map coordinates into [0, L). A value that rounds to L maps to 0."""
+    y = x - L * np.floor(x / L)
+    return np.where(y >= L, 0.0, y)
+
+
+def minimum_image(d: np.ndarray, L: float) -> np.ndarray:
+    """Minimum-image displacement in a cubic periodic box of edge L.
+
+    Reading: the paper does not say how bonds that cross the boundary are
+    measured; bonds are much shorter than L/2, so the minimum image is the
+    bond vector.
+    """
+    return d - L * np.round(d / L)
+
+
+# ---------------------------------------------------------------------------
+# Assignment weights (Sec. "Long-range interactions": spline weights from the
+# appendix of Deserno & Holm 1998, orders 1..4; Fig. pmm: order 1 uses the
+# two nearest grid points per dimension)
+# ---------------------------------------------------------------------------
+
+
+def cardinal_bspline(x: np.ndarray, P: int) -> np.ndarray:
+    """Cardinal B-spline M_P(x), the P-fold convolution of the unit box on [0, 1).
+
+    Cox-de Boor recursion: M_1 = 1 on [0, 1);
+    M_P(x) = (x M_{P-1}(x) + (P - x) M_{P-1}(x - 1)) / (P - 1).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    if P == 1:
+        return ((x >= 0.0) & (x < 1.0)).astype(np.float64)
+    return (x * cardinal_bspline(x, P - 1) + (P - x) * cardinal_bspline(x - 1.0, P - 1)) / (P - 1)
+
+
+def cardinal_bspline_derivative(x: np.ndarray, P: int) -> np.ndarray:
+    """dM_P/dx = M_{P-1}(x) - M_{P-1}(x - 1)  (P >= 2)."""
+    return cardinal_bspline(x, P - 1) - cardinal_bspline(x - 1.0, P - 1)
+
+
+def stencil(s: np.ndarray, P: int):
+    """Grid points and weights along one axis for positions s in grid units.
+
+    The Deserno-Holm charge-assignment function of order P is the centred
+    cardinal B-spline W(t) = M_P(t + P/2); a particle at s gives grid point j
+    the weight W(s - j). Its support |s - j| < P/2 holds P points, the first
+    being floor(s - P/2) + 1. Returns (j, w) with shape (len(s), P); j is
+    not yet reduced modulo the grid size.
+    """
+    j0 = np.floor(s - P / 2.0).astype(np.int64) + 1
+    j = j0[:, None] + np.arange(P, dtype=np.int64)[None, :]
+    w = cardinal_bspline(s[:, None] - j + P / 2.0, P)
+    return j, w
+
+
+def stencil_derivative(s: np.ndarray, P: int):
+    """Same points as ``stencil``; d W(s - j) / d s (grid units)."""
+    j, _ = stencil(s, P)
+    dw = cardinal_bspline_derivative(s[:, None] - j + P / 2.0, P)
+    return j, dw
+
+
+# ---------------------------------------------------------------------------
+# System description
+# ---------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Model:
+    """Parameters of one TILD system (reduced units).
+
+    chi: S x S symmetric matrix with zero diagonal (Eq. fh generalised to S
+    species pairs). rho0 = total bead number density N_b / V (Eq. HelfandP,
+    rho_0 = nN/V). a: smearing width of h, sigma^2 = 2 a^2 (Eqs. fhF/HelfandF).
+    """
+
+    L: float
+    n: int
+    P: int
+    species: np.ndarray          # (N_b,) int
+    n_species: int
+    bonds: np.ndarray            # (n_bonds, 2) int
+    b: float
+    chi: np.ndarray              # (S, S)
+    kappa: float
+    a: float
+    dt: float = 0.005
+    friction: float = 1.0
+    kT: float = 1.0
+    mass: float = 1.0
+    seed: int = 0
+
+    @property
+    def n_beads(self) -> int:
+        return int(self.species.shape[0])
+
+    @property
+    def dx(self) -> float:
+        return self.L / self.n
+
+    @property
+    def volume(self) -> float:
+        return self.L ** 3
+
+    @property
+    def rho0(self) -> float:
+        return self.n_beads / self.volume
+
+    def eps(self) -> np.ndarray:
+        """Pair matrix of U_nb = 1/2 sum_KK' eps_KK' int int rho_K u_G rho_K'.
+
+        Expanding Eq. fh plus Eq. HelfandP (rho_+ = sum_K rho_K) gives
+        eps_KK' = (chi_KK' + kappa) / rho0 with chi_KK = 0, up to a constant.
+        """
+        S = self.n_species
+        chi = np.zeros((S, S))
+        chi[: self.chi.shape[0], : self.chi.shape[1]] = self.chi[:S, :S]
+        return (chi + self.kappa) / self.rho0
+
+
+def model_from_spec(spec, species: np.ndarray, bonds: np.ndarray) -> Model:
+    """Build a Model from an input-generator SystemSpec (duck-typed)."""
+    S = 2 if int(species.max(initial=0)) >= 1 else 1
+    chi = np.zeros((S, S))
+    if S == 2:
+        chi[0, 1] = chi[1, 0] = spec.chi
+    return Model(L=spec.L, n=spec.n, P=spec.pmeorder + 1, species=species.astype(np.int64), n_species=S,
+                 bonds=bonds.astype(np.int64), b=spec.b, chi=chi, kappa=spec.kappa, a=spec.a, dt=spec.dt,
+                 friction=spec.friction, kT=spec.kT, mass=spec.mass, seed=spec.dyn_seed)
+
+
+# ---------------------------------------------------------------------------
+# Wavevectors
+# ---------------------------------------------------------------------------
+
+
+def wavenumbers(n: int, L: float) -> np.ndarray:
+    """k = 2 pi m / L with m in {0, .., n/2-1, -n/2, .., -1} (numpy FFT order)."""
+    m = np.fft.fftfreq(n, d=1.0 / n)
+    return 2.0 * np.pi * m / L
+
+
+def gradient_wavenumbers(n: int, L: float) -> np.ndarray:
+    """Wavenumbers for spectral differentiation: the Nyquist entry (m = -n/2,
+    even n) is set to zero so that the derivative of a real field stays real.
+    """
+    k = wavenumbers(n, L).copy()
+    if n % 2 == 0:
+        k[n // 2] = 0.0
+    return k
+
+
+def gaussian_kernel_hat(n: int, L: float, a: float) -> np.ndarray:
+    """u_hat(k) = exp(-|k|^2 sigma^2 / 2) = exp(-|k|^2 a^2): the continuous
+    Fourier transform of the unit Gaussian u_G (Eq. fh) with sigma^2 = 2 a^2;
+    u_hat(0) = 1. Axes (x, y, z)."""
+    k = wavenumbers(n, L)
+    k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2
+    return np.exp(-k2 * a * a)
+
+
+# ---------------------------------------------------------------------------
+# Particle-to-mesh
+# ---------------------------------------------------------------------------
+
+
+def spread(m: Model, pos: np.ndarray) -> np.ndarray:
+    """Grid densities rho_K(g) = (1/dV) sum_{i in K} prod_d W(s_id - g_d)
+    (Eq. rhohat assigned with the spline weights). Array axes (K, x, y, z)."""
+    n, P = m.n, m.P
+    s = wrap(pos, m.L) / m.dx
+    jx, wx = stencil(s[:, 0], P)
+    jy, wy = stencil(s[:, 1], P)
+    jz, wz = stencil(s[:, 2], P)
+    rho = np.zeros((m.n_species, n * n * n))
+    for K in range(m.n_species):
+        sel = m.species == K
+        for a in range(P):
+            for b in range(P):
+                for c in range(P):
+                    flat = ((jx[sel, a] % n) * n + (jy[sel, b] % n)) * n + (jz[sel, c] % n)
+                    w = wx[sel, a] * wy[sel, b] * wz[sel, c]
+                    rho[K] += np.bincount(flat, weights=w, minlength=n ** 3)
+    return rho.reshape(m.n_species, n, n, n) / m.dx ** 3
+
+
+def gather(m: Model, pos: np.ndarray, field: np.ndarray, which: Optional[np.ndarray] = None) -> np.ndarray:
+    """Interpolate per-species grid vectors field[K, d, x, y, z] to the beads
+    with the same weights as ``spread`` (caption of Fig. pmm). Returns (N, D)."""
+    idx = np.arange(m.n_beads) if which is None else np.asarray(which)
+    n, P = m.n, m.P
+    s = wrap(pos[idx], m.L) / m.dx
+    jx, wx = stencil(s[:, 0], P)
+    jy, wy = stencil(s[:, 1], P)
+    jz, wz = stencil(s[:, 2], P)
+    K = m.species[idx]
+    D = field.shape[1]
+    out = np.zeros((len(idx), D))
+    for a in range(P):
+        for b in range(P):
+            for c in range(P):
+                w = wx[:, a] * wy[:, b] * wz[:, c]
+                gx, gy, gz = jx[:, a] % n, jy[:, b] % n, jz[:, c] % n
+                for d in range(D):
+                    out[:, d] += w * field[K, d, gx, gy, gz]
+    return out
+
+
+def potential_fields(m: Model, rho: np.ndarray) -> Dict[str, np.ndarray]:
+    """Spectral evaluation of Eq. PMM for the smeared pair kernel.
+
+    rho_hat_K(k) = sum_g rho_K(g) exp(-i k.g)          (unnormalised DFT)
+    w_hat_K(k)   = u_hat(k) sum_K' eps_KK' rho_hat_K'(k)
+    w_K(g)       = (1/M) sum_k w_hat_K(k) exp(i k.g)      (potential field)
+    grad w_K(g)  = (1/M) sum_k i k~ w_hat_K(k) exp(i k.g) (k~: Nyquist zeroed)
+
+    The continuum convolution int u(r - r') rho(r') dr' becomes this sum
+    because the Fourier coefficient of rho is dV * rho_hat and V = M dV.
+    """
+    n, L = m.n, m.L
+    rho_hat = np.fft.fftn(rho, axes=(1, 2, 3))
+    u_hat = gaussian_kernel_hat(n, L, m.a)
+    eps = m.eps()
+    w_hat = np.einsum("kl,l...->k...", eps, rho_hat) * u_hat[None]
+    kt = gradient_wavenumbers(n, L)
+    kvec = (kt[:, None, None], kt[None, :, None], kt[None, None, :])
+    grad = np.empty((m.n_species, 3, n, n, n))
+    for K in range(m.n_species):
+        for d in range(3):
+            grad[K, d] = np.fft.ifftn(1j * kvec[d] * w_hat[K]).real
+    w = np.fft.ifftn(w_hat, axes=(1, 2, 3)).real
+    return {"rho_hat": rho_hat, "w_hat": w_hat, "w": w, "grad_w": grad, "u_hat": u_hat}
+
+
+# ---------------------------------------------------------------------------
+# Energies (Eqs. bonds, fh, HelfandP) and forces
+# ---------------------------------------------------------------------------
+
+
+def bond_vectors(m: Model, pos: np.ndarray) -> np.ndarray:
+    return minimum_image(pos[m.bonds[:, 0]] - pos[m.bonds[:, 1]], m.L)
+
+
+def bond_energy(m: Model, pos: np.ndarray) -> float:
+    """beta U_0 = (3 / 2b^2) sum_bonds |r_i - r_j|^2  (Eq. bonds)."""
+    d = bond_vectors(m, pos)
+    return float(1.5 / m.b ** 2 * np.sum(d * d))
+
+
+def bond_forces(m: Model, pos: np.ndarray) -> np.ndarray:
+    """-dU_0/dr_i = -(3/b^2) sum_{j bonded to i} (r_i - r_j)."""
+    d = bond_vectors(m, pos)
+    f = np.zeros((m.n_beads, 3))
+    k = 3.0 / m.b ** 2
+    np.add.at(f, m.bonds[:, 0], -k * d)
+    np.add.at(f, m.bonds[:, 1], k * d)
+    return f
+
+
+def field_energies(m: Model, rho_hat: np.ndarray) -> Dict[str, float]:
+    """Flory and Helfand energies from the density spectra (Parseval).
+
+    With rho'_K(k) = dV rho_hat_K(k) (Fourier coefficients of the gridded
+    density) the periodic double integrals of Eqs. fh and HelfandP become
+      E_chi   = sum_{K<K'} (chi_KK'/rho0) (1/V) sum_k u_hat Re[conj(rho'_K) rho'_K'],
+      E_kappa = (kappa / 2 rho0) (1/V) sum_{k != 0} u_hat |sum_K rho'_K|^2.
+    The k = 0 Helfand term cancels the -rho0 shift exactly because the
+    weights conserve mass (reading: E_chi keeps k = 0 as Eq. fh does).
+    """
+    dV = m.dx ** 3
+    V = m.volume
+    u_hat = gaussian_kernel_hat(m.n, m.L, m.a)
+    rp = dV * rho_hat
+    e_chi = 0.0
+    for K in range(m.n_species):
+        for Kp in range(K + 1, m.n_species):
+            chi = m.chi[K, Kp] if K < m.chi.shape[0] and Kp < m.chi.shape[1] else 0.0
+            e_chi += chi / m.rho0 / V * float(np.sum(u_hat * np.real(np.conj(rp[K]) * rp[Kp])))
+    tot = rp.sum(axis=0)
+    p = u_hat * np.abs(tot) ** 2
+    p[0, 0, 0] = 0.0
+    e_kappa = m.kappa / (2.0 * m.rho0) / V * float(np.sum(p))
+    return {"chi": e_chi, "kappa": e_kappa}
+
+
+def nonbonded_forces(m: Model, pos: np.ndarray, variant: str = "ik") -> np.ndarray:
+    """Particle-mesh force of Eq. PMM.
+
+    variant "ik" (the method): F_i = -sum_g W(r_i - g) grad w_K(g), the
+    spectral gradient interpolated with the assignment weights.
+    variant "analytic": F_i = -sum_g grad_r W(r_i - g) w_K(g), the exact
+    gradient of the gridded energy (used to check forces against finite
+    differences of the energy).
+    """
+    rho = spread(m, pos)
+    f = potential_fields(m, rho)
+    if variant == "ik":
+        return -gather(m, pos, f["grad_w"])
+    if variant != "analytic":
+        raise ValueError(variant)
+    n, P, dx = m.n, m.P, m.dx
+    s = wrap(pos, m.L) / dx
+    js, ws, dws = [], [], []
+    for d in range(3):
+        j, w = stencil(s[:, d], P)
+        _, dw = stencil_derivative(s[:, d], P)
+        js.append(j % n)
+        ws.append(w)
+        dws.append(dw / dx)
+    w_field = f["w"][m.species]
+    out = np.zeros((m.n_beads, 3))
+    rows = np.arange(m.n_beads)
+    for a in range(P):
+        for b in range(P):
+            for c in range(P):
+                val = w_field[rows, js[0][:, a], js[1][:, b], js[2][:, c]]
+                out[:, 0] -= dws[0][:, a] * ws[1][:, b] * ws[2][:, c] * val
+                out[:, 1] -= ws[0][:, a] * dws[1][:, b] * ws[2][:, c] * val
+                out[:, 2] -= ws[0][:, a] * ws[1][:, b] * dws[2][:, c] * val
+    return out
+
+
+def forces(m: Model, pos: np.ndarray, variant: str = "ik") -> np.ndarray:
+    return nonbonded_forces(m, pos, variant) + bond_forces(m, pos)
+
+
+def energies(m: Model, pos: np.ndarray) -> Dict[str, float]:
+    rho = spread(m, pos)
+    e = field_energies(m, np.fft.fftn(rho, axes=(1, 2, 3)))
+    e["bond"] = bond_energy(m, pos)
+    return e
+
+
+# ---------------------------------------------------------------------------
+# Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) and
+# Box-Muller normals. Counter (bead id, step lo, step hi, 0), key (seed lo,
+# seed hi). Reading: the paper says only that GJF draws its thermal noise
+# internally; any such generator defines a different (equally valid)
+# trajectory, so this choice is part of the definition of parity.
+# ---------------------------------------------------------------------------
+
+_M0 = np.uint64(0xD2511F53)
+_M1 = np.uint64(0xCD9E8D57)
+_W0 = np.uint32(0x9E3779B9)
+_W1 = np.uint32(0xBB67AE85)
+_MASK = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Ten Philox-4x32 rounds. All arguments uint32 arrays (broadcastable)."""
+    c0, c1, c2, c3 = (np.asarray(v, dtype=np.uint32) for v in (c0, c1, c2, c3))
+    k0 = np.asarray(k0, dtype=np.uint64)
+    k1 = np.asarray(k1, dtype=np.uint64)
+    for r in range(10):
+        if r > 0:  # key schedule: add the Weyl constants modulo 2^32
+            k0 = (k0 + np.uint64(_W0)) & _MASK
+            k1 = (k1 + np.uint64(_W1)) & _MASK
+        p0 = _M0 * c0.astype(np.uint64)
+        p1 = _M1 * c2.astype(np.uint64)
+        hi0 = (p0 >> np.uint64(32)).astype(np.uint32)
+        lo0 = (p0 & _MASK).astype(np.uint32)
+        hi1 = (p1 >> np.uint64(32)).astype(np.uint32)
+        lo1 = (p1 & _MASK).astype(np.uint32)
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0.astype(np.uint32), lo1, hi0 ^ c3 ^ k1.astype(np.uint32), lo0
+    return c0, c1, c2, c3
+
+
+def gaussian_triplets(ids: np.ndarray, step: int, seed: int) -> np.ndarray:
+    """Three standard normals per bead id from one Philox block.
+
+    u_j = (x_j + 1/2) 2^-32 in (0, 1); (n0, n1) = Box-Muller(u0, u1),
+    n2 = sqrt(-2 ln u2) cos(2 pi u3). step is taken modulo 2^64.
+    """
+    step = int(step) % (1 << 64)
+    ids = np.asarray(ids, dtype=np.uint64)
+    x = philox4x32_10(ids & _MASK, np.uint32(step & 0xFFFFFFFF), np.uint32(step >> 32), np.uint32(0),
+                      np.uint32(seed & 0xFFFFFFFF), np.uint32((seed >> 32) & 0xFFFFFFFF))
+    u = [(xi.astype(np.float64) + 0.5) * 2.0 ** -32 for xi in x]
+    r1 = np.sqrt(-2.0 * np.log(u[0]))
+    r2 = np.sqrt(-2.0 * np.log(u[2]))
+    return np.stack([r1 * np.cos(2 * np.pi * u[1]), r1 * np.sin(2 * np.pi * u[1]),
+                     r2 * np.cos(2 * np.pi * u[3])], axis=1)
+
+
+VELOCITY_INIT_STEP = (1 << 64) - 1
+
+
+# ---------------------------------------------------------------------------
+# Gronbech-Jensen-Farago integrator (Mol. Phys. 111, 983 (2013))
+# ---------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class State:
+    pos: np.ndarray      # (N, 3) wrapped positions r^n
+    vel: np.ndarray      # (N, 3) velocities v^n
+    force: np.ndarray    # (N, 3) total force F^n = F(r^n)
+    step: int            # n
+
+
+def initial_state(m: Model, pos: np.ndarray, force_fn=None) -> State:
+    """v^0 ~ N(0, kT/m) per component (Philox block at step 2^64-1);
+    F^0 evaluated at r^0. ``force_fn(m, pos)`` defaults to ``forces``."""
+    force_fn = forces if force_fn is None else force_fn
+    ids = np.arange(m.n_beads)
+    vel = np.sqrt(m.kT / m.mass) * gaussian_triplets(ids, VELOCITY_INIT_STEP, m.seed)
+    p = wrap(pos, m.L)
+    return State(p, vel, force_fn(m, p), 0)
+
+
+def gjf_step(m: Model, st: State, force_fn=None) -> State:
+    """One GJF step:
+      r^{n+1} = r^n + b dt v^n + (b dt^2 / 2m) F^n + (b dt / 2m) beta^{n+1}
+      v^{n+1} = a v^n + (dt / 2m)(a F^n + F^{n+1}) + (b / m) beta^{n+1}
+    with a = (1 - alpha dt/2m)/(1 + alpha dt/2m), b = 1/(1 + alpha dt/2m) and
+    beta^{n+1} ~ N(0, 2 alpha kT dt) per component (drawn with counter step
+    n+1). alpha is the friction coefficient.
+    """
+    dt, mass, alpha = m.dt, m.mass, m.friction
+    ga = (1.0 - alpha * dt / (2 * mass)) / (1.0 + alpha * dt / (2 * mass))
+    gb = 1.0 / (1.0 + alpha * dt / (2 * mass))
+    beta = np.sqrt(2.0 * alpha * m.kT * dt) * gaussian_triplets(np.arange(m.n_beads), st.step + 1, m.seed)
+    r_new = st.pos + gb * dt * st.vel + gb * dt * dt / (2 * mass) * st.force + gb * dt / (2 * mass) * beta
+    r_new = wrap(r_new, m.L)
+    f_new = (forces if force_fn is None else force_fn)(m, r_new)
+    v_new = ga * st.vel + dt / (2 * mass) * (ga * st.force + f_new) + gb / mass * beta
+    return State(r_new, v_new, f_new, st.step + 1)
+
+
+def run(m: Model, st: State, n_steps: int, force_fn=None) -> State:
+    for _ in range(n_steps):
+        st = gjf_step(m, st, force_fn)
+    return st
+
+
+def kinetic_energy(m: Model, vel: np.ndarray) -> float:
+    return float(0.5 * m.mass * np.sum(vel * vel))

@@ -1,0 +1,158 @@
+"""Seeded synthetic inputs for TILD systems (shared by the CUDA path's tests,
+the benchmark and the CPU oracle).
+
+This module holds no arithmetic of the method itself: it only describes
+systems (chain architectures, box, grid, interaction parameters) and draws
+initial coordinates. Both the oracle and the GPU path receive the arrays it
+returns.
+
+System model (MATILDA.FT, arXiv 2302.02474, Sec. "Structure of
+theoretically-informed coarse-grained and field-theoretic models"): linear
+bead-spring chains of species A and B (Eq. rhohat), joined by harmonic bonds
+of statistical segment length b (Eq. bonds).
+
+Initial coordinates ("uniform random-walk chain initialisation"): the first
+bead of every chain is uniform in the periodic box; each following bead sits
+at distance exactly b from its predecessor along a direction uniform on the
+sphere. Drawn with numpy's PCG64 in FP64 and wrapped into [0, L).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class MolType:
+    """One molecule type: ``n_chains`` linear chains of ``N`` beads.
+
+    ``n_a`` leading beads of each chain are species 0 (A); the remaining
+    ``N - n_a`` are species 1 (B). ``n_a == N`` gives an A homopolymer and
+    ``n_a == 0`` a B homopolymer.
+    """
+
+    n_chains: int
+    N: int
+    n_a: int
+
+
+@dataclasses.dataclass(frozen=True)
+class SystemSpec:
+    """A complete TILD system description (all in reduced units kT=m=b=1)."""
+
+    name: str
+    moltypes: Tuple[MolType, ...]
+    L: float            # cubic box edge
+    n: int              # grid points per edge
+    pmeorder: int       # assignment order p (p+1 stencil points per dimension)
+    a: float            # Gaussian smearing width (sigma^2 = 2 a^2)
+    chi: float          # Flory-Huggins chi between A and B
+    kappa: float        # Helfand compressibility
+    dt: float
+    friction: float
+    kT: float
+    mass: float
+    b: float            # statistical segment length (bond constant 3/b^2)
+    steps: int          # length of the run the configuration is quoted for
+    precision: str      # "fp32" or "fp64"
+    input_seed: int
+    dyn_seed: int
+
+    @property
+    def n_beads(self) -> int:
+        return sum(m.n_chains * m.N for m in self.moltypes)
+
+    @property
+    def n_species(self) -> int:
+        has_a = any(m.n_a > 0 and m.n_chains > 0 for m in self.moltypes)
+        has_b = any(m.n_a < m.N and m.n_chains > 0 for m in self.moltypes)
+        return 2 if (has_a and has_b) else 1 if has_a else 2
+
+    def with_(self, **kw) -> "SystemSpec":
+        return dataclasses.replace(self, **kw)
+
+
+def config(name: str) -> SystemSpec:
+    """Named workloads.
+
+    ``diblock_20k_32``   AB diblock melt, 1,000 x A10-B10 (20,000 beads), L=20, 32^3, FP64.
+    ``diblock_1p6M_128`` AB diblock melt, 80,000 x A8-B12 (1.6M beads), L=64, 128^3, FP32.
+    ``blend_6p4M_256``   A/B homopolymer blend (N=32) + A16-B16 compatibiliser,
+                         6.4M beads in 40/40/20 bead fractions, L=128, 256^3, FP32.
+    ``diblock_200k_64``  AB diblock melt, 10,000 x A10-B10 (200,000 beads), L=32, 64^3.
+    """
+    if name == "diblock_20k_32":
+        return SystemSpec(name, (MolType(1000, 20, 10),), 20.0, 32, 1, 0.5, 1.0, 20.0,
+                          0.005, 1.0, 1.0, 1.0, 1.0, 100, "fp64", 12345 + 1, 777 + 1)
+    if name == "diblock_1p6M_128":
+        return SystemSpec(name, (MolType(80000, 20, 8),), 64.0, 128, 1, 0.5, 0.8, 25.0,
+                          0.005, 1.0, 1.0, 1.0, 1.0, 10000, "fp32", 12345 + 2, 777 + 2)
+    if name == "blend_6p4M_256":
+        return SystemSpec(name, (MolType(80000, 32, 32), MolType(80000, 32, 0), MolType(40000, 32, 16)),
+                          128.0, 256, 1, 0.6, 0.5, 30.0, 0.005, 1.0, 1.0, 1.0, 1.0, 2000, "fp32",
+                          12345 + 3, 777 + 3)
+    if name == "diblock_200k_64":
+        return SystemSpec(name, (MolType(10000, 20, 10),), 32.0, 64, 1, 0.5, 1.0, 25.0,
+                          0.005, 1.0, 1.0, 1.0, 1.0, 200, "fp32", 12345 + 4, 777 + 4)
+    raise KeyError(name)
+
+
+def small_system(n_chains: int = 40, N: int = 10, n_a: int = 4, L: float = 6.0, n: int = 12,
+                 pmeorder: int = 1, precision: str = "fp64", chi: float = 1.3, kappa: float = 7.0,
+                 a: float = 0.5, seed: int = 5, **kw) -> SystemSpec:
+    """A small diblock melt for fast tests (ragged sizes allowed)."""
+    base = SystemSpec("small", (MolType(n_chains, N, n_a),), float(L), int(n), int(pmeorder), float(a),
+                      float(chi), float(kappa), 0.005, 1.0, 1.0, 1.0, 1.0, 10, precision, seed, seed + 1000)
+    return base.with_(**kw) if kw else base
+
+
+def species_of_beads(moltypes: Sequence[MolType]) -> np.ndarray:
+    """Species index (0=A, 1=B) of every bead, beads numbered chain by chain."""
+    out: List[np.ndarray] = []
+    for m in moltypes:
+        one = np.concatenate([np.zeros(m.n_a, np.int8), np.ones(m.N - m.n_a, np.int8)])
+        out.append(np.tile(one, m.n_chains))
+    return np.concatenate(out) if out else np.zeros(0, np.int8)
+
+
+def bond_pairs(moltypes: Sequence[MolType]) -> np.ndarray:
+    """(n_bonds, 2) int64 array of bonded bead pairs (i, i+1) along every chain."""
+    out: List[np.ndarray] = []
+    start = 0
+    for m in moltypes:
+        if m.N >= 2 and m.n_chains > 0:
+            first = start + np.arange(m.n_chains, dtype=np.int64)[:, None] * m.N
+            i = (first + np.arange(m.N - 1, dtype=np.int64)[None, :]).reshape(-1)
+            out.append(np.stack([i, i + 1], axis=1))
+        start += m.n_chains * m.N
+    return np.concatenate(out) if out else np.zeros((0, 2), np.int64)
+
+
+def random_walk_positions(moltypes: Sequence[MolType], L: float, b: float, seed: int) -> np.ndarray:
+    """(n_beads, 3) float64 coordinates wrapped into [0, L), chain by chain."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    chunks: List[np.ndarray] = []
+    for m in moltypes:
+        if m.n_chains == 0:
+            continue
+        first = rng.uniform(0.0, L, size=(m.n_chains, 1, 3))
+        u = rng.normal(size=(m.n_chains, m.N - 1, 3))
+        u /= np.linalg.norm(u, axis=2, keepdims=True)
+        steps = np.concatenate([np.zeros((m.n_chains, 1, 3)), b * u], axis=1)
+        chunks.append((first + np.cumsum(steps, axis=1)).reshape(-1, 3))
+    r = np.concatenate(chunks) if chunks else np.zeros((0, 3))
+    r = np.mod(r, L)
+    r[r >= L] = 0.0
+    return r
+
+
+def initial_positions(spec: SystemSpec) -> np.ndarray:
+    return random_walk_positions(spec.moltypes, spec.L, spec.b, spec.input_seed)
+
+
+def random_positions(n_beads: int, L: float, seed: int) -> np.ndarray:
+    """Uniform positions in [0, L)^3 (for kernel-level tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(0.0, L, size=(n_beads, 3))

@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test names what it pins. None of them re-types an oracle formula: they
+compare against published vectors, hand-derived closed forms, direct
+real-space sums, invariants or brute force on tiny inputs.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import tild_oracle as O
+from paper_2302_02474_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _model(n_chains=6, N=5, n_a=2, L=4.0, n=8, P=2, chi=1.7, kappa=3.0, a=1.0, seed=3, **kw):
+    mt = (I.MolType(n_chains, N, n_a),)
+    sp = I.species_of_beads(mt)
+    bonds = I.bond_pairs(mt)
+    m = O.Model(L=L, n=n, P=P, species=sp.astype(np.int64), n_species=2, bonds=bonds, b=1.0,
+                chi=np.array([[0.0, chi], [chi, 0.0]]), kappa=kappa, a=a, seed=seed, **kw)
+    pos = I.random_walk_positions(mt, L, 1.0, seed)
+    return m, pos
+
+
+# --------------------------------------------------------------------- RNG
+
+
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the published known-answer vectors."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox4x32_10(*v[:6])
+        assert [int(x) for x in out] == v[6:]
+
+
+def test_gaussian_triplets_moments():
+    """Box-Muller normals: zero mean, unit variance, uncorrelated, and a
+    different stream for each (id, step)."""
+    g = O.gaussian_triplets(np.arange(200000), 7, 99)
+    assert abs(g.mean()) < 5e-3
+    assert np.allclose(g.var(axis=0), 1.0, atol=1e-2)
+    c = np.corrcoef(g.T)
+    assert np.all(np.abs(c - np.eye(3)) < 1e-2)
+    g2 = O.gaussian_triplets(np.arange(200000), 8, 99)
+    assert abs(np.corrcoef(g[:, 0], g2[:, 0])[0, 1]) < 1e-2
+    # fourth moment of a normal is 3
+    assert abs(np.mean(g ** 4) - 3.0) < 0.05
+
+
+# ----------------------------------------------------------------- weights
+
+
+def test_assignment_weights_golden():
+    """Deserno-Holm closed forms at t = 1/4 for P = 2..5."""
+    for line in open(os.path.join(GOLDEN, "assignment_weights.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(x) for x in line.split()]
+        P, first, nums, den = v[0], v[1], v[2:-1], v[-1]
+        j, w = O.stencil(np.array([3.25]), P)
+        assert j[0, 0] == first
+        np.testing.assert_allclose(w[0], np.array(nums) / den, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("P", [2, 3, 4, 5])
+def test_assignment_weights_invariants(P):
+    """Partition of unity, reproduction of linear functions (first moment),
+    symmetry W(t) = W(-t), continuity across cell boundaries."""
+    rng = np.random.default_rng(P)
+    s = rng.uniform(0, 50, 5000)
+    j, w = O.stencil(s, P)
+    np.testing.assert_allclose(w.sum(1), 1.0, atol=1e-14)
+    np.testing.assert_allclose((j * w).sum(1), s, atol=1e-12)
+    assert np.all(w >= -1e-16)
+    t = rng.uniform(-P / 2, P / 2, 1000)
+    np.testing.assert_allclose(O.cardinal_bspline(t + P / 2, P), O.cardinal_bspline(-t + P / 2, P), atol=1e-14)
+    # continuity: weights seen from just below and just above an integer agree
+    for base in (3.0, 3.5):
+        lo, hi = base - 1e-12, base + 1e-12
+        jl, wl = O.stencil(np.array([lo]), P)
+        jh, wh = O.stencil(np.array([hi]), P)
+        fl = {int(a): b for a, b in zip(jl[0], wl[0])}
+        fh = {int(a): b for a, b in zip(jh[0], wh[0])}
+        for k in set(fl) | set(fh):
+            assert abs(fl.get(k, 0.0) - fh.get(k, 0.0)) < 1e-10
+
+
+def test_cic_is_two_nearest_points():
+    """Order 1 maps a particle to the two nearest grid points per dimension
+    with linear weights (Fig. pmm)."""
+    j, w = O.stencil(np.array([5.3]), 2)
+    assert list(j[0]) == [5, 6]
+    np.testing.assert_allclose(w[0], [0.7, 0.3], atol=1e-14)
+
+
+def test_bspline_derivative_matches_finite_difference():
+    x = np.linspace(0.01, 3.99, 397)
+    h = 1e-6
+    fd = (O.cardinal_bspline(x + h, 4) - O.cardinal_bspline(x - h, 4)) / (2 * h)
+    np.testing.assert_allclose(O.cardinal_bspline_derivative(x, 4), fd, atol=1e-8)
+
+
+# ------------------------------------------------------------------ spread
+
+
+@pytest.mark.parametrize("P", [2, 3, 4, 5])
+def test_spread_conserves_mass(P):
+    """sum_g rho_K dV = number of beads of species K (Eq. rhohat)."""
+    m, pos = _model(P=P, n_chains=13, N=7, n_a=3, L=5.0, n=10)
+    rho = O.spread(m, pos)
+    dV = m.dx ** 3
+    for K in range(2):
+        assert abs(rho[K].sum() * dV - np.sum(m.species == K)) < 1e-12
+
+
+def test_spread_bead_on_node_and_wrap():
+    """A bead on a grid node (order 1) puts 1/dV on that node only; a bead
+    at L - eps contributes to the node at index 0 through the wrap."""
+    m = O.Model(L=4.0, n=8, P=2, species=np.array([0, 1]), n_species=2, bonds=np.zeros((0, 2), np.int64),
+                b=1.0, chi=np.zeros((2, 2)), kappa=1.0, a=0.5)
+    pos = np.array([[1.0, 1.5, 2.0], [4.0 - 1e-13, 0.0, 0.0]])
+    rho = O.spread(m, pos)
+    dV = 0.5 ** 3
+    assert rho[0, 2, 3, 4] == pytest.approx(1 / dV, abs=1e-12)
+    assert np.count_nonzero(np.abs(rho[0]) > 1e-15) == 1
+    assert rho[1, 0, 0, 0] == pytest.approx(1 / dV, rel=1e-9)
+    assert rho[1].sum() * dV == pytest.approx(1.0, abs=1e-14)
+    # exactly L maps to 0
+    assert O.wrap(np.array([4.0, -4.0, 8.0]), 4.0).tolist() == [0.0, 0.0, 0.0]
+
+
+# ----------------------------------------------- convolution vs real space
+
+
+def _periodic_gaussian(disp, L, sigma, n_img=3):
+    """Unit 3D Gaussian u_G summed over periodic images, and its gradient,
+    evaluated directly in real space (Eq. fh's u_G)."""
+    u = np.zeros(disp.shape[:-1])
+    g = np.zeros(disp.shape)
+    norm = (2 * np.pi * sigma * sigma) ** -1.5
+    rng = range(-n_img, n_img + 1)
+    for ix in rng:
+        for iy in rng:
+            for iz in rng:
+                r = disp + L * np.array([ix, iy, iz])
+                e = norm * np.exp(-np.sum(r * r, axis=-1) / (2 * sigma * sigma))
+                u += e
+                g += -r / (sigma * sigma) * e[..., None]
+    return u, g
+
+
+def test_fft_convolution_matches_real_space_sum():
+    """With a >= 2 dx (aliasing below 1e-16) the spectral potential field and
+    its ik gradient equal the direct periodic real-space convolution
+    w_K(g) = sum_K' eps_KK' dV sum_g' u_G(g - g') rho_K'(g') (Eqs. fh,
+    HelfandP, PMM; sigma^2 = 2 a^2). Pins eps, u_hat(0)=1, the sigma-a
+    relation, dV and 1/M factors, the sign of i k and the axis order."""
+    m, pos = _model(L=4.0, n=8, a=1.0, P=3)
+    rho = O.spread(m, pos)
+    f = O.potential_fields(m, rho)
+    n, dx = m.n, m.dx
+    g = np.stack(np.meshgrid(*[np.arange(n) * dx] * 3, indexing="ij"), axis=-1).reshape(-1, 3)
+    disp = g[:, None, :] - g[None, :, :]
+    u, gu = _periodic_gaussian(disp, m.L, np.sqrt(2) * m.a)
+    eps = m.eps()
+    dV = dx ** 3
+    for K in range(2):
+        w_direct = sum(eps[K, Kp] * dV * (u @ rho[Kp].reshape(-1)) for Kp in range(2))
+        np.testing.assert_allclose(f["w"][K].reshape(-1), w_direct, rtol=0, atol=1e-12 * np.abs(w_direct).max())
+        for d in range(3):
+            gd = sum(eps[K, Kp] * dV * (gu[..., d] @ rho[Kp].reshape(-1)) for Kp in range(2))
+            np.testing.assert_allclose(f["grad_w"][K, d].reshape(-1), gd, rtol=0, atol=1e-11 * np.abs(gd).max())
+
+
+def test_field_energies_match_real_space_double_sum():
+    """E_chi = (chi/rho0) dV^2 sum_gg' rho_A u_G rho_B (Eq. fh) and
+    E_kappa = (kappa/2rho0) dV^2 sum_gg' (rho_+ - rho0) u_G (rho_+ - rho0)
+    (Eq. HelfandP), evaluated directly on the grid."""
+    m, pos = _model(L=4.0, n=8, a=1.0, P=2)
+    rho = O.spread(m, pos)
+    e = O.field_energies(m, np.fft.fftn(rho, axes=(1, 2, 3)))
+    n, dx = m.n, m.dx
+    g = np.stack(np.meshgrid(*[np.arange(n) * dx] * 3, indexing="ij"), axis=-1).reshape(-1, 3)
+    u, _ = _periodic_gaussian(g[:, None, :] - g[None, :, :], m.L, np.sqrt(2) * m.a)
+    dV = dx ** 3
+    ra, rb = rho[0].reshape(-1), rho[1].reshape(-1)
+    chi = m.chi[0, 1]
+    e_chi = chi / m.rho0 * dV * dV * ra @ u @ rb
+    dp = ra + rb - m.rho0
+    e_kap = m.kappa / (2 * m.rho0) * dV * dV * dp @ u @ dp
+    assert e["chi"] == pytest.approx(e_chi, rel=1e-12)
+    assert e["kappa"] == pytest.approx(e_kap, rel=1e-11)
+
+
+# ------------------------------------------------------------ force checks
+
+
+@pytest.mark.parametrize("P", [2, 3, 4, 5])
+def test_net_nonbonded_force_vanishes(P):
+    """ik differentiation with the same assignment weights conserves momentum."""
+    m, pos = _model(P=P, n_chains=20, N=6, n_a=2, L=5.0, n=10, a=0.5)
+    f = O.nonbonded_forces(m, pos, "ik")
+    assert np.abs(f.sum(0)).max() < 1e-12 * np.abs(f).sum()
+    fb = O.bond_forces(m, pos)
+    assert np.abs(fb.sum(0)).max() < 1e-12 * max(1.0, np.abs(fb).sum())
+
+
+def test_homogeneous_melt_has_no_field_force():
+    """One A and one B bead on every node: uniform densities, zero field
+    force, zero Helfand energy, E_chi = chi N_A N_B / (rho0 V)."""
+    L, n = 4.0, 8
+    g = np.stack(np.meshgrid(*[np.arange(n) * (L / n)] * 3, indexing="ij"), axis=-1).reshape(-1, 3)
+    pos = np.concatenate([g, g])
+    sp = np.concatenate([np.zeros(len(g), np.int64), np.ones(len(g), np.int64)])
+    m = O.Model(L=L, n=n, P=2, species=sp, n_species=2, bonds=np.zeros((0, 2), np.int64), b=1.0,
+                chi=np.array([[0.0, 2.0], [2.0, 0.0]]), kappa=5.0, a=0.5)
+    f = O.nonbonded_forces(m, pos)
+    assert np.abs(f).max() < 1e-12
+    e = O.energies(m, pos)
+    assert abs(e["kappa"]) < 1e-10
+    assert e["chi"] == pytest.approx(2.0 * len(g) * len(g) / (m.rho0 * L ** 3), rel=1e-12)
+
+
+def test_translation_by_grid_vector():
+    """Shifting every bead by an integer number of grid spacings leaves the
+    energies and the forces unchanged."""
+    m, pos = _model(P=3, L=5.0, n=10, a=0.6)
+    shift = m.dx * np.array([3, -2, 7])
+    f0, f1 = O.forces(m, pos), O.forces(m, O.wrap(pos + shift, m.L))
+    np.testing.assert_allclose(f1, f0, atol=1e-11 * np.abs(f0).max())
+    e0, e1 = O.energies(m, pos), O.energies(m, O.wrap(pos + shift, m.L))
+    for k in e0:
+        assert e1[k] == pytest.approx(e0[k], rel=1e-11, abs=1e-12)
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_analytic_forces_are_energy_gradient(P):
+    """Central differences of E_bond + E_chi + E_kappa equal the analytic
+    gradient of the gridded energy (bond force of Eq. bonds: -3/b^2 dr)."""
+    m, pos = _model(P=P, n_chains=4, N=4, n_a=2, L=4.0, n=8, a=0.5)
+    f = O.forces(m, pos, variant="analytic")
+
+    def etot(p):
+        e = O.energies(m, p)
+        return e["bond"] + e["chi"] + e["kappa"]
+
+    h = 1e-5
+    for i in (0, 3, 9, 15):
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            fd = -(etot(pp) - etot(pm)) / (2 * h)
+            assert abs(fd - f[i, d]) < 1e-7 * max(1.0, np.abs(f).max())
+
+
+def test_ik_forces_converge_to_analytic_with_refinement():
+    """The ik and analytic forces of the same gridded model approach each
+    other as the grid is refined (both converge to the continuum force)."""
+    errs = []
+    for n in (8, 16, 32):
+        m, pos = _model(P=4, n_chains=4, N=4, n_a=2, L=4.0, n=n, a=0.5)
+        fa = O.nonbonded_forces(m, pos, "analytic")
+        fi = O.nonbonded_forces(m, pos, "ik")
+        errs.append(np.linalg.norm(fi - fa) / np.linalg.norm(fa))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 2e-3
+
+
+def test_two_bead_bond_closed_form():
+    """Eq. bonds for one bond: E = 3/(2b^2) d^2, F_1 = -3/b^2 d; across the
+    periodic boundary the minimum image is used."""
+    m = O.Model(L=10.0, n=8, P=2, species=np.array([0, 0]), n_species=1, bonds=np.array([[0, 1]]), b=1.3,
+                chi=np.zeros((1, 1)), kappa=0.0, a=0.5)
+    pos = np.array([[9.8, 1.0, 5.0], [0.4, 1.5, 4.0]])
+    d = np.array([-0.6, -0.5, 1.0])
+    assert O.bond_energy(m, pos) == pytest.approx(1.5 / 1.3 ** 2 * d @ d, rel=1e-13)
+    f = O.bond_forces(m, pos)
+    np.testing.assert_allclose(f[0], -3 / 1.3 ** 2 * d, atol=1e-13)
+    np.testing.assert_allclose(f[1], 3 / 1.3 ** 2 * d, atol=1e-13)
+
+
+# ------------------------------------------------------------- integrator
+
+
+def test_gjf_harmonic_oscillator_configurational_temperature():
+    """GJF samples <x^2> = kT/k exactly for any stable dt (Gronbech-Jensen &
+    Farago 2013); with omega dt = 0.8 Euler-type schemes would be far off."""
+    k = 4.0
+    n = 4000
+    m = O.Model(L=1000.0, n=8, P=2, species=np.zeros(n, np.int64), n_species=1, bonds=np.zeros((0, 2), np.int64),
+                b=1.0, chi=np.zeros((1, 1)), kappa=0.0, a=0.5, dt=0.4, friction=1.0, kT=1.5, seed=11)
+    c = 500.0
+
+    def force(mm, p):
+        return -k * (p - c)
+
+    st = O.initial_state(m, np.full((n, 3), c), force_fn=force)
+    xs = []
+    for it in range(400):
+        st = O.gjf_step(m, st, force)
+        if it >= 100 and it % 5 == 0:
+            xs.append(np.mean((st.pos - c) ** 2))
+    x2 = np.mean(xs)
+    assert abs(x2 - m.kT / k) < 0.03 * m.kT / k
+
+
+@pytest.mark.slow
+def test_ideal_chain_statistics_and_equipartition():
+    """chi = kappa = 0: bonds only (Eq. bonds). Equilibrium ideal Gaussian
+    chains: <|dr|^2> = b^2, <R_ee^2> = (N-1) b^2, <R_g^2> = b^2 (N^2-1)/(6N);
+    kinetic temperature <v^2> = kT/m per component."""
+    N, nc = 20, 400
+    mt = (I.MolType(nc, N, N),)
+    sp = I.species_of_beads(mt).astype(np.int64)
+    m = O.Model(L=60.0, n=8, P=2, species=sp, n_species=1, bonds=I.bond_pairs(mt), b=1.0,
+                chi=np.zeros((1, 1)), kappa=0.0, a=0.5, dt=0.05, friction=1.0, kT=1.0, seed=5)
+    pos = I.random_walk_positions(mt, m.L, 1.0, 21)
+
+    def force(mm, p):
+        return O.bond_forces(mm, p)
+
+    st = O.initial_state(m, pos, force_fn=force)
+    b2, ree, rg, v2 = [], [], [], []
+    for it in range(3000):
+        st = O.gjf_step(m, st, force)
+        if it >= 500 and it % 25 == 0:
+            d = O.bond_vectors(m, st.pos).reshape(nc, N - 1, 3)
+            r = np.concatenate([np.zeros((nc, 1, 3)), np.cumsum(d * -1, axis=1)], axis=1)
+            b2.append(np.mean(np.sum(d * d, -1)))
+            ree.append(np.mean(np.sum(r[:, -1] ** 2, -1)))
+            rc = r - r.mean(1, keepdims=True)
+            rg.append(np.mean(np.sum(rc * rc, -1)))
+            v2.append(np.mean(st.vel ** 2))
+    assert abs(np.mean(b2) - 1.0) < 0.03
+    assert abs(np.mean(ree) - (N - 1)) < 0.06 * (N - 1)
+    assert abs(np.mean(rg) - (N * N - 1) / (6 * N)) < 0.06 * (N * N - 1) / (6 * N)
+    # GJF kinetic bias is O((omega dt)^2) ~ 3e-2 here at the stiffest mode
+    assert abs(np.mean(v2) - 1.0) < 0.03
+
+
+def test_gjf_free_particle_velocity_variance():
+    """No forces: <v^2> = kT/m is stationary from the Maxwell-Boltzmann start."""
+    n = 20000
+    m = O.Model(L=50.0, n=8, P=2, species=np.zeros(n, np.int64), n_species=1, bonds=np.zeros((0, 2), np.int64),
+                b=1.0, chi=np.zeros((1, 1)), kappa=0.0, a=0.5, dt=0.05, friction=2.0, kT=0.7, seed=2)
+
+    def force(mm, p):
+        return np.zeros_like(p)
+
+    st = O.initial_state(m, np.full((n, 3), 1.0), force_fn=force)
+    assert abs(np.mean(st.vel ** 2) - 0.7) < 0.02
+    for _ in range(50):
+        st = O.gjf_step(m, st, force)
+    assert abs(np.mean(st.vel ** 2) - 0.7) < 0.02
