@@ -1,0 +1,332 @@
+"""Benchmark of the TILD step on GB300.
+
+Workload: AB diblock melt of 80,000 A8-B12 chains (1.6M beads), box L=64,
+128^3 grid, pmeorder 1, a=0.5, chi=0.8, kappa=25, dt=0.005, GJF (friction 1,
+kT 1), FP32 with deterministic (fixed-point) spreading; seeded random-walk
+initial coordinates. Metric: TILD steps/s and bead-steps/s, with the
+fraction of the HBM roofline.
+
+One process per GPU; under torchrun every rank runs an independent replica
+(the path has no exchange step), so per-GPU work is fixed ("weak").
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "diblock_1p6M_128"
+METRIC = "TILD steps/s and bead-steps/s (1.6M beads, 128^3) + % of HBM roofline"
+L2_BYTES = 129 * 1024 * 1024
+
+# Algorithmic bytes (FP32, S=2 species, D=3): 48 B per bead (read and write
+# r and v) plus per grid point 16 B forward transform (read densities, write
+# spectrum), 32 B spectral z pass (read 2 spectra as 8 B, write 3 gradient
+# spectra as 24 B), 48 B inverse transform (read and write the 3 gradient
+# pairs), 32 B bead kernel (gather-read 24 B, spread-write 8 B): 128 B/point.
+STAGES = ["forward_fft", "z_spectral", "inverse_fft", "bead_step", "rebin"]
+BYTES_PER_POINT = {"forward_fft": 16, "z_spectral": 32, "inverse_fft": 48, "bead_step": 32, "rebin": 0}
+BYTES_PER_BEAD = {"forward_fft": 0, "z_spectral": 0, "inverse_fft": 0, "bead_step": 48, "rebin": 0}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(values_per_rank, ms_per_rank, steps):
+    """Whole-job throughput from per-rank timings: all units / slowest rank."""
+    t = max(ms_per_rank) / 1000.0
+    return len(ms_per_rank) * steps / t, max(ms_per_rank) / steps
+
+
+def algorithmic_bytes(stage: str, n_points: int, n_beads: int) -> int:
+    return BYTES_PER_POINT[stage] * n_points + BYTES_PER_BEAD[stage] * n_beads
+
+
+def step_bytes(n_points: int, n_beads: int) -> int:
+    return sum(algorithmic_bytes(s, n_points, n_beads) for s in STAGES)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2302_02474_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        m = re.match(r"\|\s*(\w+)\s*\|\s*([0-9a-f]+)\s*\|\s*(\d+)\s*\|", line)
+        if m and m.group(1) == kernel and m.group(2) == src:
+            return int(m.group(3))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_step_rate(spec, pos, n_steps: int, budget_s: float):
+    """Time the FP64 oracle (single-threaded numpy) on the same system."""
+    from oracle import tild_oracle as O
+    from paper_2302_02474_gb300 import inputs as I
+
+    m = O.model_from_spec(spec, I.species_of_beads(spec.moltypes), I.bond_pairs(spec.moltypes))
+    t0 = time.perf_counter()
+    st = O.initial_state(m, pos)
+    t_init = time.perf_counter() - t0
+    done, t_steps = 0, 0.0
+    while done < n_steps:
+        t0 = time.perf_counter()
+        st = O.gjf_step(m, st)
+        t_steps += time.perf_counter() - t0
+        done += 1
+        if t_steps > budget_s:
+            break
+    return done / t_steps, done, t_steps, t_init
+
+
+def run_reference(args, spec, pos):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    warm = min(args.warmup, 1)
+    from oracle import tild_oracle as O  # noqa: F401
+
+    if warm:
+        oracle_step_rate(spec, pos, warm, 1e9)
+    rate, done, secs, t_init = oracle_step_rate(spec, pos, args.steps, args.reference_budget)
+    sample = (f"{done} oracle GJF steps of the full {spec.n_beads}-bead / {spec.n}^3 system "
+              f"(initial force evaluation {t_init:.1f} s excluded)")
+    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "steps/s", "n_gpus": args.gpus,
+           "steps": done, "warmup": warm, "ms_per_step": 1000.0 * secs / done, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "bead_steps_per_s": rate * spec.n_beads,
+           "config": {"workload": WORKLOAD, "beads": spec.n_beads, "grid": spec.n, "box": spec.L,
+                      "l2": "working set > L2"},
+           "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--sort-every", type=int, default=20)
+    ap.add_argument("--cpu-baseline-steps", type=int, default=3)
+    ap.add_argument("--reference-budget", type=float, default=150.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from paper_2302_02474_gb300 import inputs as I
+
+    spec = I.config(WORKLOAD)
+    pos = I.initial_positions(spec)
+    if args.impl == "reference":
+        run_reference(args, spec, pos)
+        return
+
+    import torch
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_2302_02474_gb300 import binding as B
+
+    B.load()
+    stream = torch.cuda.Stream()
+    t = B.Tild.from_spec(spec, sort_every=args.sort_every)
+    t.set_stream(stream)
+    t.set_positions(pos)
+    t.init_velocities()
+    t.step(args.warmup)
+    t.synchronize()
+
+    # per-kernel device times (CUDA events around each launch, same stream)
+    prof_steps = max(2 * args.sort_every, 40)
+    stage_ms = t.profile_steps(prof_steps)
+
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        start.record(stream)
+        t.step(args.steps)
+        end.record(stream)
+        end.synchronize()
+    t.synchronize()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    launches = t.launches(args.steps)
+    ms_all = [ms]
+    if world > 1:
+        import torch.distributed as dist
+
+        buf = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        gathered = [torch.zeros_like(buf) for _ in range(world)]
+        dist.all_gather(gathered, buf)
+        ms_all = [float(g.item()) for g in gathered]
+    value, ms_per_step = aggregate(None, ms_all, args.steps)
+
+    # end to end through the C ABI with host buffers: upload the state,
+    # run the same number of steps, read positions back
+    blob = t.get_state()
+    host_pos = np.empty(3 * spec.n_beads, dtype=np.float32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t.set_state(blob)
+    t.step(args.steps)
+    t.positions(out=host_pos)
+    e2e_s = time.perf_counter() - t0
+    h2d = len(blob)
+    d2h = host_pos.nbytes
+
+    n_points = spec.n ** 3
+    peak, peak_kind = measured_peaks()
+    stage_time = {s: stage_ms[i] for i, s in enumerate(STAGES)}
+    dom = max(["forward_fft", "z_spectral", "inverse_fft", "bead_step"], key=lambda s: stage_time[s])
+    dom_bytes = algorithmic_bytes(dom, n_points, spec.n_beads)
+    achieved = dom_bytes / (stage_time[dom] * 1e-3) / 1e9
+    kernel_names = {"forward_fft": "xy_forward_plane", "z_spectral": "z_spectral",
+                    "inverse_fft": "xy_inverse_plane", "bead_step": "bead_kernel"}
+    sb = step_bytes(n_points, spec.n_beads)
+    step_achieved = sb * (args.steps / (ms / 1000.0)) / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, done, secs, _ = oracle_step_rate(spec, pos, args.cpu_baseline_steps, 60.0)
+        cpu = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} oracle GJF steps of the full {spec.n_beads}-bead system ({secs:.1f} s, "
+                         "single-threaded numpy FP64)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "bead_steps_per_s": value * spec.n_beads,
+            "config": {"workload": WORKLOAD, "beads": spec.n_beads, "grid": spec.n, "box": spec.L,
+                       "pmeorder": spec.pmeorder, "sort_every": args.sort_every,
+                       "l2": f"step working set {(2 * n_points * 8 + 7 * n_points * 8 + spec.n_beads * 64) / 1e6:.0f} MB > L2, no flush"},
+            "roofline": {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": profiled_traffic(kernel_names[dom]),
+                         "algorithmic_bytes_per_launch": dom_bytes},
+            "step_roofline": {"algorithmic_bytes_per_step": sb, "achieved": step_achieved, "peak": peak,
+                              "unit": "GB/s", "frac": step_achieved / peak},
+            "stage_ms": stage_time,
+            "cpu_baseline": cpu,
+            "e2e": {"value": args.steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(out))
+    t.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,235 @@
+/*
+ * tild.h — C ABI of a GB300 (sm_103a) implementation of the
+ * theoretically-informed Langevin (TILD) timestep of MATILDA.FT
+ * (arXiv 2302.02474).
+ *
+ * One call of tild_step advances a coarse-grained polymer system by one or
+ * more steps of the particle-mesh method the paper describes:
+ *   1. assign bead densities to a periodic grid with the spline weights of
+ *      order pmeorder (Eq. rhohat; Sec. "Long-range interactions", weights
+ *      from the appendix of Deserno & Holm 1998; Fig. pmm);
+ *   2. Fourier-transform the species densities;
+ *   3. multiply by the Fourier transform of the Gaussian-smeared Flory (chi,
+ *      Eq. fh) and Helfand (kappa, Eq. HelfandP) pair kernel and by i k
+ *      (the convolution of Eq. PMM);
+ *   4. inverse-transform the field gradients;
+ *   5. interpolate the forces back to the beads with the same weights
+ *      (caption of Fig. pmm), add harmonic bond forces (Eq. bonds);
+ *   6. advance positions and velocities with the Gronbech-Jensen-Farago
+ *      Langevin integrator (GJF; Sec. "Integrator Class", Listing infile).
+ *
+ * Units are the paper's reduced units (Sec. "Units"): energy kT, mass m of
+ * a monomer, length b.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns a tild_status: TILD_OK (0) or a negative error.
+ *     On error the context is unchanged unless stated otherwise, and
+ *     tild_last_error() returns a one-line description.
+ *   - Beads are numbered 0..n_beads-1 chain by chain, in the order of the
+ *     molecule types given to tild_set_chains (bead s of chain c of type t
+ *     has id start_t + c*N_t + s).
+ *   - Arrays of per-bead vectors are AoS, [n_beads][3], in bead-id order.
+ *     Their element type is given by a tild_dtype; `where` says whether the
+ *     pointer is host or device memory (TILD_HOST / TILD_DEVICE). The caller
+ *     owns every buffer it passes; the library copies in or out and keeps no
+ *     pointer after the call returns.
+ *   - Grid arrays are C-ordered [z][y][x] (x fastest) with n^3 points.
+ *   - All device work is ordered on the context's stream. Calls that return
+ *     data to the caller synchronise that stream before returning; tild_step
+ *     does not (use tild_synchronize).
+ *   - The library owns its device state (bead arrays, grids, spectra),
+ *     allocated with cudaMalloc by tild_create / tild_set_chains and freed by
+ *     tild_destroy.
+ *   - A context is bound to the CUDA device that was current when it was
+ *     created; calls on it must be made with that device current.
+ *   - Not thread-safe: one host thread at a time per context.
+ */
+#ifndef TILD_H
+#define TILD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int tild_status;
+
+#define TILD_OK 0
+#define TILD_EINVAL (-1)        /* bad argument (NULL, out of range, wrong size) */
+#define TILD_ENOMEM (-2)        /* device or host allocation failed */
+#define TILD_EUNSUPPORTED (-3)  /* valid request outside what this build implements */
+#define TILD_EDEVICE (-4)       /* a CUDA call failed; see tild_last_error */
+#define TILD_ENAN (-5)          /* a non-finite force was detected on the device */
+#define TILD_ESTATE (-6)        /* call made before the state it needs exists */
+
+typedef enum { TILD_FP32 = 0, TILD_FP64 = 1 } tild_precision;
+typedef enum { TILD_DTYPE_F32 = 0, TILD_DTYPE_F64 = 1 } tild_dtype;
+typedef enum { TILD_HOST = 0, TILD_DEVICE = 1 } tild_where;
+
+typedef struct tild_ctx tild_ctx;
+
+/*
+ * Box, grid and numerics (Listing infile: box and grid size, pmeorder).
+ *   L[3]        box edges; this build requires a cubic box (L[0]=L[1]=L[2] > 0).
+ *   n[3]        grid points per edge; cubic, a power of two in [8, 256]
+ *               (FP64 grids up to 128). Others give TILD_EUNSUPPORTED.
+ *   pmeorder    assignment order p in 1..4: p+1 grid points per dimension
+ *               (order 1 = the two nearest points, Fig. pmm).
+ *   precision   TILD_FP32 (grids, FFT and bead state in FP32; energies in
+ *               FP64) or TILD_FP64 (everything FP64).
+ *   seed        64-bit key of the Philox4x32-10 stream of the thermal noise.
+ *   sort_every  re-bin beads by grid tile every this many steps (>= 1;
+ *               0 selects the default of 20). Results do not depend on it.
+ */
+typedef struct {
+    double L[3];
+    int n[3];
+    int pmeorder;
+    int precision;
+    uint64_t seed;
+    int sort_every;
+} tild_params;
+
+/*
+ * One molecule type (Sec. "Structure of ... models": chains of N_A + N_B = N
+ * beads joined by harmonic bonds, Eq. bonds): n_chains linear chains of N
+ * beads whose first n_a beads are species A (0) and the rest species B (1).
+ */
+typedef struct {
+    int64_t n_chains;
+    int N;
+    int n_a;
+} tild_moltype;
+
+/* Energies in kT (Eqs. bonds, fh, HelfandP) and diagnostics of the current
+ * configuration. e_chi keeps the k=0 Fourier term of Eq. fh; e_kappa drops
+ * the k=0 term, which cancels the -rho_0 shift of Eq. HelfandP exactly.
+ * kinetic = sum_i m |v_i|^2 / 2. net_force = sum_i F_i. */
+typedef struct {
+    double e_bond;
+    double e_chi;
+    double e_kappa;
+    double kinetic;
+    double net_force[3];
+} tild_energy;
+
+#define TILD_COMPUTE_ENERGY 1u
+#define TILD_COMPUTE_FORCES 2u
+
+/* Create a context for the box/grid in *p on the current CUDA device. On
+ * success *out owns device memory for the grids. */
+tild_status tild_create(const tild_params* p, tild_ctx** out);
+
+/* Free everything the context owns. NULL is accepted. */
+tild_status tild_destroy(tild_ctx* ctx);
+
+/* Define the chains (and so the number of beads, the species and the bond
+ * topology). b is the statistical segment length of Eq. bonds (bond force
+ * -(3/b^2)(r_i - r_j)). At most 8 types, 1 <= N, 0 <= n_a <= N, at least one
+ * bead, fewer than 2^31 beads. At most two species (A, B). Allocates the
+ * bead arrays; existing positions are discarded. */
+tild_status tild_set_chains(tild_ctx* ctx, int n_types, const tild_moltype* types, double b);
+
+/* Interactions (Eqs. fh, HelfandP; sigma^2 = 2 a^2 per Eqs. fhF, HelfandF):
+ * chi_ab = Flory chi between A and B, kappa = Helfand compressibility,
+ * a = smearing width of h (the pair kernel's Fourier transform is
+ * exp(-|k|^2 a^2)). a > 0, kappa >= 0. rho_0 = n_beads / V.
+ * Defaults before the first call: chi_ab = 0, kappa = 0, a = 0.5. If
+ * velocities exist, v^n is kept and the carried state is updated to the
+ * new forces. */
+tild_status tild_set_interactions(tild_ctx* ctx, double chi_ab, double kappa, double a);
+
+/* GJF integrator (Sec. "Integrator Class"): time step dt > 0, friction
+ * alpha >= 0, temperature kT >= 0, bead mass > 0. Defaults: dt = 0.005,
+ * alpha = 1, kT = 1, mass = 1. If velocities exist, v^n is kept. */
+tild_status tild_set_integrator(tild_ctx* ctx, double dt, double friction, double kT, double mass);
+
+/* Order all work of this context on `stream` (a cudaStream_t; NULL = the
+ * context's own stream). The stream must belong to the context's device and
+ * outlive its use by the context. */
+tild_status tild_set_stream(tild_ctx* ctx, void* stream);
+
+/* Copy in positions [n_beads][3] (wrapped into [0, L)). Requires chains.
+ * Invalidates velocities: call tild_init_velocities or tild_set_velocities
+ * before stepping. */
+tild_status tild_set_positions(tild_ctx* ctx, const void* xyz, int dtype, int where);
+
+/* Draw Maxwell-Boltzmann velocities (each component N(0, kT/m), Philox
+ * counter (bead id, 2^64-1)) and evaluate the forces at the current
+ * positions. Resets the step counter to 0. */
+tild_status tild_init_velocities(tild_ctx* ctx);
+
+/* Copy in velocities [n_beads][3] and evaluate the forces at the current
+ * positions. Resets the step counter to 0. */
+tild_status tild_set_velocities(tild_ctx* ctx, const void* v, int dtype, int where);
+
+/* Advance n_steps >= 0 GJF steps, asynchronously on the context's stream.
+ * The thermal noise of step n -> n+1 for bead i is drawn from Philox counter
+ * (i, n+1). Launch errors are reported here; a non-finite force raised by
+ * a step is reported by the next tild_synchronize or tild_compute. */
+tild_status tild_step(tild_ctx* ctx, int64_t n_steps);
+
+/* Wait for the context's stream. Returns TILD_ENAN if any step flagged a
+ * non-finite force since the last check (the flag is then cleared). */
+tild_status tild_synchronize(tild_ctx* ctx);
+
+/* Evaluate at the current positions: `what` = TILD_COMPUTE_ENERGY and/or
+ * TILD_COMPUTE_FORCES. Energies go to *e (may be NULL if not requested);
+ * total forces (field + bonds) to forces_out [n_beads][3] (may be NULL if
+ * not requested). Does not change the state. */
+tild_status tild_compute(tild_ctx* ctx, unsigned what, tild_energy* e, void* forces_out, int dtype, int where);
+
+/* Current positions (wrapped into [0, L)), [n_beads][3]. */
+tild_status tild_get_positions(tild_ctx* ctx, void* out, int dtype, int where);
+
+/* Current velocities v^n, [n_beads][3]. */
+tild_status tild_get_velocities(tild_ctx* ctx, void* out, int dtype, int where);
+
+/* Species densities rho_K(g) on the grid (beads per unit volume) of the
+ * current positions: [2][n][n][n], species A then B, [z][y][x] order. */
+tild_status tild_get_density(tild_ctx* ctx, void* out, int dtype, int where);
+
+/* Discrete Fourier transform Z(k) = sum_g (rho_A(g) + i rho_B(g)) e^{-i k.g}
+ * of the current densities, as interleaved (re, im) pairs [n][n][n][2] in
+ * [kz][ky][kx] FFT index order (index m < n/2 is frequency m, else m - n). */
+tild_status tild_get_spectrum(tild_ctx* ctx, void* out, int dtype, int where);
+
+/* Gradients of the potential fields w_K = sum_K' eps_KK' u_G * rho_K' on
+ * the grid, [3][n][n][n][2]: for direction d (x, y, z), point (z, y, x), the
+ * pair (d w_A / d r_d, d w_B / d r_d). eps_KK = kappa/rho_0,
+ * eps_AB = (chi_ab + kappa)/rho_0. */
+tild_status tild_get_field_gradient(tild_ctx* ctx, void* out, int dtype, int where);
+
+/* Number of steps taken since velocities were set. */
+tild_status tild_get_step(tild_ctx* ctx, int64_t* step);
+
+/* Checkpoint: tild_state_bytes gives the size of the opaque host blob that
+ * tild_get_state writes (positions, carried velocities, step counter, seed,
+ * in the context's precision). tild_set_state restores it into a context
+ * with the same chains and precision; continuing from a restored state
+ * reproduces the original trajectory bit for bit. */
+tild_status tild_state_bytes(tild_ctx* ctx, size_t* bytes);
+tild_status tild_get_state(tild_ctx* ctx, void* host_blob, size_t bytes);
+tild_status tild_set_state(tild_ctx* ctx, const void* host_blob, size_t bytes);
+
+/* Time each kernel of the step: runs n_steps steps with CUDA events around
+ * every kernel launch (no graph) and writes the mean device time in
+ * milliseconds of the kernels of each stage to ms[5]:
+ * [0] forward FFT passes (density in), [1] spectral z pass,
+ * [2] inverse FFT passes (gradients out), [3] bead kernel (gather, bonds,
+ * GJF, spread), [4] re-binning (per step, amortised). */
+tild_status tild_profile_steps(tild_ctx* ctx, int n_steps, double* ms);
+
+/* Number of kernel launches one tild_step(ctx, n) issues for this context. */
+tild_status tild_launches_per_steps(tild_ctx* ctx, int64_t n_steps, int64_t* launches);
+
+/* Description of the last error on this context (or of the last failed
+ * tild_create when ctx is NULL). Never NULL. */
+const char* tild_last_error(tild_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TILD_H */

@@ -1,0 +1,305 @@
+"""ctypes binding of the TILD C ABI (include/tild.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library. Functions keep the C names; ``Tild`` wraps one context for
+convenience (numpy arrays are host buffers, CUDA torch tensors device
+buffers). There is no CPU fallback: loading fails loudly when the library
+has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from ._build import LIB_PATH
+
+TILD_OK = 0
+TILD_EINVAL = -1
+TILD_ENOMEM = -2
+TILD_EUNSUPPORTED = -3
+TILD_EDEVICE = -4
+TILD_ENAN = -5
+TILD_ESTATE = -6
+
+TILD_FP32, TILD_FP64 = 0, 1
+TILD_DTYPE_F32, TILD_DTYPE_F64 = 0, 1
+TILD_HOST, TILD_DEVICE = 0, 1
+TILD_COMPUTE_ENERGY, TILD_COMPUTE_FORCES = 1, 2
+
+STATUS_NAMES = {0: "TILD_OK", -1: "TILD_EINVAL", -2: "TILD_ENOMEM", -3: "TILD_EUNSUPPORTED", -4: "TILD_EDEVICE",
+                -5: "TILD_ENAN", -6: "TILD_ESTATE"}
+
+
+class tild_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double * 3), ("n", ctypes.c_int * 3), ("pmeorder", ctypes.c_int),
+                ("precision", ctypes.c_int), ("seed", ctypes.c_uint64), ("sort_every", ctypes.c_int)]
+
+
+class tild_moltype(ctypes.Structure):
+    _fields_ = [("n_chains", ctypes.c_int64), ("N", ctypes.c_int), ("n_a", ctypes.c_int)]
+
+
+class tild_energy(ctypes.Structure):
+    _fields_ = [("e_bond", ctypes.c_double), ("e_chi", ctypes.c_double), ("e_kappa", ctypes.c_double),
+                ("kinetic", ctypes.c_double), ("net_force", ctypes.c_double * 3)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_SIGS = {
+    "tild_create": [ctypes.POINTER(tild_params), ctypes.POINTER(_P)],
+    "tild_destroy": [_P],
+    "tild_set_chains": [_P, _I, ctypes.POINTER(tild_moltype), ctypes.c_double],
+    "tild_set_interactions": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+    "tild_set_integrator": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+    "tild_set_stream": [_P, _P],
+    "tild_set_positions": [_P, _P, _I, _I],
+    "tild_init_velocities": [_P],
+    "tild_set_velocities": [_P, _P, _I, _I],
+    "tild_step": [_P, _I64],
+    "tild_synchronize": [_P],
+    "tild_compute": [_P, ctypes.c_uint, ctypes.POINTER(tild_energy), _P, _I, _I],
+    "tild_get_positions": [_P, _P, _I, _I],
+    "tild_get_velocities": [_P, _P, _I, _I],
+    "tild_get_density": [_P, _P, _I, _I],
+    "tild_get_spectrum": [_P, _P, _I, _I],
+    "tild_get_field_gradient": [_P, _P, _I, _I],
+    "tild_get_step": [_P, ctypes.POINTER(_I64)],
+    "tild_state_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "tild_get_state": [_P, _P, ctypes.c_size_t],
+    "tild_set_state": [_P, _P, ctypes.c_size_t],
+    "tild_profile_steps": [_P, _I, ctypes.POINTER(ctypes.c_double)],
+    "tild_launches_per_steps": [_P, _I64, ctypes.POINTER(_I64)],
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def library_path() -> str:
+    return os.environ.get("TILD_LIBRARY", LIB_PATH)
+
+
+def load() -> ctypes.CDLL:
+    """Load libtild.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"TILD CUDA library not found at {path}; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.tild_last_error.argtypes = [_P]
+    lib.tild_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class TildError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status: int, ctx=None) -> None:
+    if status != TILD_OK:
+        msg = load().tild_last_error(ctx).decode()
+        raise TildError(status, msg)
+
+
+def declared_symbols() -> Sequence[str]:
+    return list(_SIGS) + ["tild_last_error"]
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def _buffer(arr, n_elems: int):
+    """(pointer, dtype code, where code, keepalive) for a numpy array or torch tensor."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(arr, torch.Tensor):
+        if not arr.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if arr.dtype not in (torch.float32, torch.float64):
+            raise ValueError("tensor dtype must be float32 or float64")
+        if arr.numel() != n_elems:
+            raise ValueError(f"expected {n_elems} elements, got {arr.numel()}")
+        code = TILD_DTYPE_F32 if arr.dtype == torch.float32 else TILD_DTYPE_F64
+        where = TILD_DEVICE if arr.is_cuda else TILD_HOST
+        return ctypes.c_void_p(arr.data_ptr()), code, where, arr
+    a = np.ascontiguousarray(arr)
+    if a.dtype not in (np.float32, np.float64):
+        a = a.astype(np.float64)
+    if a.size != n_elems:
+        raise ValueError(f"expected {n_elems} elements, got {a.size}")
+    code = TILD_DTYPE_F32 if a.dtype == np.float32 else TILD_DTYPE_F64
+    return ctypes.c_void_p(a.ctypes.data), code, TILD_HOST, a
+
+
+class Tild:
+    """One TILD context (thin wrapper over the C ABI)."""
+
+    def __init__(self, L: float, n: int, pmeorder: int = 1, precision: str = "fp32", seed: int = 0,
+                 sort_every: int = 0):
+        lib = load()
+        p = tild_params()
+        p.L[:] = [L, L, L]
+        p.n[:] = [n, n, n]
+        p.pmeorder = pmeorder
+        p.precision = TILD_FP32 if precision == "fp32" else TILD_FP64
+        p.seed = seed
+        p.sort_every = sort_every
+        ctx = ctypes.c_void_p()
+        check(lib.tild_create(ctypes.byref(p), ctypes.byref(ctx)), None)
+        self.ctx = ctx
+        self.lib = lib
+        self.n = n
+        self.L = L
+        self.np_dtype = np.float32 if precision == "fp32" else np.float64
+        self.n_beads = 0
+
+    @classmethod
+    def from_spec(cls, spec, sort_every: int = 0, precision: Optional[str] = None) -> "Tild":
+        t = cls(spec.L, spec.n, spec.pmeorder, precision or spec.precision, spec.dyn_seed, sort_every)
+        t.set_chains([(m.n_chains, m.N, m.n_a) for m in spec.moltypes], spec.b)
+        t.set_interactions(spec.chi, spec.kappa, spec.a)
+        t.set_integrator(spec.dt, spec.friction, spec.kT, spec.mass)
+        return t
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.lib.tild_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _chk(self, st: int) -> None:
+        check(st, self.ctx)
+
+    def set_chains(self, types, b: float = 1.0) -> None:
+        arr = (tild_moltype * len(types))()
+        total = 0
+        for i, (nc, N, na) in enumerate(types):
+            arr[i].n_chains, arr[i].N, arr[i].n_a = nc, N, na
+            total += nc * N
+        self._chk(self.lib.tild_set_chains(self.ctx, len(types), arr, b))
+        self.n_beads = total
+
+    def set_interactions(self, chi: float, kappa: float, a: float) -> None:
+        self._chk(self.lib.tild_set_interactions(self.ctx, chi, kappa, a))
+
+    def set_integrator(self, dt: float, friction: float, kT: float, mass: float = 1.0) -> None:
+        self._chk(self.lib.tild_set_integrator(self.ctx, dt, friction, kT, mass))
+
+    def set_stream(self, stream) -> None:
+        handle = getattr(stream, "cuda_stream", stream)
+        self._chk(self.lib.tild_set_stream(self.ctx, ctypes.c_void_p(handle or 0)))
+
+    def set_positions(self, xyz) -> None:
+        ptr, code, where, _keep = _buffer(xyz, 3 * self.n_beads)
+        self._chk(self.lib.tild_set_positions(self.ctx, ptr, code, where))
+
+    def init_velocities(self) -> None:
+        self._chk(self.lib.tild_init_velocities(self.ctx))
+
+    def set_velocities(self, v) -> None:
+        ptr, code, where, _keep = _buffer(v, 3 * self.n_beads)
+        self._chk(self.lib.tild_set_velocities(self.ctx, ptr, code, where))
+
+    def step(self, n: int = 1) -> None:
+        self._chk(self.lib.tild_step(self.ctx, int(n)))
+
+    def synchronize(self) -> None:
+        self._chk(self.lib.tild_synchronize(self.ctx))
+
+    def _out(self, fn, count: int, out=None, dtype=np.float64):
+        if out is None:
+            out = np.empty(count, dtype=dtype)
+        ptr, code, where, _keep = _buffer(out, count)
+        self._chk(fn(self.ctx, ptr, code, where))
+        return out
+
+    def positions(self, out=None, dtype=np.float64):
+        r = self._out(self.lib.tild_get_positions, 3 * self.n_beads, out, dtype)
+        return r.reshape(-1, 3) if isinstance(r, np.ndarray) else r
+
+    def velocities(self, out=None, dtype=np.float64):
+        r = self._out(self.lib.tild_get_velocities, 3 * self.n_beads, out, dtype)
+        return r.reshape(-1, 3) if isinstance(r, np.ndarray) else r
+
+    def density(self, out=None, dtype=np.float64):
+        r = self._out(self.lib.tild_get_density, 2 * self.n ** 3, out, dtype)
+        return r.reshape(2, self.n, self.n, self.n) if isinstance(r, np.ndarray) else r
+
+    def spectrum(self, out=None, dtype=np.float64):
+        r = self._out(self.lib.tild_get_spectrum, 2 * self.n ** 3, out, dtype)
+        if isinstance(r, np.ndarray):
+            r = r.reshape(self.n, self.n, self.n, 2)
+            return r[..., 0] + 1j * r[..., 1]
+        return r
+
+    def field_gradient(self, out=None, dtype=np.float64):
+        r = self._out(self.lib.tild_get_field_gradient, 6 * self.n ** 3, out, dtype)
+        return r.reshape(3, self.n, self.n, self.n, 2) if isinstance(r, np.ndarray) else r
+
+    def compute(self, forces: bool = True, energy: bool = True, out=None, dtype=np.float64):
+        e = tild_energy()
+        what = (TILD_COMPUTE_ENERGY if energy else 0) | (TILD_COMPUTE_FORCES if forces else 0)
+        f = None
+        ptr, code, where = ctypes.c_void_p(), TILD_DTYPE_F64, TILD_HOST
+        if forces:
+            f = np.empty(3 * self.n_beads, dtype=dtype) if out is None else out
+            ptr, code, where, _keep = _buffer(f, 3 * self.n_beads)
+        self._chk(self.lib.tild_compute(self.ctx, what, ctypes.byref(e), ptr, code, where))
+        en = {"bond": e.e_bond, "chi": e.e_chi, "kappa": e.e_kappa, "kinetic": e.kinetic,
+              "net_force": np.array(e.net_force[:])}
+        if f is not None and isinstance(f, np.ndarray):
+            f = f.reshape(-1, 3)
+        return f, en
+
+    def step_count(self) -> int:
+        s = ctypes.c_int64()
+        self._chk(self.lib.tild_get_step(self.ctx, ctypes.byref(s)))
+        return s.value
+
+    def get_state(self) -> bytes:
+        nb = ctypes.c_size_t()
+        self._chk(self.lib.tild_state_bytes(self.ctx, ctypes.byref(nb)))
+        buf = ctypes.create_string_buffer(nb.value)
+        self._chk(self.lib.tild_get_state(self.ctx, buf, nb))
+        return buf.raw
+
+    def set_state(self, blob: bytes) -> None:
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._chk(self.lib.tild_set_state(self.ctx, buf, len(blob)))
+
+    def profile_steps(self, n: int):
+        ms = (ctypes.c_double * 5)()
+        self._chk(self.lib.tild_profile_steps(self.ctx, int(n), ms))
+        return list(ms)
+
+    def launches(self, n_steps: int) -> int:
+        v = ctypes.c_int64()
+        self._chk(self.lib.tild_launches_per_steps(self.ctx, int(n_steps), ctypes.byref(v)))
+        return v.value

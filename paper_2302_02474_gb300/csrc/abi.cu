@@ -1,0 +1,290 @@
+// extern "C" boundary of the TILD engine: argument validation, error text,
+// and dispatch to the FP32 or FP64 engine.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "engine_api.h"
+
+using namespace tild;
+
+struct tild_ctx {
+    HostConfig cfg;
+    std::unique_ptr<EngineBase> eng;
+    bool have_chains = false;
+    std::string err;
+};
+
+namespace {
+
+std::string g_create_error = "no error";
+
+tild_status fail(tild_ctx* c, tild_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+tild_status from_engine(tild_ctx* c, tild_status st) {
+    if (st != TILD_OK) c->err = c->eng->err.empty() ? "engine error" : c->eng->err;
+    return st;
+}
+
+bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+bool valid_io(int dtype, int where) {
+    return (dtype == TILD_DTYPE_F32 || dtype == TILD_DTYPE_F64) && (where == TILD_HOST || where == TILD_DEVICE);
+}
+
+}  // namespace
+
+extern "C" {
+
+tild_status tild_create(const tild_params* p, tild_ctx** out) {
+    if (!p || !out) {
+        g_create_error = "tild_create: NULL argument";
+        return TILD_EINVAL;
+    }
+    *out = nullptr;
+    if (!(p->L[0] > 0) || p->L[0] != p->L[1] || p->L[0] != p->L[2] || !std::isfinite(p->L[0])) {
+        g_create_error = "tild_create: the box must be cubic with L > 0";
+        return TILD_EUNSUPPORTED;
+    }
+    if (p->n[0] != p->n[1] || p->n[0] != p->n[2] || !pow2_in(p->n[0], 8, 256)) {
+        g_create_error = "tild_create: the grid must be cubic with n a power of two in [8, 256]";
+        return TILD_EUNSUPPORTED;
+    }
+    if (p->pmeorder < 1 || p->pmeorder > 4) {
+        g_create_error = "tild_create: pmeorder must be in 1..4";
+        return TILD_EINVAL;
+    }
+    if (p->precision != TILD_FP32 && p->precision != TILD_FP64) {
+        g_create_error = "tild_create: precision must be TILD_FP32 or TILD_FP64";
+        return TILD_EINVAL;
+    }
+    if (p->precision == TILD_FP64 && p->n[0] > 128) {
+        g_create_error = "tild_create: FP64 grids are limited to 128^3";
+        return TILD_EUNSUPPORTED;
+    }
+    if (p->sort_every < 0) {
+        g_create_error = "tild_create: sort_every must be >= 0";
+        return TILD_EINVAL;
+    }
+    std::unique_ptr<tild_ctx> c(new tild_ctx());
+    c->cfg.L = p->L[0];
+    c->cfg.n = p->n[0];
+    c->cfg.pmeorder = p->pmeorder;
+    c->cfg.precision = p->precision;
+    c->cfg.seed = p->seed;
+    c->cfg.sort_every = p->sort_every == 0 ? 20 : p->sort_every;
+    std::memset(&c->cfg.topo, 0, sizeof(c->cfg.topo));
+    c->eng.reset(p->precision == TILD_FP32 ? make_engine_f32() : make_engine_f64());
+    const tild_status st = c->eng->init(&c->cfg);
+    if (st != TILD_OK) {
+        g_create_error = "tild_create: " + c->eng->err;
+        return st;
+    }
+    *out = c.release();
+    return TILD_OK;
+}
+
+tild_status tild_destroy(tild_ctx* ctx) {
+    delete ctx;
+    return TILD_OK;
+}
+
+tild_status tild_set_chains(tild_ctx* c, int n_types, const tild_moltype* t, double b) {
+    if (!c) return TILD_EINVAL;
+    if (!t || n_types < 1 || n_types > kMaxTypes) return fail(c, TILD_EINVAL, "set_chains: 1..8 molecule types required");
+    if (!(b > 0) || !std::isfinite(b)) return fail(c, TILD_EINVAL, "set_chains: b must be > 0");
+    Topology topo;
+    std::memset(&topo, 0, sizeof(topo));
+    int64_t total = 0;
+    for (int k = 0; k < n_types; ++k) {
+        if (t[k].n_chains < 0 || t[k].N < 1 || t[k].n_a < 0 || t[k].n_a > t[k].N)
+            return fail(c, TILD_EINVAL, "set_chains: need n_chains >= 0, N >= 1, 0 <= n_a <= N");
+        topo.start[k] = (int)total;
+        topo.N[k] = t[k].N;
+        topo.n_a[k] = t[k].n_a;
+        total += t[k].n_chains * (int64_t)t[k].N;
+        if (total >= (int64_t)1 << 31) return fail(c, TILD_EUNSUPPORTED, "set_chains: at most 2^31-1 beads");
+    }
+    if (total < 1) return fail(c, TILD_EINVAL, "set_chains: no beads");
+    topo.start[n_types] = (int)total;
+    topo.n_types = n_types;
+    c->cfg.topo = topo;
+    c->cfg.n_beads = (int)total;
+    c->cfg.b = b;
+    const tild_status st = c->eng->set_chains();
+    if (st) return from_engine(c, st);
+    c->have_chains = true;
+    return TILD_OK;
+}
+
+static tild_status reparam(tild_ctx* c, const HostConfig& next) {
+    // keep v^n = u^n + (dt/2m) F^n across the change
+    const bool keep = c->eng->has_velocities();
+    tild_status st;
+    if (keep && (st = c->eng->save_velocities())) return from_engine(c, st);
+    c->cfg = next;
+    c->eng->params_changed();
+    if (keep && (st = c->eng->restore_velocities())) return from_engine(c, st);
+    return TILD_OK;
+}
+
+tild_status tild_set_interactions(tild_ctx* c, double chi_ab, double kappa, double a) {
+    if (!c) return TILD_EINVAL;
+    if (!std::isfinite(chi_ab) || !std::isfinite(kappa) || !(kappa >= 0) || !(a > 0) || !std::isfinite(a))
+        return fail(c, TILD_EINVAL, "set_interactions: need finite chi, kappa >= 0, a > 0");
+    HostConfig next = c->cfg;
+    next.chi = chi_ab;
+    next.kappa = kappa;
+    next.a = a;
+    next.have_interactions = true;
+    return reparam(c, next);
+}
+
+tild_status tild_set_integrator(tild_ctx* c, double dt, double friction, double kT, double mass) {
+    if (!c) return TILD_EINVAL;
+    if (!(dt > 0) || !(friction >= 0) || !(kT >= 0) || !(mass > 0) || !std::isfinite(dt) || !std::isfinite(friction) ||
+        !std::isfinite(kT) || !std::isfinite(mass))
+        return fail(c, TILD_EINVAL, "set_integrator: need dt > 0, friction >= 0, kT >= 0, mass > 0");
+    HostConfig next = c->cfg;
+    next.dt = dt;
+    next.friction = friction;
+    next.kT = kT;
+    next.mass = mass;
+    return reparam(c, next);
+}
+
+tild_status tild_set_stream(tild_ctx* c, void* stream) {
+    if (!c) return TILD_EINVAL;
+    return from_engine(c, c->eng->set_stream((cudaStream_t)stream));
+}
+
+tild_status tild_set_positions(tild_ctx* c, const void* xyz, int dtype, int where) {
+    if (!c) return TILD_EINVAL;
+    if (!xyz || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "set_positions: bad pointer, dtype or where");
+    if (!c->have_chains) return fail(c, TILD_ESTATE, "set_positions: call tild_set_chains first");
+    return from_engine(c, c->eng->set_positions(xyz, dtype, where));
+}
+
+tild_status tild_init_velocities(tild_ctx* c) {
+    if (!c) return TILD_EINVAL;
+    if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "init_velocities: positions not set");
+    return from_engine(c, c->eng->set_velocities(nullptr, TILD_DTYPE_F64, TILD_DEVICE));
+}
+
+tild_status tild_set_velocities(tild_ctx* c, const void* v, int dtype, int where) {
+    if (!c) return TILD_EINVAL;
+    if (!v || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "set_velocities: bad pointer, dtype or where");
+    if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "set_velocities: positions not set");
+    return from_engine(c, c->eng->set_velocities(v, dtype, where));
+}
+
+tild_status tild_step(tild_ctx* c, int64_t n_steps) {
+    if (!c) return TILD_EINVAL;
+    if (n_steps < 0) return fail(c, TILD_EINVAL, "step: n_steps < 0");
+    if (!c->eng->has_velocities()) return fail(c, TILD_ESTATE, "step: velocities not set");
+    return from_engine(c, c->eng->step(n_steps));
+}
+
+tild_status tild_synchronize(tild_ctx* c) {
+    if (!c) return TILD_EINVAL;
+    return from_engine(c, c->eng->synchronize());
+}
+
+tild_status tild_compute(tild_ctx* c, unsigned what, tild_energy* e, void* forces_out, int dtype, int where) {
+    if (!c) return TILD_EINVAL;
+    if (what & ~(TILD_COMPUTE_ENERGY | TILD_COMPUTE_FORCES)) return fail(c, TILD_EINVAL, "compute: unknown flags");
+    if ((what & TILD_COMPUTE_ENERGY) && !e) return fail(c, TILD_EINVAL, "compute: energy requested with e == NULL");
+    if ((what & TILD_COMPUTE_FORCES) && (!forces_out || !valid_io(dtype, where)))
+        return fail(c, TILD_EINVAL, "compute: forces requested with a bad buffer, dtype or where");
+    if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "compute: positions not set");
+    return from_engine(c, c->eng->compute(what, e, (what & TILD_COMPUTE_FORCES) ? forces_out : nullptr, dtype, where));
+}
+
+tild_status tild_get_positions(tild_ctx* c, void* out, int dtype, int where) {
+    if (!c) return TILD_EINVAL;
+    if (!out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "get_positions: bad pointer, dtype or where");
+    if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "get_positions: positions not set");
+    return from_engine(c, c->eng->get_positions(out, dtype, where));
+}
+
+tild_status tild_get_velocities(tild_ctx* c, void* out, int dtype, int where) {
+    if (!c) return TILD_EINVAL;
+    if (!out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "get_velocities: bad pointer, dtype or where");
+    if (!c->eng->has_velocities()) return fail(c, TILD_ESTATE, "get_velocities: velocities not set");
+    return from_engine(c, c->eng->get_velocities(out, dtype, where));
+}
+
+tild_status tild_get_density(tild_ctx* c, void* out, int dtype, int where) {
+    if (!c) return TILD_EINVAL;
+    if (!out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "get_density: bad pointer, dtype or where");
+    if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "get_density: positions not set");
+    return from_engine(c, c->eng->get_density(out, dtype, where));
+}
+
+tild_status tild_get_spectrum(tild_ctx* c, void* out, int dtype, int where) {
+    if (!c) return TILD_EINVAL;
+    if (!out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "get_spectrum: bad pointer, dtype or where");
+    if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "get_spectrum: positions not set");
+    return from_engine(c, c->eng->get_spectrum(out, dtype, where));
+}
+
+tild_status tild_get_field_gradient(tild_ctx* c, void* out, int dtype, int where) {
+    if (!c) return TILD_EINVAL;
+    if (!out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "get_field_gradient: bad pointer, dtype or where");
+    if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "get_field_gradient: positions not set");
+    return from_engine(c, c->eng->get_field_gradient(out, dtype, where));
+}
+
+tild_status tild_get_step(tild_ctx* c, int64_t* step) {
+    if (!c || !step) return fail(c, TILD_EINVAL, "get_step: NULL argument");
+    *step = c->eng->host_step();
+    return TILD_OK;
+}
+
+tild_status tild_state_bytes(tild_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return fail(c, TILD_EINVAL, "state_bytes: NULL argument");
+    if (!c->have_chains) return fail(c, TILD_ESTATE, "state_bytes: chains not set");
+    *bytes = c->eng->state_bytes();
+    return TILD_OK;
+}
+
+tild_status tild_get_state(tild_ctx* c, void* blob, size_t bytes) {
+    if (!c) return TILD_EINVAL;
+    if (!blob) return fail(c, TILD_EINVAL, "get_state: NULL blob");
+    if (!c->eng->has_velocities()) return fail(c, TILD_ESTATE, "get_state: velocities not set");
+    if (bytes < c->eng->state_bytes()) return fail(c, TILD_EINVAL, "get_state: blob too small");
+    return from_engine(c, c->eng->get_state(blob));
+}
+
+tild_status tild_set_state(tild_ctx* c, const void* blob, size_t bytes) {
+    if (!c) return TILD_EINVAL;
+    if (!blob) return fail(c, TILD_EINVAL, "set_state: NULL blob");
+    if (!c->have_chains) return fail(c, TILD_ESTATE, "set_state: chains not set");
+    if (bytes < c->eng->state_bytes()) return fail(c, TILD_EINVAL, "set_state: blob too small");
+    return from_engine(c, c->eng->set_state(blob));
+}
+
+tild_status tild_profile_steps(tild_ctx* c, int n_steps, double* ms) {
+    if (!c) return TILD_EINVAL;
+    if (!ms || n_steps < 1) return fail(c, TILD_EINVAL, "profile_steps: need ms[5] and n_steps >= 1");
+    if (!c->eng->has_velocities()) return fail(c, TILD_ESTATE, "profile_steps: velocities not set");
+    return from_engine(c, c->eng->profile(n_steps, ms));
+}
+
+tild_status tild_launches_per_steps(tild_ctx* c, int64_t n_steps, int64_t* launches) {
+    if (!c || !launches || n_steps < 0) return fail(c, TILD_EINVAL, "launches_per_steps: bad argument");
+    if (!c->have_chains) return fail(c, TILD_ESTATE, "launches_per_steps: chains not set");
+    *launches = c->eng->launches(n_steps);
+    return TILD_OK;
+}
+
+const char* tild_last_error(tild_ctx* c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+}  // extern "C"

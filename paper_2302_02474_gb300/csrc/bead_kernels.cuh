@@ -1,0 +1,456 @@
+// Bead stages of the TILD step: one CTA per 8x8x8-cell tile of beads.
+//
+//   gather  F_i = -sum_g W(r_i - g) grad w_K(g)   (same weights as the
+//           assignment, caption of Fig. pmm; Eq. PMM)
+//   bonds   F_i -= (3/b^2) sum_{j bonded to i} mic(r_i - r_j)   (Eq. bonds)
+//   GJF     Gronbech-Jensen-Farago update in carried-velocity form
+//   spread  rho_K(g) += W(r_i - g)/dV at the new positions (Eq. rhohat),
+//           accumulated as 64-bit fixed point: first in a shared-memory
+//           patch covering the tile (integer shared atomics), then flushed
+//           with 64-bit global atomic adds. Integer sums make the grid
+//           bit-identical for any order of beads or blocks.
+//
+// Carried velocity: the state between steps is r^n and
+//   u^n = a v^{n-1} + (dt/2m) a F^{n-1} + (b/m) beta^n,
+// so that v^n = u^n + (dt/2m) F^n once F^n is known, and one pass gives
+//   r^{n+1} = r^n + b dt (v^n + (dt/2m) F^n + beta^{n+1}/(2m)),
+//   u^{n+1} = a (v^n + (dt/2m) F^n) + (b/m) beta^{n+1},
+// which is the GJF update with a = (1 - alpha dt/2m)/(1 + alpha dt/2m),
+// b = 1/(1 + alpha dt/2m), beta ~ N(0, 2 alpha kT dt).
+//
+// Bead arrays are SoA in "slot" order: beads binned by cell (tile-major)
+// every few steps. Slot -> bead id in `id`; bonded neighbours by slot in
+// `nbr`. All results are independent of the slot order.
+#pragma once
+
+#include "common.cuh"
+
+namespace tild {
+
+enum BeadMode : int { kModeSpread = 0, kModeForce = 1, kModeSetVel = 2, kModeStep = 3 };
+
+template <typename T> struct BeadParams {
+    int n_beads;
+    int n;            // grid points per edge (power of two)
+    int tiles;        // tiles per edge
+    int margin;       // drift margin (cells) of the shared patch
+    T L, inv_L, inv_dx;
+    T k_bond;         // 3 / b^2
+    // GJF constants
+    T hdm;            // dt / (2m)
+    T gb_dt;          // b dt
+    T inv_2m;         // 1 / (2m)
+    T ga;             // a
+    T gb_m;           // b / m
+    T sigma_beta;     // sqrt(2 alpha kT dt)
+    T sigma_v;        // sqrt(kT / m) (initial velocities)
+    T mass;
+    uint64_t seed;
+    Topology topo;
+};
+
+template <typename T> struct BeadBuffers {
+    const T* __restrict__ px;
+    const T* __restrict__ py;
+    const T* __restrict__ pz;
+    T* __restrict__ qx;  // new positions (STEP)
+    T* __restrict__ qy;
+    T* __restrict__ qz;
+    T* __restrict__ ux;  // carried velocity (read/write in place)
+    T* __restrict__ uy;
+    T* __restrict__ uz;
+    const int* __restrict__ id;
+    const int2* __restrict__ nbr;
+    const int* __restrict__ cell_start;
+    const cplx_t<T>* __restrict__ grad;  // [3][M] (A, B) pairs
+    unsigned long long* __restrict__ rho_fx;  // [2][M]
+    unsigned long long* step;  // device step counter n
+    unsigned int* done;        // CTA completion counter (STEP)
+    unsigned int* err;
+    T* __restrict__ f_out;        // FORCE: [n_beads][3] by id (may be null)
+    T* __restrict__ v_out;        // FORCE: velocities by id (may be null)
+    const T* __restrict__ v_in;   // SETVEL: velocities by id (null: Maxwell-Boltzmann)
+    double* __restrict__ partials;  // FORCE: [blocks][5]
+};
+
+template <typename T> __device__ __forceinline__ T wrap_coord(T x, T L, T inv_L) {
+    T y = x - L * floor(x * inv_L);
+    return (y >= L) ? T(0) : y;
+}
+
+template <typename T> __device__ __forceinline__ T min_image(T d, T L, T inv_L) { return d - L * rint(d * inv_L); }
+
+template <int P, typename T>
+__device__ __forceinline__ void gather_force(const BeadParams<T>& p, const cplx_t<T>* __restrict__ grad, T x, T y,
+                                             T z, int species, T& fx, T& fy, T& fz) {
+    T wx[P], wy[P], wz[P];
+    int jx, jy, jz;
+    dh_weights<P>(x * p.inv_dx, jx, wx);
+    dh_weights<P>(y * p.inv_dx, jy, wy);
+    dh_weights<P>(z * p.inv_dx, jz, wz);
+    const int nm = p.n - 1;
+    const size_t M = (size_t)p.n * p.n * p.n;
+    T gx = 0, gy = 0, gz = 0;
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+        const size_t oz = (size_t)((jz + c) & nm) * p.n * p.n;
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            const size_t oy = oz + (size_t)((jy + b) & nm) * p.n;
+            const T wyz = wy[b] * wz[c];
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                const size_t g = oy + ((jx + a) & nm);
+                const T w = wx[a] * wyz;
+                const cplx_t<T> vx = __ldg(grad + g);
+                const cplx_t<T> vy = __ldg(grad + M + g);
+                const cplx_t<T> vz = __ldg(grad + 2 * M + g);
+                gx += w * (species ? vx.y : vx.x);
+                gy += w * (species ? vy.y : vy.x);
+                gz += w * (species ? vz.y : vz.x);
+            }
+        }
+    }
+    fx = -gx;
+    fy = -gy;
+    fz = -gz;
+}
+
+// Spread one bead (species K) at (x, y, z). The patch covers grid points
+// [org, org + W) per dimension; contributions outside it go straight to
+// global memory.
+template <int P, typename T>
+__device__ __forceinline__ void spread_bead(const BeadParams<T>& p, unsigned long long* patch, int W, int3 org,
+                                            unsigned long long* __restrict__ rho_fx, T x, T y, T z, int K) {
+    T wx[P], wy[P], wz[P];
+    int jx, jy, jz;
+    dh_weights<P>(x * p.inv_dx, jx, wx);
+    dh_weights<P>(y * p.inv_dx, jy, wy);
+    dh_weights<P>(z * p.inv_dx, jz, wz);
+    const int lx = jx - org.x, ly = jy - org.y, lz = jz - org.z;
+    const bool inside = lx >= 0 && ly >= 0 && lz >= 0 && lx + P <= W && ly + P <= W && lz + P <= W;
+    if (inside) {
+        unsigned long long* base = patch + (size_t)K * W * W * W;
+#pragma unroll
+        for (int c = 0; c < P; ++c)
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const T wyz = wy[b] * wz[c];
+#pragma unroll
+                for (int a = 0; a < P; ++a) {
+                    const long long v = to_fixed(wx[a] * wyz);
+                    atomicAdd(base + ((lz + c) * W + (ly + b)) * W + (lx + a), (unsigned long long)v);
+                }
+            }
+    } else {
+        const int nm = p.n - 1;
+        const size_t M = (size_t)p.n * p.n * p.n;
+#pragma unroll
+        for (int c = 0; c < P; ++c)
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const T wyz = wy[b] * wz[c];
+#pragma unroll
+                for (int a = 0; a < P; ++a) {
+                    const long long v = to_fixed(wx[a] * wyz);
+                    const size_t g = ((size_t)((jz + c) & nm) * p.n + ((jy + b) & nm)) * p.n + ((jx + a) & nm);
+                    atomicAdd(rho_fx + K * M + g, (unsigned long long)v);
+                }
+            }
+    }
+}
+
+template <int P, int MODE, typename T>
+__global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long* patch = reinterpret_cast<unsigned long long*>(smem_raw);
+    constexpr bool kSpread = (MODE == kModeSpread || MODE == kModeStep);
+    constexpr bool kForce = (MODE != kModeSpread);
+    using SE = stencil_extent<P>;
+    const int W = kTile + SE::hi - SE::lo + 2 * p.margin;
+    const int t = blockIdx.x;
+    const int tx = t % p.tiles, ty = (t / p.tiles) % p.tiles, tz = t / (p.tiles * p.tiles);
+    const int3 org = {tx * kTile + SE::lo - p.margin, ty * kTile + SE::lo - p.margin, tz * kTile + SE::lo - p.margin};
+    const int W3 = W * W * W;
+    if (kSpread) {
+        for (int i = threadIdx.x; i < 2 * W3; i += blockDim.x) patch[i] = 0ull;
+        __syncthreads();
+    }
+    const int start = bf.cell_start[(size_t)t * kTileCells];
+    const int end = bf.cell_start[(size_t)(t + 1) * kTileCells];
+    const uint64_t step = (MODE == kModeStep) ? *((volatile unsigned long long*)bf.step) : 0ull;
+    double acc[5] = {0, 0, 0, 0, 0};
+
+    for (int i = start + threadIdx.x; i < end; i += blockDim.x) {
+        T x = bf.px[i], y = bf.py[i], z = bf.pz[i];
+        const int bid = bf.id[i];
+        const BeadInfo info = bead_info(p.topo, bid);
+        if (kForce) {
+            T fx, fy, fz;
+            gather_force<P>(p, bf.grad, x, y, z, info.species, fx, fy, fz);
+            const int2 nb = bf.nbr[i];
+            if (nb.x >= 0) {
+                const T dx = min_image(x - bf.px[nb.x], p.L, p.inv_L);
+                const T dy = min_image(y - bf.py[nb.x], p.L, p.inv_L);
+                const T dz = min_image(z - bf.pz[nb.x], p.L, p.inv_L);
+                fx -= p.k_bond * dx;
+                fy -= p.k_bond * dy;
+                fz -= p.k_bond * dz;
+            }
+            if (nb.y >= 0) {
+                const T dx = min_image(x - bf.px[nb.y], p.L, p.inv_L);
+                const T dy = min_image(y - bf.py[nb.y], p.L, p.inv_L);
+                const T dz = min_image(z - bf.pz[nb.y], p.L, p.inv_L);
+                fx -= p.k_bond * dx;
+                fy -= p.k_bond * dy;
+                fz -= p.k_bond * dz;
+                if (MODE == kModeForce) acc[0] += 0.5 * (double)p.k_bond * ((double)dx * dx + (double)dy * dy + (double)dz * dz);
+            }
+            if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(bf.err, kErrNonFinite);
+            if (MODE == kModeForce) {
+                const T vx = bf.ux[i] + p.hdm * fx, vy = bf.uy[i] + p.hdm * fy, vz = bf.uz[i] + p.hdm * fz;
+                acc[1] += 0.5 * (double)p.mass * ((double)vx * vx + (double)vy * vy + (double)vz * vz);
+                acc[2] += fx;
+                acc[3] += fy;
+                acc[4] += fz;
+                if (bf.f_out) {
+                    bf.f_out[3 * (size_t)bid + 0] = fx;
+                    bf.f_out[3 * (size_t)bid + 1] = fy;
+                    bf.f_out[3 * (size_t)bid + 2] = fz;
+                }
+                if (bf.v_out) {
+                    bf.v_out[3 * (size_t)bid + 0] = vx;
+                    bf.v_out[3 * (size_t)bid + 1] = vy;
+                    bf.v_out[3 * (size_t)bid + 2] = vz;
+                }
+            } else if (MODE == kModeSetVel) {
+                T vx, vy, vz;
+                if (bf.v_in) {
+                    vx = bf.v_in[3 * (size_t)bid + 0];
+                    vy = bf.v_in[3 * (size_t)bid + 1];
+                    vz = bf.v_in[3 * (size_t)bid + 2];
+                } else {
+                    const normal3<T> g = gaussian3((uint32_t)bid, ~0ull, p.seed, T(0));
+                    vx = p.sigma_v * g.a;
+                    vy = p.sigma_v * g.b;
+                    vz = p.sigma_v * g.c;
+                }
+                bf.ux[i] = vx - p.hdm * fx;
+                bf.uy[i] = vy - p.hdm * fy;
+                bf.uz[i] = vz - p.hdm * fz;
+            } else if (MODE == kModeStep) {
+                const normal3<T> g = gaussian3((uint32_t)bid, step + 1, p.seed, T(0));
+                const T bx = p.sigma_beta * g.a, by = p.sigma_beta * g.b, bz = p.sigma_beta * g.c;
+                // v^n + (dt/2m) F^n
+                const T hx = bf.ux[i] + T(2) * p.hdm * fx;
+                const T hy = bf.uy[i] + T(2) * p.hdm * fy;
+                const T hz = bf.uz[i] + T(2) * p.hdm * fz;
+                x = wrap_coord(x + p.gb_dt * (hx + p.inv_2m * bx), p.L, p.inv_L);
+                y = wrap_coord(y + p.gb_dt * (hy + p.inv_2m * by), p.L, p.inv_L);
+                z = wrap_coord(z + p.gb_dt * (hz + p.inv_2m * bz), p.L, p.inv_L);
+                bf.qx[i] = x;
+                bf.qy[i] = y;
+                bf.qz[i] = z;
+                bf.ux[i] = p.ga * hx + p.gb_m * bx;
+                bf.uy[i] = p.ga * hy + p.gb_m * by;
+                bf.uz[i] = p.ga * hz + p.gb_m * bz;
+            }
+        }
+        if (kSpread) spread_bead<P>(p, patch, W, org, bf.rho_fx, x, y, z, info.species);
+    }
+
+    if (kSpread) {
+        __syncthreads();
+        const int nm = p.n - 1;
+        const size_t M = (size_t)p.n * p.n * p.n;
+        for (int i = threadIdx.x; i < 2 * W3; i += blockDim.x) {
+            const unsigned long long v = patch[i];
+            if (v) {
+                const int K = i / W3, r = i % W3;
+                const int lx = r % W, ly = (r / W) % W, lz = r / (W * W);
+                const size_t g = ((size_t)((org.z + lz) & nm) * p.n + ((org.y + ly) & nm)) * p.n + ((org.x + lx) & nm);
+                atomicAdd(bf.rho_fx + K * M + g, v);
+            }
+        }
+    }
+    if (MODE == kModeForce) {
+        __shared__ double red[5][8];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double v = acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[k][wid] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 5) {
+            double s = 0;
+            for (int w = 0; w < (int)blockDim.x / 32; ++w) s += red[threadIdx.x][w];
+            bf.partials[5 * (size_t)t + threadIdx.x] = s;
+        }
+    }
+    if (MODE == kModeStep) {
+        // the last CTA to finish advances the step counter (every CTA has
+        // read it by then)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(bf.done, 1u);
+            if (prev == gridDim.x - 1) {
+                *((volatile unsigned long long*)bf.step) = step + 1;
+                *((volatile unsigned int*)bf.done) = 0u;
+                __threadfence();
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- binning
+
+// Cell key of a position: tile-major index of the grid cell floor(r/dx).
+template <typename T> __device__ __forceinline__ int cell_key(T x, T y, T z, T inv_dx, int n, int tiles) {
+    const int cx = min(max((int)floor(x * inv_dx), 0), n - 1);
+    const int cy = min(max((int)floor(y * inv_dx), 0), n - 1);
+    const int cz = min(max((int)floor(z * inv_dx), 0), n - 1);
+    const int t = ((cz / kTile) * tiles + cy / kTile) * tiles + cx / kTile;
+    const int l = ((cz % kTile) * kTile + cy % kTile) * kTile + cx % kTile;
+    return t * kTileCells + l;
+}
+
+template <typename T>
+__global__ void bin_count(int n_beads, const T* __restrict__ px, const T* __restrict__ py, const T* __restrict__ pz,
+                          T inv_dx, int n, int tiles, int* __restrict__ keys, int* __restrict__ counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_beads) return;
+    const int k = cell_key(px[i], py[i], pz[i], inv_dx, n, tiles);
+    keys[i] = k;
+    atomicAdd(counts + k, 1);
+}
+
+template <typename T>
+__global__ void bin_scatter_pos(int n_beads, const int* __restrict__ keys, const int* __restrict__ cell_start,
+                                int* __restrict__ cursor, const T* __restrict__ src /*[3][N]*/, T* __restrict__ dst,
+                                const int* __restrict__ id_src, int* __restrict__ id_dst, int* __restrict__ slot_of_id) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_beads) return;
+    const int k = keys[i];
+    const int s = cell_start[k] + atomicAdd(cursor + k, 1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dst[(size_t)c * n_beads + s] = src[(size_t)c * n_beads + i];
+    const int b = id_src[i];
+    id_dst[s] = b;
+    slot_of_id[b] = s;
+}
+
+// Move the carried velocities to the slots assigned by bin_scatter_pos.
+template <typename T>
+__global__ void bin_move_u(int n_beads, const int* __restrict__ id_src, const int* __restrict__ slot_of_id,
+                           const T* __restrict__ src /*[3][N]*/, T* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_beads) return;
+    const int s = slot_of_id[id_src[i]];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dst[(size_t)c * n_beads + s] = src[(size_t)c * n_beads + i];
+}
+
+static __global__ void bin_neighbours(int n_beads, Topology topo, const int* __restrict__ id, const int* __restrict__ slot_of_id,
+                               int2* __restrict__ nbr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_beads) return;
+    const BeadInfo b = bead_info(topo, id[i]);
+    nbr[i] = make_int2(b.prev >= 0 ? slot_of_id[b.prev] : -1, b.next >= 0 ? slot_of_id[b.next] : -1);
+}
+
+// Exclusive scan of `count` ints in blocks of 1024 (three kernels).
+static __global__ void scan_blocks(const int* __restrict__ in, int* __restrict__ out, int* __restrict__ block_sums, int count) {
+    __shared__ int s[1024];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int v = i < count ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < count) out[i] = s[threadIdx.x] - v;
+    if (threadIdx.x == 1023) block_sums[blockIdx.x] = s[1023];
+}
+
+static __global__ void scan_top(int* __restrict__ block_sums, int nblocks) {
+    // single CTA of 1024 threads; sequential over chunks of 1024
+    __shared__ int s[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nblocks; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < nblocks ? block_sums[i] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nblocks) block_sums[i] = carry + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += s[1023];
+        __syncthreads();
+    }
+}
+
+static __global__ void scan_add(int* __restrict__ out, const int* __restrict__ block_sums, int count) {
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    if (i < count) out[i] += block_sums[blockIdx.x];
+}
+
+// -------------------------------------------------------------- I/O
+
+// In: AoS [n][3] by bead id (type TI). Out: SoA slot order = id order.
+template <typename T, typename TI>
+__global__ void load_positions(int n_beads, const TI* __restrict__ in, T L, T inv_L, T* __restrict__ pos /*[3][N]*/,
+                               int* __restrict__ id) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_beads) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) pos[(size_t)d * n_beads + i] = wrap_coord((T)in[3 * (size_t)i + d], L, inv_L);
+    id[i] = i;
+}
+
+// SoA slot order -> AoS by id (type TO).
+template <typename T, typename TO>
+__global__ void store_by_id(int n_beads, const T* __restrict__ src /*[3][N]*/, const int* __restrict__ id,
+                            TO* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_beads) return;
+    const int b = id[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[3 * (size_t)b + d] = (TO)src[(size_t)d * n_beads + i];
+}
+
+// AoS by id (type TI) -> SoA slot order.
+template <typename T, typename TI>
+__global__ void load_by_id(int n_beads, const TI* __restrict__ in, const int* __restrict__ id, T* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_beads) return;
+    const int b = id[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dst[(size_t)d * n_beads + i] = (T)in[3 * (size_t)b + d];
+}
+
+template <typename TO>
+__global__ void density_out(size_t count, const unsigned long long* __restrict__ rho_fx, double scale, TO* __restrict__ out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = (TO)((double)(long long)rho_fx[i] * scale);
+}
+
+template <typename TI, typename TO>
+__global__ void convert_copy(size_t count, const TI* __restrict__ in, TO* __restrict__ out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = (TO)in[i];
+}
+
+}  // namespace tild

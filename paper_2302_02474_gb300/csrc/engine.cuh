@@ -1,0 +1,871 @@
+// Host engine of the TILD step: owns device buffers, launches the kernels
+// of one step in stream order and replays whole re-binning cycles as CUDA
+// graphs. Instantiated once per precision (engine_f32.cu, engine_f64.cu).
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bead_kernels.cuh"
+#include "engine_api.h"
+#include "grid_kernels.cuh"
+
+namespace tild {
+
+#define TILD_CUDA(call)                                                                        \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                          \
+            return e_ == cudaErrorMemoryAllocation ? TILD_ENOMEM : TILD_EDEVICE;               \
+        }                                                                                      \
+    } while (0)
+
+constexpr uint64_t kStateMagic = 0x54494c4453544154ull;  // "TILDSTAT"
+
+template <typename T> class Engine final : public EngineBase {
+    using V = cplx_t<T>;
+
+   public:
+    ~Engine() override { release(); }
+
+    tild_status init(HostConfig* cfg) override {
+        cfg_ = cfg;
+        n_ = cfg->n;
+        M_ = (size_t)n_ * n_ * n_;
+        tiles_ = n_ / kTile;
+        P_ = cfg->pmeorder + 1;
+        plane_fits_ = plane_smem() <= 200 * 1024;
+        C_ = std::min(n_, (int)(128 / sizeof(V)));
+        TILD_CUDA(cudaGetDevice(&device_));
+        TILD_CUDA(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
+        stream_ = own_stream_;
+        TILD_CUDA(cudaMalloc(&rho_fx_, 2 * M_ * sizeof(unsigned long long)));
+        TILD_CUDA(cudaMalloc(&Zxy_, M_ * sizeof(V)));
+        TILD_CUDA(cudaMalloc(&H_, 3 * M_ * sizeof(V)));
+        TILD_CUDA(cudaMalloc(&grad_, 3 * M_ * sizeof(V)));
+        TILD_CUDA(cudaMalloc(&tw_, n_ * sizeof(V)));
+        TILD_CUDA(cudaMalloc(&counters_, 4 * sizeof(unsigned long long)));
+        TILD_CUDA(cudaMemset(counters_, 0, 4 * sizeof(unsigned long long)));
+        TILD_CUDA(cudaMemset(rho_fx_, 0, 2 * M_ * sizeof(unsigned long long)));
+        TILD_CUDA(cudaMalloc(&counts_, (M_ + 1) * sizeof(int)));
+        TILD_CUDA(cudaMalloc(&cell_start_, (M_ + 1) * sizeof(int)));
+        TILD_CUDA(cudaMalloc(&cursor_, (M_ + 1) * sizeof(int)));
+        scan_blocks_ = (int)((M_ + 1 + 1023) / 1024);
+        TILD_CUDA(cudaMalloc(&block_sums_, scan_blocks_ * sizeof(int)));
+        n_z_blocks_ = (size_t)(n_ / C_) * n_;
+        n_partials_ = std::max(2 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
+        TILD_CUDA(cudaMalloc(&partials_, n_partials_ * sizeof(double)));
+        // twiddles W_n^m = exp(-2 pi i m / n) in FP64, rounded to T
+        std::vector<V> tw(n_);
+        for (int m = 0; m < n_; ++m) {
+            const double ang = -2.0 * 3.14159265358979323846 * (double)m / (double)n_;
+            tw[m] = V{(T)std::cos(ang), (T)std::sin(ang)};
+        }
+        TILD_CUDA(cudaMemcpy(tw_, tw.data(), n_ * sizeof(V), cudaMemcpyHostToDevice));
+        return set_kernel_attributes();
+    }
+
+    tild_status set_chains() override {
+        invalidate_graph();
+        free_beads();
+        const size_t N = (size_t)cfg_->n_beads;
+        for (int k = 0; k < 2; ++k) {
+            TILD_CUDA(cudaMalloc(&pos_[k], 3 * N * sizeof(T)));
+            TILD_CUDA(cudaMalloc(&u_[k], 3 * N * sizeof(T)));
+            TILD_CUDA(cudaMalloc(&id_[k], N * sizeof(int)));
+            TILD_CUDA(cudaMemset(u_[k], 0, 3 * N * sizeof(T)));
+        }
+        TILD_CUDA(cudaMalloc(&nbr_, N * sizeof(int2)));
+        TILD_CUDA(cudaMalloc(&slot_of_id_, N * sizeof(int)));
+        TILD_CUDA(cudaMalloc(&keys_, N * sizeof(int)));
+        have_pos_ = have_vel_ = false;
+        return TILD_OK;
+    }
+
+    tild_status set_stream(cudaStream_t s) override {
+        invalidate_graph();
+        stream_ = s ? s : own_stream_;
+        return TILD_OK;
+    }
+    cudaStream_t stream() const override { return stream_; }
+
+    tild_status set_positions(const void* xyz, int dtype, int where) override {
+        const int N = cfg_->n_beads;
+        const void* src = xyz;
+        tild_status st = stage_in(&src, xyz, (size_t)3 * N, dtype, where);
+        if (st) return st;
+        cur_pos_ = cur_u_ = cur_id_ = 0;
+        const T L = (T)cfg_->L;
+        if (dtype == TILD_DTYPE_F32)
+            load_positions<T, float><<<blocks(N), 256, 0, stream_>>>(N, (const float*)src, L, (T)(1.0 / cfg_->L), pos_[0], id_[0]);
+        else
+            load_positions<T, double><<<blocks(N), 256, 0, stream_>>>(N, (const double*)src, L, (T)(1.0 / cfg_->L), pos_[0], id_[0]);
+        TILD_CUDA(cudaGetLastError());
+        if ((st = enqueue_sort())) return st;
+        if ((st = respread())) return st;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        have_pos_ = true;
+        have_vel_ = false;
+        return TILD_OK;
+    }
+
+    tild_status set_velocities(const void* v, int dtype, int where) override {
+        const int N = cfg_->n_beads;
+        tild_status st;
+        const T* vin = nullptr;
+        if (v) {
+            // bring to device in precision T (AoS by id)
+            const void* src = v;
+            if ((st = stage_in(&src, v, (size_t)3 * N, dtype, where))) return st;
+            if ((st = ensure_aux((size_t)3 * N * sizeof(T)))) return st;
+            if (dtype == TILD_DTYPE_F32)
+                convert_copy<float, T><<<blocks(3 * (size_t)N), 256, 0, stream_>>>((size_t)3 * N, (const float*)src, (T*)aux_);
+            else
+                convert_copy<double, T><<<blocks(3 * (size_t)N), 256, 0, stream_>>>((size_t)3 * N, (const double*)src, (T*)aux_);
+            TILD_CUDA(cudaGetLastError());
+            vin = (const T*)aux_;
+        }
+        if ((st = enqueue_fields(false, nullptr, nullptr))) return st;
+        BeadBuffers<T> bf = bead_buffers();
+        bf.v_in = vin;
+        if ((st = launch_bead(kModeSetVel, bf))) return st;
+        TILD_CUDA(cudaMemsetAsync(counters_, 0, 4 * sizeof(unsigned long long), stream_));
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        host_step_ = 0;
+        steps_since_sort_ = 0;
+        have_vel_ = true;
+        return TILD_OK;
+    }
+
+    tild_status step(int64_t n) override {
+        tild_status st;
+        const int K = cfg_->sort_every;
+        while (n > 0) {
+            if (steps_since_sort_ >= K && n >= 2 * (int64_t)K) {
+                // a full cycle (sort, K steps, sort, K steps) as one graph
+                if ((st = run_cycle_graph())) return st;
+                n -= 2 * (int64_t)K;
+                host_step_ += 2 * (int64_t)K;
+                continue;
+            }
+            if (steps_since_sort_ >= K) {
+                if ((st = enqueue_sort())) return st;
+            }
+            if ((st = enqueue_step())) return st;
+            --n;
+            ++host_step_;
+        }
+        return TILD_OK;
+    }
+
+    tild_status synchronize() override {
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return check_err();
+    }
+
+    tild_status compute(unsigned what, tild_energy* e, void* f, int dtype, int where) override {
+        tild_status st;
+        const bool want_e = (what & TILD_COMPUTE_ENERGY) != 0;
+        if ((st = enqueue_fields(want_e, partials_, nullptr))) return st;
+        std::vector<double> zpart;
+        if (want_e) {
+            zpart.resize(2 * n_z_blocks_);
+            TILD_CUDA(cudaMemcpyAsync(zpart.data(), partials_, zpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        }
+        BeadBuffers<T> bf = bead_buffers();
+        T* fdev = nullptr;
+        if (f) {
+            if ((st = ensure_aux((size_t)3 * cfg_->n_beads * sizeof(T)))) return st;
+            fdev = (T*)aux_;
+            bf.f_out = fdev;
+        }
+        if ((st = launch_bead(kModeForce, bf))) return st;
+        std::vector<double> bpart(5 * (size_t)tiles_ * tiles_ * tiles_);
+        TILD_CUDA(cudaMemcpyAsync(bpart.data(), partials_, bpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        if (f && (st = stage_out_vec(fdev, (size_t)3 * cfg_->n_beads, f, dtype, where))) return st;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        if ((st = check_err())) return st;
+        if (want_e && e) {
+            double s0 = 0, s1 = 0;
+            for (size_t b = 0; b < n_z_blocks_; ++b) {
+                s0 += zpart[2 * b];
+                s1 += zpart[2 * b + 1];
+            }
+            const double V = cfg_->L * cfg_->L * cfg_->L;
+            const double dV = V / (double)M_;
+            const double rho0 = cfg_->n_beads / V;
+            e->e_chi = cfg_->chi / rho0 * dV * dV / V * s0;
+            e->e_kappa = cfg_->kappa / (2.0 * rho0) * dV * dV / V * s1;
+        }
+        if (e) {
+            double acc[5] = {0, 0, 0, 0, 0};
+            for (size_t b = 0; b < bpart.size() / 5; ++b)
+                for (int k = 0; k < 5; ++k) acc[k] += bpart[5 * b + k];
+            e->e_bond = acc[0];
+            e->kinetic = acc[1];
+            for (int d = 0; d < 3; ++d) e->net_force[d] = acc[2 + d];
+            if (!want_e) e->e_chi = e->e_kappa = 0.0;
+        }
+        return TILD_OK;
+    }
+
+    tild_status get_positions(void* out, int dtype, int where) override {
+        return out_by_id(pos_[cur_pos_], out, dtype, where);
+    }
+
+    tild_status get_velocities(void* out, int dtype, int where) override {
+        tild_status st;
+        if ((st = enqueue_fields(false, nullptr, nullptr))) return st;
+        if ((st = ensure_aux((size_t)3 * cfg_->n_beads * sizeof(T)))) return st;
+        BeadBuffers<T> bf = bead_buffers();
+        bf.v_out = (T*)aux_;
+        if ((st = launch_bead(kModeForce, bf))) return st;
+        if ((st = stage_out_vec((T*)aux_, (size_t)3 * cfg_->n_beads, out, dtype, where))) return st;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return check_err();
+    }
+
+    tild_status get_density(void* out, int dtype, int where) override {
+        const double scale = kFixInv / (cfg_->L * cfg_->L * cfg_->L / (double)M_);
+        const size_t count = 2 * M_;
+        tild_status st;
+        void* dst = out;
+        if (where == TILD_HOST) {
+            if ((st = ensure_aux(count * 8))) return st;
+            dst = aux_;
+        }
+        if (dtype == TILD_DTYPE_F32)
+            density_out<float><<<blocks(count), 256, 0, stream_>>>(count, rho_fx_, scale, (float*)dst);
+        else
+            density_out<double><<<blocks(count), 256, 0, stream_>>>(count, rho_fx_, scale, (double*)dst);
+        TILD_CUDA(cudaGetLastError());
+        if (where == TILD_HOST)
+            TILD_CUDA(cudaMemcpyAsync(out, dst, count * dtype_size(dtype), cudaMemcpyDeviceToHost, stream_));
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return TILD_OK;
+    }
+
+    tild_status get_spectrum(void* out, int dtype, int where) override {
+        tild_status st;
+        if (!spec_) TILD_CUDA(cudaMalloc(&spec_, M_ * sizeof(V)));
+        if ((st = enqueue_fields(false, nullptr, spec_))) return st;
+        if ((st = stage_out_vec((T*)spec_, 2 * M_, out, dtype, where))) return st;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return TILD_OK;
+    }
+
+    tild_status get_field_gradient(void* out, int dtype, int where) override {
+        tild_status st;
+        if ((st = enqueue_fields(false, nullptr, nullptr))) return st;
+        if ((st = stage_out_vec((T*)grad_, 6 * M_, out, dtype, where))) return st;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return TILD_OK;
+    }
+
+    int64_t host_step() const override { return host_step_; }
+
+    // blob: magic, n_beads, sizeof(T), step, seed | pos[N][3] | u[N][3] (by id, T)
+    size_t state_bytes() const override { return 5 * sizeof(uint64_t) + 6 * (size_t)cfg_->n_beads * sizeof(T); }
+
+    tild_status get_state(void* blob) override {
+        const size_t N = cfg_->n_beads;
+        uint64_t* h = (uint64_t*)blob;
+        h[0] = kStateMagic;
+        h[1] = N;
+        h[2] = sizeof(T);
+        h[3] = (uint64_t)host_step_;
+        h[4] = cfg_->seed;
+        tild_status st;
+        if ((st = ensure_aux(6 * N * sizeof(T)))) return st;
+        T* d = (T*)aux_;
+        store_by_id<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, pos_[cur_pos_], id_[cur_id_], d);
+        store_by_id<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, u_[cur_u_], id_[cur_id_], d + 3 * N);
+        TILD_CUDA(cudaGetLastError());
+        TILD_CUDA(cudaMemcpyAsync(h + 5, d, 6 * N * sizeof(T), cudaMemcpyDeviceToHost, stream_));
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return TILD_OK;
+    }
+
+    tild_status set_state(const void* blob) override {
+        const size_t N = cfg_->n_beads;
+        const uint64_t* h = (const uint64_t*)blob;
+        if (h[0] != kStateMagic || h[1] != N || h[2] != sizeof(T) || h[4] != cfg_->seed) {
+            err = "state blob does not match this context (beads, precision or seed)";
+            return TILD_EINVAL;
+        }
+        invalidate_graph();
+        tild_status st;
+        if ((st = ensure_aux(6 * N * sizeof(T)))) return st;
+        T* d = (T*)aux_;
+        TILD_CUDA(cudaMemcpyAsync(d, h + 5, 6 * N * sizeof(T), cudaMemcpyHostToDevice, stream_));
+        cur_pos_ = cur_u_ = cur_id_ = 0;
+        load_positions<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, d, (T)cfg_->L, (T)(1.0 / cfg_->L), pos_[0], id_[0]);
+        load_by_id<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, d + 3 * N, id_[0], u_[0]);
+        TILD_CUDA(cudaGetLastError());
+        if ((st = enqueue_sort())) return st;
+        if ((st = respread())) return st;
+        host_step_ = (int64_t)h[3];
+        const unsigned long long dstep = h[3];
+        TILD_CUDA(cudaMemcpyAsync(counters_, &dstep, sizeof(dstep), cudaMemcpyHostToDevice, stream_));
+        TILD_CUDA(cudaMemsetAsync(counters_ + 1, 0, sizeof(unsigned long long), stream_));
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        steps_since_sort_ = 0;
+        have_pos_ = have_vel_ = true;
+        return TILD_OK;
+    }
+
+    tild_status profile(int nsteps, double* ms) override {
+        tild_status st;
+        cudaEvent_t ev[6];
+        for (auto& e : ev) TILD_CUDA(cudaEventCreate(&e));
+        double acc[5] = {0, 0, 0, 0, 0};
+        const int K = cfg_->sort_every;
+        for (int s = 0; s < nsteps; ++s) {
+            TILD_CUDA(cudaEventRecord(ev[0], stream_));
+            if (steps_since_sort_ >= K) {
+                if ((st = enqueue_sort())) return st;
+            }
+            TILD_CUDA(cudaEventRecord(ev[1], stream_));
+            if ((st = enqueue_forward(true))) return st;
+            TILD_CUDA(cudaEventRecord(ev[2], stream_));
+            if ((st = enqueue_zpass(nullptr, nullptr))) return st;
+            TILD_CUDA(cudaEventRecord(ev[3], stream_));
+            if ((st = enqueue_inverse())) return st;
+            TILD_CUDA(cudaEventRecord(ev[4], stream_));
+            BeadBuffers<T> bf = bead_buffers();
+            bf.qx = pos_[1 - cur_pos_];
+            bf.qy = bf.qx + cfg_->n_beads;
+            bf.qz = bf.qy + cfg_->n_beads;
+            if ((st = launch_bead(kModeStep, bf))) return st;
+            TILD_CUDA(cudaEventRecord(ev[5], stream_));
+            cur_pos_ = 1 - cur_pos_;
+            ++steps_since_sort_;
+            ++host_step_;
+            TILD_CUDA(cudaEventSynchronize(ev[5]));
+            float t;
+            TILD_CUDA(cudaEventElapsedTime(&t, ev[1], ev[2])); acc[0] += t;
+            TILD_CUDA(cudaEventElapsedTime(&t, ev[2], ev[3])); acc[1] += t;
+            TILD_CUDA(cudaEventElapsedTime(&t, ev[3], ev[4])); acc[2] += t;
+            TILD_CUDA(cudaEventElapsedTime(&t, ev[4], ev[5])); acc[3] += t;
+            TILD_CUDA(cudaEventElapsedTime(&t, ev[0], ev[1])); acc[4] += t;
+        }
+        for (auto& e : ev) cudaEventDestroy(e);
+        for (int k = 0; k < 5; ++k) ms[k] = nsteps > 0 ? acc[k] / nsteps : 0.0;
+        return check_err();
+    }
+
+    int64_t launches(int64_t n) const override {
+        const int64_t per_step = (plane_fits_ ? 2 : 4) + 2;
+        const int64_t per_sort = 7;
+        const int K = cfg_->sort_every;
+        int64_t since = steps_since_sort_, sorts = 0;
+        for (int64_t s = 0; s < n; ++s) {
+            if (since >= K) {
+                ++sorts;
+                since = 0;
+            }
+            ++since;
+        }
+        return n * per_step + sorts * per_sort;
+    }
+
+    bool has_positions() const override { return have_pos_; }
+    bool has_velocities() const override { return have_vel_; }
+
+    tild_status save_velocities() override {
+        const size_t N = cfg_->n_beads;
+        if (!vsave_) TILD_CUDA(cudaMalloc(&vsave_, 3 * N * sizeof(T)));
+        tild_status st;
+        if ((st = enqueue_fields(false, nullptr, nullptr))) return st;
+        BeadBuffers<T> bf = bead_buffers();
+        bf.v_out = vsave_;
+        if ((st = launch_bead(kModeForce, bf))) return st;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return TILD_OK;
+    }
+
+    tild_status restore_velocities() override {
+        invalidate_graph();
+        tild_status st;
+        if ((st = enqueue_fields(false, nullptr, nullptr))) return st;
+        BeadBuffers<T> bf = bead_buffers();
+        bf.v_in = vsave_;
+        if ((st = launch_bead(kModeSetVel, bf))) return st;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return TILD_OK;
+    }
+
+    void params_changed() override { invalidate_graph(); }
+
+   private:
+    T* vsave_ = nullptr;
+    HostConfig* cfg_ = nullptr;
+    int device_ = 0;
+    int n_ = 0, tiles_ = 0, P_ = 2, C_ = 16;
+    size_t M_ = 0;
+    bool plane_fits_ = true;
+    cudaStream_t own_stream_ = nullptr, stream_ = nullptr;
+    // grids
+    unsigned long long* rho_fx_ = nullptr;
+    V* Zxy_ = nullptr;
+    V* H_ = nullptr;
+    V* grad_ = nullptr;
+    V* tw_ = nullptr;
+    V* spec_ = nullptr;
+    unsigned long long* counters_ = nullptr;  // [0] step, [1] done | err
+    double* partials_ = nullptr;
+    size_t n_partials_ = 0, n_z_blocks_ = 0;
+    // beads
+    T* pos_[2] = {nullptr, nullptr};
+    T* u_[2] = {nullptr, nullptr};
+    int* id_[2] = {nullptr, nullptr};
+    int2* nbr_ = nullptr;
+    int* slot_of_id_ = nullptr;
+    int* keys_ = nullptr;
+    int* counts_ = nullptr;
+    int* cell_start_ = nullptr;
+    int* cursor_ = nullptr;
+    int* block_sums_ = nullptr;
+    int scan_blocks_ = 0;
+    int cur_pos_ = 0, cur_u_ = 0, cur_id_ = 0;
+    int steps_since_sort_ = 0;
+    int64_t host_step_ = 0;
+    bool have_pos_ = false, have_vel_ = false;
+    // staging
+    void* aux_ = nullptr;
+    size_t aux_bytes_ = 0;
+    void* stage_ = nullptr;
+    size_t stage_bytes_ = 0;
+    // graph cache
+    cudaGraphExec_t graph_ = nullptr;
+    int graph_key_ = -1;
+
+    unsigned int* done_ptr() const { return reinterpret_cast<unsigned int*>(counters_ + 1); }
+    unsigned int* err_ptr() const { return reinterpret_cast<unsigned int*>(counters_ + 1) + 1; }
+
+    static unsigned blocks(size_t count) { return (unsigned)((count + 255) / 256); }
+    static size_t dtype_size(int dtype) { return dtype == TILD_DTYPE_F32 ? 4 : 8; }
+
+    size_t plane_smem() const { return ((size_t)n_ + (size_t)n_ * row_pitch(n_)) * sizeof(V); }
+    size_t rows_smem() const { return ((size_t)n_ + (size_t)16 * row_pitch(n_)) * sizeof(V); }
+    size_t ycol_smem() const { return ((size_t)n_ + (size_t)n_ * C_) * sizeof(V); }
+    size_t zpass_smem() const { return ((size_t)n_ + 3 * (size_t)n_ * C_) * sizeof(V); }
+    int patch_width() const {
+        const int lo = (P_ % 2 == 0) ? -(P_ / 2 - 1) : -((P_ - 1) / 2);
+        const int hi = (P_ % 2 == 0) ? (P_ / 2) : ((P_ - 1) / 2 + 1);
+        return kTile + hi - lo + 2 * kMargin;
+    }
+    size_t bead_smem() const {
+        const size_t W = patch_width();
+        return 2 * W * W * W * sizeof(unsigned long long);
+    }
+    static constexpr int kMargin = 1;
+
+    void free_beads() {
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(pos_[k]);
+            cudaFree(u_[k]);
+            cudaFree(id_[k]);
+            pos_[k] = u_[k] = nullptr;
+            id_[k] = nullptr;
+        }
+        cudaFree(nbr_);
+        cudaFree(slot_of_id_);
+        cudaFree(keys_);
+        cudaFree(vsave_);
+        vsave_ = nullptr;
+        nbr_ = nullptr;
+        slot_of_id_ = keys_ = nullptr;
+    }
+
+    void release() {
+        invalidate_graph();
+        free_beads();
+        void* ptrs[] = {rho_fx_, Zxy_, H_, grad_, tw_, spec_, counters_, partials_, counts_,
+                        cell_start_, cursor_, block_sums_, aux_, stage_};
+        for (void* p : ptrs) cudaFree(p);
+        rho_fx_ = nullptr;
+        if (own_stream_) cudaStreamDestroy(own_stream_);
+        own_stream_ = nullptr;
+    }
+
+    void invalidate_graph() {
+        if (graph_) cudaGraphExecDestroy(graph_);
+        graph_ = nullptr;
+        graph_key_ = -1;
+    }
+
+    tild_status check_err() {
+        unsigned int h = 0;
+        TILD_CUDA(cudaMemcpy(&h, err_ptr(), sizeof(h), cudaMemcpyDeviceToHost));
+        if (h & kErrNonFinite) {
+            TILD_CUDA(cudaMemset(err_ptr(), 0, sizeof(unsigned int)));
+            err = "non-finite force detected on the device";
+            return TILD_ENAN;
+        }
+        return TILD_OK;
+    }
+
+    tild_status ensure_aux(size_t bytes) {
+        if (aux_bytes_ >= bytes) return TILD_OK;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        cudaFree(aux_);
+        aux_ = nullptr;
+        aux_bytes_ = 0;
+        TILD_CUDA(cudaMalloc(&aux_, bytes));
+        aux_bytes_ = bytes;
+        return TILD_OK;
+    }
+
+    tild_status ensure_stage(size_t bytes) {
+        if (stage_bytes_ >= bytes) return TILD_OK;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        cudaFree(stage_);
+        stage_ = nullptr;
+        stage_bytes_ = 0;
+        TILD_CUDA(cudaMalloc(&stage_, bytes));
+        stage_bytes_ = bytes;
+        return TILD_OK;
+    }
+
+    // Host input -> device staging buffer (same dtype); device input as is.
+    tild_status stage_in(const void** dev, const void* src, size_t count, int dtype, int where) {
+        if (where == TILD_DEVICE) {
+            *dev = src;
+            return TILD_OK;
+        }
+        tild_status st;
+        if ((st = ensure_stage(count * dtype_size(dtype)))) return st;
+        TILD_CUDA(cudaMemcpyAsync(stage_, src, count * dtype_size(dtype), cudaMemcpyHostToDevice, stream_));
+        *dev = stage_;
+        return TILD_OK;
+    }
+
+    // Device array of T -> caller buffer (dtype, host or device).
+    tild_status stage_out_vec(const T* src, size_t count, void* out, int dtype, int where) {
+        tild_status st;
+        void* dst = out;
+        if (where == TILD_HOST) {
+            if ((st = ensure_stage(count * dtype_size(dtype)))) return st;
+            dst = stage_;
+        }
+        if (dtype == TILD_DTYPE_F32)
+            convert_copy<T, float><<<blocks(count), 256, 0, stream_>>>(count, src, (float*)dst);
+        else
+            convert_copy<T, double><<<blocks(count), 256, 0, stream_>>>(count, src, (double*)dst);
+        TILD_CUDA(cudaGetLastError());
+        if (where == TILD_HOST)
+            TILD_CUDA(cudaMemcpyAsync(out, dst, count * dtype_size(dtype), cudaMemcpyDeviceToHost, stream_));
+        return TILD_OK;
+    }
+
+    tild_status out_by_id(const T* src, void* out, int dtype, int where) {
+        const int N = cfg_->n_beads;
+        tild_status st;
+        void* dst = out;
+        if (where == TILD_HOST) {
+            if ((st = ensure_stage((size_t)3 * N * dtype_size(dtype)))) return st;
+            dst = stage_;
+        }
+        if (dtype == TILD_DTYPE_F32)
+            store_by_id<T, float><<<blocks(N), 256, 0, stream_>>>(N, src, id_[cur_id_], (float*)dst);
+        else
+            store_by_id<T, double><<<blocks(N), 256, 0, stream_>>>(N, src, id_[cur_id_], (double*)dst);
+        TILD_CUDA(cudaGetLastError());
+        if (where == TILD_HOST)
+            TILD_CUDA(cudaMemcpyAsync(out, dst, (size_t)3 * N * dtype_size(dtype), cudaMemcpyDeviceToHost, stream_));
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return TILD_OK;
+    }
+
+    // ---------------------------------------------------------- kernels
+
+    template <int NN> tild_status attrs_n() {
+        if (plane_fits_) {
+            TILD_CUDA(cudaFuncSetAttribute(xy_forward_plane<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+            TILD_CUDA(cudaFuncSetAttribute(xy_inverse_plane<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+        } else {
+            TILD_CUDA(cudaFuncSetAttribute(x_forward_rows<T, NN, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem()));
+            TILD_CUDA(cudaFuncSetAttribute(x_inverse_rows<T, NN, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem()));
+            TILD_CUDA(cudaFuncSetAttribute(y_columns<T, NN, 128 / sizeof(V), -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ycol_smem()));
+            TILD_CUDA(cudaFuncSetAttribute(y_columns<T, NN, 128 / sizeof(V), +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ycol_smem()));
+        }
+        constexpr int CC = NN < (int)(128 / sizeof(V)) ? NN : (int)(128 / sizeof(V));
+        TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
+        return TILD_OK;
+    }
+
+    template <int P> tild_status attrs_p() {
+        const int s = (int)bead_smem();
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSpread, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeForce, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSetVel, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeStep, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
+        return TILD_OK;
+    }
+
+    tild_status set_kernel_attributes() {
+        tild_status st = dispatch_n([&](auto nn) { return this->template attrs_n<decltype(nn)::value>(); });
+        if (st) return st;
+        return dispatch_p([&](auto pp) { return this->template attrs_p<decltype(pp)::value>(); });
+    }
+
+    template <int V_> struct ic { static constexpr int value = V_; };
+
+    template <class F> tild_status dispatch_n(F&& f) {
+        switch (n_) {
+            case 8: return f(ic<8>{});
+            case 16: return f(ic<16>{});
+            case 32: return f(ic<32>{});
+            case 64: return f(ic<64>{});
+            case 128: return f(ic<128>{});
+            case 256: return dispatch_256(f);
+        }
+        err = "unsupported grid size";
+        return TILD_EUNSUPPORTED;
+    }
+    template <class F> tild_status dispatch_256(F&& f) {
+        if constexpr (sizeof(T) == 4) return f(ic<256>{});
+        err = "FP64 grids are limited to 128^3";
+        return TILD_EUNSUPPORTED;
+    }
+    template <class F> tild_status dispatch_p(F&& f) {
+        switch (P_) {
+            case 2: return f(ic<2>{});
+            case 3: return f(ic<3>{});
+            case 4: return f(ic<4>{});
+            case 5: return f(ic<5>{});
+        }
+        err = "unsupported pmeorder";
+        return TILD_EUNSUPPORTED;
+    }
+
+    T density_scale() const {
+        const double dV = cfg_->L * cfg_->L * cfg_->L / (double)M_;
+        return (T)(kFixInv / dV);
+    }
+
+    template <int NN> tild_status forward_n(bool zero_after) {
+        if (plane_fits_) {
+            if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
+                xy_forward_plane<T, NN><<<NN, 512, plane_smem(), stream_>>>(rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0);
+            }
+        } else {
+            constexpr int CC = 128 / sizeof(V);
+            if constexpr (NN >= 16 && NN >= CC) {
+                x_forward_rows<T, NN, 16><<<(unsigned)((size_t)NN * NN / 16), 256, rows_smem(), stream_>>>(
+                    rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0);
+                y_columns<T, NN, CC, -1><<<dim3(NN / CC, NN, 1), 256, ycol_smem(), stream_>>>(Zxy_, tw_);
+            }
+        }
+        TILD_CUDA(cudaGetLastError());
+        return TILD_OK;
+    }
+    tild_status enqueue_forward(bool zero_after) {
+        return dispatch_n([&](auto nn) { return this->template forward_n<decltype(nn)::value>(zero_after); });
+    }
+
+    SpectralParams<T> spectral_params() const {
+        const double V = cfg_->L * cfg_->L * cfg_->L;
+        const double rho0 = cfg_->n_beads / V;
+        SpectralParams<T> sp;
+        sp.two_pi_over_L = (T)(2.0 * 3.14159265358979323846 / cfg_->L);
+        sp.a2 = (T)(cfg_->a * cfg_->a);
+        sp.eAA = (T)(cfg_->kappa / rho0 / (double)M_);
+        sp.eBB = sp.eAA;
+        sp.eAB = (T)((cfg_->chi + cfg_->kappa) / rho0 / (double)M_);
+        return sp;
+    }
+
+    template <int NN> tild_status zpass_n(double* partials, V* spec_out) {
+        constexpr int CC = NN < (int)(128 / sizeof(V)) ? NN : (int)(128 / sizeof(V));
+        z_spectral<T, NN, CC><<<dim3(NN / CC, NN), 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, spectral_params(), partials, spec_out);
+        TILD_CUDA(cudaGetLastError());
+        return TILD_OK;
+    }
+    tild_status enqueue_zpass(double* partials, V* spec_out) {
+        return dispatch_n([&](auto nn) { return this->template zpass_n<decltype(nn)::value>(partials, spec_out); });
+    }
+
+    template <int NN> tild_status inverse_n() {
+        if (plane_fits_) {
+            if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
+                xy_inverse_plane<T, NN><<<dim3(NN, 3), 512, plane_smem(), stream_>>>(H_, grad_, tw_);
+            }
+        } else {
+            constexpr int CC = 128 / sizeof(V);
+            if constexpr (NN >= 16 && NN >= CC) {
+                y_columns<T, NN, CC, +1><<<dim3(NN / CC, NN, 3), 256, ycol_smem(), stream_>>>(H_, tw_);
+                x_inverse_rows<T, NN, 16><<<dim3((unsigned)((size_t)NN * NN / 16), 3), 256, rows_smem(), stream_>>>(H_, grad_, tw_);
+            }
+        }
+        TILD_CUDA(cudaGetLastError());
+        return TILD_OK;
+    }
+    tild_status enqueue_inverse() {
+        return dispatch_n([&](auto nn) { return this->template inverse_n<decltype(nn)::value>(); });
+    }
+
+    tild_status enqueue_fields(bool energy, double* partials, V* spec_out) {
+        tild_status st;
+        if (!have_pos_) {
+            err = "positions have not been set";
+            return TILD_ESTATE;
+        }
+        if ((st = enqueue_forward(false))) return st;
+        if ((st = enqueue_zpass(energy ? partials : nullptr, spec_out))) return st;
+        return enqueue_inverse();
+    }
+
+    BeadParams<T> bead_params() const {
+        BeadParams<T> p;
+        const HostConfig& c = *cfg_;
+        p.n_beads = c.n_beads;
+        p.n = n_;
+        p.tiles = tiles_;
+        p.margin = kMargin;
+        p.L = (T)c.L;
+        p.inv_L = (T)(1.0 / c.L);
+        p.inv_dx = (T)((double)n_ / c.L);
+        p.k_bond = (T)(3.0 / (c.b * c.b));
+        const double hdm = c.dt / (2.0 * c.mass);
+        const double den = 1.0 + c.friction * c.dt / (2.0 * c.mass);
+        const double ga = (1.0 - c.friction * c.dt / (2.0 * c.mass)) / den;
+        const double gb = 1.0 / den;
+        p.hdm = (T)hdm;
+        p.gb_dt = (T)(gb * c.dt);
+        p.inv_2m = (T)(1.0 / (2.0 * c.mass));
+        p.ga = (T)ga;
+        p.gb_m = (T)(gb / c.mass);
+        p.sigma_beta = (T)std::sqrt(2.0 * c.friction * c.kT * c.dt);
+        p.sigma_v = (T)std::sqrt(c.kT / c.mass);
+        p.mass = (T)c.mass;
+        p.seed = c.seed;
+        p.topo = c.topo;
+        return p;
+    }
+
+    BeadBuffers<T> bead_buffers() const {
+        BeadBuffers<T> b;
+        const size_t N = cfg_->n_beads;
+        b.px = pos_[cur_pos_];
+        b.py = b.px + N;
+        b.pz = b.py + N;
+        b.qx = b.qy = b.qz = nullptr;
+        b.ux = u_[cur_u_];
+        b.uy = b.ux + N;
+        b.uz = b.uy + N;
+        b.id = id_[cur_id_];
+        b.nbr = nbr_;
+        b.cell_start = cell_start_;
+        b.grad = grad_;
+        b.rho_fx = rho_fx_;
+        b.step = counters_;
+        b.done = done_ptr();
+        b.err = err_ptr();
+        b.f_out = nullptr;
+        b.v_out = nullptr;
+        b.v_in = nullptr;
+        b.partials = partials_;
+        return b;
+    }
+
+    template <int P> tild_status bead_p(int mode, const BeadBuffers<T>& bf) {
+        const unsigned grid = (unsigned)tiles_ * tiles_ * tiles_;
+        const size_t sm = bead_smem();
+        const BeadParams<T> p = bead_params();
+        switch (mode) {
+            case kModeSpread: bead_kernel<P, kModeSpread, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+            case kModeForce: bead_kernel<P, kModeForce, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+            case kModeSetVel: bead_kernel<P, kModeSetVel, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+            default: bead_kernel<P, kModeStep, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+        }
+        TILD_CUDA(cudaGetLastError());
+        return TILD_OK;
+    }
+    tild_status launch_bead(int mode, const BeadBuffers<T>& bf) {
+        return dispatch_p([&](auto pp) { return this->template bead_p<decltype(pp)::value>(mode, bf); });
+    }
+
+    tild_status respread() {
+        TILD_CUDA(cudaMemsetAsync(rho_fx_, 0, 2 * M_ * sizeof(unsigned long long), stream_));
+        return launch_bead(kModeSpread, bead_buffers());
+    }
+
+    tild_status enqueue_step() {
+        tild_status st;
+        if ((st = enqueue_forward(true))) return st;
+        if ((st = enqueue_zpass(nullptr, nullptr))) return st;
+        if ((st = enqueue_inverse())) return st;
+        BeadBuffers<T> bf = bead_buffers();
+        bf.qx = pos_[1 - cur_pos_];
+        bf.qy = bf.qx + cfg_->n_beads;
+        bf.qz = bf.qy + cfg_->n_beads;
+        if ((st = launch_bead(kModeStep, bf))) return st;
+        cur_pos_ = 1 - cur_pos_;
+        ++steps_since_sort_;
+        return TILD_OK;
+    }
+
+    tild_status enqueue_sort() {
+        const int N = cfg_->n_beads;
+        const size_t N3 = N;
+        TILD_CUDA(cudaMemsetAsync(counts_, 0, (M_ + 1) * sizeof(int), stream_));
+        TILD_CUDA(cudaMemsetAsync(cursor_, 0, (M_ + 1) * sizeof(int), stream_));
+        const T* p = pos_[cur_pos_];
+        bin_count<T><<<blocks(N), 256, 0, stream_>>>(N, p, p + N3, p + 2 * N3, (T)((double)n_ / cfg_->L), n_, tiles_, keys_, counts_);
+        scan_blocks<<<scan_blocks_, 1024, 0, stream_>>>(counts_, cell_start_, block_sums_, (int)(M_ + 1));
+        scan_top<<<1, 1024, 0, stream_>>>(block_sums_, scan_blocks_);
+        scan_add<<<scan_blocks_, 1024, 0, stream_>>>(cell_start_, block_sums_, (int)(M_ + 1));
+        bin_scatter_pos<T><<<blocks(N), 256, 0, stream_>>>(N, keys_, cell_start_, cursor_, pos_[cur_pos_],
+                                                           pos_[1 - cur_pos_], id_[cur_id_], id_[1 - cur_id_], slot_of_id_);
+        bin_move_u<T><<<blocks(N), 256, 0, stream_>>>(N, id_[cur_id_], slot_of_id_, u_[cur_u_], u_[1 - cur_u_]);
+        bin_neighbours<<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, id_[1 - cur_id_], slot_of_id_, nbr_);
+        TILD_CUDA(cudaGetLastError());
+        cur_pos_ = 1 - cur_pos_;
+        cur_u_ = 1 - cur_u_;
+        cur_id_ = 1 - cur_id_;
+        steps_since_sort_ = 0;
+        return TILD_OK;
+    }
+
+    tild_status run_cycle_graph() {
+        const int key = cur_pos_ | (cur_u_ << 1) | (cur_id_ << 2);
+        tild_status st;
+        if (!graph_ || graph_key_ != key) {
+            invalidate_graph();
+            const int sp = cur_pos_, su = cur_u_, si = cur_id_, ss = steps_since_sort_;
+            cudaGraph_t g;
+            TILD_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+            for (int half = 0; half < 2; ++half) {
+                st = enqueue_sort();
+                for (int s = 0; !st && s < cfg_->sort_every; ++s) st = enqueue_step();
+                if (st) break;
+            }
+            cudaError_t e = cudaStreamEndCapture(stream_, &g);
+            if (st) return st;
+            TILD_CUDA(e);
+            e = cudaGraphInstantiate(&graph_, g, 0);
+            cudaGraphDestroy(g);
+            TILD_CUDA(e);
+            graph_key_ = key;
+            // capture only recorded the launches; restore the host-side state
+            cur_pos_ = sp;
+            cur_u_ = su;
+            cur_id_ = si;
+            steps_since_sort_ = ss;
+        }
+        TILD_CUDA(cudaGraphLaunch(graph_, stream_));
+        // two sorts and 2K steps flip every double buffer an even number of
+        // times, so the parities are those the graph was captured with
+        steps_since_sort_ = cfg_->sort_every;
+        return TILD_OK;
+    }
+};
+
+}  // namespace tild

@@ -1,0 +1,66 @@
+// Interface between the C ABI layer and the per-precision engines.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/tild.h"
+#include "common.cuh"
+
+namespace tild {
+
+// Everything the ABI layer validates and the engines read.
+struct HostConfig {
+    double L;
+    int n;
+    int pmeorder;
+    int precision;
+    uint64_t seed;
+    int sort_every;
+    // chains
+    Topology topo;
+    int n_beads = 0;
+    double b = 1.0;
+    // interactions
+    double chi = 0.0, kappa = 0.0, a = 0.5;
+    bool have_interactions = false;
+    // integrator
+    double dt = 0.005, friction = 1.0, kT = 1.0, mass = 1.0;
+};
+
+class EngineBase {
+   public:
+    virtual ~EngineBase() {}
+    std::string err;
+    virtual tild_status init(HostConfig* cfg) = 0;
+    virtual tild_status set_chains() = 0;
+    virtual tild_status set_stream(cudaStream_t s) = 0;
+    virtual cudaStream_t stream() const = 0;
+    virtual tild_status set_positions(const void* xyz, int dtype, int where) = 0;
+    virtual tild_status set_velocities(const void* v, int dtype, int where) = 0;  // v == NULL: Maxwell-Boltzmann
+    virtual tild_status step(int64_t n) = 0;
+    virtual tild_status synchronize() = 0;
+    virtual tild_status compute(unsigned what, tild_energy* e, void* f, int dtype, int where) = 0;
+    virtual tild_status get_positions(void* out, int dtype, int where) = 0;
+    virtual tild_status get_velocities(void* out, int dtype, int where) = 0;
+    virtual tild_status get_density(void* out, int dtype, int where) = 0;
+    virtual tild_status get_spectrum(void* out, int dtype, int where) = 0;
+    virtual tild_status get_field_gradient(void* out, int dtype, int where) = 0;
+    virtual int64_t host_step() const = 0;
+    virtual size_t state_bytes() const = 0;
+    virtual tild_status get_state(void* blob) = 0;
+    virtual tild_status set_state(const void* blob) = 0;
+    virtual tild_status profile(int n, double* ms) = 0;
+    virtual int64_t launches(int64_t n) const = 0;
+    virtual bool has_positions() const = 0;
+    virtual bool has_velocities() const = 0;
+    // Parameter changes: keep v^n while F^n changes (u = v - dt/2m F).
+    virtual tild_status save_velocities() = 0;
+    virtual tild_status restore_velocities() = 0;
+    virtual void params_changed() = 0;
+};
+
+EngineBase* make_engine_f32();
+EngineBase* make_engine_f64();
+
+}  // namespace tild

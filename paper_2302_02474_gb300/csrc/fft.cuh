@@ -1,0 +1,167 @@
+// Hand-written FFT building blocks for power-of-two lengths 8..256.
+//
+// A length-N transform is split N = N1 * N2 (four-step / Cooley-Tukey):
+//   input index  j = j2 + N2 * j1,  output index k = k1 + N1 * k2,
+//   X[k1 + N1 k2] = sum_j2 W_N^{j2 k1} W_N2^{j2 k2} sum_j1 x[j2 + N2 j1] W_N1^{j1 k1}.
+// Stage A does the N1-point DFTs over j1 in registers and applies the
+// twiddle W_N^{j2 k1}; stage B does the N2-point DFTs over j2 in registers
+// and writes the result in natural order. Lines live in shared memory; the
+// thread-to-data mapping puts consecutive threads on consecutive lines so
+// that every shared-memory access of a warp touches consecutive lines at
+// the same offset (conflict-free when the line stride is odd in 8-byte
+// words, or 1).
+//
+// Sign convention: forward (DIR = -1) uses exp(-2 pi i jk/N), inverse
+// (DIR = +1) exp(+2 pi i jk/N); neither is normalised.
+#pragma once
+
+#include "common.cuh"
+
+namespace tild {
+
+// ------------------------------------------------------------- radices
+
+template <int N> struct fft_split;
+template <> struct fft_split<8> { static constexpr int N1 = 8, N2 = 1; };
+template <> struct fft_split<16> { static constexpr int N1 = 4, N2 = 4; };
+template <> struct fft_split<32> { static constexpr int N1 = 8, N2 = 4; };
+template <> struct fft_split<64> { static constexpr int N1 = 8, N2 = 8; };
+template <> struct fft_split<128> { static constexpr int N1 = 16, N2 = 8; };
+template <> struct fft_split<256> { static constexpr int N1 = 16, N2 = 16; };
+
+// Multiply v by W_16^m = exp(DIR * 2 pi i m / 16); m is a compile-time
+// constant after unrolling, so the branches fold away.
+template <int DIR, class V> __device__ __forceinline__ V w16_mul(int m, V v) {
+    using T = decltype(v.x);
+    const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173);  // cos, sin(pi/8)
+    const T h = T(0.70710678118654752440);                                    // cos(pi/4)
+    m &= 15;
+    // value of exp(-2 pi i m / 16) = (cr, ci); inverse uses the conjugate
+    T cr, ci;
+    switch (m) {
+        case 0: return v;
+        case 4: return DIR < 0 ? c_mul_negi(v) : c_mul_posi(v);
+        case 8: return {-v.x, -v.y};
+        case 12: return DIR < 0 ? c_mul_posi(v) : c_mul_negi(v);
+        case 1: cr = c1; ci = -s1; break;
+        case 2: cr = h; ci = -h; break;
+        case 3: cr = s1; ci = -c1; break;
+        case 5: cr = -s1; ci = -c1; break;
+        case 6: cr = -h; ci = -h; break;
+        case 7: cr = -c1; ci = -s1; break;
+        case 9: cr = -c1; ci = s1; break;
+        case 10: cr = -h; ci = h; break;
+        case 11: cr = -s1; ci = c1; break;
+        case 13: cr = s1; ci = c1; break;
+        case 14: cr = h; ci = h; break;
+        default: cr = c1; ci = s1; break;  // 15
+    }
+    if (DIR > 0) ci = -ci;
+    return {v.x * cr - v.y * ci, v.x * ci + v.y * cr};
+}
+
+// In-register DFT of R points (R = 1, 2, 4, 8, 16), natural order in and
+// out, radix-2 decimation in time.
+template <int R, int DIR, class V> struct reg_dft {
+    static __device__ __forceinline__ void run(V (&v)[R]) {
+        V e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        reg_dft<R / 2, DIR, V>::run(e);
+        reg_dft<R / 2, DIR, V>::run(o);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            const V t = w16_mul<DIR>(k * (16 / R), o[k]);
+            v[k] = c_add(e[k], t);
+            v[k + R / 2] = c_sub(e[k], t);
+        }
+    }
+};
+template <int DIR, class V> struct reg_dft<1, DIR, V> {
+    static __device__ __forceinline__ void run(V (&)[1]) {}
+};
+
+// Twiddle table W_N^m = exp(-2 pi i m / N), m in [0, N), computed on the
+// host in FP64 and rounded to T; copied to shared memory by each CTA.
+template <int DIR, class V> __device__ __forceinline__ V twiddle(const V* tw, int m) {
+    const V w = tw[m];
+    return DIR < 0 ? w : c_conj(w);
+}
+
+// ----------------------------------------------------- line transforms
+
+// FFT of `nlines` lines of length N held in shared memory. Element e of
+// line l lives at buf[addr(l) + e * es]. All threads of the CTA call this;
+// it ends with __syncthreads(). UPT bounds the stage-B work units a thread
+// keeps in registers (nlines * N1 <= UPT * blockDim is processed in one
+// round; more lines are processed in several rounds).
+template <int N, int DIR, int UPT, class V, class Addr>
+__device__ __forceinline__ void smem_fft_lines(V* buf, Addr addr, int es, int nlines, const V* tw) {
+    constexpr int N1 = fft_split<N>::N1;
+    constexpr int N2 = fft_split<N>::N2;
+    const int nthr = blockDim.x;
+    const int tid = threadIdx.x;
+
+    // Stage A: unit (line, j2); reads and writes only its own positions.
+    for (int u = tid; u < nlines * N2; u += nthr) {
+        const int l = u % nlines;
+        const int j2 = u / nlines;
+        V* p = buf + addr(l) + j2 * es;
+        V v[N1];
+#pragma unroll
+        for (int j1 = 0; j1 < N1; ++j1) v[j1] = p[j1 * N2 * es];
+        reg_dft<N1, DIR, V>::run(v);
+        if (N2 > 1) {
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mul(v[k1], twiddle<DIR>(tw, j2 * k1));
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) p[k1 * N2 * es] = v[k1];
+    }
+    __syncthreads();
+    if (N2 == 1) return;
+
+    // Stage B: unit (line, k1) reads the N2 positions j2 + N2 k1 and writes
+    // X[k1 + N1 k2]; positions overlap other units, so every unit of a
+    // round is loaded before any is stored.
+    const int lines_per_round = max(1, (UPT * nthr) / N1);
+    for (int l0 = 0; l0 < nlines; l0 += lines_per_round) {
+        const int nl = min(lines_per_round, nlines - l0);
+        V v[UPT][N2];
+#pragma unroll
+        for (int r = 0; r < UPT; ++r) {
+            const int u = tid + r * nthr;
+            if (u < nl * N1) {
+                const int l = l0 + u % nl;
+                const int k1 = u / nl;
+                const V* p = buf + addr(l) + k1 * N2 * es;
+#pragma unroll
+                for (int j2 = 0; j2 < N2; ++j2) v[r][j2] = p[j2 * es];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < UPT; ++r) {
+            const int u = tid + r * nthr;
+            if (u < nl * N1) {
+                const int l = l0 + u % nl;
+                const int k1 = u / nl;
+                reg_dft<N2, DIR, V>::run(v[r]);
+                V* p = buf + addr(l) + k1 * es;
+#pragma unroll
+                for (int k2 = 0; k2 < N2; ++k2) p[k2 * N1 * es] = v[r][k2];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+struct StridedLines {
+    int ls;
+    __device__ __forceinline__ int operator()(int l) const { return l * ls; }
+};
+
+}  // namespace tild
