@@ -208,6 +208,8 @@ def main():
     ap.add_argument("--cpu-baseline-steps", type=int, default=3)
     ap.add_argument("--reference-budget", type=float, default=150.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "run"],
+                    help="run: set up, warm up and take --steps steps only (for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -241,6 +243,11 @@ def main():
     t.init_velocities()
     t.step(args.warmup)
     t.synchronize()
+    if args.mode == "run":
+        t.step(args.steps)
+        t.synchronize()
+        t.close()
+        return
 
     # per-kernel device times (CUDA events around each launch, same stream)
     prof_steps = max(2 * args.sort_every, 40)
