@@ -33,7 +33,6 @@ template <typename T> struct BeadParams {
     int n_beads;
     int n;            // grid points per edge (power of two)
     int tiles;        // tiles per edge
-    int margin;       // drift margin (cells) of the shared patch
     T L, inv_L, inv_dx;
     T k_bond;         // 3 / b^2
     // GJF constants
@@ -80,34 +79,78 @@ template <typename T> __device__ __forceinline__ T wrap_coord(T x, T L, T inv_L)
 
 template <typename T> __device__ __forceinline__ T min_image(T d, T L, T inv_L) { return d - L * rint(d * inv_L); }
 
-template <int P, typename T>
-__device__ __forceinline__ void gather_force(const BeadParams<T>& p, const cplx_t<T>* __restrict__ grad, T x, T y,
-                                             T z, int species, T& fx, T& fy, T& fz) {
+// Bead slots carry the bead id in bits 0..30 and the species in bit 31.
+__host__ __device__ __forceinline__ int slot_bead_id(int v) { return v & 0x7fffffff; }
+__host__ __device__ __forceinline__ int slot_species(int v) { return (int)((unsigned)v >> 31); }
+
+// Shared-memory patch of one tile: grid points [org, org + W) per dimension
+// with W = 8 cells + stencil reach + a drift margin of kMargin cells on
+// each side, so beads that moved up to kMargin cells since the last
+// re-binning still find their whole stencil inside.
+constexpr int kMargin = 1;
+template <int P> struct Patch {
+    static constexpr int W = kTile + stencil_extent<P>::hi - stencil_extent<P>::lo + 2 * kMargin;
+    static constexpr int W3 = W * W * W;
+    static constexpr int lo = stencil_extent<P>::lo - kMargin;  // org = tile origin + lo
+};
+
+template <int P, typename T> struct Stencil {
     T wx[P], wy[P], wz[P];
     int jx, jy, jz;
-    dh_weights<P>(x * p.inv_dx, jx, wx);
-    dh_weights<P>(y * p.inv_dx, jy, wy);
-    dh_weights<P>(z * p.inv_dx, jz, wz);
-    const int nm = p.n - 1;
-    const size_t M = (size_t)p.n * p.n * p.n;
+    __device__ __forceinline__ void set(T x, T y, T z, T inv_dx) {
+        dh_weights<P>(x * inv_dx, jx, wx);
+        dh_weights<P>(y * inv_dx, jy, wy);
+        dh_weights<P>(z * inv_dx, jz, wz);
+    }
+};
+
+// -grad w_K interpolated at a bead, from the staged patch (in_patch) or
+// from global memory.
+template <int P, typename T>
+__device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_patch, int3 l, const cplx_t<T>* s_grad,
+                                             const cplx_t<T>* __restrict__ grad, int n, int species, T& fx, T& fy,
+                                             T& fz) {
+    using PT = Patch<P>;
     T gx = 0, gy = 0, gz = 0;
+    if (in_patch) {
 #pragma unroll
-    for (int c = 0; c < P; ++c) {
-        const size_t oz = (size_t)((jz + c) & nm) * p.n * p.n;
+        for (int c = 0; c < P; ++c)
 #pragma unroll
-        for (int b = 0; b < P; ++b) {
-            const size_t oy = oz + (size_t)((jy + b) & nm) * p.n;
-            const T wyz = wy[b] * wz[c];
+            for (int b = 0; b < P; ++b) {
+                const T wyz = st.wy[b] * st.wz[c];
+                const int row = ((l.z + c) * PT::W + (l.y + b)) * PT::W + l.x;
 #pragma unroll
-            for (int a = 0; a < P; ++a) {
-                const size_t g = oy + ((jx + a) & nm);
-                const T w = wx[a] * wyz;
-                const cplx_t<T> vx = __ldg(grad + g);
-                const cplx_t<T> vy = __ldg(grad + M + g);
-                const cplx_t<T> vz = __ldg(grad + 2 * M + g);
-                gx += w * (species ? vx.y : vx.x);
-                gy += w * (species ? vy.y : vy.x);
-                gz += w * (species ? vz.y : vz.x);
+                for (int a = 0; a < P; ++a) {
+                    const T w = st.wx[a] * wyz;
+                    const cplx_t<T> vx = s_grad[row + a];
+                    const cplx_t<T> vy = s_grad[PT::W3 + row + a];
+                    const cplx_t<T> vz = s_grad[2 * PT::W3 + row + a];
+                    gx += w * (species ? vx.y : vx.x);
+                    gy += w * (species ? vy.y : vy.x);
+                    gz += w * (species ? vz.y : vz.x);
+                }
+            }
+    } else {
+        const int nm = n - 1;
+        const size_t M = (size_t)n * n * n;
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+            const size_t oz = (size_t)((st.jz + c) & nm) * n * n;
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const size_t oy = oz + (size_t)((st.jy + b) & nm) * n;
+                const T wyz = st.wy[b] * st.wz[c];
+#pragma unroll
+                for (int a = 0; a < P; ++a) {
+                    const size_t g = oy + ((st.jx + a) & nm);
+                    const T w = st.wx[a] * wyz;
+                    const cplx_t<T> vx = __ldg(grad + g);
+                    const cplx_t<T> vy = __ldg(grad + M + g);
+                    const cplx_t<T> vz = __ldg(grad + 2 * M + g);
+                    gx += w * (species ? vx.y : vx.x);
+                    gy += w * (species ? vy.y : vy.x);
+                    gz += w * (species ? vz.y : vz.x);
+                }
             }
         }
     }
@@ -116,66 +159,78 @@ __device__ __forceinline__ void gather_force(const BeadParams<T>& p, const cplx_
     fz = -gz;
 }
 
-// Spread one bead (species K) at (x, y, z). The patch covers grid points
-// [org, org + W) per dimension; contributions outside it go straight to
-// global memory.
+// Spread one bead of species K into the fixed-point patch (in_patch) or
+// straight into the global grid.
 template <int P, typename T>
-__device__ __forceinline__ void spread_bead(const BeadParams<T>& p, unsigned long long* patch, int W, int3 org,
-                                            unsigned long long* __restrict__ rho_fx, T x, T y, T z, int K) {
-    T wx[P], wy[P], wz[P];
-    int jx, jy, jz;
-    dh_weights<P>(x * p.inv_dx, jx, wx);
-    dh_weights<P>(y * p.inv_dx, jy, wy);
-    dh_weights<P>(z * p.inv_dx, jz, wz);
-    const int lx = jx - org.x, ly = jy - org.y, lz = jz - org.z;
-    const bool inside = lx >= 0 && ly >= 0 && lz >= 0 && lx + P <= W && ly + P <= W && lz + P <= W;
-    if (inside) {
-        unsigned long long* base = patch + (size_t)K * W * W * W;
+__device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_patch, int3 l, unsigned long long* patch,
+                                            unsigned long long* __restrict__ rho_fx, int n, int K) {
+    using PT = Patch<P>;
+    if (in_patch) {
+        unsigned long long* base = patch + K * PT::W3;
 #pragma unroll
         for (int c = 0; c < P; ++c)
 #pragma unroll
             for (int b = 0; b < P; ++b) {
-                const T wyz = wy[b] * wz[c];
+                const T wyz = st.wy[b] * st.wz[c];
+                const int row = ((l.z + c) * PT::W + (l.y + b)) * PT::W + l.x;
 #pragma unroll
-                for (int a = 0; a < P; ++a) {
-                    const long long v = to_fixed(wx[a] * wyz);
-                    atomicAdd(base + ((lz + c) * W + (ly + b)) * W + (lx + a), (unsigned long long)v);
-                }
+                for (int a = 0; a < P; ++a) atomicAdd(base + row + a, (unsigned long long)to_fixed(st.wx[a] * wyz));
             }
     } else {
-        const int nm = p.n - 1;
-        const size_t M = (size_t)p.n * p.n * p.n;
+        const int nm = n - 1;
+        const size_t M = (size_t)n * n * n;
 #pragma unroll
         for (int c = 0; c < P; ++c)
 #pragma unroll
             for (int b = 0; b < P; ++b) {
-                const T wyz = wy[b] * wz[c];
+                const T wyz = st.wy[b] * st.wz[c];
 #pragma unroll
                 for (int a = 0; a < P; ++a) {
-                    const long long v = to_fixed(wx[a] * wyz);
-                    const size_t g = ((size_t)((jz + c) & nm) * p.n + ((jy + b) & nm)) * p.n + ((jx + a) & nm);
-                    atomicAdd(rho_fx + K * M + g, (unsigned long long)v);
+                    const size_t g = ((size_t)((st.jz + c) & nm) * n + ((st.jy + b) & nm)) * n + ((st.jx + a) & nm);
+                    atomicAdd(rho_fx + K * M + g, (unsigned long long)to_fixed(st.wx[a] * wyz));
                 }
             }
     }
 }
 
+template <int P, typename T> __device__ __forceinline__ bool patch_local(const Stencil<P, T>& st, int3 org, int3& l) {
+    using PT = Patch<P>;
+    l = make_int3(st.jx - org.x, st.jy - org.y, st.jz - org.z);
+    return (unsigned)l.x <= (unsigned)(PT::W - P) && (unsigned)l.y <= (unsigned)(PT::W - P) &&
+           (unsigned)l.z <= (unsigned)(PT::W - P);
+}
+
+template <int P, typename T> constexpr size_t bead_smem_bytes(bool with_grad) {
+    return 2 * Patch<P>::W3 * sizeof(unsigned long long) + (with_grad ? 3 * Patch<P>::W3 * sizeof(cplx_t<T>) : 0);
+}
+
 template <int P, int MODE, typename T>
 __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long* patch = reinterpret_cast<unsigned long long*>(smem_raw);
+    using PT = Patch<P>;
+    using V = cplx_t<T>;
     constexpr bool kSpread = (MODE == kModeSpread || MODE == kModeStep);
     constexpr bool kForce = (MODE != kModeSpread);
-    using SE = stencil_extent<P>;
-    const int W = kTile + SE::hi - SE::lo + 2 * p.margin;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long* patch = reinterpret_cast<unsigned long long*>(smem_raw);
+    V* s_grad = reinterpret_cast<V*>(smem_raw + 2 * PT::W3 * sizeof(unsigned long long));
     const int t = blockIdx.x;
     const int tx = t % p.tiles, ty = (t / p.tiles) % p.tiles, tz = t / (p.tiles * p.tiles);
-    const int3 org = {tx * kTile + SE::lo - p.margin, ty * kTile + SE::lo - p.margin, tz * kTile + SE::lo - p.margin};
-    const int W3 = W * W * W;
+    const int3 org = {tx * kTile + PT::lo, ty * kTile + PT::lo, tz * kTile + PT::lo};
+    const int nm = p.n - 1;
     if (kSpread) {
-        for (int i = threadIdx.x; i < 2 * W3; i += blockDim.x) patch[i] = 0ull;
-        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * PT::W3; i += blockDim.x) patch[i] = 0ull;
     }
+    if (kForce) {
+        // stage the gradient fields of the patch (rows of W points along x)
+        const size_t M = (size_t)p.n * p.n * p.n;
+        for (int i = threadIdx.x; i < 3 * PT::W3; i += blockDim.x) {
+            const int d = i / PT::W3, r = i - d * PT::W3;
+            const int lx = r % PT::W, ly = (r / PT::W) % PT::W, lz = r / (PT::W * PT::W);
+            const size_t g = ((size_t)((org.z + lz) & nm) * p.n + ((org.y + ly) & nm)) * p.n + ((org.x + lx) & nm);
+            s_grad[i] = __ldg(bf.grad + d * M + g);
+        }
+    }
+    __syncthreads();
     const int start = bf.cell_start[(size_t)t * kTileCells];
     const int end = bf.cell_start[(size_t)(t + 1) * kTileCells];
     const uint64_t step = (MODE == kModeStep) ? *((volatile unsigned long long*)bf.step) : 0ull;
@@ -183,11 +238,16 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
 
     for (int i = start + threadIdx.x; i < end; i += blockDim.x) {
         T x = bf.px[i], y = bf.py[i], z = bf.pz[i];
-        const int bid = bf.id[i];
-        const BeadInfo info = bead_info(p.topo, bid);
+        const int tag = bf.id[i];
+        const int bid = slot_bead_id(tag);
+        const int species = slot_species(tag);
+        Stencil<P, T> st;
+        st.set(x, y, z, p.inv_dx);
+        int3 l;
+        bool inside = patch_local(st, org, l);
         if (kForce) {
             T fx, fy, fz;
-            gather_force<P>(p, bf.grad, x, y, z, info.species, fx, fy, fz);
+            gather_force<P>(st, inside, l, s_grad, bf.grad, p.n, species, fx, fy, fz);
             const int2 nb = bf.nbr[i];
             if (nb.x >= 0) {
                 const T dx = min_image(x - bf.px[nb.x], p.L, p.inv_L);
@@ -254,20 +314,21 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
                 bf.ux[i] = p.ga * hx + p.gb_m * bx;
                 bf.uy[i] = p.ga * hy + p.gb_m * by;
                 bf.uz[i] = p.ga * hz + p.gb_m * bz;
+                st.set(x, y, z, p.inv_dx);
+                inside = patch_local(st, org, l);
             }
         }
-        if (kSpread) spread_bead<P>(p, patch, W, org, bf.rho_fx, x, y, z, info.species);
+        if (kSpread) spread_bead<P>(st, inside, l, patch, bf.rho_fx, p.n, species);
     }
 
     if (kSpread) {
         __syncthreads();
-        const int nm = p.n - 1;
         const size_t M = (size_t)p.n * p.n * p.n;
-        for (int i = threadIdx.x; i < 2 * W3; i += blockDim.x) {
+        for (int i = threadIdx.x; i < 2 * PT::W3; i += blockDim.x) {
             const unsigned long long v = patch[i];
             if (v) {
-                const int K = i / W3, r = i % W3;
-                const int lx = r % W, ly = (r / W) % W, lz = r / (W * W);
+                const int K = i / PT::W3, r = i - K * PT::W3;
+                const int lx = r % PT::W, ly = (r / PT::W) % PT::W, lz = r / (PT::W * PT::W);
                 const size_t g = ((size_t)((org.z + lz) & nm) * p.n + ((org.y + ly) & nm)) * p.n + ((org.x + lx) & nm);
                 atomicAdd(bf.rho_fx + K * M + g, v);
             }
@@ -328,7 +389,7 @@ __global__ void bin_count(int n_beads, const T* __restrict__ px, const T* __rest
 }
 
 template <typename T>
-__global__ void bin_scatter_pos(int n_beads, const int* __restrict__ keys, const int* __restrict__ cell_start,
+__global__ void bin_scatter_pos(int n_beads, Topology topo, const int* __restrict__ keys, const int* __restrict__ cell_start,
                                 int* __restrict__ cursor, const T* __restrict__ src /*[3][N]*/, T* __restrict__ dst,
                                 const int* __restrict__ id_src, int* __restrict__ id_dst, int* __restrict__ slot_of_id) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -337,8 +398,8 @@ __global__ void bin_scatter_pos(int n_beads, const int* __restrict__ keys, const
     const int s = cell_start[k] + atomicAdd(cursor + k, 1);
 #pragma unroll
     for (int c = 0; c < 3; ++c) dst[(size_t)c * n_beads + s] = src[(size_t)c * n_beads + i];
-    const int b = id_src[i];
-    id_dst[s] = b;
+    const int b = slot_bead_id(id_src[i]);
+    id_dst[s] = b | (bead_info(topo, b).species << 31);
     slot_of_id[b] = s;
 }
 
@@ -348,7 +409,7 @@ __global__ void bin_move_u(int n_beads, const int* __restrict__ id_src, const in
                            const T* __restrict__ src /*[3][N]*/, T* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_beads) return;
-    const int s = slot_of_id[id_src[i]];
+    const int s = slot_of_id[slot_bead_id(id_src[i])];
 #pragma unroll
     for (int c = 0; c < 3; ++c) dst[(size_t)c * n_beads + s] = src[(size_t)c * n_beads + i];
 }
@@ -357,7 +418,7 @@ static __global__ void bin_neighbours(int n_beads, Topology topo, const int* __r
                                int2* __restrict__ nbr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_beads) return;
-    const BeadInfo b = bead_info(topo, id[i]);
+    const BeadInfo b = bead_info(topo, slot_bead_id(id[i]));
     nbr[i] = make_int2(b.prev >= 0 ? slot_of_id[b.prev] : -1, b.next >= 0 ? slot_of_id[b.next] : -1);
 }
 
@@ -426,7 +487,7 @@ __global__ void store_by_id(int n_beads, const T* __restrict__ src /*[3][N]*/, c
                             TO* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_beads) return;
-    const int b = id[i];
+    const int b = slot_bead_id(id[i]);
 #pragma unroll
     for (int d = 0; d < 3; ++d) out[3 * (size_t)b + d] = (TO)src[(size_t)d * n_beads + i];
 }
@@ -436,7 +497,7 @@ template <typename T, typename TI>
 __global__ void load_by_id(int n_beads, const TI* __restrict__ in, const int* __restrict__ id, T* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_beads) return;
-    const int b = id[i];
+    const int b = slot_bead_id(id[i]);
 #pragma unroll
     for (int d = 0; d < 3; ++d) dst[(size_t)d * n_beads + i] = (T)in[3 * (size_t)b + d];
 }

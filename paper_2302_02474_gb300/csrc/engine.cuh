@@ -455,16 +455,14 @@ template <typename T> class Engine final : public EngineBase {
     size_t rows_smem() const { return ((size_t)n_ + (size_t)16 * row_pitch(n_)) * sizeof(V); }
     size_t ycol_smem() const { return ((size_t)n_ + (size_t)n_ * C_) * sizeof(V); }
     size_t zpass_smem() const { return ((size_t)n_ + 3 * (size_t)n_ * C_) * sizeof(V); }
-    int patch_width() const {
-        const int lo = (P_ % 2 == 0) ? -(P_ / 2 - 1) : -((P_ - 1) / 2);
-        const int hi = (P_ % 2 == 0) ? (P_ / 2) : ((P_ - 1) / 2 + 1);
-        return kTile + hi - lo + 2 * kMargin;
-    }
     size_t bead_smem() const {
-        const size_t W = patch_width();
-        return 2 * W * W * W * sizeof(unsigned long long);
+        switch (P_) {
+            case 2: return bead_smem_bytes<2, T>(true);
+            case 3: return bead_smem_bytes<3, T>(true);
+            case 4: return bead_smem_bytes<4, T>(true);
+            default: return bead_smem_bytes<5, T>(true);
+        }
     }
-    static constexpr int kMargin = 1;
 
     void free_beads() {
         for (int k = 0; k < 2; ++k) {
@@ -587,8 +585,10 @@ template <typename T> class Engine final : public EngineBase {
 
     template <int NN> tild_status attrs_n() {
         if (plane_fits_) {
-            TILD_CUDA(cudaFuncSetAttribute(xy_forward_plane<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
-            TILD_CUDA(cudaFuncSetAttribute(xy_inverse_plane<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+            if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
+                TILD_CUDA(cudaFuncSetAttribute(xy_forward_plane<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+                TILD_CUDA(cudaFuncSetAttribute(xy_inverse_plane<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+            }
         } else {
             TILD_CUDA(cudaFuncSetAttribute(x_forward_rows<T, NN, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem()));
             TILD_CUDA(cudaFuncSetAttribute(x_inverse_rows<T, NN, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem()));
@@ -728,7 +728,6 @@ template <typename T> class Engine final : public EngineBase {
         p.n_beads = c.n_beads;
         p.n = n_;
         p.tiles = tiles_;
-        p.margin = kMargin;
         p.L = (T)c.L;
         p.inv_L = (T)(1.0 / c.L);
         p.inv_dx = (T)((double)n_ / c.L);
@@ -822,7 +821,7 @@ template <typename T> class Engine final : public EngineBase {
         scan_blocks<<<scan_blocks_, 1024, 0, stream_>>>(counts_, cell_start_, block_sums_, (int)(M_ + 1));
         scan_top<<<1, 1024, 0, stream_>>>(block_sums_, scan_blocks_);
         scan_add<<<scan_blocks_, 1024, 0, stream_>>>(cell_start_, block_sums_, (int)(M_ + 1));
-        bin_scatter_pos<T><<<blocks(N), 256, 0, stream_>>>(N, keys_, cell_start_, cursor_, pos_[cur_pos_],
+        bin_scatter_pos<T><<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, keys_, cell_start_, cursor_, pos_[cur_pos_],
                                                            pos_[1 - cur_pos_], id_[cur_id_], id_[1 - cur_id_], slot_of_id_);
         bin_move_u<T><<<blocks(N), 256, 0, stream_>>>(N, id_[cur_id_], slot_of_id_, u_[cur_u_], u_[1 - cur_u_]);
         bin_neighbours<<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, id_[1 - cur_id_], slot_of_id_, nbr_);

@@ -93,16 +93,17 @@ template <int DIR, class V> __device__ __forceinline__ V twiddle(const V* tw, in
 
 // ----------------------------------------------------- line transforms
 
-// FFT of `nlines` lines of length N held in shared memory. Element e of
-// line l lives at buf[addr(l) + e * es]. All threads of the CTA call this;
-// it ends with __syncthreads(). UPT bounds the stage-B work units a thread
-// keeps in registers (nlines * N1 <= UPT * blockDim is processed in one
-// round; more lines are processed in several rounds).
-template <int N, int DIR, int UPT, class V, class Addr>
-__device__ __forceinline__ void smem_fft_lines(V* buf, Addr addr, int es, int nlines, const V* tw) {
+// FFT of NLINES lines of length N held in shared memory. Element e of
+// line l lives at buf[addr(l) + e * es]. All NTHR threads of the CTA call
+// this; it ends with __syncthreads(). Stage B keeps all of its work units
+// in registers (UPT per thread), so one round covers every line.
+template <int N, int DIR, int NLINES, int NTHR, class V, class Addr>
+__device__ __forceinline__ void smem_fft_lines(V* buf, Addr addr, int es, const V* tw) {
     constexpr int N1 = fft_split<N>::N1;
     constexpr int N2 = fft_split<N>::N2;
-    const int nthr = blockDim.x;
+    constexpr int nlines = NLINES;
+    constexpr int nthr = NTHR;
+    constexpr int UPT = (NLINES * N1 + NTHR - 1) / NTHR;
     const int tid = threadIdx.x;
 
     // Stage A: unit (line, j2); reads and writes only its own positions.
@@ -127,9 +128,9 @@ __device__ __forceinline__ void smem_fft_lines(V* buf, Addr addr, int es, int nl
     // Stage B: unit (line, k1) reads the N2 positions j2 + N2 k1 and writes
     // X[k1 + N1 k2]; positions overlap other units, so every unit of a
     // round is loaded before any is stored.
-    const int lines_per_round = max(1, (UPT * nthr) / N1);
-    for (int l0 = 0; l0 < nlines; l0 += lines_per_round) {
-        const int nl = min(lines_per_round, nlines - l0);
+    {
+        constexpr int l0 = 0;
+        constexpr int nl = NLINES;
         V v[UPT][N2];
 #pragma unroll
         for (int r = 0; r < UPT; ++r) {
@@ -159,9 +160,8 @@ __device__ __forceinline__ void smem_fft_lines(V* buf, Addr addr, int es, int nl
     }
 }
 
-struct StridedLines {
-    int ls;
-    __device__ __forceinline__ int operator()(int l) const { return l * ls; }
+template <int LS> struct StridedLines {
+    __device__ __forceinline__ int operator()(int l) const { return l * LS; }
 };
 
 }  // namespace tild

@@ -42,6 +42,45 @@ template <int N, int THREADS> __host__ __device__ constexpr int upt_for(int line
     return (lines * fft_split<N>::N1 + THREADS - 1) / THREADS;
 }
 
+// Load ROWS rows of N fixed-point densities of both species (16-byte
+// vectors), optionally zero them, and store rho_A + i rho_B to shared rows of
+// pitch PITCH. Loads are issued in batches before any store so that the
+// zeroing stores do not serialise them.
+template <int N, int PITCH, int ROWS, int NTHR, class V, typename T>
+__device__ __forceinline__ void load_fixed_rows(unsigned long long* __restrict__ ga, unsigned long long* __restrict__ gb,
+                                                V* rows, T scale, int zero_after) {
+    constexpr int PAIRS = ROWS * N / 2;
+    constexpr int ITER = (PAIRS + NTHR - 1) / NTHR;
+    constexpr int BATCH = ITER < 4 ? ITER : 4;
+    longlong2* pa = reinterpret_cast<longlong2*>(ga);
+    longlong2* pb = reinterpret_cast<longlong2*>(gb);
+#pragma unroll 1
+    for (int k0 = 0; k0 < ITER; k0 += BATCH) {
+        longlong2 a[BATCH], b[BATCH];
+#pragma unroll
+        for (int k = 0; k < BATCH; ++k) {
+            const int i = threadIdx.x + (k0 + k) * NTHR;
+            if (i < PAIRS) {
+                a[k] = __ldcs(pa + i);
+                b[k] = __ldcs(pb + i);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < BATCH; ++k) {
+            const int i = threadIdx.x + (k0 + k) * NTHR;
+            if (i < PAIRS) {
+                if (zero_after) {
+                    pa[i] = make_longlong2(0, 0);
+                    pb[i] = make_longlong2(0, 0);
+                }
+                const int r = (2 * i) / N, x = (2 * i) % N;
+                rows[r * PITCH + x] = V{from_fixed(a[k].x, scale), from_fixed(b[k].x, scale)};
+                rows[r * PITCH + x + 1] = V{from_fixed(a[k].y, scale), from_fixed(b[k].y, scale)};
+            }
+        }
+    }
+}
+
 // --------------------------------------------------------------------------
 // Forward xy pass on whole z-planes (plane fits in shared memory).
 // grid = n (one CTA per z-plane), block = 512.
@@ -53,7 +92,6 @@ __global__ void __launch_bounds__(512) xy_forward_plane(unsigned long long* __re
                                                          int zero_after) {
     using V = cplx_t<T>;
     constexpr int PITCH = row_pitch(N);
-    constexpr int UPT = upt_for<N, 512>(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* plane = tw + N;
@@ -63,21 +101,10 @@ __global__ void __launch_bounds__(512) xy_forward_plane(unsigned long long* __re
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)z * N * N;
     // load + convert: pairs of x so that global accesses are 16-byte vectors
-    for (int i = threadIdx.x; i < N * N / 2; i += blockDim.x) {
-        const int y = (2 * i) / N, x = (2 * i) % N;
-        longlong2* pa = reinterpret_cast<longlong2*>(rho_fx + base) + i;
-        longlong2* pb = reinterpret_cast<longlong2*>(rho_fx + M + base) + i;
-        const longlong2 a = *pa, b = *pb;
-        if (zero_after) {
-            *pa = make_longlong2(0, 0);
-            *pb = make_longlong2(0, 0);
-        }
-        plane[y * PITCH + x] = V{from_fixed(a.x, scale), from_fixed(b.x, scale)};
-        plane[y * PITCH + x + 1] = V{from_fixed(a.y, scale), from_fixed(b.y, scale)};
-    }
+    load_fixed_rows<N, PITCH, N, 512>(rho_fx + base, rho_fx + M + base, plane, scale, zero_after);
     __syncthreads();
-    smem_fft_lines<N, -1, UPT>(plane, StridedLines{PITCH}, 1, N, tw);  // along x
-    smem_fft_lines<N, -1, UPT>(plane, StridedLines{1}, PITCH, N, tw);  // along y
+    smem_fft_lines<N, -1, N, 512>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
+    smem_fft_lines<N, -1, N, 512>(plane, StridedLines<1>{}, PITCH, tw);  // along y
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
         const int y = i / N, x = i % N;
         Zxy[base + i] = plane[y * PITCH + x];
@@ -93,7 +120,6 @@ __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restr
                                                          const cplx_t<T>* __restrict__ tw_g) {
     using V = cplx_t<T>;
     constexpr int PITCH = row_pitch(N);
-    constexpr int UPT = upt_for<N, 512>(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* plane = tw + N;
@@ -103,8 +129,8 @@ __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restr
     const size_t base = (size_t)blockIdx.y * M + (size_t)blockIdx.x * N * N;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) plane[(i / N) * PITCH + i % N] = H[base + i];
     __syncthreads();
-    smem_fft_lines<N, +1, UPT>(plane, StridedLines{1}, PITCH, N, tw);  // along y
-    smem_fft_lines<N, +1, UPT>(plane, StridedLines{PITCH}, 1, N, tw);  // along x
+    smem_fft_lines<N, +1, N, 512>(plane, StridedLines<1>{}, PITCH, tw);  // along y
+    smem_fft_lines<N, +1, N, 512>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) grad[base + i] = plane[(i / N) * PITCH + i % N];
 }
 
@@ -119,27 +145,15 @@ __global__ void __launch_bounds__(256) x_forward_rows(unsigned long long* __rest
                                                        int zero_after) {
     using V = cplx_t<T>;
     constexpr int PITCH = row_pitch(N);
-    constexpr int UPT = upt_for<N, 256>(R);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* rows = tw + N;
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)blockIdx.x * R * N;
-    for (int i = threadIdx.x; i < R * N / 2; i += blockDim.x) {
-        const int r = (2 * i) / N, x = (2 * i) % N;
-        longlong2* pa = reinterpret_cast<longlong2*>(rho_fx + base) + i;
-        longlong2* pb = reinterpret_cast<longlong2*>(rho_fx + M + base) + i;
-        const longlong2 a = *pa, b = *pb;
-        if (zero_after) {
-            *pa = make_longlong2(0, 0);
-            *pb = make_longlong2(0, 0);
-        }
-        rows[r * PITCH + x] = V{from_fixed(a.x, scale), from_fixed(b.x, scale)};
-        rows[r * PITCH + x + 1] = V{from_fixed(a.y, scale), from_fixed(b.y, scale)};
-    }
+    load_fixed_rows<N, PITCH, R, 256>(rho_fx + base, rho_fx + M + base, rows, scale, zero_after);
     __syncthreads();
-    smem_fft_lines<N, -1, UPT>(rows, StridedLines{PITCH}, 1, R, tw);
+    smem_fft_lines<N, -1, R, 256>(rows, StridedLines<PITCH>{}, 1, tw);
     for (int i = threadIdx.x; i < R * N; i += blockDim.x) Zxy[base + i] = rows[(i / N) * PITCH + i % N];
 }
 
@@ -148,7 +162,6 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
                                                        const cplx_t<T>* __restrict__ tw_g) {
     using V = cplx_t<T>;
     constexpr int PITCH = row_pitch(N);
-    constexpr int UPT = upt_for<N, 256>(R);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* rows = tw + N;
@@ -157,7 +170,7 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
     const size_t base = (size_t)blockIdx.y * M + (size_t)blockIdx.x * R * N;
     for (int i = threadIdx.x; i < R * N; i += blockDim.x) rows[(i / N) * PITCH + i % N] = H[base + i];
     __syncthreads();
-    smem_fft_lines<N, +1, UPT>(rows, StridedLines{PITCH}, 1, R, tw);
+    smem_fft_lines<N, +1, R, 256>(rows, StridedLines<PITCH>{}, 1, tw);
     for (int i = threadIdx.x; i < R * N; i += blockDim.x) grad[base + i] = rows[(i / N) * PITCH + i % N];
 }
 
@@ -165,7 +178,6 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
 template <typename T, int N, int C, int DIR>
 __global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, const cplx_t<T>* __restrict__ tw_g) {
     using V = cplx_t<T>;
-    constexpr int UPT = upt_for<N, 256>(C);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* tile = tw + N;  // [y][c]
@@ -174,7 +186,7 @@ __global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, c
     const size_t base = (size_t)blockIdx.z * M + (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * C;
     for (int i = threadIdx.x; i < N * C; i += blockDim.x) tile[i] = data[base + (size_t)(i / C) * N + i % C];
     __syncthreads();
-    smem_fft_lines<N, DIR, UPT>(tile, StridedLines{1}, C, C, tw);
+    smem_fft_lines<N, DIR, C, 256>(tile, StridedLines<1>{}, C, tw);
     for (int i = threadIdx.x; i < N * C; i += blockDim.x) data[base + (size_t)(i / C) * N + i % C] = tile[i];
 }
 
@@ -183,9 +195,8 @@ __global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, c
 // along z. CTA (kx tile of C columns, ky). Loads its own tile and the
 // mirror tile (-kx, -ky) that Hermitian separation needs.
 // --------------------------------------------------------------------------
-template <class V> struct TileAddr {
-    int C, stride;  // buffer b of a tile set starts at b * stride
-    __device__ __forceinline__ int operator()(int l) const { return (l / C) * stride + l % C; }
+template <int C, int STRIDE> struct TileAddr {  // buffer b of a tile set starts at b * STRIDE
+    __device__ __forceinline__ int operator()(int l) const { return (l / C) * STRIDE + l % C; }
 };
 
 template <typename T> __device__ __forceinline__ int freq_index(int i, int n) { return i < n / 2 ? i : i - n; }
@@ -196,8 +207,6 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
                                                   double* __restrict__ energy_partials,
                                                   cplx_t<T>* __restrict__ spectrum_out) {
     using V = cplx_t<T>;
-    constexpr int UPT_F = upt_for<N, 256>(2 * C);
-    constexpr int UPT_I = upt_for<N, 256>(3 * C);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* buf = tw + N;          // 3 buffers [N][C]: own, mirror, third
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
         buf[TS + i] = Zxy[z * NN + (size_t)kym * N + kxm];
     }
     __syncthreads();
-    smem_fft_lines<N, -1, UPT_F>(buf, TileAddr<V>{C, TS}, C, 2 * C, tw);
+    smem_fft_lines<N, -1, 2 * C, 256>(buf, TileAddr<C, N * C>{}, C, tw);
 
     if (spectrum_out) {
         for (int i = threadIdx.x; i < TS; i += blockDim.x)
@@ -293,7 +302,7 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
         energy_partials[2 * b] = s0;
         energy_partials[2 * b + 1] = s1;
     }
-    smem_fft_lines<N, +1, UPT_I>(buf, TileAddr<V>{C, TS}, C, 3 * C, tw);
+    smem_fft_lines<N, +1, 3 * C, 256>(buf, TileAddr<C, N * C>{}, C, tw);
     const size_t M = NN * N;
     for (int i = threadIdx.x; i < 3 * TS; i += blockDim.x) {
         const int d = i / TS, r = i % TS;
