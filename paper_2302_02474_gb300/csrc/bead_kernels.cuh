@@ -60,7 +60,7 @@ template <typename T> struct BeadBuffers {
     T* __restrict__ uz;
     const int* __restrict__ id;
     const int2* __restrict__ nbr;
-    const int* __restrict__ cell_start;
+    const int* __restrict__ tile_start;  // [tiles^3 + 1] first slot of each tile
     const cplx_t<T>* __restrict__ grad;  // [3][M] (A, B) pairs
     unsigned long long* __restrict__ rho_fx;  // [2][M]
     unsigned long long* step;  // device step counter n
@@ -200,137 +200,200 @@ template <int P, typename T> __device__ __forceinline__ bool patch_local(const S
            (unsigned)l.z <= (unsigned)(PT::W - P);
 }
 
-template <int P, typename T> constexpr size_t bead_smem_bytes(bool with_grad) {
-    return 2 * Patch<P>::W3 * sizeof(unsigned long long) + (with_grad ? 3 * Patch<P>::W3 * sizeof(cplx_t<T>) : 0);
+// Beads of a tile are staged in shared memory in chunks of up to kBeadChunk.
+constexpr int kBeadChunk = 512;
+
+template <int P, typename T> struct BeadSmem {
+    static constexpr int W3 = Patch<P>::W3;
+    static constexpr size_t patch_off = 0;                                              // uint64 [2][W3]
+    static constexpr size_t grad_off = patch_off + 2 * W3 * sizeof(unsigned long long);  // cplx [3][W3]
+    static constexpr size_t pos_off = grad_off + 3 * W3 * sizeof(cplx_t<T>);             // T [3][chunk]
+    static constexpr size_t nbr_off = pos_off + 3 * kBeadChunk * sizeof(T);               // int2 [chunk]
+    static constexpr size_t tag_off = nbr_off + kBeadChunk * sizeof(int2);                // int [chunk]
+    static constexpr size_t bytes = tag_off + kBeadChunk * sizeof(int);
+};
+
+template <int P, typename T> constexpr size_t bead_smem_bytes() { return BeadSmem<P, T>::bytes; }
+
+// Grid offset (within one field) of the first point of patch row `row`,
+// row = (plane * W + lz) * W + ly over stacked patches; sets the plane.
+template <int P> __device__ __forceinline__ size_t patch_row_base(int row, int3 org, int n, int& plane) {
+    constexpr int W = Patch<P>::W;
+    plane = row / (W * W);
+    const int rem = row - plane * W * W;
+    const int lz = rem / W, ly = rem - lz * W;
+    const int nm = n - 1;
+    return ((size_t)((org.z + lz) & nm) * n + ((org.y + ly) & nm)) * n;
 }
 
 template <int P, int MODE, typename T>
 __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
     using PT = Patch<P>;
+    using SM = BeadSmem<P, T>;
     using V = cplx_t<T>;
+    constexpr int W = PT::W;
     constexpr bool kSpread = (MODE == kModeSpread || MODE == kModeStep);
     constexpr bool kForce = (MODE != kModeSpread);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long* patch = reinterpret_cast<unsigned long long*>(smem_raw);
-    V* s_grad = reinterpret_cast<V*>(smem_raw + 2 * PT::W3 * sizeof(unsigned long long));
+    unsigned long long* patch = reinterpret_cast<unsigned long long*>(smem_raw + SM::patch_off);
+    V* s_grad = reinterpret_cast<V*>(smem_raw + SM::grad_off);
+    T* s_pos = reinterpret_cast<T*>(smem_raw + SM::pos_off);
+    int2* s_nbr = reinterpret_cast<int2*>(smem_raw + SM::nbr_off);
+    int* s_tag = reinterpret_cast<int*>(smem_raw + SM::tag_off);
+
     const int t = blockIdx.x;
     const int tx = t % p.tiles, ty = (t / p.tiles) % p.tiles, tz = t / (p.tiles * p.tiles);
     const int3 org = {tx * kTile + PT::lo, ty * kTile + PT::lo, tz * kTile + PT::lo};
     const int nm = p.n - 1;
+    const size_t M = (size_t)p.n * p.n * p.n;
+    const int lane16 = threadIdx.x & 15;
+    const int half = threadIdx.x >> 4;  // one patch row per 16 threads
+    const int nhalf = blockDim.x >> 4;
     if (kSpread) {
         for (int i = threadIdx.x; i < 2 * PT::W3; i += blockDim.x) patch[i] = 0ull;
     }
     if (kForce) {
-        // stage the gradient fields of the patch (rows of W points along x)
-        const size_t M = (size_t)p.n * p.n * p.n;
-        for (int i = threadIdx.x; i < 3 * PT::W3; i += blockDim.x) {
-            const int d = i / PT::W3, r = i - d * PT::W3;
-            const int lx = r % PT::W, ly = (r / PT::W) % PT::W, lz = r / (PT::W * PT::W);
-            const size_t g = ((size_t)((org.z + lz) & nm) * p.n + ((org.y + ly) & nm)) * p.n + ((org.x + lx) & nm);
-            s_grad[i] = __ldg(bf.grad + d * M + g);
+        // stage the gradient fields of the patch, one row of W points per 16 threads
+        const int gx = (org.x + lane16) & nm;
+        for (int row = half; row < 3 * W * W; row += nhalf) {
+            int d;
+            const size_t base = patch_row_base<P>(row, org, p.n, d);
+            if (lane16 < W) s_grad[row * W + lane16] = __ldg(bf.grad + d * M + base + gx);
         }
     }
-    __syncthreads();
-    const int start = bf.cell_start[(size_t)t * kTileCells];
-    const int end = bf.cell_start[(size_t)(t + 1) * kTileCells];
+    const int start = bf.tile_start[t];
+    const int end = bf.tile_start[t + 1];
     const uint64_t step = (MODE == kModeStep) ? *((volatile unsigned long long*)bf.step) : 0ull;
     double acc[5] = {0, 0, 0, 0, 0};
 
-    for (int i = start + threadIdx.x; i < end; i += blockDim.x) {
-        T x = bf.px[i], y = bf.py[i], z = bf.pz[i];
-        const int tag = bf.id[i];
-        const int bid = slot_bead_id(tag);
-        const int species = slot_species(tag);
-        Stencil<P, T> st;
-        st.set(x, y, z, p.inv_dx);
-        int3 l;
-        bool inside = patch_local(st, org, l);
-        if (kForce) {
-            T fx, fy, fz;
-            gather_force<P>(st, inside, l, s_grad, bf.grad, p.n, species, fx, fy, fz);
-            const int2 nb = bf.nbr[i];
-            if (nb.x >= 0) {
-                const T dx = min_image(x - bf.px[nb.x], p.L, p.inv_L);
-                const T dy = min_image(y - bf.py[nb.x], p.L, p.inv_L);
-                const T dz = min_image(z - bf.pz[nb.x], p.L, p.inv_L);
-                fx -= p.k_bond * dx;
-                fy -= p.k_bond * dy;
-                fz -= p.k_bond * dz;
-            }
-            if (nb.y >= 0) {
-                const T dx = min_image(x - bf.px[nb.y], p.L, p.inv_L);
-                const T dy = min_image(y - bf.py[nb.y], p.L, p.inv_L);
-                const T dz = min_image(z - bf.pz[nb.y], p.L, p.inv_L);
-                fx -= p.k_bond * dx;
-                fy -= p.k_bond * dy;
-                fz -= p.k_bond * dz;
-                if (MODE == kModeForce) acc[0] += 0.5 * (double)p.k_bond * ((double)dx * dx + (double)dy * dy + (double)dz * dz);
-            }
-            if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(bf.err, kErrNonFinite);
-            if (MODE == kModeForce) {
-                const T vx = bf.ux[i] + p.hdm * fx, vy = bf.uy[i] + p.hdm * fy, vz = bf.uz[i] + p.hdm * fz;
-                acc[1] += 0.5 * (double)p.mass * ((double)vx * vx + (double)vy * vy + (double)vz * vz);
-                acc[2] += fx;
-                acc[3] += fy;
-                acc[4] += fz;
-                if (bf.f_out) {
-                    bf.f_out[3 * (size_t)bid + 0] = fx;
-                    bf.f_out[3 * (size_t)bid + 1] = fy;
-                    bf.f_out[3 * (size_t)bid + 2] = fz;
-                }
-                if (bf.v_out) {
-                    bf.v_out[3 * (size_t)bid + 0] = vx;
-                    bf.v_out[3 * (size_t)bid + 1] = vy;
-                    bf.v_out[3 * (size_t)bid + 2] = vz;
-                }
-            } else if (MODE == kModeSetVel) {
-                T vx, vy, vz;
-                if (bf.v_in) {
-                    vx = bf.v_in[3 * (size_t)bid + 0];
-                    vy = bf.v_in[3 * (size_t)bid + 1];
-                    vz = bf.v_in[3 * (size_t)bid + 2];
-                } else {
-                    const normal3<T> g = gaussian3((uint32_t)bid, ~0ull, p.seed, T(0));
-                    vx = p.sigma_v * g.a;
-                    vy = p.sigma_v * g.b;
-                    vz = p.sigma_v * g.c;
-                }
-                bf.ux[i] = vx - p.hdm * fx;
-                bf.uy[i] = vy - p.hdm * fy;
-                bf.uz[i] = vz - p.hdm * fz;
-            } else if (MODE == kModeStep) {
-                const normal3<T> g = gaussian3((uint32_t)bid, step + 1, p.seed, T(0));
-                const T bx = p.sigma_beta * g.a, by = p.sigma_beta * g.b, bz = p.sigma_beta * g.c;
-                // v^n + (dt/2m) F^n
-                const T hx = bf.ux[i] + T(2) * p.hdm * fx;
-                const T hy = bf.uy[i] + T(2) * p.hdm * fy;
-                const T hz = bf.uz[i] + T(2) * p.hdm * fz;
-                x = wrap_coord(x + p.gb_dt * (hx + p.inv_2m * bx), p.L, p.inv_L);
-                y = wrap_coord(y + p.gb_dt * (hy + p.inv_2m * by), p.L, p.inv_L);
-                z = wrap_coord(z + p.gb_dt * (hz + p.inv_2m * bz), p.L, p.inv_L);
-                bf.qx[i] = x;
-                bf.qy[i] = y;
-                bf.qz[i] = z;
-                bf.ux[i] = p.ga * hx + p.gb_m * bx;
-                bf.uy[i] = p.ga * hy + p.gb_m * by;
-                bf.uz[i] = p.ga * hz + p.gb_m * bz;
-                st.set(x, y, z, p.inv_dx);
-                inside = patch_local(st, org, l);
-            }
+    for (int c0 = start; c0 < end; c0 += kBeadChunk) {
+        const int cnt = min(kBeadChunk, end - c0);
+        if (c0 != start) __syncthreads();  // the previous chunk is done with the staged beads
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            s_pos[j] = bf.px[c0 + j];
+            s_pos[kBeadChunk + j] = bf.py[c0 + j];
+            s_pos[2 * kBeadChunk + j] = bf.pz[c0 + j];
+            s_tag[j] = bf.id[c0 + j];
+            if (kForce) s_nbr[j] = bf.nbr[c0 + j];
         }
-        if (kSpread) spread_bead<P>(st, inside, l, patch, bf.rho_fx, p.n, species);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            const int i = c0 + j;
+            T x = s_pos[j], y = s_pos[kBeadChunk + j], z = s_pos[2 * kBeadChunk + j];
+            const int tag = s_tag[j];
+            const int bid = slot_bead_id(tag);
+            const int species = slot_species(tag);
+            Stencil<P, T> st;
+            st.set(x, y, z, p.inv_dx);
+            int3 l;
+            bool inside = patch_local(st, org, l);
+            if (kForce) {
+                T ux = 0, uy = 0, uz = 0;
+                if (MODE != kModeSetVel) {
+                    ux = bf.ux[i];
+                    uy = bf.uy[i];
+                    uz = bf.uz[i];
+                }
+                // bonded neighbours: from the staged chunk when they are in it
+                const int2 nb = s_nbr[j];
+                T nx[2], ny[2], nz[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int s = k == 0 ? nb.x : nb.y;
+                    if (s >= c0 && s < c0 + cnt) {
+                        nx[k] = s_pos[s - c0];
+                        ny[k] = s_pos[kBeadChunk + s - c0];
+                        nz[k] = s_pos[2 * kBeadChunk + s - c0];
+                    } else if (s >= 0) {
+                        nx[k] = bf.px[s];
+                        ny[k] = bf.py[s];
+                        nz[k] = bf.pz[s];
+                    } else {
+                        nx[k] = ny[k] = nz[k] = T(0);
+                    }
+                }
+                T fx, fy, fz;
+                gather_force<P>(st, inside, l, s_grad, bf.grad, p.n, species, fx, fy, fz);
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if ((k == 0 ? nb.x : nb.y) >= 0) {
+                        const T dx = min_image(x - nx[k], p.L, p.inv_L);
+                        const T dy = min_image(y - ny[k], p.L, p.inv_L);
+                        const T dz = min_image(z - nz[k], p.L, p.inv_L);
+                        fx -= p.k_bond * dx;
+                        fy -= p.k_bond * dy;
+                        fz -= p.k_bond * dz;
+                        if (MODE == kModeForce && k == 1)
+                            acc[0] += 0.5 * (double)p.k_bond * ((double)dx * dx + (double)dy * dy + (double)dz * dz);
+                    }
+                }
+                if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(bf.err, kErrNonFinite);
+                if (MODE == kModeForce) {
+                    const T vx = ux + p.hdm * fx, vy = uy + p.hdm * fy, vz = uz + p.hdm * fz;
+                    acc[1] += 0.5 * (double)p.mass * ((double)vx * vx + (double)vy * vy + (double)vz * vz);
+                    acc[2] += fx;
+                    acc[3] += fy;
+                    acc[4] += fz;
+                    if (bf.f_out) {
+                        bf.f_out[3 * (size_t)bid + 0] = fx;
+                        bf.f_out[3 * (size_t)bid + 1] = fy;
+                        bf.f_out[3 * (size_t)bid + 2] = fz;
+                    }
+                    if (bf.v_out) {
+                        bf.v_out[3 * (size_t)bid + 0] = vx;
+                        bf.v_out[3 * (size_t)bid + 1] = vy;
+                        bf.v_out[3 * (size_t)bid + 2] = vz;
+                    }
+                } else if (MODE == kModeSetVel) {
+                    T vx, vy, vz;
+                    if (bf.v_in) {
+                        vx = bf.v_in[3 * (size_t)bid + 0];
+                        vy = bf.v_in[3 * (size_t)bid + 1];
+                        vz = bf.v_in[3 * (size_t)bid + 2];
+                    } else {
+                        const normal3<T> g = gaussian3((uint32_t)bid, ~0ull, p.seed, T(0));
+                        vx = p.sigma_v * g.a;
+                        vy = p.sigma_v * g.b;
+                        vz = p.sigma_v * g.c;
+                    }
+                    bf.ux[i] = vx - p.hdm * fx;
+                    bf.uy[i] = vy - p.hdm * fy;
+                    bf.uz[i] = vz - p.hdm * fz;
+                } else if (MODE == kModeStep) {
+                    const normal3<T> g = gaussian3((uint32_t)bid, step + 1, p.seed, T(0));
+                    const T bx = p.sigma_beta * g.a, by = p.sigma_beta * g.b, bz = p.sigma_beta * g.c;
+                    // v^n + (dt/2m) F^n
+                    const T hx = ux + T(2) * p.hdm * fx;
+                    const T hy = uy + T(2) * p.hdm * fy;
+                    const T hz = uz + T(2) * p.hdm * fz;
+                    x = wrap_coord(x + p.gb_dt * (hx + p.inv_2m * bx), p.L, p.inv_L);
+                    y = wrap_coord(y + p.gb_dt * (hy + p.inv_2m * by), p.L, p.inv_L);
+                    z = wrap_coord(z + p.gb_dt * (hz + p.inv_2m * bz), p.L, p.inv_L);
+                    bf.qx[i] = x;
+                    bf.qy[i] = y;
+                    bf.qz[i] = z;
+                    bf.ux[i] = p.ga * hx + p.gb_m * bx;
+                    bf.uy[i] = p.ga * hy + p.gb_m * by;
+                    bf.uz[i] = p.ga * hz + p.gb_m * bz;
+                    st.set(x, y, z, p.inv_dx);
+                    inside = patch_local(st, org, l);
+                }
+            }
+            if (kSpread) spread_bead<P>(st, inside, l, patch, bf.rho_fx, p.n, species);
+        }
     }
 
     if (kSpread) {
         __syncthreads();
-        const size_t M = (size_t)p.n * p.n * p.n;
-        for (int i = threadIdx.x; i < 2 * PT::W3; i += blockDim.x) {
-            const unsigned long long v = patch[i];
-            if (v) {
-                const int K = i / PT::W3, r = i - K * PT::W3;
-                const int lx = r % PT::W, ly = (r / PT::W) % PT::W, lz = r / (PT::W * PT::W);
-                const size_t g = ((size_t)((org.z + lz) & nm) * p.n + ((org.y + ly) & nm)) * p.n + ((org.x + lx) & nm);
-                atomicAdd(bf.rho_fx + K * M + g, v);
+        const int gx = (org.x + lane16) & nm;
+        for (int row = half; row < 2 * W * W; row += nhalf) {
+            if (lane16 < W) {
+                const unsigned long long v = patch[row * W + lane16];
+                if (v) {
+                    int K;
+                    const size_t base = patch_row_base<P>(row, org, p.n, K);
+                    atomicAdd(bf.rho_fx + K * M + base + gx, v);
+                }
             }
         }
     }
@@ -368,14 +431,26 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
 
 // ------------------------------------------------------------- binning
 
-// Cell key of a position: tile-major index of the grid cell floor(r/dx).
-template <typename T> __device__ __forceinline__ int cell_key(T x, T y, T z, T inv_dx, int n, int tiles) {
+// Tile of a position: index of the 8x8x8-cell tile holding floor(r/dx).
+template <typename T> __device__ __forceinline__ int tile_key(T x, T y, T z, T inv_dx, int n, int tiles) {
     const int cx = min(max((int)floor(x * inv_dx), 0), n - 1);
     const int cy = min(max((int)floor(y * inv_dx), 0), n - 1);
     const int cz = min(max((int)floor(z * inv_dx), 0), n - 1);
-    const int t = ((cz / kTile) * tiles + cy / kTile) * tiles + cx / kTile;
-    const int l = ((cz % kTile) * kTile + cy % kTile) * kTile + cx % kTile;
-    return t * kTileCells + l;
+    return ((cz / kTile) * tiles + cy / kTile) * tiles + cx / kTile;
+}
+
+// atomicAdd(counter + key, 1) for every active lane with one atomic per
+// distinct key in the warp; returns this lane's value before its increment.
+__device__ __forceinline__ int warp_aggregated_inc(int* counter, int key) {
+    const unsigned active = __activemask();
+    const unsigned peers = __match_any_sync(active, key);
+    const int leader = __ffs(peers) - 1;
+    const int lane = threadIdx.x & 31;
+    const int rank = __popc(peers & ((1u << lane) - 1));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter + key, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + rank;
 }
 
 template <typename T>
@@ -383,19 +458,19 @@ __global__ void bin_count(int n_beads, const T* __restrict__ px, const T* __rest
                           T inv_dx, int n, int tiles, int* __restrict__ keys, int* __restrict__ counts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_beads) return;
-    const int k = cell_key(px[i], py[i], pz[i], inv_dx, n, tiles);
+    const int k = tile_key(px[i], py[i], pz[i], inv_dx, n, tiles);
     keys[i] = k;
-    atomicAdd(counts + k, 1);
+    warp_aggregated_inc(counts, k);
 }
 
 template <typename T>
-__global__ void bin_scatter_pos(int n_beads, Topology topo, const int* __restrict__ keys, const int* __restrict__ cell_start,
+__global__ void bin_scatter_pos(int n_beads, Topology topo, const int* __restrict__ keys, const int* __restrict__ tile_start,
                                 int* __restrict__ cursor, const T* __restrict__ src /*[3][N]*/, T* __restrict__ dst,
                                 const int* __restrict__ id_src, int* __restrict__ id_dst, int* __restrict__ slot_of_id) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_beads) return;
     const int k = keys[i];
-    const int s = cell_start[k] + atomicAdd(cursor + k, 1);
+    const int s = tile_start[k] + warp_aggregated_inc(cursor, k);
 #pragma unroll
     for (int c = 0; c < 3; ++c) dst[(size_t)c * n_beads + s] = src[(size_t)c * n_beads + i];
     const int b = slot_bead_id(id_src[i]);

@@ -52,10 +52,11 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(cudaMalloc(&counters_, 4 * sizeof(unsigned long long)));
         TILD_CUDA(cudaMemset(counters_, 0, 4 * sizeof(unsigned long long)));
         TILD_CUDA(cudaMemset(rho_fx_, 0, 2 * M_ * sizeof(unsigned long long)));
-        TILD_CUDA(cudaMalloc(&counts_, (M_ + 1) * sizeof(int)));
-        TILD_CUDA(cudaMalloc(&cell_start_, (M_ + 1) * sizeof(int)));
-        TILD_CUDA(cudaMalloc(&cursor_, (M_ + 1) * sizeof(int)));
-        scan_blocks_ = (int)((M_ + 1 + 1023) / 1024);
+        n_tiles_ = tiles_ * tiles_ * tiles_;
+        TILD_CUDA(cudaMalloc(&counts_, (n_tiles_ + 1) * sizeof(int)));
+        TILD_CUDA(cudaMalloc(&tile_start_, (n_tiles_ + 1) * sizeof(int)));
+        TILD_CUDA(cudaMalloc(&cursor_, (n_tiles_ + 1) * sizeof(int)));
+        scan_blocks_ = (int)((n_tiles_ + 1 + 1023) / 1024);
         TILD_CUDA(cudaMalloc(&block_sums_, scan_blocks_ * sizeof(int)));
         n_z_blocks_ = (size_t)(n_ / C_) * n_;
         n_partials_ = std::max(2 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
@@ -428,7 +429,8 @@ template <typename T> class Engine final : public EngineBase {
     int* slot_of_id_ = nullptr;
     int* keys_ = nullptr;
     int* counts_ = nullptr;
-    int* cell_start_ = nullptr;
+    int* tile_start_ = nullptr;
+    int n_tiles_ = 0;
     int* cursor_ = nullptr;
     int* block_sums_ = nullptr;
     int scan_blocks_ = 0;
@@ -457,10 +459,10 @@ template <typename T> class Engine final : public EngineBase {
     size_t zpass_smem() const { return ((size_t)n_ + 3 * (size_t)n_ * C_) * sizeof(V); }
     size_t bead_smem() const {
         switch (P_) {
-            case 2: return bead_smem_bytes<2, T>(true);
-            case 3: return bead_smem_bytes<3, T>(true);
-            case 4: return bead_smem_bytes<4, T>(true);
-            default: return bead_smem_bytes<5, T>(true);
+            case 2: return bead_smem_bytes<2, T>();
+            case 3: return bead_smem_bytes<3, T>();
+            case 4: return bead_smem_bytes<4, T>();
+            default: return bead_smem_bytes<5, T>();
         }
     }
 
@@ -485,7 +487,7 @@ template <typename T> class Engine final : public EngineBase {
         invalidate_graph();
         free_beads();
         void* ptrs[] = {rho_fx_, Zxy_, H_, grad_, tw_, spec_, counters_, partials_, counts_,
-                        cell_start_, cursor_, block_sums_, aux_, stage_};
+                        tile_start_, cursor_, block_sums_, aux_, stage_};
         for (void* p : ptrs) cudaFree(p);
         rho_fx_ = nullptr;
         if (own_stream_) cudaStreamDestroy(own_stream_);
@@ -761,7 +763,7 @@ template <typename T> class Engine final : public EngineBase {
         b.uz = b.uy + N;
         b.id = id_[cur_id_];
         b.nbr = nbr_;
-        b.cell_start = cell_start_;
+        b.tile_start = tile_start_;
         b.grad = grad_;
         b.rho_fx = rho_fx_;
         b.step = counters_;
@@ -814,14 +816,14 @@ template <typename T> class Engine final : public EngineBase {
     tild_status enqueue_sort() {
         const int N = cfg_->n_beads;
         const size_t N3 = N;
-        TILD_CUDA(cudaMemsetAsync(counts_, 0, (M_ + 1) * sizeof(int), stream_));
-        TILD_CUDA(cudaMemsetAsync(cursor_, 0, (M_ + 1) * sizeof(int), stream_));
+        TILD_CUDA(cudaMemsetAsync(counts_, 0, (n_tiles_ + 1) * sizeof(int), stream_));
+        TILD_CUDA(cudaMemsetAsync(cursor_, 0, (n_tiles_ + 1) * sizeof(int), stream_));
         const T* p = pos_[cur_pos_];
         bin_count<T><<<blocks(N), 256, 0, stream_>>>(N, p, p + N3, p + 2 * N3, (T)((double)n_ / cfg_->L), n_, tiles_, keys_, counts_);
-        scan_blocks<<<scan_blocks_, 1024, 0, stream_>>>(counts_, cell_start_, block_sums_, (int)(M_ + 1));
+        scan_blocks<<<scan_blocks_, 1024, 0, stream_>>>(counts_, tile_start_, block_sums_, n_tiles_ + 1);
         scan_top<<<1, 1024, 0, stream_>>>(block_sums_, scan_blocks_);
-        scan_add<<<scan_blocks_, 1024, 0, stream_>>>(cell_start_, block_sums_, (int)(M_ + 1));
-        bin_scatter_pos<T><<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, keys_, cell_start_, cursor_, pos_[cur_pos_],
+        scan_add<<<scan_blocks_, 1024, 0, stream_>>>(tile_start_, block_sums_, n_tiles_ + 1);
+        bin_scatter_pos<T><<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, keys_, tile_start_, cursor_, pos_[cur_pos_],
                                                            pos_[1 - cur_pos_], id_[cur_id_], id_[1 - cur_id_], slot_of_id_);
         bin_move_u<T><<<blocks(N), 256, 0, stream_>>>(N, id_[cur_id_], slot_of_id_, u_[cur_u_], u_[1 - cur_u_]);
         bin_neighbours<<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, id_[1 - cur_id_], slot_of_id_, nbr_);

@@ -4,7 +4,7 @@
 #include <cstdint>
 #include <string>
 
-#include "../../include/tild.h"
+#include "tild.h"
 #include "common.cuh"
 
 namespace tild {
