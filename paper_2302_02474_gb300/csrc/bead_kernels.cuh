@@ -63,8 +63,7 @@ template <typename T> struct BeadBuffers {
     const int* __restrict__ tile_start;  // [tiles^3 + 1] first slot of each tile
     const cplx_t<T>* __restrict__ grad;  // [3][M] (A, B) pairs
     unsigned long long* __restrict__ rho_fx;  // [2][M]
-    unsigned long long* step;  // device step counter n
-    unsigned int* done;        // CTA completion counter (STEP)
+    const unsigned long long* step;  // device step counter: n+1 while step n -> n+1 runs
     unsigned int* err;
     T* __restrict__ f_out;        // FORCE: [n_beads][3] by id (may be null)
     T* __restrict__ v_out;        // FORCE: velocities by id (may be null)
@@ -162,11 +161,13 @@ __device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_pa
 // Spread one bead of species K into the fixed-point patch (in_patch) or
 // straight into the global grid.
 template <int P, typename T>
-__device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_patch, int3 l, unsigned long long* patch,
+__device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_patch, int3 l,
+                                            typename FixedPoint<T>::patch_t* patch,
                                             unsigned long long* __restrict__ rho_fx, int n, int K) {
     using PT = Patch<P>;
+    using FP = FixedPoint<T>;
     if (in_patch) {
-        unsigned long long* base = patch + K * PT::W3;
+        typename FP::patch_t* base = patch + K * PT::W3;
 #pragma unroll
         for (int c = 0; c < P; ++c)
 #pragma unroll
@@ -174,7 +175,7 @@ __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_pat
                 const T wyz = st.wy[b] * st.wz[c];
                 const int row = ((l.z + c) * PT::W + (l.y + b)) * PT::W + l.x;
 #pragma unroll
-                for (int a = 0; a < P; ++a) atomicAdd(base + row + a, (unsigned long long)to_fixed(st.wx[a] * wyz));
+                for (int a = 0; a < P; ++a) atomicAdd(base + row + a, FP::to_patch(st.wx[a] * wyz));
             }
     } else {
         const int nm = n - 1;
@@ -187,7 +188,7 @@ __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_pat
 #pragma unroll
                 for (int a = 0; a < P; ++a) {
                     const size_t g = ((size_t)((st.jz + c) & nm) * n + ((st.jy + b) & nm)) * n + ((st.jx + a) & nm);
-                    atomicAdd(rho_fx + K * M + g, (unsigned long long)to_fixed(st.wx[a] * wyz));
+                    atomicAdd(rho_fx + K * M + g, (unsigned long long)FP::to_patch(st.wx[a] * wyz));
                 }
             }
     }
@@ -204,12 +205,15 @@ template <int P, typename T> __device__ __forceinline__ bool patch_local(const S
 constexpr int kBeadChunk = 512;
 
 template <int P, typename T> struct BeadSmem {
+    using patch_t = typename FixedPoint<T>::patch_t;
     static constexpr int W3 = Patch<P>::W3;
-    static constexpr size_t patch_off = 0;                                              // uint64 [2][W3]
-    static constexpr size_t grad_off = patch_off + 2 * W3 * sizeof(unsigned long long);  // cplx [3][W3]
-    static constexpr size_t pos_off = grad_off + 3 * W3 * sizeof(cplx_t<T>);             // T [3][chunk]
-    static constexpr size_t nbr_off = pos_off + 3 * kBeadChunk * sizeof(T);               // int2 [chunk]
-    static constexpr size_t tag_off = nbr_off + kBeadChunk * sizeof(int2);                // int [chunk]
+    // the gradient patch is staged when it is small (else gathered from global)
+    static constexpr bool stage_grad = 3 * W3 * sizeof(cplx_t<T>) <= 48 * 1024;
+    static constexpr size_t patch_off = 0;                                                       // patch_t [2][W3]
+    static constexpr size_t grad_off = (patch_off + 2 * W3 * sizeof(patch_t) + 15) / 16 * 16;    // cplx [3][W3]
+    static constexpr size_t pos_off = grad_off + (stage_grad ? 3 * W3 * sizeof(cplx_t<T>) : 0);  // T [3][chunk]
+    static constexpr size_t nbr_off = pos_off + 3 * kBeadChunk * sizeof(T);                       // int2 [chunk]
+    static constexpr size_t tag_off = nbr_off + kBeadChunk * sizeof(int2);                        // int [chunk]
     static constexpr size_t bytes = tag_off + kBeadChunk * sizeof(int);
 };
 
@@ -227,15 +231,17 @@ template <int P> __device__ __forceinline__ size_t patch_row_base(int row, int3 
 }
 
 template <int P, int MODE, typename T>
-__global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
     using PT = Patch<P>;
     using SM = BeadSmem<P, T>;
+    using FP = FixedPoint<T>;
+    using patch_t = typename FP::patch_t;
     using V = cplx_t<T>;
     constexpr int W = PT::W;
     constexpr bool kSpread = (MODE == kModeSpread || MODE == kModeStep);
     constexpr bool kForce = (MODE != kModeSpread);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long* patch = reinterpret_cast<unsigned long long*>(smem_raw + SM::patch_off);
+    patch_t* patch = reinterpret_cast<patch_t*>(smem_raw + SM::patch_off);
     V* s_grad = reinterpret_cast<V*>(smem_raw + SM::grad_off);
     T* s_pos = reinterpret_cast<T*>(smem_raw + SM::pos_off);
     int2* s_nbr = reinterpret_cast<int2*>(smem_raw + SM::nbr_off);
@@ -250,9 +256,9 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
     const int half = threadIdx.x >> 4;  // one patch row per 16 threads
     const int nhalf = blockDim.x >> 4;
     if (kSpread) {
-        for (int i = threadIdx.x; i < 2 * PT::W3; i += blockDim.x) patch[i] = 0ull;
+        for (int i = threadIdx.x; i < 2 * PT::W3; i += blockDim.x) patch[i] = 0;
     }
-    if (kForce) {
+    if (kForce && SM::stage_grad) {
         // stage the gradient fields of the patch, one row of W points per 16 threads
         const int gx = (org.x + lane16) & nm;
         for (int row = half; row < 3 * W * W; row += nhalf) {
@@ -263,7 +269,10 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
     }
     const int start = bf.tile_start[t];
     const int end = bf.tile_start[t + 1];
-    const uint64_t step = (MODE == kModeStep) ? *((volatile unsigned long long*)bf.step) : 0ull;
+    // noise counter n+1 of this step (advanced by the first kernel of the step)
+    const uint64_t step_next = (MODE == kModeStep) ? *bf.step : 0ull;
+    // 32-bit patch sums cannot overflow below this many beads per tile
+    const bool patch_ok = end - start <= FP::max_tile_beads;
     double acc[5] = {0, 0, 0, 0, 0};
 
     for (int c0 = start; c0 < end; c0 += kBeadChunk) {
@@ -289,6 +298,7 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
             bool inside = patch_local(st, org, l);
             if (kForce) {
                 T ux = 0, uy = 0, uz = 0;
+                const bool staged = SM::stage_grad && inside;
                 if (MODE != kModeSetVel) {
                     ux = bf.ux[i];
                     uy = bf.uy[i];
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
                     }
                 }
                 T fx, fy, fz;
-                gather_force<P>(st, inside, l, s_grad, bf.grad, p.n, species, fx, fy, fz);
+                gather_force<P>(st, staged, l, s_grad, bf.grad, p.n, species, fx, fy, fz);
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if ((k == 0 ? nb.x : nb.y) >= 0) {
@@ -360,7 +370,7 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
                     bf.uy[i] = vy - p.hdm * fy;
                     bf.uz[i] = vz - p.hdm * fz;
                 } else if (MODE == kModeStep) {
-                    const normal3<T> g = gaussian3((uint32_t)bid, step + 1, p.seed, T(0));
+                    const normal3<T> g = gaussian3((uint32_t)bid, step_next, p.seed, T(0));
                     const T bx = p.sigma_beta * g.a, by = p.sigma_beta * g.b, bz = p.sigma_beta * g.c;
                     // v^n + (dt/2m) F^n
                     const T hx = ux + T(2) * p.hdm * fx;
@@ -379,7 +389,7 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
                     inside = patch_local(st, org, l);
                 }
             }
-            if (kSpread) spread_bead<P>(st, inside, l, patch, bf.rho_fx, p.n, species);
+            if (kSpread) spread_bead<P>(st, inside && patch_ok, l, patch, bf.rho_fx, p.n, species);
         }
     }
 
@@ -389,7 +399,7 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
         for (int row = half; row < 2 * W * W; row += nhalf) {
             if (lane16 < W) {
                 const unsigned long long v = patch[row * W + lane16];
-                if (v) {
+                if (v != 0ull) {
                     int K;
                     const size_t base = patch_row_base<P>(row, org, p.n, K);
                     atomicAdd(bf.rho_fx + K * M + base + gx, v);
@@ -411,20 +421,6 @@ __global__ void __launch_bounds__(256) bead_kernel(BeadParams<T> p, BeadBuffers<
             double s = 0;
             for (int w = 0; w < (int)blockDim.x / 32; ++w) s += red[threadIdx.x][w];
             bf.partials[5 * (size_t)t + threadIdx.x] = s;
-        }
-    }
-    if (MODE == kModeStep) {
-        // the last CTA to finish advances the step counter (every CTA has
-        // read it by then)
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(bf.done, 1u);
-            if (prev == gridDim.x - 1) {
-                *((volatile unsigned long long*)bf.step) = step + 1;
-                *((volatile unsigned int*)bf.done) = 0u;
-                __threadfence();
-            }
         }
     }
 }

@@ -26,18 +26,30 @@ template <class V, typename T> __device__ __forceinline__ V c_scale(V a, T s) { 
 template <class V> __device__ __forceinline__ V c_mul_negi(V a) { return {a.y, -a.x}; }
 template <class V> __device__ __forceinline__ V c_mul_posi(V a) { return {-a.y, a.x}; }
 
-// Fixed-point scale of the deterministic density accumulation: one bead
-// weight w in [0, 1] is added as round(w * 2^44) to a 64-bit integer.
-// Integer addition is associative, so the grid sums are bit-identical for
-// any order of contributions. A grid point holds up to 2^19 unit weights.
-constexpr double kFixScale = 17592186044416.0;          // 2^44
-constexpr double kFixInv = 1.0 / 17592186044416.0;      // 2^-44
-
-// Weight -> fixed point (round to nearest). Scaling by 2^44 is exact in
-// both precisions, so the integer is a function of the weight alone.
-__device__ __forceinline__ long long to_fixed(float w) { return __float2ll_rn(w * 17592186044416.0f); }
-__device__ __forceinline__ long long to_fixed(double w) { return __double2ll_rn(w * kFixScale); }
-// Fixed point -> density (scale = 2^-44 / dV); no FP64 in the FP32 path.
+// Deterministic density accumulation: every bead weight w in [0, 1] is
+// rounded once to an integer, round(w * 2^F), and all sums are integer sums,
+// which are associative: the grids are bit-identical for any order of
+// contributions, blocks or re-binning.
+//   FP32 path: F = 22. A tile's shared-memory patch holds 32-bit sums; a tile
+//     of at most 1023 beads cannot overflow (1023 * 2^22 < 2^32), larger tiles
+//     spread straight into the 64-bit grid. Quantisation <= 2^-23 per
+//     contribution, below the FP32 rounding of the weights themselves.
+//   FP64 path: F = 44, 64-bit patch sums; quantisation <= 2^-45.
+// The global grid is 64-bit in both cases.
+template <typename T> struct FixedPoint;
+template <> struct FixedPoint<float> {
+    using patch_t = unsigned int;
+    static constexpr double scale = 4194304.0;  // 2^22
+    static constexpr int max_tile_beads = 1023;
+    static __device__ __forceinline__ patch_t to_patch(float w) { return __float2uint_rn(w * 4194304.0f); }
+};
+template <> struct FixedPoint<double> {
+    using patch_t = unsigned long long;
+    static constexpr double scale = 17592186044416.0;  // 2^44
+    static constexpr int max_tile_beads = 0x7fffffff;
+    static __device__ __forceinline__ patch_t to_patch(double w) { return (patch_t)__double2ll_rn(w * scale); }
+};
+// Fixed point -> density (scale = 2^-F / dV); no FP64 in the FP32 path.
 __device__ __forceinline__ float from_fixed(long long v, float scale) { return __ll2float_rn(v) * scale; }
 __device__ __forceinline__ double from_fixed(long long v, double scale) { return (double)v * scale; }
 

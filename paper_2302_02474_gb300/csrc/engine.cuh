@@ -232,7 +232,7 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     tild_status get_density(void* out, int dtype, int where) override {
-        const double scale = kFixInv / (cfg_->L * cfg_->L * cfg_->L / (double)M_);
+        const double scale = 1.0 / FixedPoint<T>::scale / (cfg_->L * cfg_->L * cfg_->L / (double)M_);
         const size_t count = 2 * M_;
         tild_status st;
         void* dst = out;
@@ -313,7 +313,6 @@ template <typename T> class Engine final : public EngineBase {
         host_step_ = (int64_t)h[3];
         const unsigned long long dstep = h[3];
         TILD_CUDA(cudaMemcpyAsync(counters_, &dstep, sizeof(dstep), cudaMemcpyHostToDevice, stream_));
-        TILD_CUDA(cudaMemsetAsync(counters_ + 1, 0, sizeof(unsigned long long), stream_));
         TILD_CUDA(cudaStreamSynchronize(stream_));
         steps_since_sort_ = 0;
         have_pos_ = have_vel_ = true;
@@ -418,7 +417,7 @@ template <typename T> class Engine final : public EngineBase {
     V* grad_ = nullptr;
     V* tw_ = nullptr;
     V* spec_ = nullptr;
-    unsigned long long* counters_ = nullptr;  // [0] step, [1] done | err
+    unsigned long long* counters_ = nullptr;  // [0] noise step counter, [1] error flags
     double* partials_ = nullptr;
     size_t n_partials_ = 0, n_z_blocks_ = 0;
     // beads
@@ -447,7 +446,6 @@ template <typename T> class Engine final : public EngineBase {
     cudaGraphExec_t graph_ = nullptr;
     int graph_key_ = -1;
 
-    unsigned int* done_ptr() const { return reinterpret_cast<unsigned int*>(counters_ + 1); }
     unsigned int* err_ptr() const { return reinterpret_cast<unsigned int*>(counters_ + 1) + 1; }
 
     static unsigned blocks(size_t count) { return (unsigned)((count + 255) / 256); }
@@ -649,19 +647,20 @@ template <typename T> class Engine final : public EngineBase {
 
     T density_scale() const {
         const double dV = cfg_->L * cfg_->L * cfg_->L / (double)M_;
-        return (T)(kFixInv / dV);
+        return (T)(1.0 / FixedPoint<T>::scale / dV);
     }
 
     template <int NN> tild_status forward_n(bool zero_after) {
         if (plane_fits_) {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
-                xy_forward_plane<T, NN><<<NN, 512, plane_smem(), stream_>>>(rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0);
+                xy_forward_plane<T, NN><<<NN, 512, plane_smem(), stream_>>>(rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0,
+                                                                            zero_after ? counters_ : nullptr);
             }
         } else {
             constexpr int CC = 128 / sizeof(V);
             if constexpr (NN >= 16 && NN >= CC) {
                 x_forward_rows<T, NN, 16><<<(unsigned)((size_t)NN * NN / 16), 256, rows_smem(), stream_>>>(
-                    rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0);
+                    rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0, zero_after ? counters_ : nullptr);
                 y_columns<T, NN, CC, -1><<<dim3(NN / CC, NN, 1), 256, ycol_smem(), stream_>>>(Zxy_, tw_);
             }
         }
@@ -767,7 +766,6 @@ template <typename T> class Engine final : public EngineBase {
         b.grad = grad_;
         b.rho_fx = rho_fx_;
         b.step = counters_;
-        b.done = done_ptr();
         b.err = err_ptr();
         b.f_out = nullptr;
         b.v_out = nullptr;

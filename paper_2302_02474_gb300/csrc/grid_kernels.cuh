@@ -89,13 +89,15 @@ template <typename T, int N>
 __global__ void __launch_bounds__(512) xy_forward_plane(unsigned long long* __restrict__ rho_fx,
                                                          cplx_t<T>* __restrict__ Zxy,
                                                          const cplx_t<T>* __restrict__ tw_g, T scale,
-                                                         int zero_after) {
+                                                         int zero_after, unsigned long long* step_ctr) {
     using V = cplx_t<T>;
     constexpr int PITCH = row_pitch(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* plane = tw + N;
     load_twiddles(tw, tw_g, N);
+    // a step's first kernel advances the noise counter to n+1
+    if (step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1ull;
 
     const int z = blockIdx.x;
     const size_t M = (size_t)N * N * N;
@@ -142,7 +144,7 @@ template <typename T, int N, int R>
 __global__ void __launch_bounds__(256) x_forward_rows(unsigned long long* __restrict__ rho_fx,
                                                        cplx_t<T>* __restrict__ Zxy,
                                                        const cplx_t<T>* __restrict__ tw_g, T scale,
-                                                       int zero_after) {
+                                                       int zero_after, unsigned long long* step_ctr) {
     using V = cplx_t<T>;
     constexpr int PITCH = row_pitch(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(256) x_forward_rows(unsigned long long* __rest
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)blockIdx.x * R * N;
+    if (step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1ull;
     load_fixed_rows<N, PITCH, R, 256>(rho_fx + base, rho_fx + M + base, rows, scale, zero_after);
     __syncthreads();
     smem_fft_lines<N, -1, R, 256>(rows, StridedLines<PITCH>{}, 1, tw);
