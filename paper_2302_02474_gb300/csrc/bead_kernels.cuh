@@ -83,10 +83,11 @@ __host__ __device__ __forceinline__ int slot_bead_id(int v) { return v & 0x7ffff
 __host__ __device__ __forceinline__ int slot_species(int v) { return (int)((unsigned)v >> 31); }
 
 // Shared-memory patch of one tile: grid points [org, org + W) per dimension
-// with W = 8 cells + stencil reach + a drift margin of kMargin cells on
-// each side, so beads that moved up to kMargin cells since the last
-// re-binning still find their whole stencil inside.
-constexpr int kMargin = 1;
+// with W = 8 cells + stencil reach (+ an optional drift margin of kMargin
+// cells). Beads are re-binned every few steps and move a small fraction of
+// a cell per step, so nearly every bead's stencil lies inside its tile's
+// patch; the others take the global-memory path.
+constexpr int kMargin = 0;
 template <int P> struct Patch {
     static constexpr int W = kTile + stencil_extent<P>::hi - stencil_extent<P>::lo + 2 * kMargin;
     static constexpr int W3 = W * W * W;
@@ -167,7 +168,7 @@ __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_pat
     using PT = Patch<P>;
     using FP = FixedPoint<T>;
     if (in_patch) {
-        typename FP::patch_t* base = patch + K * PT::W3;
+        typename FP::patch_t* base = FP::packed ? patch : patch + K * PT::W3;
 #pragma unroll
         for (int c = 0; c < P; ++c)
 #pragma unroll
@@ -175,7 +176,7 @@ __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_pat
                 const T wyz = st.wy[b] * st.wz[c];
                 const int row = ((l.z + c) * PT::W + (l.y + b)) * PT::W + l.x;
 #pragma unroll
-                for (int a = 0; a < P; ++a) atomicAdd(base + row + a, FP::to_patch(st.wx[a] * wyz));
+                for (int a = 0; a < P; ++a) atomicAdd(base + row + a, FP::to_patch(st.wx[a] * wyz, K));
             }
     } else {
         const int nm = n - 1;
@@ -188,7 +189,7 @@ __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_pat
 #pragma unroll
                 for (int a = 0; a < P; ++a) {
                     const size_t g = ((size_t)((st.jz + c) & nm) * n + ((st.jy + b) & nm)) * n + ((st.jx + a) & nm);
-                    atomicAdd(rho_fx + K * M + g, (unsigned long long)FP::to_patch(st.wx[a] * wyz));
+                    atomicAdd(rho_fx + K * M + g, FP::to_grid(st.wx[a] * wyz));
                 }
             }
     }
@@ -209,8 +210,9 @@ template <int P, typename T> struct BeadSmem {
     static constexpr int W3 = Patch<P>::W3;
     // the gradient patch is staged when it is small (else gathered from global)
     static constexpr bool stage_grad = 3 * W3 * sizeof(cplx_t<T>) <= 48 * 1024;
-    static constexpr size_t patch_off = 0;                                                       // patch_t [2][W3]
-    static constexpr size_t grad_off = (patch_off + 2 * W3 * sizeof(patch_t) + 15) / 16 * 16;    // cplx [3][W3]
+    static constexpr int patches = FixedPoint<T>::packed ? 1 : 2;
+    static constexpr size_t patch_off = 0;                                                       // patch_t [patches][W3]
+    static constexpr size_t grad_off = (patch_off + patches * W3 * sizeof(patch_t) + 15) / 16 * 16;  // cplx [3][W3]
     static constexpr size_t pos_off = grad_off + (stage_grad ? 3 * W3 * sizeof(cplx_t<T>) : 0);  // T [3][chunk]
     static constexpr size_t nbr_off = pos_off + 3 * kBeadChunk * sizeof(T);                       // int2 [chunk]
     static constexpr size_t tag_off = nbr_off + kBeadChunk * sizeof(int2);                        // int [chunk]
@@ -252,19 +254,23 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
     const int3 org = {tx * kTile + PT::lo, ty * kTile + PT::lo, tz * kTile + PT::lo};
     const int nm = p.n - 1;
     const size_t M = (size_t)p.n * p.n * p.n;
-    const int lane16 = threadIdx.x & 15;
-    const int half = threadIdx.x >> 4;  // one patch row per 16 threads
-    const int nhalf = blockDim.x >> 4;
+    // patch rows of W points: RPW rows per warp, lane -> (row offset, x)
+    constexpr int RPW = 32 / W;
+    const int lane = threadIdx.x & 31;
+    const int rsub = lane / W, lx = lane - rsub * W;
+    const bool row_lane = rsub < RPW;
+    const int row0 = (threadIdx.x >> 5) * RPW + rsub;
+    const int rstride = (blockDim.x >> 5) * RPW;
+    const int gx = (org.x + lx) & nm;
     if (kSpread) {
-        for (int i = threadIdx.x; i < 2 * PT::W3; i += blockDim.x) patch[i] = 0;
+        for (int i = threadIdx.x; i < SM::patches * PT::W3; i += blockDim.x) patch[i] = 0;
     }
-    if (kForce && SM::stage_grad) {
-        // stage the gradient fields of the patch, one row of W points per 16 threads
-        const int gx = (org.x + lane16) & nm;
-        for (int row = half; row < 3 * W * W; row += nhalf) {
+    if (kForce && SM::stage_grad && row_lane) {
+        // stage the gradient fields of the patch
+        for (int row = row0; row < 3 * W * W; row += rstride) {
             int d;
             const size_t base = patch_row_base<P>(row, org, p.n, d);
-            if (lane16 < W) s_grad[row * W + lane16] = __ldg(bf.grad + d * M + base + gx);
+            s_grad[row * W + lx] = __ldg(bf.grad + d * M + base + gx);
         }
     }
     const int start = bf.tile_start[t];
@@ -395,14 +401,19 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
 
     if (kSpread) {
         __syncthreads();
-        const int gx = (org.x + lane16) & nm;
-        for (int row = half; row < 2 * W * W; row += nhalf) {
-            if (lane16 < W) {
-                const unsigned long long v = patch[row * W + lane16];
+        if (row_lane) {
+            for (int row = row0; row < SM::patches * W * W; row += rstride) {
+                const unsigned long long v = patch[row * W + lx];
                 if (v != 0ull) {
                     int K;
                     const size_t base = patch_row_base<P>(row, org, p.n, K);
-                    atomicAdd(bf.rho_fx + K * M + base + gx, v);
+                    if (FP::packed) {
+                        const unsigned long long a = v & 0xffffffffull, b = v >> 32;
+                        if (a) atomicAdd(bf.rho_fx + base + gx, a);
+                        if (b) atomicAdd(bf.rho_fx + M + base + gx, b);
+                    } else {
+                        atomicAdd(bf.rho_fx + K * M + base + gx, v);
+                    }
                 }
             }
         }
