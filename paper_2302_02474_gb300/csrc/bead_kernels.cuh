@@ -104,15 +104,21 @@ template <int P, typename T> struct Stencil {
     }
 };
 
-// -grad w_K interpolated at a bead, from the staged patch (in_patch) or
-// from global memory.
+template <typename T> struct vec4_of;
+template <> struct vec4_of<float> { using type = float4; };
+template <> struct vec4_of<double> { using type = double4; };
+
+// -grad w_K interpolated at a bead, from the staged patch (in_patch: one
+// (gx, gy, gz) record per point and species) or from global memory.
 template <int P, typename T>
-__device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_patch, int3 l, const cplx_t<T>* s_grad,
+__device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_patch, int3 l,
+                                             const typename vec4_of<T>::type* s_grad,
                                              const cplx_t<T>* __restrict__ grad, int n, int species, T& fx, T& fy,
                                              T& fz) {
     using PT = Patch<P>;
     T gx = 0, gy = 0, gz = 0;
     if (in_patch) {
+        const typename vec4_of<T>::type* sg = s_grad + species * PT::W3;
 #pragma unroll
         for (int c = 0; c < P; ++c)
 #pragma unroll
@@ -122,12 +128,10 @@ __device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_pa
 #pragma unroll
                 for (int a = 0; a < P; ++a) {
                     const T w = st.wx[a] * wyz;
-                    const cplx_t<T> vx = s_grad[row + a];
-                    const cplx_t<T> vy = s_grad[PT::W3 + row + a];
-                    const cplx_t<T> vz = s_grad[2 * PT::W3 + row + a];
-                    gx += w * (species ? vx.y : vx.x);
-                    gy += w * (species ? vy.y : vy.x);
-                    gz += w * (species ? vz.y : vz.x);
+                    const typename vec4_of<T>::type g = sg[row + a];
+                    gx += w * g.x;
+                    gy += w * g.y;
+                    gz += w * g.z;
                 }
             }
     } else {
@@ -168,7 +172,7 @@ __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_pat
     using PT = Patch<P>;
     using FP = FixedPoint<T>;
     if (in_patch) {
-        typename FP::patch_t* base = FP::packed ? patch : patch + K * PT::W3;
+        typename FP::patch_t* base = patch + K * PT::W3;
 #pragma unroll
         for (int c = 0; c < P; ++c)
 #pragma unroll
@@ -176,7 +180,7 @@ __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_pat
                 const T wyz = st.wy[b] * st.wz[c];
                 const int row = ((l.z + c) * PT::W + (l.y + b)) * PT::W + l.x;
 #pragma unroll
-                for (int a = 0; a < P; ++a) atomicAdd(base + row + a, FP::to_patch(st.wx[a] * wyz, K));
+                for (int a = 0; a < P; ++a) atomicAdd(base + row + a, FP::to_patch(st.wx[a] * wyz));
             }
     } else {
         const int nm = n - 1;
@@ -208,12 +212,13 @@ constexpr int kBeadChunk = 512;
 template <int P, typename T> struct BeadSmem {
     using patch_t = typename FixedPoint<T>::patch_t;
     static constexpr int W3 = Patch<P>::W3;
-    // the gradient patch is staged when it is small (else gathered from global)
-    static constexpr bool stage_grad = 3 * W3 * sizeof(cplx_t<T>) <= 48 * 1024;
-    static constexpr int patches = FixedPoint<T>::packed ? 1 : 2;
+    // the gradient patch ([2 species][W3] of (gx, gy, gz, -)) is staged when
+    // it is small (else gathered from global memory)
+    static constexpr bool stage_grad = 2 * W3 * sizeof(typename vec4_of<T>::type) <= 48 * 1024;
+    static constexpr int patches = 2;
     static constexpr size_t patch_off = 0;                                                       // patch_t [patches][W3]
-    static constexpr size_t grad_off = (patch_off + patches * W3 * sizeof(patch_t) + 15) / 16 * 16;  // cplx [3][W3]
-    static constexpr size_t pos_off = grad_off + (stage_grad ? 3 * W3 * sizeof(cplx_t<T>) : 0);  // T [3][chunk]
+    static constexpr size_t grad_off = (patch_off + patches * W3 * sizeof(patch_t) + 31) / 32 * 32;  // vec4 [2][W3]
+    static constexpr size_t pos_off = grad_off + (stage_grad ? 2 * W3 * sizeof(typename vec4_of<T>::type) : 0);
     static constexpr size_t nbr_off = pos_off + 3 * kBeadChunk * sizeof(T);                       // int2 [chunk]
     static constexpr size_t tag_off = nbr_off + kBeadChunk * sizeof(int2);                        // int [chunk]
     static constexpr size_t bytes = tag_off + kBeadChunk * sizeof(int);
@@ -244,7 +249,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
     constexpr bool kForce = (MODE != kModeSpread);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     patch_t* patch = reinterpret_cast<patch_t*>(smem_raw + SM::patch_off);
-    V* s_grad = reinterpret_cast<V*>(smem_raw + SM::grad_off);
+    using V4 = typename vec4_of<T>::type;
+    V4* s_grad = reinterpret_cast<V4*>(smem_raw + SM::grad_off);
     T* s_pos = reinterpret_cast<T*>(smem_raw + SM::pos_off);
     int2* s_nbr = reinterpret_cast<int2*>(smem_raw + SM::nbr_off);
     int* s_tag = reinterpret_cast<int*>(smem_raw + SM::tag_off);
@@ -266,11 +272,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
         for (int i = threadIdx.x; i < SM::patches * PT::W3; i += blockDim.x) patch[i] = 0;
     }
     if (kForce && SM::stage_grad && row_lane) {
-        // stage the gradient fields of the patch
-        for (int row = row0; row < 3 * W * W; row += rstride) {
-            int d;
-            const size_t base = patch_row_base<P>(row, org, p.n, d);
-            s_grad[row * W + lx] = __ldg(bf.grad + d * M + base + gx);
+        // stage the gradient fields of the patch as per-species (gx, gy, gz)
+        for (int row = row0; row < W * W; row += rstride) {
+            int unused;
+            const size_t g = patch_row_base<P>(row, org, p.n, unused) + gx;
+            const V vx = __ldg(bf.grad + g), vy = __ldg(bf.grad + M + g), vz = __ldg(bf.grad + 2 * M + g);
+            s_grad[row * W + lx] = V4{vx.x, vy.x, vz.x, T(0)};
+            s_grad[PT::W3 + row * W + lx] = V4{vx.y, vy.y, vz.y, T(0)};
         }
     }
     const int start = bf.tile_start[t];
@@ -407,13 +415,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
                 if (v != 0ull) {
                     int K;
                     const size_t base = patch_row_base<P>(row, org, p.n, K);
-                    if (FP::packed) {
-                        const unsigned long long a = v & 0xffffffffull, b = v >> 32;
-                        if (a) atomicAdd(bf.rho_fx + base + gx, a);
-                        if (b) atomicAdd(bf.rho_fx + M + base + gx, b);
-                    } else {
-                        atomicAdd(bf.rho_fx + K * M + base + gx, v);
-                    }
+                    atomicAdd(bf.rho_fx + K * M + base + gx, v);
                 }
             }
         }

@@ -37,28 +37,23 @@ template <class V> __device__ __forceinline__ V c_mul_posi(V a) { return {-a.y, 
 //   FP64 path: F = 44, 64-bit patch sums; quantisation <= 2^-45.
 // The global grid is 64-bit in both cases.
 template <typename T> struct FixedPoint;
-// FP32: one 64-bit shared word per patch point holds both species, A in the
-// low and B in the high 32 bits (no carry can cross below 1024 beads).
+// FP32: one 32-bit shared word per patch point and species.
 template <> struct FixedPoint<float> {
-    using patch_t = unsigned long long;
-    static constexpr bool packed = true;
+    using patch_t = unsigned int;
     static constexpr double scale = 4194304.0;  // 2^22
     static constexpr int max_tile_beads = 1023;
-    static __device__ __forceinline__ unsigned long long to_patch(float w, int K) {
-        return (unsigned long long)__float2uint_rn(w * 4194304.0f) << (32 * K);
-    }
-    static __device__ __forceinline__ unsigned long long to_grid(float w) { return __float2uint_rn(w * 4194304.0f); }
+    static __device__ __forceinline__ unsigned int to_patch(float w) { return __float2uint_rn(w * 4194304.0f); }
+    static __device__ __forceinline__ unsigned long long to_grid(float w) { return to_patch(w); }
 };
 // FP64: one 64-bit shared word per point and species.
 template <> struct FixedPoint<double> {
     using patch_t = unsigned long long;
-    static constexpr bool packed = false;
     static constexpr double scale = 17592186044416.0;  // 2^44
     static constexpr int max_tile_beads = 0x7fffffff;
-    static __device__ __forceinline__ unsigned long long to_patch(double w, int) {
+    static __device__ __forceinline__ unsigned long long to_patch(double w) {
         return (unsigned long long)__double2ll_rn(w * scale);
     }
-    static __device__ __forceinline__ unsigned long long to_grid(double w) { return to_patch(w, 0); }
+    static __device__ __forceinline__ unsigned long long to_grid(double w) { return to_patch(w); }
 };
 // Fixed point -> density (scale = 2^-F / dV); no FP64 in the FP32 path.
 __device__ __forceinline__ float from_fixed(long long v, float scale) { return __ll2float_rn(v) * scale; }

@@ -49,6 +49,7 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(cudaMalloc(&H_, 3 * M_ * sizeof(V)));
         TILD_CUDA(cudaMalloc(&grad_, 3 * M_ * sizeof(V)));
         TILD_CUDA(cudaMalloc(&tw_, n_ * sizeof(V)));
+        TILD_CUDA(cudaMalloc(&kernel1d_, n_ * sizeof(T)));
         TILD_CUDA(cudaMalloc(&counters_, 4 * sizeof(unsigned long long)));
         TILD_CUDA(cudaMemset(counters_, 0, 4 * sizeof(unsigned long long)));
         TILD_CUDA(cudaMemset(rho_fx_, 0, 2 * M_ * sizeof(unsigned long long)));
@@ -416,6 +417,8 @@ template <typename T> class Engine final : public EngineBase {
     V* H_ = nullptr;
     V* grad_ = nullptr;
     V* tw_ = nullptr;
+    T* kernel1d_ = nullptr;
+    double kernel_a_ = -1.0;
     V* spec_ = nullptr;
     unsigned long long* counters_ = nullptr;  // [0] noise step counter, [1] error flags
     double* partials_ = nullptr;
@@ -484,7 +487,7 @@ template <typename T> class Engine final : public EngineBase {
     void release() {
         invalidate_graph();
         free_beads();
-        void* ptrs[] = {rho_fx_, Zxy_, H_, grad_, tw_, spec_, counters_, partials_, counts_,
+        void* ptrs[] = {rho_fx_, Zxy_, H_, grad_, tw_, kernel1d_, spec_, counters_, partials_, counts_,
                         tile_start_, cursor_, block_sums_, aux_, stage_};
         for (void* p : ptrs) cudaFree(p);
         rho_fx_ = nullptr;
@@ -676,10 +679,10 @@ template <typename T> class Engine final : public EngineBase {
         const double rho0 = cfg_->n_beads / V;
         SpectralParams<T> sp;
         sp.two_pi_over_L = (T)(2.0 * 3.14159265358979323846 / cfg_->L);
-        sp.a2 = (T)(cfg_->a * cfg_->a);
         sp.eAA = (T)(cfg_->kappa / rho0 / (double)M_);
         sp.eBB = sp.eAA;
         sp.eAB = (T)((cfg_->chi + cfg_->kappa) / rho0 / (double)M_);
+        sp.kernel1d = kernel1d_;
         return sp;
     }
 
@@ -690,6 +693,18 @@ template <typename T> class Engine final : public EngineBase {
         return TILD_OK;
     }
     tild_status enqueue_zpass(double* partials, V* spec_out) {
+        if (kernel_a_ != cfg_->a) {
+            // exp(-a^2 k_m^2), k_m = 2 pi m / L with m in FFT index order
+            std::vector<T> e(n_);
+            for (int i = 0; i < n_; ++i) {
+                const double m = i < n_ / 2 ? i : i - n_;
+                const double k = 2.0 * 3.14159265358979323846 * m / cfg_->L;
+                e[i] = (T)std::exp(-cfg_->a * cfg_->a * k * k);
+            }
+            TILD_CUDA(cudaStreamSynchronize(stream_));  // no z pass may still read the old table
+            TILD_CUDA(cudaMemcpy(kernel1d_, e.data(), n_ * sizeof(T), cudaMemcpyHostToDevice));
+            kernel_a_ = cfg_->a;
+        }
         return dispatch_n([&](auto nn) { return this->template zpass_n<decltype(nn)::value>(partials, spec_out); });
     }
 

@@ -25,8 +25,8 @@ namespace tild {
 
 template <typename T> struct SpectralParams {
     T two_pi_over_L;   // 2 pi / L
-    T a2;              // a^2 (kernel exp(-|k|^2 a^2))
     T eAA, eAB, eBB;   // eps matrix / M (the 1/M of the inverse DFT folded in)
+    const T* kernel1d; // exp(-a^2 k_m^2) per 1-D frequency index m (FP64 on the host)
 };
 
 // Pitch (in complex elements) of a row of n elements in shared memory: odd
@@ -215,7 +215,9 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
     V* buf = tw + N;          // 3 buffers [N][C]: own, mirror, third
     const int TS = N * C;     // tile size
     __shared__ double red[2][32];
+    __shared__ T e1[N];       // separable Gaussian kernel: u_hat = e1[kx] e1[ky] e1[kz]
     load_twiddles(tw, tw_g, N);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) e1[i] = sp.kernel1d[i];
 
     const int c0 = blockIdx.x * C;
     const int ky = blockIdx.y;
@@ -258,8 +260,7 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
             const V Zm = s == 0 ? Mkm : Mk;  // Z(-k)
             const T kzv = sp.two_pi_over_L * (T)freq_index<T>(kzs, N);
             const T kzg = (kzs == N / 2) ? T(0) : kzv;
-            const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
-            const T uh = exp(-k2 * sp.a2);
+            const T uh = e1[kx] * e1[ky] * e1[kzs];
             // rho~_A = (Z + conj Zm)/2, rho~_B = -i (Z - conj Zm)/2
             const V A = {T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y)};
             const V B = {T(0.5) * (Z.y + Zm.y), -T(0.5) * (Z.x - Zm.x)};
