@@ -225,9 +225,41 @@ tild_status tild_profile_steps(tild_ctx* ctx, int n_steps, double* ms);
 /* Number of kernel launches one tild_step(ctx, n) issues for this context. */
 tild_status tild_launches_per_steps(tild_ctx* ctx, int64_t n_steps, int64_t* launches);
 
-/* Description of the last error on this context (or of the last failed
- * tild_create when ctx is NULL). Never NULL. */
+/* Description of the last error on this context (or, when ctx is NULL, of
+ * the last failed tild_create or tild_spread_density_noalloc). Never NULL. */
 const char* tild_last_error(tild_ctx* ctx);
+
+/*
+ * Allocation-free density assignment (the paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory, such as code
+ * running while a framework's caching allocator owns all device memory,
+ * plug-ins held to a fixed memory budget, or loops where an allocation, which
+ * can synchronise the device, is not acceptable).
+ *
+ * Computes the same species densities as tild_get_density, in FP32, for one
+ * set of beads, without a context and without allocating: the 64-bit
+ * fixed-point scratch grid is a static device array of 2 * 64^3 points
+ * (4 MiB) that every GPU which loads this library holds until the process
+ * exits.
+ *   xyz      device, [n_beads][3] FP32 positions (wrapped into [0, L) here).
+ *   species  device, [n_beads] bytes: 0 = A, anything else = B.
+ *   L        cubic box edge (> 0).
+ *   n        grid points per edge: a power of two in [8, 64]; larger grids
+ *            return TILD_EINVAL (the scratch is sized for 64^3).
+ *   pmeorder assignment order 1..4.
+ *   rho_out  device, [2][n][n][n] FP32 output (species A then B, [z][y][x]).
+ *   stream   cudaStream_t to order the work on (NULL = legacy default stream).
+ * Work is asynchronous on `stream`. The first call on a device looks up the
+ * device address of the scratch array (with that device current), so make
+ * that first call before any stream capture. Every call shares the one
+ * scratch array, which keeps the previous call's contents; each call clears
+ * the part it uses first. Calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on the scratch and must be serialised
+ * by the caller. Errors: TILD_EINVAL (NULL pointer, bad size or order),
+ * TILD_EDEVICE (a CUDA call failed); text in tild_last_error(NULL).
+ */
+tild_status tild_spread_density_noalloc(const float* xyz, const unsigned char* species, int64_t n_beads, double L,
+                                        int n, int pmeorder, float* rho_out, void* stream);
 
 #ifdef __cplusplus
 }

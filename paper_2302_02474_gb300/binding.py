@@ -74,6 +74,7 @@ _SIGS = {
     "tild_set_state": [_P, _P, ctypes.c_size_t],
     "tild_profile_steps": [_P, _I, ctypes.POINTER(ctypes.c_double)],
     "tild_launches_per_steps": [_P, _I64, ctypes.POINTER(_I64)],
+    "tild_spread_density_noalloc": [_P, _P, _I64, ctypes.c_double, _I, _I, _P, _P],
 }
 
 _lib: Optional[ctypes.CDLL] = None

@@ -38,6 +38,8 @@ bool valid_io(int dtype, int where) {
 
 }  // namespace
 
+void tild::set_global_error(const std::string& msg) { g_create_error = msg; }
+
 extern "C" {
 
 tild_status tild_create(const tild_params* p, tild_ctx** out) {

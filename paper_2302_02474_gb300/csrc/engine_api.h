@@ -60,6 +60,9 @@ class EngineBase {
     virtual void params_changed() = 0;
 };
 
+// Error text returned by tild_last_error(NULL).
+void set_global_error(const std::string& msg);
+
 EngineBase* make_engine_f32();
 EngineBase* make_engine_f64();
 
