@@ -40,7 +40,8 @@ template <typename T> class Engine final : public EngineBase {
         tiles_ = n_ / kTile;
         P_ = cfg->pmeorder + 1;
         plane_fits_ = plane_smem() <= 200 * 1024;
-        C_ = std::min(n_, (int)(128 / sizeof(V)));
+        C_ = std::min(n_, (int)(128 / sizeof(V)));  // y-column tiles of the split passes
+        CZ_ = std::min(n_, (int)(64 / sizeof(V)));   // column tiles of the z pass
         TILD_CUDA(cudaGetDevice(&device_));
         TILD_CUDA(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
         stream_ = own_stream_;
@@ -59,7 +60,7 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(cudaMalloc(&cursor_, (n_tiles_ + 1) * sizeof(int)));
         scan_blocks_ = (int)((n_tiles_ + 1 + 1023) / 1024);
         TILD_CUDA(cudaMalloc(&block_sums_, scan_blocks_ * sizeof(int)));
-        n_z_blocks_ = (size_t)(n_ / C_) * n_;
+        n_z_blocks_ = (size_t)(n_ / CZ_) * (n_ / 2 + 1);
         n_partials_ = std::max(2 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
         TILD_CUDA(cudaMalloc(&partials_, n_partials_ * sizeof(double)));
         // twiddles W_n^m = exp(-2 pi i m / n) in FP64, rounded to T
@@ -407,7 +408,7 @@ template <typename T> class Engine final : public EngineBase {
     T* vsave_ = nullptr;
     HostConfig* cfg_ = nullptr;
     int device_ = 0;
-    int n_ = 0, tiles_ = 0, P_ = 2, C_ = 16;
+    int n_ = 0, tiles_ = 0, P_ = 2, C_ = 16, CZ_ = 8;
     size_t M_ = 0;
     bool plane_fits_ = true;
     cudaStream_t own_stream_ = nullptr, stream_ = nullptr;
@@ -457,7 +458,7 @@ template <typename T> class Engine final : public EngineBase {
     size_t plane_smem() const { return ((size_t)n_ + (size_t)n_ * row_pitch(n_)) * sizeof(V); }
     size_t rows_smem() const { return ((size_t)n_ + (size_t)16 * row_pitch(n_)) * sizeof(V); }
     size_t ycol_smem() const { return ((size_t)n_ + (size_t)n_ * C_) * sizeof(V); }
-    size_t zpass_smem() const { return ((size_t)n_ + 3 * (size_t)n_ * C_) * sizeof(V); }
+    size_t zpass_smem() const { return ((size_t)n_ + 6 * (size_t)n_ * CZ_) * sizeof(V); }
     size_t bead_smem() const {
         switch (P_) {
             case 2: return bead_smem_bytes<2, T>();
@@ -598,7 +599,7 @@ template <typename T> class Engine final : public EngineBase {
             TILD_CUDA(cudaFuncSetAttribute(y_columns<T, NN, 128 / sizeof(V), -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ycol_smem()));
             TILD_CUDA(cudaFuncSetAttribute(y_columns<T, NN, 128 / sizeof(V), +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ycol_smem()));
         }
-        constexpr int CC = NN < (int)(128 / sizeof(V)) ? NN : (int)(128 / sizeof(V));
+        constexpr int CC = NN < (int)(64 / sizeof(V)) ? NN : (int)(64 / sizeof(V));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
         return TILD_OK;
     }
@@ -687,8 +688,8 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     template <int NN> tild_status zpass_n(double* partials, V* spec_out) {
-        constexpr int CC = NN < (int)(128 / sizeof(V)) ? NN : (int)(128 / sizeof(V));
-        z_spectral<T, NN, CC><<<dim3(NN / CC, NN), 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, spectral_params(), partials, spec_out);
+        constexpr int CC = NN < (int)(64 / sizeof(V)) ? NN : (int)(64 / sizeof(V));
+        z_spectral<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1), 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, spectral_params(), partials, spec_out);
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
     }

@@ -14,8 +14,9 @@
 //
 // Memory layouts (n^3 points, index g = (z n + y) n + x):
 //   rho_fx  int64 [2][M]             fixed-point densities (2^44 per bead weight)
-//   Zxy     complex [z][ky][kx]       after the forward x and y transforms
-//   H       complex [3][z][ky][kx]    after the z pass (z back in real space)
+//   Zxy     complex [z][ky][pos(kx)]  after the forward x and y transforms
+//   H       complex [3][z][ky][pos(kx)] after the z pass (z back in real space)
+// (pos(kx): mirror-paired column order, see kx_of_pos)
 //   grad    complex [3][z][y][x]      (d w_A, d w_B) per point and direction
 #pragma once
 
@@ -28,6 +29,8 @@ template <typename T> struct SpectralParams {
     T eAA, eAB, eBB;   // eps matrix / M (the 1/M of the inverse DFT folded in)
     const T* kernel1d; // exp(-a^2 k_m^2) per 1-D frequency index m (FP64 on the host)
 };
+
+template <int N> __host__ __device__ __forceinline__ int kx_of_pos(int p);
 
 // Pitch (in complex elements) of a row of n elements in shared memory: odd
 // so that threads on consecutive rows hit distinct banks.
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(512) xy_forward_plane(unsigned long long* __re
     smem_fft_lines<N, -1, N, 512>(plane, StridedLines<1>{}, PITCH, tw);  // along y
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
         const int y = i / N, x = i % N;
-        Zxy[base + i] = plane[y * PITCH + x];
+        Zxy[base + i] = plane[y * PITCH + kx_of_pos<N>(x)];  // mirror-paired column order
     }
 }
 
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restr
 
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)blockIdx.y * M + (size_t)blockIdx.x * N * N;
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) plane[(i / N) * PITCH + i % N] = H[base + i];
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) plane[(i / N) * PITCH + kx_of_pos<N>(i % N)] = H[base + i];
     __syncthreads();
     smem_fft_lines<N, +1, N, 512>(plane, StridedLines<1>{}, PITCH, tw);  // along y
     smem_fft_lines<N, +1, N, 512>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(256) x_forward_rows(unsigned long long* __rest
     load_fixed_rows<N, PITCH, R, 256>(rho_fx + base, rho_fx + M + base, rows, scale, zero_after);
     __syncthreads();
     smem_fft_lines<N, -1, R, 256>(rows, StridedLines<PITCH>{}, 1, tw);
-    for (int i = threadIdx.x; i < R * N; i += blockDim.x) Zxy[base + i] = rows[(i / N) * PITCH + i % N];
+    for (int i = threadIdx.x; i < R * N; i += blockDim.x) Zxy[base + i] = rows[(i / N) * PITCH + kx_of_pos<N>(i % N)];
 }
 
 template <typename T, int N, int R>
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)blockIdx.y * M + (size_t)blockIdx.x * R * N;
-    for (int i = threadIdx.x; i < R * N; i += blockDim.x) rows[(i / N) * PITCH + i % N] = H[base + i];
+    for (int i = threadIdx.x; i < R * N; i += blockDim.x) rows[(i / N) * PITCH + kx_of_pos<N>(i % N)] = H[base + i];
     __syncthreads();
     smem_fft_lines<N, +1, R, 256>(rows, StridedLines<PITCH>{}, 1, tw);
     for (int i = threadIdx.x; i < R * N; i += blockDim.x) grad[base + i] = rows[(i / N) * PITCH + i % N];
@@ -194,15 +197,84 @@ __global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, c
 }
 
 // --------------------------------------------------------------------------
-// z pass: forward DFT along z, spectral multiply + gradient, inverse DFT
-// along z. CTA (kx tile of C columns, ky). Loads its own tile and the
-// mirror tile (-kx, -ky) that Hermitian separation needs.
+// Column order of the xy-transformed arrays (Zxy and H): mirror pairs
+// (kx, -kx) are adjacent so that a tile of an even number of positions is
+// closed under kx -> -kx. Position 0 holds kx = 0, position 1 kx = n/2, and
+// positions 2k, 2k+1 hold kx = k and n - k (k = 1 .. n/2 - 1).
 // --------------------------------------------------------------------------
+template <int N> __host__ __device__ __forceinline__ int kx_of_pos(int p) {
+    return p == 0 ? 0 : p == 1 ? N / 2 : (p & 1) ? N - (p >> 1) : (p >> 1);
+}
+__host__ __device__ __forceinline__ int mirror_pos(int p) { return p < 2 ? p : (p ^ 1); }
+
 template <int C, int STRIDE> struct TileAddr {  // buffer b of a tile set starts at b * STRIDE
     __device__ __forceinline__ int operator()(int l) const { return (l / C) * STRIDE + l % C; }
 };
 
 template <typename T> __device__ __forceinline__ int freq_index(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// --------------------------------------------------------------------------
+// z pass: forward DFT along z, spectral multiply + gradient, inverse DFT
+// along z. CTA (tile of C column positions, ky pair {ky, -ky}); the tile
+// holds every column's mirror, so each CTA has Z(k) and Z(-k) for all of its
+// elements and transforms each input line once.
+//   R = 1 row when ky = -ky (ky = 0 or n/2), else 2 rows.
+//   buffers [3R][N][C]: output direction d of row r lives in buffer d*R + r
+//   (direction 0 overwrites the input rows in place).
+// --------------------------------------------------------------------------
+template <typename T, int N, int C, int R>
+__device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, const T* e1, const SpectralParams<T>& sp,
+                                       int p0, const int (&ky)[2], bool want_e, double& e_chi, double& e_kap) {
+    using V = cplx_t<T>;
+    constexpr int TS = N * C;
+    smem_fft_lines<N, -1, R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+    for (int q = threadIdx.x; q < C * N; q += blockDim.x) {
+        const int c = q % C, kz = q / C;
+        const int cB = mirror_pos(p0 + c) - p0;
+        const int kzB = (N - kz) & (N - 1);
+        constexpr int rB = R - 1;
+        if (R == 1 && kzB * C + cB < kz * C + c) continue;  // the mirror element owns this pair
+        const bool same = (R == 1) && (kzB == kz) && (cB == c);
+        const V ZA = buf[kz * C + c];
+        const V ZB = buf[rB * TS + kzB * C + cB];
+        V out[2][3];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (s == 1 && same) break;
+            const V Z = s == 0 ? ZA : ZB;   // Z(k)
+            const V Zm = s == 0 ? ZB : ZA;  // Z(-k)
+            const int kxi = kx_of_pos<N>(p0 + (s == 0 ? c : cB));
+            const int kyi = ky[s == 0 ? 0 : rB];
+            const int kzi = s == 0 ? kz : kzB;
+            const T kxv = (kxi == N / 2) ? T(0) : sp.two_pi_over_L * (T)freq_index<T>(kxi, N);
+            const T kyv = (kyi == N / 2) ? T(0) : sp.two_pi_over_L * (T)freq_index<T>(kyi, N);
+            const T kzv = (kzi == N / 2) ? T(0) : sp.two_pi_over_L * (T)freq_index<T>(kzi, N);
+            const T uh = e1[kxi] * e1[kyi] * e1[kzi];
+            // rho~_A = (Z + conj Zm)/2, rho~_B = -i (Z - conj Zm)/2
+            const V A = {T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y)};
+            const V B = {T(0.5) * (Z.y + Zm.y), -T(0.5) * (Z.x - Zm.x)};
+            if (want_e) {
+                const double ar = A.x, ai = A.y, br = B.x, bi = B.y;
+                e_chi += (double)uh * (ar * br + ai * bi);
+                if (!(kxi == 0 && kyi == 0 && kzi == 0))
+                    e_kap += (double)uh * ((ar + br) * (ar + br) + (ai + bi) * (ai + bi));
+            }
+            const V wA = {uh * (sp.eAA * A.x + sp.eAB * B.x), uh * (sp.eAA * A.y + sp.eAB * B.y)};
+            const V wB = {uh * (sp.eAB * A.x + sp.eBB * B.x), uh * (sp.eAB * A.y + sp.eBB * B.y)};
+            const V iQ = {-(wA.y + wB.x), wA.x - wB.y};  // i (w~_A + i w~_B)
+            out[s][0] = {kxv * iQ.x, kxv * iQ.y};
+            out[s][1] = {kyv * iQ.x, kyv * iQ.y};
+            out[s][2] = {kzv * iQ.x, kzv * iQ.y};
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            buf[(d * R) * TS + kz * C + c] = out[0][d];
+            if (!same) buf[(d * R + rB) * TS + kzB * C + cB] = out[1][d];
+        }
+    }
+    __syncthreads();
+    smem_fft_lines<N, +1, 3 * R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+}
 
 template <typename T, int N, int C>
 __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ Zxy, cplx_t<T>* __restrict__ H,
@@ -212,78 +284,43 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
-    V* buf = tw + N;          // 3 buffers [N][C]: own, mirror, third
-    const int TS = N * C;     // tile size
-    __shared__ double red[2][32];
-    __shared__ T e1[N];       // separable Gaussian kernel: u_hat = e1[kx] e1[ky] e1[kz]
+    V* buf = tw + N;
+    constexpr int TS = N * C;
+    __shared__ double red[2][8];
+    __shared__ T e1[N];  // separable Gaussian kernel: u_hat = e1[kx] e1[ky] e1[kz]
     load_twiddles(tw, tw_g, N);
     for (int i = threadIdx.x; i < N; i += blockDim.x) e1[i] = sp.kernel1d[i];
 
-    const int c0 = blockIdx.x * C;
-    const int ky = blockIdx.y;
-    const int kym = (N - ky) & (N - 1);
+    const int p0 = blockIdx.x * C;
+    const int ky[2] = {(int)blockIdx.y, (N - (int)blockIdx.y) & (N - 1)};
+    const int R = (ky[0] == ky[1]) ? 1 : 2;
     const size_t NN = (size_t)N * N;
-    for (int i = threadIdx.x; i < TS; i += blockDim.x) {
-        const int z = i / C, c = i % C;
-        const int kx = c0 + c;
-        const int kxm = (N - kx) & (N - 1);
-        buf[i] = Zxy[z * NN + (size_t)ky * N + kx];
-        buf[TS + i] = Zxy[z * NN + (size_t)kym * N + kxm];
+    for (int i = threadIdx.x; i < R * TS; i += blockDim.x) {
+        const int r = i / TS, rem = i % TS;
+        const int z = rem / C, c = rem % C;
+        buf[i] = Zxy[z * NN + (size_t)ky[r] * N + p0 + c];
     }
     __syncthreads();
-    smem_fft_lines<N, -1, 2 * C, 256>(buf, TileAddr<C, N * C>{}, C, tw);
-
-    if (spectrum_out) {
-        for (int i = threadIdx.x; i < TS; i += blockDim.x)
-            spectrum_out[(i / C) * NN + (size_t)ky * N + c0 + i % C] = buf[i];
-    }
-
-    const int my = freq_index<T>(ky, N);
-    const T kyv = sp.two_pi_over_L * (T)my;
-    const T kyg = (ky == N / 2) ? T(0) : kyv;
     double e_chi = 0.0, e_kap = 0.0;
-    // pairs (kz, -kz): each thread owns both so in-place writes are safe
-    for (int p = threadIdx.x; p < C * (N / 2 + 1); p += blockDim.x) {
-        const int c = p % C, kz = p / C;
-        const int kzm = (N - kz) & (N - 1);
-        const int kx = c0 + c;
-        const int mx = freq_index<T>(kx, N);
-        const T kxv = sp.two_pi_over_L * (T)mx;
-        const T kxg = (kx == N / 2) ? T(0) : kxv;
-        const V Zk = buf[kz * C + c], Zkm = buf[kzm * C + c];
-        const V Mk = buf[TS + kz * C + c], Mkm = buf[TS + kzm * C + c];
-        V out[2][3];
-        const int nsel = (kzm == kz) ? 1 : 2;
-        for (int s = 0; s < nsel; ++s) {
-            const int kzs = s == 0 ? kz : kzm;
-            const V Z = s == 0 ? Zk : Zkm;   // Z(k)
-            const V Zm = s == 0 ? Mkm : Mk;  // Z(-k)
-            const T kzv = sp.two_pi_over_L * (T)freq_index<T>(kzs, N);
-            const T kzg = (kzs == N / 2) ? T(0) : kzv;
-            const T uh = e1[kx] * e1[ky] * e1[kzs];
-            // rho~_A = (Z + conj Zm)/2, rho~_B = -i (Z - conj Zm)/2
-            const V A = {T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y)};
-            const V B = {T(0.5) * (Z.y + Zm.y), -T(0.5) * (Z.x - Zm.x)};
-            if (energy_partials) {
-                const double ar = A.x, ai = A.y, br = B.x, bi = B.y;
-                e_chi += (double)uh * (ar * br + ai * bi);
-                if (!(kx == 0 && ky == 0 && kzs == 0))
-                    e_kap += (double)uh * ((ar + br) * (ar + br) + (ai + bi) * (ai + bi));
-            }
-            const V wA = {uh * (sp.eAA * A.x + sp.eAB * B.x), uh * (sp.eAA * A.y + sp.eAB * B.y)};
-            const V wB = {uh * (sp.eAB * A.x + sp.eBB * B.x), uh * (sp.eAB * A.y + sp.eBB * B.y)};
-            const V Q = {wA.x - wB.y, wA.y + wB.x};      // w~_A + i w~_B
-            const V iQ = {-Q.y, Q.x};                     // i Q
-            out[s][0] = {kxg * iQ.x, kxg * iQ.y};
-            out[s][1] = {kyg * iQ.x, kyg * iQ.y};
-            out[s][2] = {kzg * iQ.x, kzg * iQ.y};
+    const bool want_e = energy_partials != nullptr;
+    if (spectrum_out) {
+        // forward transform only, written out in natural kx order
+        if (R == 1)
+            smem_fft_lines<N, -1, C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+        else
+            smem_fft_lines<N, -1, 2 * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+        for (int i = threadIdx.x; i < R * TS; i += blockDim.x) {
+            const int r = i / TS, rem = i % TS;
+            const int z = rem / C, c = rem % C;
+            spectrum_out[z * NN + (size_t)ky[r] * N + kx_of_pos<N>(p0 + c)] = buf[i];
         }
-        for (int s = 0; s < nsel; ++s) {
-            const int kzs = s == 0 ? kz : kzm;
-            for (int d = 0; d < 3; ++d) buf[d * TS + kzs * C + c] = out[s][d];
-        }
+        return;
     }
-    if (energy_partials) {
+    if (R == 1)
+        z_tile<T, N, C, 1>(buf, tw, e1, sp, p0, ky, want_e, e_chi, e_kap);
+    else
+        z_tile<T, N, C, 2>(buf, tw, e1, sp, p0, ky, want_e, e_chi, e_kap);
+    if (want_e) {
         // block reduction in a fixed order (deterministic)
         for (int o = 16; o > 0; o >>= 1) {
             e_chi += __shfl_down_sync(0xffffffffu, e_chi, o);
@@ -294,23 +331,24 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
             red[0][wid] = e_chi;
             red[1][wid] = e_kap;
         }
-    }
-    __syncthreads();
-    if (energy_partials && threadIdx.x == 0) {
-        double s0 = 0, s1 = 0;
-        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
-            s0 += red[0][w];
-            s1 += red[1][w];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s0 = 0, s1 = 0;
+            for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
+                s0 += red[0][w];
+                s1 += red[1][w];
+            }
+            const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+            energy_partials[2 * b] = s0;
+            energy_partials[2 * b + 1] = s1;
         }
-        const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-        energy_partials[2 * b] = s0;
-        energy_partials[2 * b + 1] = s1;
     }
-    smem_fft_lines<N, +1, 3 * C, 256>(buf, TileAddr<C, N * C>{}, C, tw);
     const size_t M = NN * N;
-    for (int i = threadIdx.x; i < 3 * TS; i += blockDim.x) {
-        const int d = i / TS, r = i % TS;
-        H[d * M + (r / C) * NN + (size_t)ky * N + c0 + r % C] = buf[i];
+    for (int i = threadIdx.x; i < 3 * R * TS; i += blockDim.x) {
+        const int b = i / TS, rem = i % TS;
+        const int d = b / R, r = b % R;
+        const int z = rem / C, c = rem % C;
+        H[d * M + z * NN + (size_t)ky[r] * N + p0 + c] = buf[i];
     }
 }
 
