@@ -41,7 +41,7 @@ template <typename T> class Engine final : public EngineBase {
         P_ = cfg->pmeorder + 1;
         plane_fits_ = plane_smem() <= 200 * 1024;
         C_ = std::min(n_, (int)(128 / sizeof(V)));  // y-column tiles of the split passes
-        CZ_ = std::min(n_, (int)(64 / sizeof(V)));   // column tiles of the z pass
+        CZ_ = std::min(n_, (int)(128 / sizeof(V)));  // column tiles of the z pass
         TILD_CUDA(cudaGetDevice(&device_));
         TILD_CUDA(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
         stream_ = own_stream_;
@@ -457,8 +457,8 @@ template <typename T> class Engine final : public EngineBase {
 
     size_t plane_smem() const { return ((size_t)n_ + (size_t)n_ * row_pitch(n_)) * sizeof(V); }
     size_t rows_smem() const { return ((size_t)n_ + (size_t)16 * row_pitch(n_)) * sizeof(V); }
-    size_t ycol_smem() const { return ((size_t)n_ + (size_t)n_ * C_) * sizeof(V); }
-    size_t zpass_smem() const { return ((size_t)n_ + 6 * (size_t)n_ * CZ_) * sizeof(V); }
+    size_t ycol_smem() const { return ((size_t)n_ + 2 * (size_t)n_ * C_) * sizeof(V); }
+    size_t zpass_smem() const { return ((size_t)n_ + 4 * (size_t)n_ * CZ_) * sizeof(V); }
     size_t bead_smem() const {
         switch (P_) {
             case 2: return bead_smem_bytes<2, T>();
@@ -599,7 +599,7 @@ template <typename T> class Engine final : public EngineBase {
             TILD_CUDA(cudaFuncSetAttribute(y_columns<T, NN, 128 / sizeof(V), -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ycol_smem()));
             TILD_CUDA(cudaFuncSetAttribute(y_columns<T, NN, 128 / sizeof(V), +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ycol_smem()));
         }
-        constexpr int CC = NN < (int)(64 / sizeof(V)) ? NN : (int)(64 / sizeof(V));
+        constexpr int CC = NN < (int)(128 / sizeof(V)) ? NN : (int)(128 / sizeof(V));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
         return TILD_OK;
     }
@@ -665,7 +665,7 @@ template <typename T> class Engine final : public EngineBase {
             if constexpr (NN >= 16 && NN >= CC) {
                 x_forward_rows<T, NN, 16><<<(unsigned)((size_t)NN * NN / 16), 256, rows_smem(), stream_>>>(
                     rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0, zero_after ? counters_ : nullptr);
-                y_columns<T, NN, CC, -1><<<dim3(NN / CC, NN, 1), 256, ycol_smem(), stream_>>>(Zxy_, tw_);
+                y_columns<T, NN, CC, -1><<<dim3(NN / CC, NN, 1), 256, ycol_smem(), stream_>>>(Zxy_, tw_, two_pi_L());
             }
         }
         TILD_CUDA(cudaGetLastError());
@@ -674,6 +674,8 @@ template <typename T> class Engine final : public EngineBase {
     tild_status enqueue_forward(bool zero_after) {
         return dispatch_n([&](auto nn) { return this->template forward_n<decltype(nn)::value>(zero_after); });
     }
+
+    T two_pi_L() const { return (T)(2.0 * 3.14159265358979323846 / cfg_->L); }
 
     SpectralParams<T> spectral_params() const {
         const double V = cfg_->L * cfg_->L * cfg_->L;
@@ -688,7 +690,7 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     template <int NN> tild_status zpass_n(double* partials, V* spec_out) {
-        constexpr int CC = NN < (int)(64 / sizeof(V)) ? NN : (int)(64 / sizeof(V));
+        constexpr int CC = NN < (int)(128 / sizeof(V)) ? NN : (int)(128 / sizeof(V));
         z_spectral<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1), 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, spectral_params(), partials, spec_out);
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
@@ -712,13 +714,13 @@ template <typename T> class Engine final : public EngineBase {
     template <int NN> tild_status inverse_n() {
         if (plane_fits_) {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
-                xy_inverse_plane<T, NN><<<dim3(NN, 3), 512, plane_smem(), stream_>>>(H_, grad_, tw_);
+                xy_inverse_plane<T, NN><<<dim3(NN, 3), 512, plane_smem(), stream_>>>(H_, grad_, tw_, two_pi_L());
             }
         } else {
             constexpr int CC = 128 / sizeof(V);
             if constexpr (NN >= 16 && NN >= CC) {
-                y_columns<T, NN, CC, +1><<<dim3(NN / CC, NN, 3), 256, ycol_smem(), stream_>>>(H_, tw_);
-                x_inverse_rows<T, NN, 16><<<dim3((unsigned)((size_t)NN * NN / 16), 3), 256, rows_smem(), stream_>>>(H_, grad_, tw_);
+                y_columns<T, NN, CC, +1><<<dim3(NN / CC, NN, 2), 256, ycol_smem(), stream_>>>(H_, tw_, two_pi_L());
+                x_inverse_rows<T, NN, 16><<<dim3((unsigned)((size_t)NN * NN / 16), 3), 256, rows_smem(), stream_>>>(H_, grad_, tw_, two_pi_L());
             }
         }
         TILD_CUDA(cudaGetLastError());

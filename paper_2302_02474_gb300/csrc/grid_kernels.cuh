@@ -32,6 +32,12 @@ template <typename T> struct SpectralParams {
 
 template <int N> __host__ __device__ __forceinline__ int kx_of_pos(int p);
 
+// Wavenumber used for spectral differentiation at FFT index i: 2 pi m / L
+// with m = i (i < n/2) or i - n, and 0 at the Nyquist index n/2.
+template <typename T, int N> __device__ __forceinline__ T grad_k(int i, T two_pi_over_L) {
+    return i == N / 2 ? T(0) : two_pi_over_L * (T)(i < N / 2 ? i : i - N);
+}
+
 // Pitch (in complex elements) of a row of n elements in shared memory: odd
 // so that threads on consecutive rows hit distinct banks.
 __host__ __device__ constexpr int row_pitch(int n) { return n + 1; }
@@ -122,7 +128,7 @@ __global__ void __launch_bounds__(512) xy_forward_plane(unsigned long long* __re
 template <typename T, int N>
 __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restrict__ H,
                                                          cplx_t<T>* __restrict__ grad,
-                                                         const cplx_t<T>* __restrict__ tw_g) {
+                                                         const cplx_t<T>* __restrict__ tw_g, T two_pi_over_L) {
     using V = cplx_t<T>;
     constexpr int PITCH = row_pitch(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -130,13 +136,28 @@ __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restr
     V* plane = tw + N;
     load_twiddles(tw, tw_g, N);
 
+    // direction d: x from i k_x G, y from i k_y G, z from G_z (field 2)
+    const int d = blockIdx.y;
     const size_t M = (size_t)N * N * N;
-    const size_t base = (size_t)blockIdx.y * M + (size_t)blockIdx.x * N * N;
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) plane[(i / N) * PITCH + kx_of_pos<N>(i % N)] = H[base + i];
+    const size_t src = (d == 2 ? 2 * M : 0) + (size_t)blockIdx.x * N * N;
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        const int ky = i / N;
+        V v = H[src + i];
+        if (d == 1) v = c_scale(v, grad_k<T, N>(ky, two_pi_over_L));
+        plane[ky * PITCH + kx_of_pos<N>(i % N)] = v;
+    }
     __syncthreads();
     smem_fft_lines<N, +1, N, 512>(plane, StridedLines<1>{}, PITCH, tw);  // along y
+    if (d == 0) {
+        for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+            const int y = i / N, kx = i % N;
+            plane[y * PITCH + kx] = c_scale(plane[y * PITCH + kx], grad_k<T, N>(kx, two_pi_over_L));
+        }
+        __syncthreads();
+    }
     smem_fft_lines<N, +1, N, 512>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) grad[base + i] = plane[(i / N) * PITCH + i % N];
+    const size_t dst = (size_t)d * M + (size_t)blockIdx.x * N * N;
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) grad[dst + i] = plane[(i / N) * PITCH + i % N];
 }
 
 // --------------------------------------------------------------------------
@@ -165,7 +186,7 @@ __global__ void __launch_bounds__(256) x_forward_rows(unsigned long long* __rest
 
 template <typename T, int N, int R>
 __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restrict__ H, cplx_t<T>* __restrict__ grad,
-                                                       const cplx_t<T>* __restrict__ tw_g) {
+                                                       const cplx_t<T>* __restrict__ tw_g, T two_pi_over_L) {
     using V = cplx_t<T>;
     constexpr int PITCH = row_pitch(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -174,26 +195,52 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)blockIdx.y * M + (size_t)blockIdx.x * R * N;
-    for (int i = threadIdx.x; i < R * N; i += blockDim.x) rows[(i / N) * PITCH + kx_of_pos<N>(i % N)] = H[base + i];
+    const bool kx_mult = blockIdx.y == 0;  // d_x: multiply by k_x before the x transform
+    for (int i = threadIdx.x; i < R * N; i += blockDim.x) {
+        const int kx = kx_of_pos<N>(i % N);
+        V v = H[base + i];
+        if (kx_mult) v = c_scale(v, grad_k<T, N>(kx, two_pi_over_L));
+        rows[(i / N) * PITCH + kx] = v;
+    }
     __syncthreads();
     smem_fft_lines<N, +1, R, 256>(rows, StridedLines<PITCH>{}, 1, tw);
     for (int i = threadIdx.x; i < R * N; i += blockDim.x) grad[base + i] = rows[(i / N) * PITCH + i % N];
 }
 
-// Column pass along y, in place: CTA (x tile, z, field) handles C columns.
+// Column pass along y: CTA (x tile, z plane, part) handles C columns.
+// Forward (DIR = -1, part 0): Zxy in place.
+// Inverse (DIR = +1) on H: part 0 loads a tile of G (field 0) and writes
+// the transforms of G (field 0) and of i k_y G (field 1) from the same
+// load; part 1 transforms G_z (field 2) in place.
 template <typename T, int N, int C, int DIR>
-__global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, const cplx_t<T>* __restrict__ tw_g) {
+__global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, const cplx_t<T>* __restrict__ tw_g,
+                                                 T two_pi_over_L) {
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
-    V* tile = tw + N;  // [y][c]
+    V* tile = tw + N;  // [2][y][c]
+    constexpr int TS = N * C;
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
-    const size_t base = (size_t)blockIdx.z * M + (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * C;
-    for (int i = threadIdx.x; i < N * C; i += blockDim.x) tile[i] = data[base + (size_t)(i / C) * N + i % C];
+    const bool two = DIR > 0 && blockIdx.z == 0;
+    const size_t off = (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * C;
+    const size_t src = (DIR > 0 && blockIdx.z == 1 ? 2 * M : 0) + off;
+    for (int i = threadIdx.x; i < TS; i += blockDim.x) {
+        const V v = data[src + (size_t)(i / C) * N + i % C];
+        tile[i] = v;
+        if (two) tile[TS + i] = c_scale(v, grad_k<T, N>(i / C, two_pi_over_L));
+    }
     __syncthreads();
-    smem_fft_lines<N, DIR, C, 256>(tile, StridedLines<1>{}, C, tw);
-    for (int i = threadIdx.x; i < N * C; i += blockDim.x) data[base + (size_t)(i / C) * N + i % C] = tile[i];
+    if (two) {
+        smem_fft_lines<N, DIR, 2 * C, 256>(tile, StridedLines<1>{}, C, tw);
+        for (int i = threadIdx.x; i < TS; i += blockDim.x) {
+            data[off + (size_t)(i / C) * N + i % C] = tile[i];
+            data[M + off + (size_t)(i / C) * N + i % C] = tile[TS + i];
+        }
+    } else {
+        smem_fft_lines<N, DIR, C, 256>(tile, StridedLines<1>{}, C, tw);
+        for (int i = threadIdx.x; i < TS; i += blockDim.x) data[src + (size_t)(i / C) * N + i % C] = tile[i];
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -219,8 +266,11 @@ template <typename T> __device__ __forceinline__ int freq_index(int i, int n) { 
 // holds every column's mirror, so each CTA has Z(k) and Z(-k) for all of its
 // elements and transforms each input line once.
 //   R = 1 row when ky = -ky (ky = 0 or n/2), else 2 rows.
-//   buffers [3R][N][C]: output direction d of row r lives in buffer d*R + r
-//   (direction 0 overwrites the input rows in place).
+// Outputs (linearity: k_x and k_y are constant along a z line):
+//   G   = IDFT_z[ i Q ]       (field 0; d_x and d_y follow in the xy pass)
+//   G_z = IDFT_z[ i k_z Q ]   (field 2)
+// with Q = w~_A + i w~_B. Buffers [2R][N][C]: G of row r in buffer r
+// (overwriting the input), G_z in buffer R + r.
 // --------------------------------------------------------------------------
 template <typename T, int N, int C, int R>
 __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, const T* e1, const SpectralParams<T>& sp,
@@ -237,7 +287,7 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
         const bool same = (R == 1) && (kzB == kz) && (cB == c);
         const V ZA = buf[kz * C + c];
         const V ZB = buf[rB * TS + kzB * C + cB];
-        V out[2][3];
+        V out[2][2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (s == 1 && same) break;
@@ -246,8 +296,6 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
             const int kxi = kx_of_pos<N>(p0 + (s == 0 ? c : cB));
             const int kyi = ky[s == 0 ? 0 : rB];
             const int kzi = s == 0 ? kz : kzB;
-            const T kxv = (kxi == N / 2) ? T(0) : sp.two_pi_over_L * (T)freq_index<T>(kxi, N);
-            const T kyv = (kyi == N / 2) ? T(0) : sp.two_pi_over_L * (T)freq_index<T>(kyi, N);
             const T kzv = (kzi == N / 2) ? T(0) : sp.two_pi_over_L * (T)freq_index<T>(kzi, N);
             const T uh = e1[kxi] * e1[kyi] * e1[kzi];
             // rho~_A = (Z + conj Zm)/2, rho~_B = -i (Z - conj Zm)/2
@@ -262,18 +310,17 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
             const V wA = {uh * (sp.eAA * A.x + sp.eAB * B.x), uh * (sp.eAA * A.y + sp.eAB * B.y)};
             const V wB = {uh * (sp.eAB * A.x + sp.eBB * B.x), uh * (sp.eAB * A.y + sp.eBB * B.y)};
             const V iQ = {-(wA.y + wB.x), wA.x - wB.y};  // i (w~_A + i w~_B)
-            out[s][0] = {kxv * iQ.x, kxv * iQ.y};
-            out[s][1] = {kyv * iQ.x, kyv * iQ.y};
-            out[s][2] = {kzv * iQ.x, kzv * iQ.y};
+            out[s][0] = iQ;                               // x, y: k_x, k_y applied in the xy pass
+            out[s][1] = {kzv * iQ.x, kzv * iQ.y};         // z
         }
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
+        for (int d = 0; d < 2; ++d) {
             buf[(d * R) * TS + kz * C + c] = out[0][d];
             if (!same) buf[(d * R + rB) * TS + kzB * C + cB] = out[1][d];
         }
     }
     __syncthreads();
-    smem_fft_lines<N, +1, 3 * R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+    smem_fft_lines<N, +1, 2 * R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
 }
 
 template <typename T, int N, int C>
@@ -344,11 +391,11 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
         }
     }
     const size_t M = NN * N;
-    for (int i = threadIdx.x; i < 3 * R * TS; i += blockDim.x) {
+    for (int i = threadIdx.x; i < 2 * R * TS; i += blockDim.x) {
         const int b = i / TS, rem = i % TS;
-        const int d = b / R, r = b % R;
+        const int f = (b / R) * 2, r = b % R;  // fields 0 (G) and 2 (G_z)
         const int z = rem / C, c = rem % C;
-        H[d * M + z * NN + (size_t)ky[r] * N + p0 + c] = buf[i];
+        H[f * M + z * NN + (size_t)ky[r] * N + p0 + c] = buf[i];
     }
 }
 
