@@ -31,6 +31,7 @@ template <typename T> struct SpectralParams {
 };
 
 template <int N> __host__ __device__ __forceinline__ int kx_of_pos(int p);
+template <int C, int STRIDE> struct TileAddr;
 
 // Wavenumber used for spectral differentiation at FFT index i: 2 pi m / L
 // with m = i (i < n/2) or i - n, and 0 at the Nyquist index n/2.
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, c
     }
     __syncthreads();
     if (two) {
-        smem_fft_lines<N, DIR, 2 * C, 256>(tile, StridedLines<1>{}, C, tw);
+        smem_fft_lines<N, DIR, 2 * C, 256>(tile, TileAddr<C, TS>{}, C, tw);
         for (int i = threadIdx.x; i < TS; i += blockDim.x) {
             data[off + (size_t)(i / C) * N + i % C] = tile[i];
             data[M + off + (size_t)(i / C) * N + i % C] = tile[TS + i];
