@@ -272,13 +272,29 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
         for (int i = threadIdx.x; i < SM::patches * PT::W3; i += blockDim.x) patch[i] = 0;
     }
     if (kForce && SM::stage_grad && row_lane) {
-        // stage the gradient fields of the patch as per-species (gx, gy, gz)
-        for (int row = row0; row < W * W; row += rstride) {
-            int unused;
-            const size_t g = patch_row_base<P>(row, org, p.n, unused) + gx;
-            const V vx = __ldg(bf.grad + g), vy = __ldg(bf.grad + M + g), vz = __ldg(bf.grad + 2 * M + g);
-            s_grad[row * W + lx] = V4{vx.x, vy.x, vz.x, T(0)};
-            s_grad[PT::W3 + row * W + lx] = V4{vx.y, vy.y, vz.y, T(0)};
+        // stage the gradient fields of the patch as per-species (gx, gy, gz);
+        // every row's loads are issued before any is used
+        constexpr int NWARP = 8;  // 256 threads
+        constexpr int ROWS_PER_LANE = (W * W + NWARP * RPW - 1) / (NWARP * RPW);
+        V v[ROWS_PER_LANE][3];
+#pragma unroll
+        for (int k = 0; k < ROWS_PER_LANE; ++k) {
+            const int row = row0 + k * rstride;
+            if (row < W * W) {
+                int unused;
+                const size_t g = patch_row_base<P>(row, org, p.n, unused) + gx;
+                v[k][0] = __ldg(bf.grad + g);
+                v[k][1] = __ldg(bf.grad + M + g);
+                v[k][2] = __ldg(bf.grad + 2 * M + g);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < ROWS_PER_LANE; ++k) {
+            const int row = row0 + k * rstride;
+            if (row < W * W) {
+                s_grad[row * W + lx] = V4{v[k][0].x, v[k][1].x, v[k][2].x, T(0)};
+                s_grad[PT::W3 + row * W + lx] = V4{v[k][0].y, v[k][1].y, v[k][2].y, T(0)};
+            }
         }
     }
     const int start = bf.tile_start[t];
@@ -292,12 +308,34 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
     for (int c0 = start; c0 < end; c0 += kBeadChunk) {
         const int cnt = min(kBeadChunk, end - c0);
         if (c0 != start) __syncthreads();  // the previous chunk is done with the staged beads
-        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-            s_pos[j] = bf.px[c0 + j];
-            s_pos[kBeadChunk + j] = bf.py[c0 + j];
-            s_pos[2 * kBeadChunk + j] = bf.pz[c0 + j];
-            s_tag[j] = bf.id[c0 + j];
-            if (kForce) s_nbr[j] = bf.nbr[c0 + j];
+        {
+            // all loads of the chunk in flight before the shared stores
+            constexpr int PER = kBeadChunk / 256;
+            T vx[PER], vy[PER], vz[PER];
+            int vt[PER];
+            int2 vn[PER];
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int j = threadIdx.x + k * 256;
+                if (j < cnt) {
+                    vx[k] = bf.px[c0 + j];
+                    vy[k] = bf.py[c0 + j];
+                    vz[k] = bf.pz[c0 + j];
+                    vt[k] = bf.id[c0 + j];
+                    if (kForce) vn[k] = bf.nbr[c0 + j];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int j = threadIdx.x + k * 256;
+                if (j < cnt) {
+                    s_pos[j] = vx[k];
+                    s_pos[kBeadChunk + j] = vy[k];
+                    s_pos[2 * kBeadChunk + j] = vz[k];
+                    s_tag[j] = vt[k];
+                    if (kForce) s_nbr[j] = vn[k];
+                }
+            }
         }
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += blockDim.x) {

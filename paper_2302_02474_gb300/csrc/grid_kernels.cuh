@@ -52,6 +52,28 @@ template <int N, int THREADS> __host__ __device__ constexpr int upt_for(int line
     return (lines * fft_split<N>::N1 + THREADS - 1) / THREADS;
 }
 
+// Copy COUNT elements from global to shared memory with up to 16
+// independent loads in flight per thread: dst(i, value) stores element i.
+template <int COUNT, int NTHR, class V, class Src, class Dst>
+__device__ __forceinline__ void batched_load(Src src, Dst dst) {
+    constexpr int PER = (COUNT + NTHR - 1) / NTHR;
+    constexpr int B = PER < 16 ? PER : 16;
+#pragma unroll 1
+    for (int k0 = 0; k0 < PER; k0 += B) {
+        V v[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const int i = threadIdx.x + (k0 + k) * NTHR;
+            if (COUNT % NTHR == 0 || i < COUNT) v[k] = src(i);
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const int i = threadIdx.x + (k0 + k) * NTHR;
+            if (COUNT % NTHR == 0 || i < COUNT) dst(i, v[k]);
+        }
+    }
+}
+
 // Load ROWS rows of N fixed-point densities of both species (16-byte
 // vectors), optionally zero them, and store rho_A + i rho_B to shared rows of
 // pitch PITCH. Loads are issued in batches before any store so that the
@@ -61,7 +83,7 @@ __device__ __forceinline__ void load_fixed_rows(unsigned long long* __restrict__
                                                 V* rows, T scale, int zero_after) {
     constexpr int PAIRS = ROWS * N / 2;
     constexpr int ITER = (PAIRS + NTHR - 1) / NTHR;
-    constexpr int BATCH = ITER < 4 ? ITER : 4;
+    constexpr int BATCH = ITER < 8 ? ITER : 8;
     longlong2* pa = reinterpret_cast<longlong2*>(ga);
     longlong2* pb = reinterpret_cast<longlong2*>(gb);
 #pragma unroll 1
@@ -141,12 +163,12 @@ __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restr
     const int d = blockIdx.y;
     const size_t M = (size_t)N * N * N;
     const size_t src = (d == 2 ? 2 * M : 0) + (size_t)blockIdx.x * N * N;
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-        const int ky = i / N;
-        V v = H[src + i];
-        if (d == 1) v = c_scale(v, grad_k<T, N>(ky, two_pi_over_L));
-        plane[ky * PITCH + kx_of_pos<N>(i % N)] = v;
-    }
+    batched_load<N * N, 512, V>([&](int i) { return H[src + i]; },
+                                [&](int i, V v) {
+                                    const int ky = i / N;
+                                    if (d == 1) v = c_scale(v, grad_k<T, N>(ky, two_pi_over_L));
+                                    plane[ky * PITCH + kx_of_pos<N>(i % N)] = v;
+                                });
     __syncthreads();
     smem_fft_lines<N, +1, N, 512>(plane, StridedLines<1>{}, PITCH, tw);  // along y
     if (d == 0) {
@@ -197,12 +219,12 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)blockIdx.y * M + (size_t)blockIdx.x * R * N;
     const bool kx_mult = blockIdx.y == 0;  // d_x: multiply by k_x before the x transform
-    for (int i = threadIdx.x; i < R * N; i += blockDim.x) {
-        const int kx = kx_of_pos<N>(i % N);
-        V v = H[base + i];
-        if (kx_mult) v = c_scale(v, grad_k<T, N>(kx, two_pi_over_L));
-        rows[(i / N) * PITCH + kx] = v;
-    }
+    batched_load<R * N, 256, V>([&](int i) { return H[base + i]; },
+                                [&](int i, V v) {
+                                    const int kx = kx_of_pos<N>(i % N);
+                                    if (kx_mult) v = c_scale(v, grad_k<T, N>(kx, two_pi_over_L));
+                                    rows[(i / N) * PITCH + kx] = v;
+                                });
     __syncthreads();
     smem_fft_lines<N, +1, R, 256>(rows, StridedLines<PITCH>{}, 1, tw);
     for (int i = threadIdx.x; i < R * N; i += blockDim.x) grad[base + i] = rows[(i / N) * PITCH + i % N];
@@ -226,11 +248,11 @@ __global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, c
     const bool two = DIR > 0 && blockIdx.z == 0;
     const size_t off = (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * C;
     const size_t src = (DIR > 0 && blockIdx.z == 1 ? 2 * M : 0) + off;
-    for (int i = threadIdx.x; i < TS; i += blockDim.x) {
-        const V v = data[src + (size_t)(i / C) * N + i % C];
-        tile[i] = v;
-        if (two) tile[TS + i] = c_scale(v, grad_k<T, N>(i / C, two_pi_over_L));
-    }
+    batched_load<TS, 256, V>([&](int i) { return data[src + (size_t)(i / C) * N + i % C]; },
+                             [&](int i, V v) {
+                                 tile[i] = v;
+                                 if (two) tile[TS + i] = c_scale(v, grad_k<T, N>(i / C, two_pi_over_L));
+                             });
     __syncthreads();
     if (two) {
         smem_fft_lines<N, DIR, 2 * C, 256>(tile, TileAddr<C, TS>{}, C, tw);
@@ -279,11 +301,16 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
     using V = cplx_t<T>;
     constexpr int TS = N * C;
     smem_fft_lines<N, -1, R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
-    for (int q = threadIdx.x; q < C * N; q += blockDim.x) {
-        const int c = q % C, kz = q / C;
-        const int cB = mirror_pos(p0 + c) - p0;
+    static_assert(256 % C == 0, "a thread keeps one column");
+    constexpr int rB = R - 1;
+    // per-thread column constants (element A in row 0, its mirror B in row rB)
+    const int c = threadIdx.x % C;
+    const int cB = mirror_pos(p0 + c) - p0;
+    const int kxA = kx_of_pos<N>(p0 + c), kxB = kx_of_pos<N>(p0 + cB);
+    const T exyA = e1[kxA] * e1[ky[0]], exyB = e1[kxB] * e1[ky[rB]];
+    const bool zeroA = (kxA == 0 && ky[0] == 0), zeroB = (kxB == 0 && ky[rB] == 0);
+    for (int kz = threadIdx.x / C; kz < N; kz += 256 / C) {
         const int kzB = (N - kz) & (N - 1);
-        constexpr int rB = R - 1;
         if (R == 1 && kzB * C + cB < kz * C + c) continue;  // the mirror element owns this pair
         const bool same = (R == 1) && (kzB == kz) && (cB == c);
         const V ZA = buf[kz * C + c];
@@ -294,18 +321,16 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
             if (s == 1 && same) break;
             const V Z = s == 0 ? ZA : ZB;   // Z(k)
             const V Zm = s == 0 ? ZB : ZA;  // Z(-k)
-            const int kxi = kx_of_pos<N>(p0 + (s == 0 ? c : cB));
-            const int kyi = ky[s == 0 ? 0 : rB];
             const int kzi = s == 0 ? kz : kzB;
-            const T kzv = (kzi == N / 2) ? T(0) : sp.two_pi_over_L * (T)freq_index<T>(kzi, N);
-            const T uh = e1[kxi] * e1[kyi] * e1[kzi];
+            const T kzv = grad_k<T, N>(kzi, sp.two_pi_over_L);
+            const T uh = (s == 0 ? exyA : exyB) * e1[kzi];
             // rho~_A = (Z + conj Zm)/2, rho~_B = -i (Z - conj Zm)/2
             const V A = {T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y)};
             const V B = {T(0.5) * (Z.y + Zm.y), -T(0.5) * (Z.x - Zm.x)};
             if (want_e) {
                 const double ar = A.x, ai = A.y, br = B.x, bi = B.y;
                 e_chi += (double)uh * (ar * br + ai * bi);
-                if (!(kxi == 0 && kyi == 0 && kzi == 0))
+                if (!((s == 0 ? zeroA : zeroB) && kzi == 0))
                     e_kap += (double)uh * ((ar + br) * (ar + br) + (ai + bi) * (ai + bi));
             }
             const V wA = {uh * (sp.eAA * A.x + sp.eAB * B.x), uh * (sp.eAA * A.y + sp.eAB * B.y)};
@@ -343,11 +368,16 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
     const int ky[2] = {(int)blockIdx.y, (N - (int)blockIdx.y) & (N - 1)};
     const int R = (ky[0] == ky[1]) ? 1 : 2;
     const size_t NN = (size_t)N * N;
-    for (int i = threadIdx.x; i < R * TS; i += blockDim.x) {
+    auto zsrc = [&](int i) {
         const int r = i / TS, rem = i % TS;
         const int z = rem / C, c = rem % C;
-        buf[i] = Zxy[z * NN + (size_t)ky[r] * N + p0 + c];
-    }
+        return Zxy[z * NN + (size_t)ky[r] * N + p0 + c];
+    };
+    auto zdst = [&](int i, V v) { buf[i] = v; };
+    if (R == 1)
+        batched_load<TS, 256, V>(zsrc, zdst);
+    else
+        batched_load<2 * TS, 256, V>(zsrc, zdst);
     __syncthreads();
     double e_chi = 0.0, e_kap = 0.0;
     const bool want_e = energy_partials != nullptr;
