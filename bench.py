@@ -56,6 +56,20 @@ def aggregate(values_per_rank, ms_per_rank, steps):
     return len(ms_per_rank) * steps / t, max(ms_per_rank) / steps
 
 
+def gather_times(ms: float, world: int, device: str):
+    """Every rank's timed-region length (ms), gathered on all ranks. Replicas
+    exchange nothing else: the path has no data-path collective."""
+    if world <= 1:
+        return [ms]
+    import torch
+    import torch.distributed as dist
+
+    buf = torch.tensor([ms], device=device, dtype=torch.float64)
+    gathered = [torch.zeros_like(buf) for _ in range(world)]
+    dist.all_gather(gathered, buf)
+    return [float(g.item()) for g in gathered]
+
+
 def algorithmic_bytes(stage: str, n_points: int, n_beads: int) -> int:
     return BYTES_PER_POINT[stage] * n_points + BYTES_PER_BEAD[stage] * n_beads
 
@@ -266,14 +280,7 @@ def main():
     torch.cuda.synchronize()
     ms = start.elapsed_time(end)
     launches = t.launches(args.steps)
-    ms_all = [ms]
-    if world > 1:
-        import torch.distributed as dist
-
-        buf = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        gathered = [torch.zeros_like(buf) for _ in range(world)]
-        dist.all_gather(gathered, buf)
-        ms_all = [float(g.item()) for g in gathered]
+    ms_all = gather_times(ms, world, "cuda")
     value, ms_per_step = aggregate(None, ms_all, args.steps)
 
     # end to end through the C ABI with host buffers: upload the state,
