@@ -169,6 +169,38 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def cufft_comparison(n: int, stage_ms):
+    """Library FFTs on the same grid, timed for comparison only (cuFFT through
+    torch.fft; never on the product path): one forward 3D complex transform
+    of n^3 points and three inverse ones, the work of our forward and inverse
+    passes (ours also spread/convert, multiply and write gradients)."""
+    import torch
+
+    x = torch.randn(n, n, n, dtype=torch.complex64, device="cuda")
+    y3 = torch.randn(3, n, n, n, dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        torch.fft.fftn(x)
+        torch.fft.ifftn(y3, dim=(1, 2, 3))
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 50
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        torch.fft.fftn(x)
+    e.record()
+    e.synchronize()
+    fwd = s.elapsed_time(e) / reps
+    s.record()
+    for _ in range(reps):
+        torch.fft.ifftn(y3, dim=(1, 2, 3))
+    e.record()
+    e.synchronize()
+    inv = s.elapsed_time(e) / reps
+    ours = stage_ms["forward_fft"] + stage_ms["z_spectral"] + stage_ms["inverse_fft"]
+    return {"cufft_fwd_c2c_ms": fwd, "cufft_inv_3xc2c_ms": inv, "cufft_total_ms": fwd + inv,
+            "ours_fwd_z_inv_ms": ours, "note": "cuFFT time excludes the spectral multiply and the fixed-point conversion"}
+
+
 def oracle_step_rate(spec, pos, n_steps: int, budget_s: float):
     """Time the FP64 oracle (single-threaded numpy) on the same system."""
     from oracle import tild_oracle as O
@@ -307,6 +339,8 @@ def main():
     sb = step_bytes(n_points, spec.n_beads)
     step_achieved = sb * (args.steps / (ms / 1000.0)) / 1e9
 
+    cufft = cufft_comparison(spec.n, stage_time)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, done, secs, _ = oracle_step_rate(spec, pos, args.cpu_baseline_steps, 60.0)
@@ -330,6 +364,7 @@ def main():
             "step_roofline": {"algorithmic_bytes_per_step": sb, "achieved": step_achieved, "peak": peak,
                               "unit": "GB/s", "frac": step_achieved / peak},
             "stage_ms": stage_time,
+            "cufft_comparison": cufft,
             "cpu_baseline": cpu,
             "e2e": {"value": args.steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps},

@@ -115,6 +115,23 @@ typedef struct {
     double net_force[3];
 } tild_energy;
 
+/* Energy of the current configuration and its derivatives with respect to
+ * the interaction parameters (the model's energy U = E_bond + E_chi +
+ * E_kappa of Eqs. bonds, fh and HelfandP, on the grid):
+ *   dU/dchi   = (1/rho_0) int int rho_A u_G rho_B          (Eq. fh)
+ *   dU/dkappa = (1/2rho_0) int int (rho_+ - rho_0) u_G (rho_+ - rho_0)
+ *   dU/da     = sum over k of (d u_hat/d a) (...), d u_hat/d a = -2 a |k|^2 u_hat
+ * (sigma^2 = 2 a^2, Eqs. fhF, HelfandF), all reduced in FP64 on the device. */
+typedef struct {
+    double energy;
+    double e_bond;
+    double e_chi;
+    double e_kappa;
+    double dU_dchi;
+    double dU_dkappa;
+    double dU_da;
+} tild_energy_grad;
+
 #define TILD_COMPUTE_ENERGY 1u
 #define TILD_COMPUTE_FORCES 2u
 
@@ -180,6 +197,16 @@ tild_status tild_synchronize(tild_ctx* ctx);
  * total forces (field + bonds) to forces_out [n_beads][3] (may be NULL if
  * not requested). Does not change the state. */
 tild_status tild_compute(tild_ctx* ctx, unsigned what, tild_energy* e, void* forces_out, int dtype, int where);
+
+/* Energy and its gradients at the current positions: *g receives U and
+ * dU/dchi, dU/dkappa, dU/da; dU_dr (may be NULL) receives dU/dr_i,
+ * [n_beads][3], the exact gradient of the gridded energy: the adjoint of the
+ * density assignment (the assignment weights differentiated, Sec.
+ * "Long-range interactions") applied to the potential fields w_K, plus the
+ * bond term of Eq. bonds. (The forces of tild_compute use the spectral
+ * gradient instead, as the method does; the two agree as the grid is
+ * refined.) Does not change the state. */
+tild_status tild_energy_gradient(tild_ctx* ctx, tild_energy_grad* g, void* dU_dr, int dtype, int where);
 
 /* Current positions (wrapped into [0, L)), [n_beads][3]. */
 tild_status tild_get_positions(tild_ctx* ctx, void* out, int dtype, int where);

@@ -42,6 +42,10 @@ class tild_moltype(ctypes.Structure):
     _fields_ = [("n_chains", ctypes.c_int64), ("N", ctypes.c_int), ("n_a", ctypes.c_int)]
 
 
+class tild_energy_grad(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("energy", "e_bond", "e_chi", "e_kappa", "dU_dchi", "dU_dkappa", "dU_da")]
+
+
 class tild_energy(ctypes.Structure):
     _fields_ = [("e_bond", ctypes.c_double), ("e_chi", ctypes.c_double), ("e_kappa", ctypes.c_double),
                 ("kinetic", ctypes.c_double), ("net_force", ctypes.c_double * 3)]
@@ -63,6 +67,7 @@ _SIGS = {
     "tild_step": [_P, _I64],
     "tild_synchronize": [_P],
     "tild_compute": [_P, ctypes.c_uint, ctypes.POINTER(tild_energy), _P, _I, _I],
+    "tild_energy_gradient": [_P, ctypes.POINTER(tild_energy_grad), _P, _I, _I],
     "tild_get_positions": [_P, _P, _I, _I],
     "tild_get_velocities": [_P, _P, _I, _I],
     "tild_get_density": [_P, _P, _I, _I],
@@ -278,6 +283,19 @@ class Tild:
         if f is not None and isinstance(f, np.ndarray):
             f = f.reshape(-1, 3)
         return f, en
+
+    def energy_gradient(self, with_positions: bool = True, out=None, dtype=np.float64):
+        """(dict of U, its terms and dU/dchi, dU/dkappa, dU/da; dU/dr or None)."""
+        g = tild_energy_grad()
+        ptr, code, where, buf = ctypes.c_void_p(), TILD_DTYPE_F64, TILD_HOST, None
+        if with_positions:
+            buf = np.empty(3 * self.n_beads, dtype=dtype) if out is None else out
+            ptr, code, where, _keep = _buffer(buf, 3 * self.n_beads)
+        self._chk(self.lib.tild_energy_gradient(self.ctx, ctypes.byref(g), ptr, code, where))
+        d = {k: getattr(g, k) for k, _ in tild_energy_grad._fields_}
+        if isinstance(buf, np.ndarray):
+            buf = buf.reshape(-1, 3)
+        return d, buf
 
     def step_count(self) -> int:
         s = ctypes.c_int64()

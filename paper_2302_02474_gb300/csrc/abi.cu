@@ -206,6 +206,14 @@ tild_status tild_compute(tild_ctx* c, unsigned what, tild_energy* e, void* force
     return from_engine(c, c->eng->compute(what, e, (what & TILD_COMPUTE_FORCES) ? forces_out : nullptr, dtype, where));
 }
 
+tild_status tild_energy_gradient(tild_ctx* c, tild_energy_grad* g, void* dU_dr, int dtype, int where) {
+    if (!c) return TILD_EINVAL;
+    if (!g) return fail(c, TILD_EINVAL, "energy_gradient: g == NULL");
+    if (dU_dr && !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "energy_gradient: bad dtype or where");
+    if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "energy_gradient: positions not set");
+    return from_engine(c, c->eng->energy_gradient(g, dU_dr, dtype, where));
+}
+
 tild_status tild_get_positions(tild_ctx* c, void* out, int dtype, int where) {
     if (!c) return TILD_EINVAL;
     if (!out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "get_positions: bad pointer, dtype or where");

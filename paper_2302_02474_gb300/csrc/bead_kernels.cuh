@@ -476,6 +476,59 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
     }
 }
 
+// Exact gradient of the gridded energy with respect to the bead positions:
+//   dU/dr_i = sum_g grad_r W(r_i - g) w_K(g) + (3/b^2) sum_j mic(r_i - r_j),
+// i.e. the adjoint of the spread (the same weights, differentiated) applied
+// to the potential field w_K, plus the bond term. `pot` holds
+// i (w_A + i w_B) per grid point. Output by bead id.
+template <int P, typename T>
+__global__ void __launch_bounds__(256) adjoint_kernel(BeadParams<T> p, BeadBuffers<T> bf, const cplx_t<T>* __restrict__ pot,
+                                                      T* __restrict__ grad_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n_beads) return;
+    const T x = bf.px[i], y = bf.py[i], z = bf.pz[i];
+    const int tag = bf.id[i];
+    const int bid = slot_bead_id(tag);
+    const int species = slot_species(tag);
+    Stencil<P, T> st;
+    st.set(x, y, z, p.inv_dx);
+    T dx[P], dy[P], dz[P];
+    dh_weight_derivs<P>(x * p.inv_dx, dx);
+    dh_weight_derivs<P>(y * p.inv_dx, dy);
+    dh_weight_derivs<P>(z * p.inv_dx, dz);
+    const int nm = p.n - 1;
+    T gx = 0, gy = 0, gz = 0;
+#pragma unroll
+    for (int c = 0; c < P; ++c)
+#pragma unroll
+        for (int b = 0; b < P; ++b)
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                const size_t g = ((size_t)((st.jz + c) & nm) * p.n + ((st.jy + b) & nm)) * p.n + ((st.jx + a) & nm);
+                const cplx_t<T> v = pot[g];
+                const T w = species ? -v.x : v.y;  // w_A = Im, w_B = -Re of i (w_A + i w_B)
+                gx += dx[a] * st.wy[b] * st.wz[c] * w;
+                gy += st.wx[a] * dy[b] * st.wz[c] * w;
+                gz += st.wx[a] * st.wy[b] * dz[c] * w;
+            }
+    gx *= p.inv_dx;
+    gy *= p.inv_dx;
+    gz *= p.inv_dx;
+    const int2 nb = bf.nbr[i];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int s = k == 0 ? nb.x : nb.y;
+        if (s >= 0) {
+            gx += p.k_bond * min_image(x - bf.px[s], p.L, p.inv_L);
+            gy += p.k_bond * min_image(y - bf.py[s], p.L, p.inv_L);
+            gz += p.k_bond * min_image(z - bf.pz[s], p.L, p.inv_L);
+        }
+    }
+    grad_out[3 * (size_t)bid + 0] = gx;
+    grad_out[3 * (size_t)bid + 1] = gy;
+    grad_out[3 * (size_t)bid + 2] = gz;
+}
+
 // ------------------------------------------------------------- binning
 
 // Tile of a position: index of the 8x8x8-cell tile holding floor(r/dx).

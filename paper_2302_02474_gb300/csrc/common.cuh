@@ -171,6 +171,35 @@ template <int P, typename T> __device__ __forceinline__ void dh_weights(T s, int
     }
 }
 
+// d/ds of the weights of dh_weights (same points).
+template <int P, typename T> __device__ __forceinline__ void dh_weight_derivs(T s, T (&dw)[P]) {
+    if constexpr (P == 2) {
+        dw[0] = T(-1);
+        dw[1] = T(1);
+    } else if constexpr (P == 3) {
+        const T t = s - floor(s + T(0.5));
+        dw[0] = t - T(0.5);
+        dw[1] = T(-2) * t;
+        dw[2] = T(0.5) + t;
+    } else if constexpr (P == 4) {
+        const T t = s - floor(s);
+        const T u = T(1) - t;
+        dw[0] = T(-0.5) * u * u;
+        dw[1] = T(-2) * t + T(1.5) * t * t;
+        dw[2] = T(0.5) + t - T(1.5) * t * t;
+        dw[3] = T(0.5) * t * t;
+    } else {
+        const T t = s - floor(s + T(0.5));
+        const T t2 = t * t, t3 = t2 * t;
+        const T a = T(1) - T(2) * t, b = T(1) + T(2) * t;
+        dw[0] = -a * a * a * T(1.0 / 48.0);
+        dw[1] = (T(-44) + T(48) * t + T(48) * t2 - T(64) * t3) * T(1.0 / 96.0);
+        dw[2] = T(-1.25) * t + t3;
+        dw[3] = (T(44) + T(48) * t - T(48) * t2 - T(64) * t3) * T(1.0 / 96.0);
+        dw[4] = b * b * b * T(1.0 / 48.0);
+    }
+}
+
 // Stencil extent relative to the cell floor(s): points floor(s)+lo ..
 // floor(s)+hi can receive weight.
 template <int P> struct stencil_extent {

@@ -48,7 +48,7 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(cudaMalloc(&rho_fx_, 2 * M_ * sizeof(unsigned long long)));
         TILD_CUDA(cudaMalloc(&Zxy_, M_ * sizeof(V)));
         TILD_CUDA(cudaMalloc(&H_, 3 * M_ * sizeof(V)));
-        TILD_CUDA(cudaMalloc(&grad_, 3 * M_ * sizeof(V)));
+        TILD_CUDA(cudaMalloc(&grad_, 4 * M_ * sizeof(V)));  // 3 gradients + (optional) potentials
         TILD_CUDA(cudaMalloc(&tw_, n_ * sizeof(V)));
         TILD_CUDA(cudaMalloc(&kernel1d_, n_ * sizeof(T)));
         TILD_CUDA(cudaMalloc(&counters_, 4 * sizeof(unsigned long long)));
@@ -61,7 +61,7 @@ template <typename T> class Engine final : public EngineBase {
         scan_blocks_ = (int)((n_tiles_ + 1 + 1023) / 1024);
         TILD_CUDA(cudaMalloc(&block_sums_, scan_blocks_ * sizeof(int)));
         n_z_blocks_ = (size_t)(n_ / CZ_) * (n_ / 2 + 1);
-        n_partials_ = std::max(2 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
+        n_partials_ = std::max(4 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
         TILD_CUDA(cudaMalloc(&partials_, n_partials_ * sizeof(double)));
         // twiddles W_n^m = exp(-2 pi i m / n) in FP64, rounded to T
         std::vector<V> tw(n_);
@@ -177,7 +177,7 @@ template <typename T> class Engine final : public EngineBase {
         if ((st = enqueue_fields(want_e, partials_, nullptr))) return st;
         std::vector<double> zpart;
         if (want_e) {
-            zpart.resize(2 * n_z_blocks_);
+            zpart.resize(4 * n_z_blocks_);
             TILD_CUDA(cudaMemcpyAsync(zpart.data(), partials_, zpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
         }
         BeadBuffers<T> bf = bead_buffers();
@@ -196,8 +196,8 @@ template <typename T> class Engine final : public EngineBase {
         if (want_e && e) {
             double s0 = 0, s1 = 0;
             for (size_t b = 0; b < n_z_blocks_; ++b) {
-                s0 += zpart[2 * b];
-                s1 += zpart[2 * b + 1];
+                s0 += zpart[4 * b];
+                s1 += zpart[4 * b + 1];
             }
             const double V = cfg_->L * cfg_->L * cfg_->L;
             const double dV = V / (double)M_;
@@ -214,6 +214,50 @@ template <typename T> class Engine final : public EngineBase {
             for (int d = 0; d < 3; ++d) e->net_force[d] = acc[2 + d];
             if (!want_e) e->e_chi = e->e_kappa = 0.0;
         }
+        return TILD_OK;
+    }
+
+    tild_status energy_gradient(tild_energy_grad* g, void* dUdr, int dtype, int where) override {
+        tild_status st;
+        if ((st = enqueue_fields(true, partials_, nullptr, true))) return st;
+        std::vector<double> zpart(4 * n_z_blocks_);
+        TILD_CUDA(cudaMemcpyAsync(zpart.data(), partials_, zpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        BeadBuffers<T> bf = bead_buffers();
+        if ((st = launch_bead(kModeForce, bf))) return st;  // bond energy partials
+        std::vector<double> bpart(5 * (size_t)tiles_ * tiles_ * tiles_);
+        TILD_CUDA(cudaMemcpyAsync(bpart.data(), partials_, bpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        if (dUdr) {
+            const size_t N = cfg_->n_beads;
+            if ((st = ensure_aux(3 * N * sizeof(T)))) return st;
+            const BeadParams<T> p = bead_params();
+            const V* pot = grad_ + 3 * M_;
+            tild_status s2 = dispatch_p([&](auto pp) -> tild_status {
+                adjoint_kernel<decltype(pp)::value, T><<<blocks(N), 256, 0, stream_>>>(p, bf, pot, (T*)aux_);
+                return TILD_OK;
+            });
+            if (s2) return s2;
+            TILD_CUDA(cudaGetLastError());
+            if ((st = stage_out_vec((T*)aux_, 3 * N, dUdr, dtype, where))) return st;
+        }
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        if ((st = check_err())) return st;
+        double s[4] = {0, 0, 0, 0};
+        for (size_t b = 0; b < n_z_blocks_; ++b)
+            for (int k = 0; k < 4; ++k) s[k] += zpart[4 * b + k];
+        double eb = 0;
+        for (size_t b = 0; b < bpart.size() / 5; ++b) eb += bpart[5 * b];
+        const double V = cfg_->L * cfg_->L * cfg_->L;
+        const double dV = V / (double)M_;
+        const double rho0 = cfg_->n_beads / V;
+        const double f = dV * dV / V;
+        // E_chi = chi/rho0 f S0, E_kappa = kappa/(2 rho0) f S1; d u_hat/d a = -2 a |k|^2 u_hat
+        g->e_bond = eb;
+        g->e_chi = cfg_->chi / rho0 * f * s[0];
+        g->e_kappa = cfg_->kappa / (2.0 * rho0) * f * s[1];
+        g->energy = g->e_bond + g->e_chi + g->e_kappa;
+        g->dU_dchi = f * s[0] / rho0;
+        g->dU_dkappa = f * s[1] / (2.0 * rho0);
+        g->dU_da = -2.0 * cfg_->a * (cfg_->chi / rho0 * f * s[2] + cfg_->kappa / (2.0 * rho0) * f * s[3]);
         return TILD_OK;
     }
 
@@ -711,26 +755,27 @@ template <typename T> class Engine final : public EngineBase {
         return dispatch_n([&](auto nn) { return this->template zpass_n<decltype(nn)::value>(partials, spec_out); });
     }
 
-    template <int NN> tild_status inverse_n() {
+    template <int NN> tild_status inverse_n(bool with_potential) {
+        const unsigned nd = with_potential ? 4 : 3;
         if (plane_fits_) {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
-                xy_inverse_plane<T, NN><<<dim3(NN, 3), 512, plane_smem(), stream_>>>(H_, grad_, tw_, two_pi_L());
+                xy_inverse_plane<T, NN><<<dim3(NN, nd), 512, plane_smem(), stream_>>>(H_, grad_, tw_, two_pi_L());
             }
         } else {
             constexpr int CC = 128 / sizeof(V);
             if constexpr (NN >= 16 && NN >= CC) {
                 y_columns<T, NN, CC, +1><<<dim3(NN / CC, NN, 2), 256, ycol_smem(), stream_>>>(H_, tw_, two_pi_L());
-                x_inverse_rows<T, NN, 16><<<dim3((unsigned)((size_t)NN * NN / 16), 3), 256, rows_smem(), stream_>>>(H_, grad_, tw_, two_pi_L());
+                x_inverse_rows<T, NN, 16><<<dim3((unsigned)((size_t)NN * NN / 16), nd), 256, rows_smem(), stream_>>>(H_, grad_, tw_, two_pi_L());
             }
         }
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
     }
-    tild_status enqueue_inverse() {
-        return dispatch_n([&](auto nn) { return this->template inverse_n<decltype(nn)::value>(); });
+    tild_status enqueue_inverse(bool with_potential = false) {
+        return dispatch_n([&](auto nn) { return this->template inverse_n<decltype(nn)::value>(with_potential); });
     }
 
-    tild_status enqueue_fields(bool energy, double* partials, V* spec_out) {
+    tild_status enqueue_fields(bool energy, double* partials, V* spec_out, bool with_potential = false) {
         tild_status st;
         if (!have_pos_) {
             err = "positions have not been set";
@@ -738,7 +783,7 @@ template <typename T> class Engine final : public EngineBase {
         }
         if ((st = enqueue_forward(false))) return st;
         if ((st = enqueue_zpass(energy ? partials : nullptr, spec_out))) return st;
-        return enqueue_inverse();
+        return enqueue_inverse(with_potential);
     }
 
     BeadParams<T> bead_params() const {

@@ -41,6 +41,7 @@ class EngineBase {
     virtual tild_status step(int64_t n) = 0;
     virtual tild_status synchronize() = 0;
     virtual tild_status compute(unsigned what, tild_energy* e, void* f, int dtype, int where) = 0;
+    virtual tild_status energy_gradient(tild_energy_grad* g, void* dUdr, int dtype, int where) = 0;
     virtual tild_status get_positions(void* out, int dtype, int where) = 0;
     virtual tild_status get_velocities(void* out, int dtype, int where) = 0;
     virtual tild_status get_density(void* out, int dtype, int where) = 0;

@@ -33,6 +33,12 @@ template <typename T> struct SpectralParams {
 template <int N> __host__ __device__ __forceinline__ int kx_of_pos(int p);
 template <int C, int STRIDE> struct TileAddr;
 
+// Wavenumber 2 pi m / L of FFT index i (m = i or i - n; the Nyquist index
+// n/2 counts as -n/2).
+template <typename T, int N> __device__ __forceinline__ T raw_k(int i, T two_pi_over_L) {
+    return two_pi_over_L * (T)(i < N / 2 ? i : i - N);
+}
+
 // Wavenumber used for spectral differentiation at FFT index i: 2 pi m / L
 // with m = i (i < n/2) or i - n, and 0 at the Nyquist index n/2.
 template <typename T, int N> __device__ __forceinline__ T grad_k(int i, T two_pi_over_L) {
@@ -159,7 +165,8 @@ __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restr
     V* plane = tw + N;
     load_twiddles(tw, tw_g, N);
 
-    // direction d: x from i k_x G, y from i k_y G, z from G_z (field 2)
+    // direction d: x from i k_x G, y from i k_y G, z from G_z (field 2);
+    // d = 3 (optional): the potentials themselves, i (w_A + i w_B), from G
     const int d = blockIdx.y;
     const size_t M = (size_t)N * N * N;
     const size_t src = (d == 2 ? 2 * M : 0) + (size_t)blockIdx.x * N * N;
@@ -218,8 +225,10 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)blockIdx.y * M + (size_t)blockIdx.x * R * N;
+    // field 3 (optional, the potentials) is the plain transform of field 0
+    const size_t src = (size_t)(blockIdx.y == 3 ? 0 : blockIdx.y) * M + (size_t)blockIdx.x * R * N;
     const bool kx_mult = blockIdx.y == 0;  // d_x: multiply by k_x before the x transform
-    batched_load<R * N, 256, V>([&](int i) { return H[base + i]; },
+    batched_load<R * N, 256, V>([&](int i) { return H[src + i]; },
                                 [&](int i, V v) {
                                     const int kx = kx_of_pos<N>(i % N);
                                     if (kx_mult) v = c_scale(v, grad_k<T, N>(kx, two_pi_over_L));
@@ -297,7 +306,7 @@ template <typename T> __device__ __forceinline__ int freq_index(int i, int n) { 
 // --------------------------------------------------------------------------
 template <typename T, int N, int C, int R>
 __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, const T* e1, const SpectralParams<T>& sp,
-                                       int p0, const int (&ky)[2], bool want_e, double& e_chi, double& e_kap) {
+                                       int p0, const int (&ky)[2], bool want_e, double (&acc)[4]) {
     using V = cplx_t<T>;
     constexpr int TS = N * C;
     smem_fft_lines<N, -1, R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
@@ -309,6 +318,10 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
     const int kxA = kx_of_pos<N>(p0 + c), kxB = kx_of_pos<N>(p0 + cB);
     const T exyA = e1[kxA] * e1[ky[0]], exyB = e1[kxB] * e1[ky[rB]];
     const bool zeroA = (kxA == 0 && ky[0] == 0), zeroB = (kxB == 0 && ky[rB] == 0);
+    // |k_x|^2 + |k_y|^2 of A and B (the Nyquist index counts as -n/2)
+    const T qxA = raw_k<T, N>(kxA, sp.two_pi_over_L), qyA = raw_k<T, N>(ky[0], sp.two_pi_over_L);
+    const T qxB = raw_k<T, N>(kxB, sp.two_pi_over_L), qyB = raw_k<T, N>(ky[rB], sp.two_pi_over_L);
+    const double kxy2A = (double)qxA * qxA + (double)qyA * qyA, kxy2B = (double)qxB * qxB + (double)qyB * qyB;
     for (int kz = threadIdx.x / C; kz < N; kz += 256 / C) {
         const int kzB = (N - kz) & (N - 1);
         if (R == 1 && kzB * C + cB < kz * C + c) continue;  // the mirror element owns this pair
@@ -328,10 +341,18 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
             const V A = {T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y)};
             const V B = {T(0.5) * (Z.y + Zm.y), -T(0.5) * (Z.x - Zm.x)};
             if (want_e) {
+                // energy sums and their |k|^2-weighted versions (d u_hat / d a = -2 a |k|^2 u_hat)
                 const double ar = A.x, ai = A.y, br = B.x, bi = B.y;
-                e_chi += (double)uh * (ar * br + ai * bi);
-                if (!((s == 0 ? zeroA : zeroB) && kzi == 0))
-                    e_kap += (double)uh * ((ar + br) * (ar + br) + (ai + bi) * (ai + bi));
+                const double qz = (double)raw_k<T, N>(kzi, sp.two_pi_over_L);
+                const double k2 = (s == 0 ? kxy2A : kxy2B) + qz * qz;
+                const double fchi = (double)uh * (ar * br + ai * bi);
+                acc[0] += fchi;
+                acc[2] += k2 * fchi;
+                if (!((s == 0 ? zeroA : zeroB) && kzi == 0)) {
+                    const double fkap = (double)uh * ((ar + br) * (ar + br) + (ai + bi) * (ai + bi));
+                    acc[1] += fkap;
+                    acc[3] += k2 * fkap;
+                }
             }
             const V wA = {uh * (sp.eAA * A.x + sp.eAB * B.x), uh * (sp.eAA * A.y + sp.eAB * B.y)};
             const V wB = {uh * (sp.eAB * A.x + sp.eBB * B.x), uh * (sp.eAB * A.y + sp.eBB * B.y)};
@@ -359,7 +380,7 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* buf = tw + N;
     constexpr int TS = N * C;
-    __shared__ double red[2][8];
+    __shared__ double red[4][8];
     __shared__ T e1[N];  // separable Gaussian kernel: u_hat = e1[kx] e1[ky] e1[kz]
     load_twiddles(tw, tw_g, N);
     for (int i = threadIdx.x; i < N; i += blockDim.x) e1[i] = sp.kernel1d[i];
@@ -379,7 +400,7 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
     else
         batched_load<2 * TS, 256, V>(zsrc, zdst);
     __syncthreads();
-    double e_chi = 0.0, e_kap = 0.0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     const bool want_e = energy_partials != nullptr;
     if (spectrum_out) {
         // forward transform only, written out in natural kx order
@@ -395,30 +416,24 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
         return;
     }
     if (R == 1)
-        z_tile<T, N, C, 1>(buf, tw, e1, sp, p0, ky, want_e, e_chi, e_kap);
+        z_tile<T, N, C, 1>(buf, tw, e1, sp, p0, ky, want_e, acc);
     else
-        z_tile<T, N, C, 2>(buf, tw, e1, sp, p0, ky, want_e, e_chi, e_kap);
+        z_tile<T, N, C, 2>(buf, tw, e1, sp, p0, ky, want_e, acc);
     if (want_e) {
         // block reduction in a fixed order (deterministic)
-        for (int o = 16; o > 0; o >>= 1) {
-            e_chi += __shfl_down_sync(0xffffffffu, e_chi, o);
-            e_kap += __shfl_down_sync(0xffffffffu, e_kap, o);
-        }
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) {
-            red[0][wid] = e_chi;
-            red[1][wid] = e_kap;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double v = acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[k][wid] = v;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double s0 = 0, s1 = 0;
-            for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
-                s0 += red[0][w];
-                s1 += red[1][w];
-            }
+        if (threadIdx.x < 4) {
+            double sum = 0;
+            for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) sum += red[threadIdx.x][w];
             const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-            energy_partials[2 * b] = s0;
-            energy_partials[2 * b + 1] = s1;
+            energy_partials[4 * b + threadIdx.x] = sum;
         }
     }
     const size_t M = NN * N;
