@@ -578,6 +578,71 @@ __global__ void bin_scatter_pos(int n_beads, Topology topo, const int* __restric
     slot_of_id[b] = s;
 }
 
+// Within each tile, order the beads by cell (x fastest) so that neighbouring
+// threads of the bead kernel touch neighbouring shared-memory patch points.
+// One CTA per tile; tiles with more than kLocalSortMax beads keep their order.
+template <typename T>
+__global__ void __launch_bounds__(256) bin_local_sort(const int* __restrict__ tile_start, int tiles, int n, T inv_dx,
+                                                      int n_beads, T* __restrict__ pos /*[3][N]*/,
+                                                      T* __restrict__ u /*[3][N]*/, int* __restrict__ id,
+                                                      int* __restrict__ slot_of_id) {
+    constexpr int kLocalSortMax = sizeof(T) == 4 ? 1024 : 640;  // static shared memory <= 48 KB
+    __shared__ T s_v[6][kLocalSortMax];
+    __shared__ int s_id[kLocalSortMax];
+    __shared__ short s_key[kLocalSortMax];
+    __shared__ int s_cnt[kTileCells];
+    const int t = blockIdx.x;
+    const int start = tile_start[t], cnt = tile_start[t + 1] - start;
+    if (cnt <= 1 || cnt > kLocalSortMax) return;
+    const int tx = t % tiles, ty = (t / tiles) % tiles, tz = t / (tiles * tiles);
+    for (int c = threadIdx.x; c < kTileCells; c += blockDim.x) s_cnt[c] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const int i = start + j;
+        const T x = pos[i], y = pos[(size_t)n_beads + i], z = pos[2 * (size_t)n_beads + i];
+        s_v[0][j] = x;
+        s_v[1][j] = y;
+        s_v[2][j] = z;
+        s_v[3][j] = u[i];
+        s_v[4][j] = u[(size_t)n_beads + i];
+        s_v[5][j] = u[2 * (size_t)n_beads + i];
+        s_id[j] = id[i];
+        const int cx = min(max((int)floor(x * inv_dx), 0), n - 1) - tx * kTile;
+        const int cy = min(max((int)floor(y * inv_dx), 0), n - 1) - ty * kTile;
+        const int cz = min(max((int)floor(z * inv_dx), 0), n - 1) - tz * kTile;
+        const int key = (min(max(cz, 0), kTile - 1) * kTile + min(max(cy, 0), kTile - 1)) * kTile + min(max(cx, 0), kTile - 1);
+        s_key[j] = (short)key;
+        atomicAdd(&s_cnt[key], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the 512 cell counts by one warp
+        int carry = 0;
+        for (int c0 = 0; c0 < kTileCells; c0 += 32) {
+            const int v = s_cnt[c0 + threadIdx.x];
+            int incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int n_ = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)threadIdx.x >= o) incl += n_;
+            }
+            s_cnt[c0 + threadIdx.x] = carry + incl - v;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const int r = atomicAdd(&s_cnt[s_key[j]], 1);
+        const int i = start + r;
+        pos[i] = s_v[0][j];
+        pos[(size_t)n_beads + i] = s_v[1][j];
+        pos[2 * (size_t)n_beads + i] = s_v[2][j];
+        u[i] = s_v[3][j];
+        u[(size_t)n_beads + i] = s_v[4][j];
+        u[2 * (size_t)n_beads + i] = s_v[5][j];
+        id[i] = s_id[j];
+        slot_of_id[slot_bead_id(s_id[j])] = i;
+    }
+}
+
 // Move the carried velocities to the slots assigned by bin_scatter_pos.
 template <typename T>
 __global__ void bin_move_u(int n_beads, const int* __restrict__ id_src, const int* __restrict__ slot_of_id,

@@ -407,7 +407,7 @@ template <typename T> class Engine final : public EngineBase {
 
     int64_t launches(int64_t n) const override {
         const int64_t per_step = (plane_fits_ ? 2 : 4) + 2;
-        const int64_t per_sort = 7;
+        const int64_t per_sort = 8;
         const int K = cfg_->sort_every;
         int64_t since = steps_since_sort_, sorts = 0;
         for (int64_t s = 0; s < n; ++s) {
@@ -887,6 +887,8 @@ template <typename T> class Engine final : public EngineBase {
         bin_scatter_pos<T><<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, keys_, tile_start_, cursor_, pos_[cur_pos_],
                                                            pos_[1 - cur_pos_], id_[cur_id_], id_[1 - cur_id_], slot_of_id_);
         bin_move_u<T><<<blocks(N), 256, 0, stream_>>>(N, id_[cur_id_], slot_of_id_, u_[cur_u_], u_[1 - cur_u_]);
+        bin_local_sort<T><<<n_tiles_, 256, 0, stream_>>>(tile_start_, tiles_, n_, (T)((double)n_ / cfg_->L), N,
+                                                          pos_[1 - cur_pos_], u_[1 - cur_u_], id_[1 - cur_id_], slot_of_id_);
         bin_neighbours<<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, id_[1 - cur_id_], slot_of_id_, nbr_);
         TILD_CUDA(cudaGetLastError());
         cur_pos_ = 1 - cur_pos_;
