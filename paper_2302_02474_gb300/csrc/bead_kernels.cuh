@@ -206,8 +206,10 @@ template <int P, typename T> __device__ __forceinline__ bool patch_local(const S
            (unsigned)l.z <= (unsigned)(PT::W - P);
 }
 
-// Beads of a tile are staged in shared memory in chunks of up to kBeadChunk.
+// Beads of a tile are staged in shared memory in chunks of up to kBeadChunk
+// and processed with at most one bead per thread.
 constexpr int kBeadChunk = 512;
+constexpr int kBeadThreads = 512;
 
 template <int P, typename T> struct BeadSmem {
     using patch_t = typename FixedPoint<T>::patch_t;
@@ -238,7 +240,7 @@ template <int P> __device__ __forceinline__ size_t patch_row_base(int row, int3 
 }
 
 template <int P, int MODE, typename T>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
+__global__ void __launch_bounds__(kBeadThreads, (sizeof(T) == 4 && P <= 3) ? 2 : 1) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
     using PT = Patch<P>;
     using SM = BeadSmem<P, T>;
     using FP = FixedPoint<T>;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
     if (kForce && SM::stage_grad && row_lane) {
         // stage the gradient fields of the patch as per-species (gx, gy, gz);
         // every row's loads are issued before any is used
-        constexpr int NWARP = 8;  // 256 threads
+        constexpr int NWARP = kBeadThreads / 32;
         constexpr int ROWS_PER_LANE = (W * W + NWARP * RPW - 1) / (NWARP * RPW);
         V v[ROWS_PER_LANE][3];
 #pragma unroll
@@ -310,13 +312,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
         if (c0 != start) __syncthreads();  // the previous chunk is done with the staged beads
         {
             // all loads of the chunk in flight before the shared stores
-            constexpr int PER = kBeadChunk / 256;
+            constexpr int PER = kBeadChunk / kBeadThreads;
             T vx[PER], vy[PER], vz[PER];
             int vt[PER];
             int2 vn[PER];
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
-                const int j = threadIdx.x + k * 256;
+                const int j = threadIdx.x + k * kBeadThreads;
                 if (j < cnt) {
                     vx[k] = bf.px[c0 + j];
                     vy[k] = bf.py[c0 + j];
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
             }
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
-                const int j = threadIdx.x + k * 256;
+                const int j = threadIdx.x + k * kBeadThreads;
                 if (j < cnt) {
                     s_pos[j] = vx[k];
                     s_pos[kBeadChunk + j] = vy[k];
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
         }
     }
     if (MODE == kModeForce) {
-        __shared__ double red[5][8];
+        __shared__ double red[5][kBeadThreads / 32];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
