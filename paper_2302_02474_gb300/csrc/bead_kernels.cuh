@@ -206,10 +206,8 @@ template <int P, typename T> __device__ __forceinline__ bool patch_local(const S
            (unsigned)l.z <= (unsigned)(PT::W - P);
 }
 
-// Beads of a tile are staged in shared memory in chunks of up to kBeadChunk
-// and processed with at most one bead per thread.
+// Beads of a tile are staged in shared memory in chunks of up to kBeadChunk.
 constexpr int kBeadChunk = 512;
-constexpr int kBeadThreads = 512;
 
 template <int P, typename T> struct BeadSmem {
     using patch_t = typename FixedPoint<T>::patch_t;
@@ -240,7 +238,7 @@ template <int P> __device__ __forceinline__ size_t patch_row_base(int row, int3 
 }
 
 template <int P, int MODE, typename T>
-__global__ void __launch_bounds__(kBeadThreads, (sizeof(T) == 4 && P <= 3) ? 2 : 1) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
     using PT = Patch<P>;
     using SM = BeadSmem<P, T>;
     using FP = FixedPoint<T>;
@@ -276,7 +274,7 @@ __global__ void __launch_bounds__(kBeadThreads, (sizeof(T) == 4 && P <= 3) ? 2 :
     if (kForce && SM::stage_grad && row_lane) {
         // stage the gradient fields of the patch as per-species (gx, gy, gz);
         // every row's loads are issued before any is used
-        constexpr int NWARP = kBeadThreads / 32;
+        constexpr int NWARP = 8;  // 256 threads
         constexpr int ROWS_PER_LANE = (W * W + NWARP * RPW - 1) / (NWARP * RPW);
         V v[ROWS_PER_LANE][3];
 #pragma unroll
@@ -312,13 +310,13 @@ __global__ void __launch_bounds__(kBeadThreads, (sizeof(T) == 4 && P <= 3) ? 2 :
         if (c0 != start) __syncthreads();  // the previous chunk is done with the staged beads
         {
             // all loads of the chunk in flight before the shared stores
-            constexpr int PER = kBeadChunk / kBeadThreads;
+            constexpr int PER = kBeadChunk / 256;
             T vx[PER], vy[PER], vz[PER];
             int vt[PER];
             int2 vn[PER];
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
-                const int j = threadIdx.x + k * kBeadThreads;
+                const int j = threadIdx.x + k * 256;
                 if (j < cnt) {
                     vx[k] = bf.px[c0 + j];
                     vy[k] = bf.py[c0 + j];
@@ -329,7 +327,7 @@ __global__ void __launch_bounds__(kBeadThreads, (sizeof(T) == 4 && P <= 3) ? 2 :
             }
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
-                const int j = threadIdx.x + k * kBeadThreads;
+                const int j = threadIdx.x + k * 256;
                 if (j < cnt) {
                     s_pos[j] = vx[k];
                     s_pos[kBeadChunk + j] = vy[k];
@@ -461,7 +459,7 @@ __global__ void __launch_bounds__(kBeadThreads, (sizeof(T) == 4 && P <= 3) ? 2 :
         }
     }
     if (MODE == kModeForce) {
-        __shared__ double red[5][kBeadThreads / 32];
+        __shared__ double red[5][8];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {

@@ -842,10 +842,10 @@ template <typename T> class Engine final : public EngineBase {
         const size_t sm = bead_smem();
         const BeadParams<T> p = bead_params();
         switch (mode) {
-            case kModeSpread: bead_kernel<P, kModeSpread, T><<<grid, kBeadThreads, sm, stream_>>>(p, bf); break;
-            case kModeForce: bead_kernel<P, kModeForce, T><<<grid, kBeadThreads, sm, stream_>>>(p, bf); break;
-            case kModeSetVel: bead_kernel<P, kModeSetVel, T><<<grid, kBeadThreads, sm, stream_>>>(p, bf); break;
-            default: bead_kernel<P, kModeStep, T><<<grid, kBeadThreads, sm, stream_>>>(p, bf); break;
+            case kModeSpread: bead_kernel<P, kModeSpread, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+            case kModeForce: bead_kernel<P, kModeForce, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+            case kModeSetVel: bead_kernel<P, kModeSetVel, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+            default: bead_kernel<P, kModeStep, T><<<grid, 256, sm, stream_>>>(p, bf); break;
         }
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
