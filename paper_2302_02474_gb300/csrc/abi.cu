@@ -30,7 +30,11 @@ tild_status from_engine(tild_ctx* c, tild_status st) {
     return st;
 }
 
-bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+// Grid sizes with a hand-written FFT: powers of two 8..256 and 24, 40, 48, 80.
+bool supported_n(int n) {
+    if (n >= 8 && n <= 256 && (n & (n - 1)) == 0) return true;
+    return n == 24 || n == 40 || n == 48 || n == 80;
+}
 
 bool valid_io(int dtype, int where) {
     return (dtype == TILD_DTYPE_F32 || dtype == TILD_DTYPE_F64) && (where == TILD_HOST || where == TILD_DEVICE);
@@ -52,8 +56,8 @@ tild_status tild_create(const tild_params* p, tild_ctx** out) {
         g_create_error = "tild_create: the box must be cubic with L > 0";
         return TILD_EUNSUPPORTED;
     }
-    if (p->n[0] != p->n[1] || p->n[0] != p->n[2] || !pow2_in(p->n[0], 8, 256)) {
-        g_create_error = "tild_create: the grid must be cubic with n a power of two in [8, 256]";
+    if (p->n[0] != p->n[1] || p->n[0] != p->n[2] || !supported_n(p->n[0])) {
+        g_create_error = "tild_create: the grid must be cubic with n a power of two in [8, 256] or 24, 40, 48, 80";
         return TILD_EUNSUPPORTED;
     }
     if (p->pmeorder < 1 || p->pmeorder > 4) {

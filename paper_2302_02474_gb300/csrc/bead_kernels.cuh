@@ -135,18 +135,17 @@ __device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_pa
                 }
             }
     } else {
-        const int nm = n - 1;
         const size_t M = (size_t)n * n * n;
 #pragma unroll
         for (int c = 0; c < P; ++c) {
-            const size_t oz = (size_t)((st.jz + c) & nm) * n * n;
+            const size_t oz = (size_t)pwrap(st.jz + c, n) * n * n;
 #pragma unroll
             for (int b = 0; b < P; ++b) {
-                const size_t oy = oz + (size_t)((st.jy + b) & nm) * n;
+                const size_t oy = oz + (size_t)pwrap(st.jy + b, n) * n;
                 const T wyz = st.wy[b] * st.wz[c];
 #pragma unroll
                 for (int a = 0; a < P; ++a) {
-                    const size_t g = oy + ((st.jx + a) & nm);
+                    const size_t g = oy + pwrap(st.jx + a, n);
                     const T w = st.wx[a] * wyz;
                     const cplx_t<T> vx = __ldg(grad + g);
                     const cplx_t<T> vy = __ldg(grad + M + g);
@@ -183,7 +182,6 @@ __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_pat
                 for (int a = 0; a < P; ++a) atomicAdd(base + row + a, FP::to_patch(st.wx[a] * wyz));
             }
     } else {
-        const int nm = n - 1;
         const size_t M = (size_t)n * n * n;
 #pragma unroll
         for (int c = 0; c < P; ++c)
@@ -192,7 +190,7 @@ __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_pat
                 const T wyz = st.wy[b] * st.wz[c];
 #pragma unroll
                 for (int a = 0; a < P; ++a) {
-                    const size_t g = ((size_t)((st.jz + c) & nm) * n + ((st.jy + b) & nm)) * n + ((st.jx + a) & nm);
+                    const size_t g = ((size_t)pwrap(st.jz + c, n) * n + pwrap(st.jy + b, n)) * n + pwrap(st.jx + a, n);
                     atomicAdd(rho_fx + K * M + g, FP::to_grid(st.wx[a] * wyz));
                 }
             }
@@ -233,8 +231,7 @@ template <int P> __device__ __forceinline__ size_t patch_row_base(int row, int3 
     plane = row / (W * W);
     const int rem = row - plane * W * W;
     const int lz = rem / W, ly = rem - lz * W;
-    const int nm = n - 1;
-    return ((size_t)((org.z + lz) & nm) * n + ((org.y + ly) & nm)) * n;
+    return ((size_t)pwrap(org.z + lz, n) * n + pwrap(org.y + ly, n)) * n;
 }
 
 template <int P, int MODE, typename T>
@@ -258,7 +255,6 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
     const int t = blockIdx.x;
     const int tx = t % p.tiles, ty = (t / p.tiles) % p.tiles, tz = t / (p.tiles * p.tiles);
     const int3 org = {tx * kTile + PT::lo, ty * kTile + PT::lo, tz * kTile + PT::lo};
-    const int nm = p.n - 1;
     const size_t M = (size_t)p.n * p.n * p.n;
     // patch rows of W points: RPW rows per warp, lane -> (row offset, x)
     constexpr int RPW = 32 / W;
@@ -267,7 +263,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
     const bool row_lane = rsub < RPW;
     const int row0 = (threadIdx.x >> 5) * RPW + rsub;
     const int rstride = (blockDim.x >> 5) * RPW;
-    const int gx = (org.x + lx) & nm;
+    const int gx = pwrap(org.x + lx, p.n);
     if (kSpread) {
         for (int i = threadIdx.x; i < SM::patches * PT::W3; i += blockDim.x) patch[i] = 0;
     }
@@ -496,7 +492,6 @@ __global__ void __launch_bounds__(256) adjoint_kernel(BeadParams<T> p, BeadBuffe
     dh_weight_derivs<P>(x * p.inv_dx, dx);
     dh_weight_derivs<P>(y * p.inv_dx, dy);
     dh_weight_derivs<P>(z * p.inv_dx, dz);
-    const int nm = p.n - 1;
     T gx = 0, gy = 0, gz = 0;
 #pragma unroll
     for (int c = 0; c < P; ++c)
@@ -504,7 +499,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(BeadParams<T> p, BeadBuffe
         for (int b = 0; b < P; ++b)
 #pragma unroll
             for (int a = 0; a < P; ++a) {
-                const size_t g = ((size_t)((st.jz + c) & nm) * p.n + ((st.jy + b) & nm)) * p.n + ((st.jx + a) & nm);
+                const size_t g = ((size_t)pwrap(st.jz + c, p.n) * p.n + pwrap(st.jy + b, p.n)) * p.n + pwrap(st.jx + a, p.n);
                 const cplx_t<T> v = pot[g];
                 const T w = species ? -v.x : v.y;  // w_A = Im, w_B = -Re of i (w_A + i w_B)
                 gx += dx[a] * st.wy[b] * st.wz[c] * w;

@@ -124,6 +124,10 @@ __device__ __forceinline__ normal3<double> gaussian3(uint32_t id, uint64_t step,
     return {m1 * c1, m1 * s1, m2 * c3};
 }
 
+// Periodic grid index for j in [-n, 2n) (any n; stencils and patches never
+// reach further than one period).
+__host__ __device__ __forceinline__ int pwrap(int j, int n) { return j < 0 ? j + n : (j >= n ? j - n : j); }
+
 // ------------------------------------------------- assignment weights
 
 // Charge-assignment weights of order P (P points per dimension), the

@@ -41,7 +41,7 @@ template <typename T> class Engine final : public EngineBase {
         P_ = cfg->pmeorder + 1;
         plane_fits_ = plane_smem() <= 200 * 1024;
         C_ = std::min(n_, (int)(128 / sizeof(V)));  // y-column tiles of the split passes
-        CZ_ = std::min(n_, (int)(128 / sizeof(V)));  // column tiles of the z pass
+        CZ_ = zpass_cols(n_);                          // column tiles of the z pass
         TILD_CUDA(cudaGetDevice(&device_));
         TILD_CUDA(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
         stream_ = own_stream_;
@@ -643,7 +643,7 @@ template <typename T> class Engine final : public EngineBase {
             TILD_CUDA(cudaFuncSetAttribute(y_columns<T, NN, 128 / sizeof(V), -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ycol_smem()));
             TILD_CUDA(cudaFuncSetAttribute(y_columns<T, NN, 128 / sizeof(V), +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ycol_smem()));
         }
-        constexpr int CC = NN < (int)(128 / sizeof(V)) ? NN : (int)(128 / sizeof(V));
+        constexpr int CC = zpass_cols(NN);
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
         return TILD_OK;
     }
@@ -672,6 +672,10 @@ template <typename T> class Engine final : public EngineBase {
             case 32: return f(ic<32>{});
             case 64: return f(ic<64>{});
             case 128: return f(ic<128>{});
+            case 24: return f(ic<24>{});
+            case 40: return f(ic<40>{});
+            case 48: return f(ic<48>{});
+            case 80: return f(ic<80>{});
             case 256: return dispatch_256(f);
         }
         err = "unsupported grid size";
@@ -719,6 +723,14 @@ template <typename T> class Engine final : public EngineBase {
         return dispatch_n([&](auto nn) { return this->template forward_n<decltype(nn)::value>(zero_after); });
     }
 
+    // z-pass column tile: 128 bytes of complex values, or the largest power of
+    // two dividing n when that is smaller
+    static constexpr int zpass_cols(int n) {
+        int c = (int)(128 / sizeof(V));
+        while (c > 1 && (n % c) != 0) c /= 2;
+        return c < n ? c : n;
+    }
+
     T two_pi_L() const { return (T)(2.0 * 3.14159265358979323846 / cfg_->L); }
 
     SpectralParams<T> spectral_params() const {
@@ -734,7 +746,7 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     template <int NN> tild_status zpass_n(double* partials, V* spec_out) {
-        constexpr int CC = NN < (int)(128 / sizeof(V)) ? NN : (int)(128 / sizeof(V));
+        constexpr int CC = zpass_cols(NN);
         z_spectral<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1), 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, spectral_params(), partials, spec_out);
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;

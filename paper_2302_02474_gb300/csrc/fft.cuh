@@ -1,4 +1,6 @@
-// Hand-written FFT building blocks for power-of-two lengths 8..256.
+// Hand-written FFT building blocks for lengths 8..256 that split as
+// N = N1 * N2 with N1 in {4, 8, 16} and N2 in {1, 3, 4, 5, 8, 16}
+// (powers of two, 24, 40, 48, 80).
 //
 // A length-N transform is split N = N1 * N2 (four-step / Cooley-Tukey):
 //   input index  j = j2 + N2 * j1,  output index k = k1 + N1 * k2,
@@ -28,6 +30,10 @@ template <> struct fft_split<32> { static constexpr int N1 = 8, N2 = 4; };
 template <> struct fft_split<64> { static constexpr int N1 = 8, N2 = 8; };
 template <> struct fft_split<128> { static constexpr int N1 = 16, N2 = 8; };
 template <> struct fft_split<256> { static constexpr int N1 = 16, N2 = 16; };
+template <> struct fft_split<24> { static constexpr int N1 = 8, N2 = 3; };
+template <> struct fft_split<40> { static constexpr int N1 = 8, N2 = 5; };
+template <> struct fft_split<48> { static constexpr int N1 = 16, N2 = 3; };
+template <> struct fft_split<80> { static constexpr int N1 = 16, N2 = 5; };
 
 // Multiply v by W_16^m = exp(DIR * 2 pi i m / 16); m is a compile-time
 // constant after unrolling, so the branches fold away.
@@ -60,8 +66,8 @@ template <int DIR, class V> __device__ __forceinline__ V w16_mul(int m, V v) {
     return {v.x * cr - v.y * ci, v.x * ci + v.y * cr};
 }
 
-// In-register DFT of R points (R = 1, 2, 4, 8, 16), natural order in and
-// out, radix-2 decimation in time.
+// In-register DFT of R points (R = 1, 2, 4, 8, 16 by radix-2 decimation in
+// time; 3 and 5 directly), natural order in and out.
 template <int R, int DIR, class V> struct reg_dft {
     static __device__ __forceinline__ void run(V (&v)[R]) {
         V e[R / 2], o[R / 2];
@@ -82,6 +88,44 @@ template <int R, int DIR, class V> struct reg_dft {
 };
 template <int DIR, class V> struct reg_dft<1, DIR, V> {
     static __device__ __forceinline__ void run(V (&)[1]) {}
+};
+
+// 3 points: X1,2 = x0 + cos(2pi/3)(x1 + x2) +/- i DIR' sin(2pi/3)(x1 - x2),
+// with the sign of the exponent DIR.
+template <int DIR, class V> struct reg_dft<3, DIR, V> {
+    static __device__ __forceinline__ void run(V (&v)[3]) {
+        using T = decltype(v[0].x);
+        const T c = T(-0.5), s = T(DIR) * T(0.86602540378443864676);  // DIR sin(2 pi / 3)
+        const V t1 = c_add(v[1], v[2]), t3 = c_sub(v[1], v[2]);
+        const V m = {v[0].x + c * t1.x, v[0].y + c * t1.y};
+        const V it = {-s * t3.y, s * t3.x};  // i s (x1 - x2)
+        v[0] = c_add(v[0], t1);
+        v[1] = c_add(m, it);
+        v[2] = c_sub(m, it);
+    }
+};
+
+// 5 points with t1 = x1 + x4, t2 = x2 + x3, t3 = x1 - x4, t4 = x2 - x3:
+// X1,4 = x0 + c1 t1 + c2 t2 +/- i (s1 t3 + s2 t4), X2,3 = x0 + c2 t1 + c1 t2
+// +/- i (s2 t3 - s1 t4), c_k = cos(2 pi k / 5), s_k = DIR sin(2 pi k / 5).
+template <int DIR, class V> struct reg_dft<5, DIR, V> {
+    static __device__ __forceinline__ void run(V (&v)[5]) {
+        using T = decltype(v[0].x);
+        const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);
+        const T s1 = T(DIR) * T(0.95105651629515357212), s2 = T(DIR) * T(0.58778525229247312917);
+        const V t1 = c_add(v[1], v[4]), t2 = c_add(v[2], v[3]);
+        const V t3 = c_sub(v[1], v[4]), t4 = c_sub(v[2], v[3]);
+        const V a = {v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y};
+        const V b = {v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y};
+        const V p = {s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y};
+        const V q = {s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y};
+        const V ip = {-p.y, p.x}, iq = {-q.y, q.x};
+        v[0] = {v[0].x + t1.x + t2.x, v[0].y + t1.y + t2.y};
+        v[1] = c_add(a, ip);
+        v[4] = c_sub(a, ip);
+        v[2] = c_add(b, iq);
+        v[3] = c_sub(b, iq);
+    }
 };
 
 // Twiddle table W_N^m = exp(-2 pi i m / N), m in [0, N), computed on the

@@ -323,7 +323,7 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
     const T qxB = raw_k<T, N>(kxB, sp.two_pi_over_L), qyB = raw_k<T, N>(ky[rB], sp.two_pi_over_L);
     const double kxy2A = (double)qxA * qxA + (double)qyA * qyA, kxy2B = (double)qxB * qxB + (double)qyB * qyB;
     for (int kz = threadIdx.x / C; kz < N; kz += 256 / C) {
-        const int kzB = (N - kz) & (N - 1);
+        const int kzB = kz == 0 ? 0 : N - kz;
         if (R == 1 && kzB * C + cB < kz * C + c) continue;  // the mirror element owns this pair
         const bool same = (R == 1) && (kzB == kz) && (cB == c);
         const V ZA = buf[kz * C + c];
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
     for (int i = threadIdx.x; i < N; i += blockDim.x) e1[i] = sp.kernel1d[i];
 
     const int p0 = blockIdx.x * C;
-    const int ky[2] = {(int)blockIdx.y, (N - (int)blockIdx.y) & (N - 1)};
+    const int ky[2] = {(int)blockIdx.y, blockIdx.y == 0 ? 0 : N - (int)blockIdx.y};
     const int R = (ky[0] == ky[1]) ? 1 : 2;
     const size_t NN = (size_t)N * N;
     auto zsrc = [&](int i) {

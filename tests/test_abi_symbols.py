@@ -54,7 +54,7 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.tild_create(ctypes.byref(p), ctypes.byref(ctx)) == B.TILD_EUNSUPPORTED
     assert b"cubic" in lib.tild_last_error(None)
     p.L[2] = 10.0
-    p.n[:] = [24, 24, 24]
+    p.n[:] = [20, 20, 20]
     assert lib.tild_create(ctypes.byref(p), ctypes.byref(ctx)) == B.TILD_EUNSUPPORTED
     p.n[:] = [16, 16, 16]
     p.pmeorder = 5

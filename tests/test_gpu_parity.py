@@ -84,7 +84,8 @@ def test_density_bit_identical_for_any_bead_order(B):
 # ------------------------------------------------------ spectrum / fields
 
 
-@pytest.mark.parametrize("prec,n", [("fp64", 8), ("fp64", 32), ("fp32", 16), ("fp32", 64), ("fp64", 128)])
+@pytest.mark.parametrize("prec,n", [("fp64", 8), ("fp64", 32), ("fp32", 16), ("fp32", 64), ("fp64", 128),
+                                    ("fp64", 24), ("fp32", 40), ("fp64", 48), ("fp32", 80)])
 def test_spectrum_matches_oracle_dft(B, prec, n):
     spec = I.small_system(n_chains=60, N=10, n_a=4, L=n / 2.0, n=n, precision=prec)
     t, m, pos = _setup(B, spec)
@@ -122,6 +123,25 @@ def test_forces_and_energies_match_oracle(B, prec, order):
     for k in ("bond", "chi", "kappa"):
         assert abs(e[k] - eref[k]) <= etol * abs(eref[k]), (k, e[k], eref[k])
     assert np.abs(e["net_force"]).max() < 1e-6 * np.abs(f).sum()
+
+
+@pytest.mark.parametrize("prec,n,order", [("fp64", 24, 1), ("fp64", 40, 2), ("fp32", 48, 1), ("fp64", 80, 3)])
+def test_mixed_radix_grids_forces_and_trajectory(B, prec, n, order):
+    """5-smooth grids (radix-3 and radix-5 FFT passes): forces, energies and
+    a 5-step trajectory against the oracle."""
+    spec = I.small_system(n_chains=90, N=10, n_a=4, L=n / 2.5, n=n, pmeorder=order, precision=prec, chi=1.3,
+                          kappa=8.0)
+    t, m, pos = _setup(B, spec, sort_every=3)
+    t.init_velocities()
+    f, e = t.compute()
+    assert _rel(f, O.forces(m, pos)) < FTOL[prec]
+    eref = O.energies(m, pos)
+    for k in ("chi", "kappa"):
+        assert abs(e[k] - eref[k]) <= (1e-10 if prec == "fp64" else 1e-6) * abs(eref[k])
+    t.step(5)
+    st = O.run(m, O.initial_state(m, pos), 5)
+    d = O.minimum_image(t.positions() - st.pos, m.L)
+    assert np.abs(d).max() < (1e-10 if prec == "fp64" else 1e-4 * m.L)
 
 
 def test_homogeneous_melt_zero_field_force(B):
