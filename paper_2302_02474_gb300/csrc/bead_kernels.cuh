@@ -235,7 +235,7 @@ template <int P> __device__ __forceinline__ size_t patch_row_base(int row, int3 
 }
 
 template <int P, int MODE, typename T>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
+__device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const BeadBuffers<T>& bf, int t) {
     using PT = Patch<P>;
     using SM = BeadSmem<P, T>;
     using FP = FixedPoint<T>;
@@ -252,7 +252,6 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
     int2* s_nbr = reinterpret_cast<int2*>(smem_raw + SM::nbr_off);
     int* s_tag = reinterpret_cast<int*>(smem_raw + SM::tag_off);
 
-    const int t = blockIdx.x;
     const int tx = t % p.tiles, ty = (t / p.tiles) % p.tiles, tz = t / (p.tiles * p.tiles);
     const int3 org = {tx * kTile + PT::lo, ty * kTile + PT::lo, tz * kTile + PT::lo};
     const size_t M = (size_t)p.n * p.n * p.n;
@@ -470,6 +469,23 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_
             bf.partials[5 * (size_t)t + threadIdx.x] = s;
         }
     }
+}
+
+template <int P, int MODE, typename T>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
+    bead_kernel_body<P, MODE, T>(p, bf, blockIdx.x);
+}
+
+// Batched form: blocks [r * tiles^3, (r + 1) * tiles^3) serve replica r.
+template <typename T> struct BeadArgs {
+    BeadParams<T> p;
+    BeadBuffers<T> bf;
+};
+template <int P, int MODE, typename T>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2)
+    bead_kernel_batched(const BeadArgs<T>* __restrict__ args, int tiles3) {
+    const int r = blockIdx.x / tiles3;
+    bead_kernel_body<P, MODE, T>(args[r].p, args[r].bf, blockIdx.x - r * tiles3);
 }
 
 // Exact gradient of the gridded energy with respect to the bead positions:

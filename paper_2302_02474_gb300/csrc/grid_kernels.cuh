@@ -123,21 +123,32 @@ __device__ __forceinline__ void load_fixed_rows(unsigned long long* __restrict__
 // Forward xy pass on whole z-planes (plane fits in shared memory).
 // grid = n (one CTA per z-plane), block = 512.
 // --------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(512) xy_forward_plane(unsigned long long* __restrict__ rho_fx,
-                                                         cplx_t<T>* __restrict__ Zxy,
-                                                         const cplx_t<T>* __restrict__ tw_g, T scale,
-                                                         int zero_after, unsigned long long* step_ctr) {
+template <typename T> struct ForwardArgs {
+    unsigned long long* rho_fx;
+    cplx_t<T>* Zxy;
+    const cplx_t<T>* tw;
+    T scale;
+    int zero_after;
+    unsigned long long* step_ctr;
+};
+
+template <typename T, int N> __device__ __forceinline__ void xy_forward_plane_body(const ForwardArgs<T>& args, int bx) {
     using V = cplx_t<T>;
+    unsigned long long* __restrict__ rho_fx = args.rho_fx;
+    cplx_t<T>* __restrict__ Zxy = args.Zxy;
+    const cplx_t<T>* __restrict__ tw_g = args.tw;
+    const T scale = args.scale;
+    const int zero_after = args.zero_after;
+    unsigned long long* step_ctr = args.step_ctr;
     constexpr int PITCH = row_pitch(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* plane = tw + N;
     load_twiddles(tw, tw_g, N);
     // a step's first kernel advances the noise counter to n+1
-    if (step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1ull;
+    if (step_ctr && bx == 0 && threadIdx.x == 0) *step_ctr += 1ull;
 
-    const int z = blockIdx.x;
+    const int z = bx;
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)z * N * N;
     // load + convert: pairs of x so that global accesses are 16-byte vectors
@@ -151,14 +162,36 @@ __global__ void __launch_bounds__(512) xy_forward_plane(unsigned long long* __re
     }
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(512) xy_forward_plane(unsigned long long* __restrict__ rho_fx,
+                                                         cplx_t<T>* __restrict__ Zxy,
+                                                         const cplx_t<T>* __restrict__ tw_g, T scale,
+                                                         int zero_after, unsigned long long* step_ctr) {
+    xy_forward_plane_body<T, N>(ForwardArgs<T>{rho_fx, Zxy, tw_g, scale, zero_after, step_ctr}, blockIdx.x);
+}
+
+// Batched form: replica blockIdx.y of a table of replicas with the same grid.
+template <typename T, int N>
+__global__ void __launch_bounds__(512) xy_forward_plane_batched(const ForwardArgs<T>* __restrict__ args) {
+    xy_forward_plane_body<T, N>(args[blockIdx.y], blockIdx.x);
+}
+
 // --------------------------------------------------------------------------
 // Inverse xy pass on whole z-planes: grid = (n, 3), block = 512.
 // --------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restrict__ H,
-                                                         cplx_t<T>* __restrict__ grad,
-                                                         const cplx_t<T>* __restrict__ tw_g, T two_pi_over_L) {
+template <typename T> struct InverseArgs {
+    const cplx_t<T>* H;
+    cplx_t<T>* grad;
+    const cplx_t<T>* tw;
+    T two_pi_over_L;
+};
+
+template <typename T, int N> __device__ __forceinline__ void xy_inverse_plane_body(const InverseArgs<T>& args, int bx, int by) {
     using V = cplx_t<T>;
+    const cplx_t<T>* __restrict__ H = args.H;
+    cplx_t<T>* __restrict__ grad = args.grad;
+    const cplx_t<T>* __restrict__ tw_g = args.tw;
+    const T two_pi_over_L = args.two_pi_over_L;
     constexpr int PITCH = row_pitch(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
@@ -167,9 +200,9 @@ __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restr
 
     // direction d: x from i k_x G, y from i k_y G, z from G_z (field 2);
     // d = 3 (optional): the potentials themselves, i (w_A + i w_B), from G
-    const int d = blockIdx.y;
+    const int d = by;
     const size_t M = (size_t)N * N * N;
-    const size_t src = (d == 2 ? 2 * M : 0) + (size_t)blockIdx.x * N * N;
+    const size_t src = (d == 2 ? 2 * M : 0) + (size_t)bx * N * N;
     batched_load<N * N, 512, V>([&](int i) { return H[src + i]; },
                                 [&](int i, V v) {
                                     const int ky = i / N;
@@ -186,8 +219,21 @@ __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restr
         __syncthreads();
     }
     smem_fft_lines<N, +1, N, 512>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
-    const size_t dst = (size_t)d * M + (size_t)blockIdx.x * N * N;
+    const size_t dst = (size_t)d * M + (size_t)bx * N * N;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) grad[dst + i] = plane[(i / N) * PITCH + i % N];
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restrict__ H,
+                                                         cplx_t<T>* __restrict__ grad,
+                                                         const cplx_t<T>* __restrict__ tw_g, T two_pi_over_L) {
+    xy_inverse_plane_body<T, N>(InverseArgs<T>{H, grad, tw_g, two_pi_over_L}, blockIdx.x, blockIdx.y);
+}
+
+// Batched form: replica blockIdx.z.
+template <typename T, int N>
+__global__ void __launch_bounds__(512) xy_inverse_plane_batched(const InverseArgs<T>* __restrict__ args) {
+    xy_inverse_plane_body<T, N>(args[blockIdx.z], blockIdx.x, blockIdx.y);
 }
 
 // --------------------------------------------------------------------------
@@ -370,12 +416,24 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
     smem_fft_lines<N, +1, 2 * R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
 }
 
+template <typename T> struct ZArgs {
+    const cplx_t<T>* Zxy;
+    cplx_t<T>* H;
+    const cplx_t<T>* tw;
+    SpectralParams<T> sp;
+    double* energy_partials;
+    cplx_t<T>* spectrum_out;
+};
+
 template <typename T, int N, int C>
-__global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ Zxy, cplx_t<T>* __restrict__ H,
-                                                  const cplx_t<T>* __restrict__ tw_g, SpectralParams<T> sp,
-                                                  double* __restrict__ energy_partials,
-                                                  cplx_t<T>* __restrict__ spectrum_out) {
+__device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, int by, int gdx) {
     using V = cplx_t<T>;
+    const cplx_t<T>* __restrict__ Zxy = args.Zxy;
+    cplx_t<T>* __restrict__ H = args.H;
+    const cplx_t<T>* __restrict__ tw_g = args.tw;
+    const SpectralParams<T> sp = args.sp;
+    double* __restrict__ energy_partials = args.energy_partials;
+    cplx_t<T>* __restrict__ spectrum_out = args.spectrum_out;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* buf = tw + N;
@@ -385,8 +443,8 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
     load_twiddles(tw, tw_g, N);
     for (int i = threadIdx.x; i < N; i += blockDim.x) e1[i] = sp.kernel1d[i];
 
-    const int p0 = blockIdx.x * C;
-    const int ky[2] = {(int)blockIdx.y, blockIdx.y == 0 ? 0 : N - (int)blockIdx.y};
+    const int p0 = bx * C;
+    const int ky[2] = {by, by == 0 ? 0 : N - by};
     const int R = (ky[0] == ky[1]) ? 1 : 2;
     const size_t NN = (size_t)N * N;
     auto zsrc = [&](int i) {
@@ -432,7 +490,7 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
         if (threadIdx.x < 4) {
             double sum = 0;
             for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) sum += red[threadIdx.x][w];
-            const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+            const size_t b = (size_t)by * gdx + bx;
             energy_partials[4 * b + threadIdx.x] = sum;
         }
     }
@@ -443,6 +501,21 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
         const int z = rem / C, c = rem % C;
         H[f * M + z * NN + (size_t)ky[r] * N + p0 + c] = buf[i];
     }
+}
+
+template <typename T, int N, int C>
+__global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ Zxy, cplx_t<T>* __restrict__ H,
+                                                  const cplx_t<T>* __restrict__ tw_g, SpectralParams<T> sp,
+                                                  double* __restrict__ energy_partials,
+                                                  cplx_t<T>* __restrict__ spectrum_out) {
+    z_spectral_body<T, N, C>(ZArgs<T>{Zxy, H, tw_g, sp, energy_partials, spectrum_out}, blockIdx.x, blockIdx.y,
+                             gridDim.x);
+}
+
+// Batched form: replica blockIdx.z.
+template <typename T, int N, int C>
+__global__ void __launch_bounds__(256) z_spectral_batched(const ZArgs<T>* __restrict__ args) {
+    z_spectral_body<T, N, C>(args[blockIdx.z], blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 }  // namespace tild
