@@ -252,8 +252,38 @@ tild_status tild_profile_steps(tild_ctx* ctx, int n_steps, double* ms);
 /* Number of kernel launches one tild_step(ctx, n) issues for this context. */
 tild_status tild_launches_per_steps(tild_ctx* ctx, int64_t n_steps, int64_t* launches);
 
+/*
+ * Batched form: step several independent systems ("replicas": contexts with
+ * their own chains, box, grid, chi, kappa, a and seed; same precision and
+ * device) together. Replicas with the same grid size and assignment order
+ * share every kernel launch of a step (four per group), reading their
+ * arguments from device tables; whole re-binning cycles of all replicas are
+ * captured as one CUDA graph. Each replica's trajectory is bit-identical to
+ * stepping its context alone with the same re-binning period (the batch uses
+ * the first context's sort_every).
+ *
+ * tild_batch_create: every context must have positions and velocities and a
+ * grid of at most 128 points (FP32) or 64 (FP64) per edge. The contexts stay
+ * owned by the caller and must outlive the batch; creating the batch
+ * re-bins them. While the batch exists, change no context's chains,
+ * interactions, integrator, positions or velocities (results would not
+ * reflect the change); reading a context (positions, energies, state) is
+ * fine after tild_batch_synchronize.
+ * tild_batch_step: advance every replica n_steps (asynchronous on the
+ * batch's own stream). tild_batch_synchronize waits for it and reports
+ * TILD_ENAN if any replica flagged a non-finite force. Errors are described
+ * by tild_last_error(NULL).
+ */
+typedef struct tild_batch tild_batch;
+tild_status tild_batch_create(int n_replicas, tild_ctx* const* replicas, tild_batch** out);
+tild_status tild_batch_step(tild_batch* batch, int64_t n_steps);
+tild_status tild_batch_synchronize(tild_batch* batch);
+tild_status tild_batch_launches_per_steps(tild_batch* batch, int64_t n_steps, int64_t* launches);
+tild_status tild_batch_destroy(tild_batch* batch);
+
 /* Description of the last error on this context (or, when ctx is NULL, of
- * the last failed tild_create or tild_spread_density_noalloc). Never NULL. */
+ * the last failed tild_create, tild_batch_* call or
+ * tild_spread_density_noalloc). Never NULL. */
 const char* tild_last_error(tild_ctx* ctx);
 
 /*

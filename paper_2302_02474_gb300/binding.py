@@ -80,6 +80,11 @@ _SIGS = {
     "tild_profile_steps": [_P, _I, ctypes.POINTER(ctypes.c_double)],
     "tild_launches_per_steps": [_P, _I64, ctypes.POINTER(_I64)],
     "tild_spread_density_noalloc": [_P, _P, _I64, ctypes.c_double, _I, _I, _P, _P],
+    "tild_batch_create": [_I, ctypes.POINTER(_P), ctypes.POINTER(_P)],
+    "tild_batch_step": [_P, _I64],
+    "tild_batch_synchronize": [_P],
+    "tild_batch_launches_per_steps": [_P, _I64, ctypes.POINTER(_I64)],
+    "tild_batch_destroy": [_P],
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -322,3 +327,44 @@ class Tild:
         v = ctypes.c_int64()
         self._chk(self.lib.tild_launches_per_steps(self.ctx, int(n_steps), ctypes.byref(v)))
         return v.value
+
+
+class TildBatch:
+    """Several Tild contexts stepped together (tild_batch_*)."""
+
+    def __init__(self, replicas: Sequence[Tild]):
+        lib = load()
+        self.replicas = list(replicas)
+        arr = (ctypes.c_void_p * len(self.replicas))(*[r.ctx.value for r in self.replicas])
+        h = ctypes.c_void_p()
+        check(lib.tild_batch_create(len(self.replicas), arr, ctypes.byref(h)), None)
+        self.h = h
+        self.lib = lib
+
+    def step(self, n: int = 1) -> None:
+        check(self.lib.tild_batch_step(self.h, int(n)), None)
+
+    def synchronize(self) -> None:
+        check(self.lib.tild_batch_synchronize(self.h), None)
+
+    def launches(self, n_steps: int) -> int:
+        v = ctypes.c_int64()
+        check(self.lib.tild_batch_launches_per_steps(self.h, int(n_steps), ctypes.byref(v)), None)
+        return v.value
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.tild_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

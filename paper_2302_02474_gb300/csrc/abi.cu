@@ -16,6 +16,10 @@ struct tild_ctx {
     std::string err;
 };
 
+struct tild_batch {
+    std::unique_ptr<BatchBase> b;
+};
+
 namespace {
 
 std::string g_create_error = "no error";
@@ -293,6 +297,68 @@ tild_status tild_launches_per_steps(tild_ctx* c, int64_t n_steps, int64_t* launc
     if (!c || !launches || n_steps < 0) return fail(c, TILD_EINVAL, "launches_per_steps: bad argument");
     if (!c->have_chains) return fail(c, TILD_ESTATE, "launches_per_steps: chains not set");
     *launches = c->eng->launches(n_steps);
+    return TILD_OK;
+}
+
+tild_status tild_batch_create(int n, tild_ctx* const* ctxs, tild_batch** out) {
+    if (!out || !ctxs || n < 1) {
+        g_create_error = "batch_create: need n >= 1 contexts and an output pointer";
+        return TILD_EINVAL;
+    }
+    *out = nullptr;
+    std::vector<EngineBase*> engines;
+    const int prec = ctxs[0] ? ctxs[0]->cfg.precision : -1;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) {
+            g_create_error = "batch_create: NULL context";
+            return TILD_EINVAL;
+        }
+        if (ctxs[i]->cfg.precision != prec) {
+            g_create_error = "batch_create: all contexts must have the same precision";
+            return TILD_EINVAL;
+        }
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) {
+                g_create_error = "batch_create: a context appears twice";
+                return TILD_EINVAL;
+            }
+        engines.push_back(ctxs[i]->eng.get());
+    }
+    std::string err;
+    BatchBase* b = prec == TILD_FP32 ? make_batch_f32(engines, err) : make_batch_f64(engines, err);
+    if (!b) {
+        g_create_error = "batch_create: " + err;
+        return TILD_EINVAL;
+    }
+    *out = new tild_batch{std::unique_ptr<BatchBase>(b)};
+    return TILD_OK;
+}
+
+tild_status tild_batch_step(tild_batch* b, int64_t n_steps) {
+    if (!b || n_steps < 0) {
+        g_create_error = "batch_step: bad argument";
+        return TILD_EINVAL;
+    }
+    const tild_status st = b->b->step(n_steps);
+    if (st) g_create_error = "batch_step: " + b->b->err;
+    return st;
+}
+
+tild_status tild_batch_synchronize(tild_batch* b) {
+    if (!b) return TILD_EINVAL;
+    const tild_status st = b->b->synchronize();
+    if (st) g_create_error = "batch_synchronize: " + b->b->err;
+    return st;
+}
+
+tild_status tild_batch_launches_per_steps(tild_batch* b, int64_t n_steps, int64_t* launches) {
+    if (!b || !launches || n_steps < 0) return TILD_EINVAL;
+    *launches = b->b->launches(n_steps);
+    return TILD_OK;
+}
+
+tild_status tild_batch_destroy(tild_batch* b) {
+    delete b;  // waits for the batch's stream
     return TILD_OK;
 }
 

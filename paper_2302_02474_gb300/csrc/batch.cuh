@@ -1,0 +1,345 @@
+// Batched form: many independent TILD systems (replicas with their own
+// bead counts, boxes, grids, chi, kappa and seeds) stepped together.
+//
+// Replicas are grouped by (grid size, assignment order); every step issues
+// four launches per group (forward xy, z pass, inverse xy, bead kernel) whose
+// blocks look up their replica in device tables of per-replica arguments.
+// Re-binning runs per replica. Whole re-binning cycles (re-bin, K steps,
+// re-bin, K steps for every replica) are captured once as one CUDA graph and
+// replayed. Each replica's results are bit-identical to stepping its context
+// alone: the kernels and their arguments are the same.
+#pragma once
+
+#include <map>
+#include <utility>
+
+#include "engine.cuh"
+
+namespace tild {
+
+template <typename T> class BatchEngine final : public BatchBase {
+    using V = cplx_t<T>;
+    using E = Engine<T>;
+
+    struct Group {
+        int n = 0, P = 2, C = 16, tiles3 = 0;
+        std::vector<E*> reps;
+        ForwardArgs<T>* d_fwd = nullptr;
+        ZArgs<T>* d_z = nullptr;
+        InverseArgs<T>* d_inv = nullptr;
+        BeadArgs<T>* d_bead[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [pos parity][u, id parity]
+    };
+
+   public:
+    ~BatchEngine() override {
+        if (stream_) cudaStreamSynchronize(stream_);
+        if (graph_) cudaGraphExecDestroy(graph_);
+        for (auto& g : groups_) {
+            cudaFree(g.d_fwd);
+            cudaFree(g.d_z);
+            cudaFree(g.d_inv);
+            for (auto& row : g.d_bead)
+                for (auto* q : row) cudaFree(q);
+        }
+        if (stream_) cudaStreamDestroy(stream_);
+    }
+
+    tild_status init(const std::vector<EngineBase*>& engines) {
+        if (engines.empty()) {
+            err = "batch: no replicas";
+            return TILD_EINVAL;
+        }
+        int dev0 = -1;
+        for (EngineBase* b : engines) {
+            E* e = static_cast<E*>(b);
+            if (!e->has_velocities()) {
+                err = "batch: every replica needs positions and velocities";
+                return TILD_ESTATE;
+            }
+            if (dev0 < 0) dev0 = e->device_;
+            if (e->device_ != dev0) {
+                err = "batch: replicas must share one device";
+                return TILD_EINVAL;
+            }
+            if (!e->plane_fits_) {
+                err = "batch: replica grids must fit the single-plane xy passes";
+                return TILD_EUNSUPPORTED;
+            }
+            reps_.push_back(e);
+        }
+        K_ = reps_[0]->cfg_->sort_every;
+        TILD_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+        // bring every replica to a common state: work on its stream done,
+        // freshly re-binned, current buffers in slot 0
+        for (E* e : reps_) {
+            TILD_CUDA(cudaStreamSynchronize(e->stream_));
+            tild_status st = e->enqueue_sort(stream_);
+            if (st) return fail_from(e);
+            const size_t N = e->cfg_->n_beads;
+            if (e->cur_pos_ != 0) {
+                TILD_CUDA(cudaMemcpyAsync(e->pos_[0], e->pos_[1], 3 * N * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
+                e->cur_pos_ = 0;
+            }
+            if (e->cur_u_ != 0) {
+                TILD_CUDA(cudaMemcpyAsync(e->u_[0], e->u_[1], 3 * N * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
+                TILD_CUDA(cudaMemcpyAsync(e->id_[0], e->id_[1], N * sizeof(int), cudaMemcpyDeviceToDevice, stream_));
+                e->cur_u_ = e->cur_id_ = 0;
+            }
+            e->invalidate_graph();
+        }
+        cur_pos_ = cur_uid_ = 0;
+        steps_since_sort_ = 0;
+        // groups by (grid, order)
+        std::map<std::pair<int, int>, size_t> index;
+        for (E* e : reps_) {
+            const auto key = std::make_pair(e->n_, e->P_);
+            if (!index.count(key)) {
+                index[key] = groups_.size();
+                Group g;
+                g.n = e->n_;
+                g.P = e->P_;
+                g.C = E::zpass_cols(e->n_);
+                g.tiles3 = e->n_tiles_;
+                groups_.push_back(g);
+            }
+            groups_[index[key]].reps.push_back(e);
+        }
+        for (Group& g : groups_) {
+            tild_status st = build_tables(g);
+            if (st) return st;
+        }
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return TILD_OK;
+    }
+
+    tild_status step(int64_t n) override {
+        tild_status st;
+        const int64_t n0 = n;
+        while (n > 0) {
+            if (steps_since_sort_ >= K_ && n >= 2 * (int64_t)K_) {
+                if ((st = run_cycle_graph())) return st;
+                n -= 2 * (int64_t)K_;
+                continue;
+            }
+            if (steps_since_sort_ >= K_ && (st = sort_all())) return st;
+            if ((st = step_all())) return st;
+            --n;
+        }
+        for (E* e : reps_) {
+            e->host_step_ += n0;
+            e->steps_since_sort_ = steps_since_sort_;
+        }
+        return TILD_OK;
+    }
+
+    tild_status synchronize() override {
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        for (E* e : reps_) {
+            const tild_status st = e->check_err();
+            if (st) return fail_from(e);
+        }
+        return TILD_OK;
+    }
+
+    int64_t launches(int64_t n) const override {
+        int64_t since = steps_since_sort_, sorts = 0;
+        for (int64_t s = 0; s < n; ++s) {
+            if (since >= K_) {
+                ++sorts;
+                since = 0;
+            }
+            ++since;
+        }
+        return n * 4 * (int64_t)groups_.size() + sorts * 8 * (int64_t)reps_.size();
+    }
+
+   private:
+    std::vector<E*> reps_;
+    std::vector<Group> groups_;
+    cudaStream_t stream_ = nullptr;
+    int K_ = 20;
+    int cur_pos_ = 0, cur_uid_ = 0, steps_since_sort_ = 0;
+    cudaGraphExec_t graph_ = nullptr;
+
+    tild_status fail_from(E* e) {
+        err = e->err;
+        return TILD_EDEVICE;
+    }
+
+    template <class A> tild_status upload(A** dst, const std::vector<A>& v) {
+        TILD_CUDA(cudaMalloc(dst, v.size() * sizeof(A)));
+        TILD_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(A), cudaMemcpyHostToDevice));
+        return TILD_OK;
+    }
+
+    tild_status build_tables(Group& g) {
+        std::vector<ForwardArgs<T>> f;
+        std::vector<ZArgs<T>> z;
+        std::vector<InverseArgs<T>> inv;
+        for (E* e : g.reps) {
+            f.push_back(ForwardArgs<T>{e->rho_fx_, e->Zxy_, e->tw_, e->density_scale(), 1, e->counters_});
+            // the z pass needs the kernel table of the replica's current a
+            if (e->kernel_a_ != e->cfg_->a) {
+                tild_status st = e->enqueue_zpass(nullptr, nullptr);  // refreshes the table
+                if (st) return fail_from(e);
+            }
+            z.push_back(ZArgs<T>{e->Zxy_, e->H_, e->tw_, e->spectral_params(), nullptr, nullptr});
+            inv.push_back(InverseArgs<T>{e->H_, e->grad_, e->tw_, e->two_pi_L()});
+        }
+        tild_status st;
+        if ((st = upload(&g.d_fwd, f)) || (st = upload(&g.d_z, z)) || (st = upload(&g.d_inv, inv))) return st;
+        for (int pp = 0; pp < 2; ++pp)
+            for (int q = 0; q < 2; ++q) {
+                std::vector<BeadArgs<T>> b;
+                for (E* e : g.reps) {
+                    const size_t N = e->cfg_->n_beads;
+                    BeadArgs<T> a;
+                    a.p = e->bead_params();
+                    a.bf = e->bead_buffers();
+                    a.bf.px = e->pos_[pp];
+                    a.bf.py = a.bf.px + N;
+                    a.bf.pz = a.bf.py + N;
+                    a.bf.qx = e->pos_[1 - pp];
+                    a.bf.qy = a.bf.qx + N;
+                    a.bf.qz = a.bf.qy + N;
+                    a.bf.ux = e->u_[q];
+                    a.bf.uy = a.bf.ux + N;
+                    a.bf.uz = a.bf.uy + N;
+                    a.bf.id = e->id_[q];
+                    b.push_back(a);
+                }
+                if ((st = upload(&g.d_bead[pp][q], b))) return st;
+            }
+        // kernel attributes (same dynamic shared memory as the single path)
+        E* e0 = g.reps[0];
+        return dispatch_group(g, [&](auto nn, auto pp) -> tild_status {
+            constexpr int NN = decltype(nn)::value, PP = decltype(pp)::value;
+            if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
+                constexpr int CC = E::zpass_cols(NN);
+                TILD_CUDA(cudaFuncSetAttribute(xy_forward_plane_batched<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)e0->plane_smem()));
+                TILD_CUDA(cudaFuncSetAttribute(xy_inverse_plane_batched<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)e0->plane_smem()));
+                TILD_CUDA(cudaFuncSetAttribute(z_spectral_batched<T, NN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)e0->zpass_smem()));
+                TILD_CUDA(cudaFuncSetAttribute(bead_kernel_batched<PP, kModeStep, T>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e0->bead_smem()));
+            }
+            return TILD_OK;
+        });
+    }
+
+    template <int V_> struct ic {
+        static constexpr int value = V_;
+    };
+
+    template <class F> tild_status dispatch_p(int P, F&& f) {
+        switch (P) {
+            case 2: return f(ic<2>{});
+            case 3: return f(ic<3>{});
+            case 4: return f(ic<4>{});
+            default: return f(ic<5>{});
+        }
+    }
+
+    template <class F> tild_status dispatch_group(const Group& g, F&& f) {
+        auto with_n = [&](auto nn) { return dispatch_p(g.P, [&](auto pp) { return f(nn, pp); }); };
+        switch (g.n) {
+            case 8: return with_n(ic<8>{});
+            case 16: return with_n(ic<16>{});
+            case 24: return with_n(ic<24>{});
+            case 32: return with_n(ic<32>{});
+            case 40: return with_n(ic<40>{});
+            case 48: return with_n(ic<48>{});
+            case 64: return with_n(ic<64>{});
+            case 80: return with_n(ic<80>{});
+            case 128: return with_n(ic<128>{});
+        }
+        err = "batch: unsupported replica grid";
+        return TILD_EUNSUPPORTED;
+    }
+
+    tild_status step_all() {
+        for (Group& g : groups_) {
+            const unsigned R = (unsigned)g.reps.size();
+            E* e0 = g.reps[0];
+            tild_status st = dispatch_group(g, [&](auto nn, auto pp) -> tild_status {
+                constexpr int NN = decltype(nn)::value, PP = decltype(pp)::value;
+                if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
+                    constexpr int CC = E::zpass_cols(NN);
+                    xy_forward_plane_batched<T, NN><<<dim3(NN, R), 512, e0->plane_smem(), stream_>>>(g.d_fwd);
+                    z_spectral_batched<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1, R), 256, e0->zpass_smem(), stream_>>>(g.d_z);
+                    xy_inverse_plane_batched<T, NN><<<dim3(NN, 3, R), 512, e0->plane_smem(), stream_>>>(g.d_inv);
+                    bead_kernel_batched<PP, kModeStep, T><<<(unsigned)g.tiles3 * R, 256, e0->bead_smem(), stream_>>>(
+                        g.d_bead[cur_pos_][cur_uid_], g.tiles3);
+                }
+                return TILD_OK;
+            });
+            if (st) return st;
+        }
+        TILD_CUDA(cudaGetLastError());
+        cur_pos_ ^= 1;
+        for (E* e : reps_) e->cur_pos_ ^= 1;
+        ++steps_since_sort_;
+        return TILD_OK;
+    }
+
+    tild_status sort_all() {
+        for (E* e : reps_) {
+            if (e->enqueue_sort(stream_)) return fail_from(e);
+        }
+        cur_pos_ ^= 1;
+        cur_uid_ ^= 1;
+        steps_since_sort_ = 0;
+        return TILD_OK;
+    }
+
+    tild_status run_cycle_graph() {
+        if (!graph_) {
+            // host-side parities return to their values after a full cycle
+            struct Snap {
+                int p, u, i, s;
+            };
+            std::vector<Snap> snap;
+            for (E* e : reps_) snap.push_back({e->cur_pos_, e->cur_u_, e->cur_id_, e->steps_since_sort_});
+            const int bp = cur_pos_, bu = cur_uid_, bs = steps_since_sort_;
+            cudaGraph_t g;
+            TILD_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+            tild_status st = TILD_OK;
+            for (int half = 0; half < 2 && !st; ++half) {
+                st = sort_all();
+                for (int s = 0; s < K_ && !st; ++s) st = step_all();
+            }
+            cudaError_t e = cudaStreamEndCapture(stream_, &g);
+            if (st) return st;
+            TILD_CUDA(e);
+            e = cudaGraphInstantiate(&graph_, g, 0);
+            cudaGraphDestroy(g);
+            TILD_CUDA(e);
+            for (size_t k = 0; k < reps_.size(); ++k) {
+                reps_[k]->cur_pos_ = snap[k].p;
+                reps_[k]->cur_u_ = snap[k].u;
+                reps_[k]->cur_id_ = snap[k].i;
+                reps_[k]->steps_since_sort_ = snap[k].s;
+            }
+            cur_pos_ = bp;
+            cur_uid_ = bu;
+            steps_since_sort_ = bs;
+        }
+        TILD_CUDA(cudaGraphLaunch(graph_, stream_));
+        steps_since_sort_ = K_;
+        return TILD_OK;
+    }
+};
+
+template <typename T> BatchBase* make_batch(const std::vector<EngineBase*>& engines, std::string& err) {
+    BatchEngine<T>* b = new BatchEngine<T>();
+    if (b->init(engines) != TILD_OK) {
+        err = b->err;
+        delete b;
+        return nullptr;
+    }
+    return b;
+}
+
+}  // namespace tild

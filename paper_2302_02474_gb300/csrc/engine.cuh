@@ -27,8 +27,11 @@ namespace tild {
 
 constexpr uint64_t kStateMagic = 0x54494c4453544154ull;  // "TILDSTAT"
 
+template <typename T> class BatchEngine;
+
 template <typename T> class Engine final : public EngineBase {
     using V = cplx_t<T>;
+    friend class BatchEngine<T>;
 
    public:
     ~Engine() override { release(); }
@@ -886,7 +889,8 @@ template <typename T> class Engine final : public EngineBase {
         return TILD_OK;
     }
 
-    tild_status enqueue_sort() {
+    tild_status enqueue_sort(cudaStream_t on = nullptr) {
+        cudaStream_t stream_ = on ? on : this->stream_;  // the batch re-bins on its own stream
         const int N = cfg_->n_beads;
         const size_t N3 = N;
         TILD_CUDA(cudaMemsetAsync(counts_, 0, (n_tiles_ + 1) * sizeof(int), stream_));

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "tild.h"
 #include "common.cuh"
@@ -61,10 +62,24 @@ class EngineBase {
     virtual void params_changed() = 0;
 };
 
+// Several contexts stepped together (batched form).
+class BatchBase {
+   public:
+    virtual ~BatchBase() {}
+    std::string err;
+    virtual tild_status step(int64_t n) = 0;
+    virtual tild_status synchronize() = 0;
+    virtual int64_t launches(int64_t n) const = 0;
+};
+
 // Error text returned by tild_last_error(NULL).
 void set_global_error(const std::string& msg);
 
 EngineBase* make_engine_f32();
 EngineBase* make_engine_f64();
+// Engines must all be of the factory's precision, with positions and
+// velocities set; on failure returns nullptr and sets err.
+BatchBase* make_batch_f32(const std::vector<EngineBase*>& engines, std::string& err);
+BatchBase* make_batch_f64(const std::vector<EngineBase*>& engines, std::string& err);
 
 }  // namespace tild

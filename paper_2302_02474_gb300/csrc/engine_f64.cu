@@ -1,6 +1,9 @@
-// FP64 instantiation of the TILD engine (everything in FP64).
-#include "engine.cuh"
+// FP64 instantiation of the TILD engine (everything FP64).
+#include "batch.cuh"
 
 namespace tild {
 EngineBase* make_engine_f64() { return new Engine<double>(); }
+BatchBase* make_batch_f64(const std::vector<EngineBase*>& engines, std::string& err) {
+    return make_batch<double>(engines, err);
+}
 }  // namespace tild

@@ -1,0 +1,95 @@
+"""Batched form: replicas stepped together through tild_batch_* give, bit for
+bit, the trajectories of the same systems stepped one by one (and those are
+checked against the oracle elsewhere)."""
+import numpy as np
+import pytest
+
+from oracle import tild_oracle as O
+from paper_2302_02474_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_02474_gb300 import _build, binding
+
+    _build.build()
+    return binding
+
+
+REPLICAS = [  # (n_chains, N, n_a, L, n, pmeorder, chi, seed)
+    (40, 20, 10, 9.6, 24, 1, 0.3, 11),
+    (55, 20, 8, 12.0, 32, 1, 1.2, 12),
+    (31, 20, 10, 10.0, 32, 1, 0.7, 13),
+    (70, 20, 10, 16.0, 48, 1, 1.5, 14),
+    (25, 20, 5, 8.0, 16, 2, 0.9, 15),
+    (60, 20, 12, 16.0, 40, 1, 0.4, 16),
+]
+
+
+def _spec(r, prec):
+    nc, N, na, L, n, order, chi, seed = r
+    return I.small_system(n_chains=nc, N=N, n_a=na, L=L, n=n, pmeorder=order, precision=prec, chi=chi, kappa=25.0,
+                          seed=seed)
+
+
+def _ctx(B, spec, sort_every, pos):
+    t = B.Tild.from_spec(spec, sort_every=sort_every)
+    t.set_positions(pos)
+    t.init_velocities()
+    return t
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_matches_individual_replicas_bitwise(B, prec):
+    specs = [_spec(r, prec) for r in REPLICAS]
+    pos = [I.initial_positions(s) for s in specs]
+    batch_ctx = [_ctx(B, s, 5, p) for s, p in zip(specs, pos)]
+    alone = [_ctx(B, s, 7, p) for s, p in zip(specs, pos)]
+    with B.TildBatch(batch_ctx) as bt:
+        bt.step(3)
+        bt.step(30)  # includes whole re-binning cycles replayed as a graph
+        bt.step(2)
+        bt.synchronize()
+        assert bt.launches(10) > 0
+    for t in alone:
+        t.step(35)
+        t.synchronize()
+    for tb, ta in zip(batch_ctx, alone):
+        assert tb.step_count() == ta.step_count() == 35
+        assert np.array_equal(tb.positions(), ta.positions())
+        assert np.array_equal(tb.velocities(), ta.velocities())
+
+
+def test_batch_replica_matches_oracle(B):
+    spec = _spec(REPLICAS[0], "fp64")
+    pos = I.initial_positions(spec)
+    other = _spec(REPLICAS[3], "fp64")
+    ts = [_ctx(B, spec, 4, pos), _ctx(B, other, 4, I.initial_positions(other))]
+    with B.TildBatch(ts) as bt:
+        bt.step(12)
+        bt.synchronize()
+    m = O.model_from_spec(spec, I.species_of_beads(spec.moltypes), I.bond_pairs(spec.moltypes))
+    st = O.run(m, O.initial_state(m, pos), 12)
+    assert np.abs(O.minimum_image(ts[0].positions() - st.pos, m.L)).max() < 1e-10
+
+
+def test_batch_rejects_bad_input(B):
+    spec = _spec(REPLICAS[1], "fp32")
+    t = B.Tild.from_spec(spec)
+    t.set_positions(I.initial_positions(spec))
+    with pytest.raises(B.TildError):
+        B.TildBatch([t])  # no velocities yet
+    t.init_velocities()
+    with pytest.raises(B.TildError):
+        B.TildBatch([t, t])
+    t64 = B.Tild.from_spec(_spec(REPLICAS[1], "fp64"))
+    t64.set_positions(I.initial_positions(spec))
+    t64.init_velocities()
+    with pytest.raises(B.TildError):
+        B.TildBatch([t, t64])
