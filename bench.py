@@ -244,6 +244,60 @@ def run_reference(args, spec, pos):
     print(json.dumps(out))
 
 
+def run_batch(args):
+    """256 uneven replicas: batched stepping vs one context at a time."""
+    import torch
+
+    from paper_2302_02474_gb300 import binding as B
+    from paper_2302_02474_gb300 import inputs as I
+
+    torch.cuda.set_device(0)
+    specs = I.batch_configs()
+    ctxs = []
+    for s in specs:
+        t = B.Tild.from_spec(s, sort_every=args.sort_every)
+        t.set_positions(I.initial_positions(s))
+        t.init_velocities()
+        ctxs.append(t)
+    beads = sum(s.n_beads for s in specs)
+    K = args.steps
+    # one context at a time (each with its own graph-replayed steps)
+    for t in ctxs:
+        t.step(args.warmup)
+    for t in ctxs:
+        t.synchronize()
+    t0 = time.perf_counter()
+    for t in ctxs:
+        t.step(K)
+    for t in ctxs:
+        t.synchronize()
+    seq_s = time.perf_counter() - t0
+    batch = B.TildBatch(ctxs)
+    batch.step(args.warmup)
+    batch.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(K)
+    batch.synchronize()
+    bat_s = time.perf_counter() - t0
+    launches = batch.launches(K)
+    sizes = {}
+    for s in specs:
+        sizes[s.n] = sizes.get(s.n, 0) + 1
+    out = {"metric": "replica-steps/s (256 uneven AB diblock replicas, batched)", "value": len(specs) * K / bat_s,
+           "unit": "replica-steps/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
+           "ms_per_step": 1000.0 * bat_s / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic", "bead_steps_per_s": beads * K / bat_s,
+           "config": {"workload": "batch256", "replicas": len(specs), "beads": beads, "grids": sizes,
+                      "sort_every": args.sort_every},
+           "sequential": {"value": len(specs) * K / seq_s, "unit": "replica-steps/s",
+                          "note": "same replicas stepped one context at a time"},
+           "speedup_vs_sequential": seq_s / bat_s, "gpu_launches": launches}
+    print(json.dumps(out))
+    batch.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,6 +308,8 @@ def main():
     ap.add_argument("--cpu-baseline-steps", type=int, default=3)
     ap.add_argument("--reference-budget", type=float, default=150.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256"],
+                    help="batch256: 256 uneven replicas stepped with tild_batch_* (extra measurement)")
     ap.add_argument("--mode", default="bench", choices=["bench", "run"],
                     help="run: set up, warm up and take --steps steps only (for profilers)")
     args = ap.parse_args()
@@ -261,6 +317,9 @@ def main():
 
     from paper_2302_02474_gb300 import inputs as I
 
+    if args.workload == "batch256":
+        run_batch(args)
+        return
     spec = I.config(WORKLOAD)
     pos = I.initial_positions(spec)
     if args.impl == "reference":

@@ -156,3 +156,24 @@ def random_positions(n_beads: int, L: float, seed: int) -> np.ndarray:
     """Uniform positions in [0, L)^3 (for kernel-level tests)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(0.0, L, size=(n_beads, 3))
+
+
+def batch_configs(n_replicas: int = 256, seed: int = 12345 + 5, steps: int = 5000) -> List[SystemSpec]:
+    """Uneven replicas of AB diblock melts (A10-B10, N = 20): bead counts
+    uniform in [4000, 40000] rounded to whole chains, box L uniform in
+    [16, 32], grid spacing uniform in [0.5, 0.67] with n the nearest of
+    {24, 32, 40, 48, 64} to L/dx, chi uniform in [0.2, 1.5], kappa = 25,
+    a = 0.5, independent seeds; FP32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.array([24, 32, 40, 48, 64])
+    out: List[SystemSpec] = []
+    for r in range(n_replicas):
+        beads = rng.uniform(4000, 40000)
+        n_chains = max(1, int(round(beads / 20)))
+        L = float(rng.uniform(16.0, 32.0))
+        dx = float(rng.uniform(0.5, 0.67))
+        n = int(sizes[np.argmin(np.abs(sizes - L / dx))])
+        chi = float(rng.uniform(0.2, 1.5))
+        out.append(SystemSpec(f"batch{r}", (MolType(n_chains, 20, 10),), L, n, 1, 0.5, chi, 25.0, 0.005, 1.0, 1.0, 1.0,
+                              1.0, steps, "fp32", seed * 1000 + 2 * r, seed * 1000 + 2 * r + 1))
+    return out
