@@ -24,6 +24,8 @@ template <typename T> class BatchEngine final : public BatchBase {
     struct Group {
         int n = 0, P = 2, C = 16, tiles3 = 0;
         std::vector<E*> reps;
+        cudaStream_t s = nullptr;   // the group's stream (forked from the batch stream)
+        cudaEvent_t done = nullptr;
         ForwardArgs<T>* d_fwd = nullptr;
         ZArgs<T>* d_z = nullptr;
         InverseArgs<T>* d_inv = nullptr;
@@ -35,12 +37,16 @@ template <typename T> class BatchEngine final : public BatchBase {
         if (stream_) cudaStreamSynchronize(stream_);
         if (graph_) cudaGraphExecDestroy(graph_);
         for (auto& g : groups_) {
+            if (g.s) cudaStreamDestroy(g.s);
+            if (g.done) cudaEventDestroy(g.done);
             cudaFree(g.d_fwd);
             cudaFree(g.d_z);
             cudaFree(g.d_inv);
             for (auto& row : g.d_bead)
                 for (auto* q : row) cudaFree(q);
         }
+        for (auto& st : sort_streams_) cudaStreamDestroy(st.first), cudaEventDestroy(st.second);
+        if (fork_) cudaEventDestroy(fork_);
         if (stream_) cudaStreamDestroy(stream_);
     }
 
@@ -107,7 +113,16 @@ template <typename T> class BatchEngine final : public BatchBase {
         for (Group& g : groups_) {
             tild_status st = build_tables(g);
             if (st) return st;
+            TILD_CUDA(cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking));
+            TILD_CUDA(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
         }
+        for (int k = 0; k < kSortStreams; ++k) {
+            std::pair<cudaStream_t, cudaEvent_t> st;
+            TILD_CUDA(cudaStreamCreateWithFlags(&st.first, cudaStreamNonBlocking));
+            TILD_CUDA(cudaEventCreateWithFlags(&st.second, cudaEventDisableTiming));
+            sort_streams_.push_back(st);
+        }
+        TILD_CUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
         TILD_CUDA(cudaStreamSynchronize(stream_));
         return TILD_OK;
     }
@@ -160,6 +175,24 @@ template <typename T> class BatchEngine final : public BatchBase {
     int K_ = 20;
     int cur_pos_ = 0, cur_uid_ = 0, steps_since_sort_ = 0;
     cudaGraphExec_t graph_ = nullptr;
+    static constexpr int kSortStreams = 16;
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> sort_streams_;
+    cudaEvent_t fork_ = nullptr;
+
+    // fork: every group stream waits for the batch stream
+    tild_status fork_groups() {
+        TILD_CUDA(cudaEventRecord(fork_, stream_));
+        for (Group& g : groups_) TILD_CUDA(cudaStreamWaitEvent(g.s, fork_, 0));
+        return TILD_OK;
+    }
+    // join: the batch stream waits for every group stream
+    tild_status join_groups() {
+        for (Group& g : groups_) {
+            TILD_CUDA(cudaEventRecord(g.done, g.s));
+            TILD_CUDA(cudaStreamWaitEvent(stream_, g.done, 0));
+        }
+        return TILD_OK;
+    }
 
     tild_status fail_from(E* e) {
         err = e->err;
@@ -259,7 +292,8 @@ template <typename T> class BatchEngine final : public BatchBase {
         return TILD_EUNSUPPORTED;
     }
 
-    tild_status step_all() {
+    // one step of every group, each on its own stream (after fork_groups)
+    tild_status step_groups() {
         for (Group& g : groups_) {
             const unsigned R = (unsigned)g.reps.size();
             E* e0 = g.reps[0];
@@ -267,10 +301,10 @@ template <typename T> class BatchEngine final : public BatchBase {
                 constexpr int NN = decltype(nn)::value, PP = decltype(pp)::value;
                 if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
                     constexpr int CC = E::zpass_cols(NN);
-                    xy_forward_plane_batched<T, NN><<<dim3(NN, R), 512, e0->plane_smem(), stream_>>>(g.d_fwd);
-                    z_spectral_batched<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1, R), 256, e0->zpass_smem(), stream_>>>(g.d_z);
-                    xy_inverse_plane_batched<T, NN><<<dim3(NN, 3, R), 512, e0->plane_smem(), stream_>>>(g.d_inv);
-                    bead_kernel_batched<PP, kModeStep, T><<<(unsigned)g.tiles3 * R, 256, e0->bead_smem(), stream_>>>(
+                    xy_forward_plane_batched<T, NN><<<dim3(NN, R), 512, e0->plane_smem(), g.s>>>(g.d_fwd);
+                    z_spectral_batched<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1, R), 256, e0->zpass_smem(), g.s>>>(g.d_z);
+                    xy_inverse_plane_batched<T, NN><<<dim3(NN, 3, R), 512, e0->plane_smem(), g.s>>>(g.d_inv);
+                    bead_kernel_batched<PP, kModeStep, T><<<(unsigned)g.tiles3 * R, 256, e0->bead_smem(), g.s>>>(
                         g.d_bead[cur_pos_][cur_uid_], g.tiles3);
                 }
                 return TILD_OK;
@@ -284,9 +318,24 @@ template <typename T> class BatchEngine final : public BatchBase {
         return TILD_OK;
     }
 
+    tild_status step_all() {
+        tild_status st;
+        if ((st = fork_groups()) || (st = step_groups())) return st;
+        return join_groups();
+    }
+
+    // re-bin every replica, spread over a pool of streams (forked from and
+    // joined back into the batch stream)
     tild_status sort_all() {
-        for (E* e : reps_) {
-            if (e->enqueue_sort(stream_)) return fail_from(e);
+        TILD_CUDA(cudaEventRecord(fork_, stream_));
+        for (auto& ss : sort_streams_) TILD_CUDA(cudaStreamWaitEvent(ss.first, fork_, 0));
+        for (size_t k = 0; k < reps_.size(); ++k) {
+            E* e = reps_[k];
+            if (e->enqueue_sort(sort_streams_[k % sort_streams_.size()].first)) return fail_from(e);
+        }
+        for (auto& ss : sort_streams_) {
+            TILD_CUDA(cudaEventRecord(ss.second, ss.first));
+            TILD_CUDA(cudaStreamWaitEvent(stream_, ss.second, 0));
         }
         cur_pos_ ^= 1;
         cur_uid_ ^= 1;
@@ -308,7 +357,9 @@ template <typename T> class BatchEngine final : public BatchBase {
             tild_status st = TILD_OK;
             for (int half = 0; half < 2 && !st; ++half) {
                 st = sort_all();
-                for (int s = 0; s < K_ && !st; ++s) st = step_all();
+                if (!st) st = fork_groups();
+                for (int s = 0; s < K_ && !st; ++s) st = step_groups();
+                if (!st) st = join_groups();
             }
             cudaError_t e = cudaStreamEndCapture(stream_, &g);
             if (st) return st;
