@@ -61,7 +61,7 @@ typedef int tild_status;
 #define TILD_ENOMEM (-2)        /* device or host allocation failed */
 #define TILD_EUNSUPPORTED (-3)  /* valid request outside what this build implements */
 #define TILD_EDEVICE (-4)       /* a CUDA call failed; see tild_last_error */
-#define TILD_ENAN (-5)          /* a non-finite force was detected on the device */
+#define TILD_ENAN (-5)          /* a non-finite position or force was detected on the device */
 #define TILD_ESTATE (-6)        /* call made before the state it needs exists */
 
 typedef enum { TILD_FP32 = 0, TILD_FP64 = 1 } tild_precision;
@@ -170,7 +170,8 @@ tild_status tild_set_stream(tild_ctx* ctx, void* stream);
 
 /* Copy in positions [n_beads][3] (wrapped into [0, L)). Requires chains.
  * Invalidates velocities: call tild_init_velocities or tild_set_velocities
- * before stepping. */
+ * before stepping. A non-finite coordinate returns TILD_ENAN (the bead is
+ * placed at 0 on that axis). */
 tild_status tild_set_positions(tild_ctx* ctx, const void* xyz, int dtype, int where);
 
 /* Draw Maxwell-Boltzmann velocities (each component N(0, kT/m), Philox

@@ -72,8 +72,11 @@ template <typename T> struct BeadBuffers {
 };
 
 template <typename T> __device__ __forceinline__ T wrap_coord(T x, T L, T inv_L) {
-    T y = x - L * floor(x * inv_L);
-    return (y >= L) ? T(0) : y;
+    const T y = x - L * floor(x * inv_L);
+    // rounding can give exactly L (mapped to 0) or a tiny negative value
+    // (kept); anything else out of range, i.e. a non-finite or huge input,
+    // maps to 0 so that no grid index derived from it leaves the grid
+    return (y >= L || !(y >= T(-0.5) * L)) ? T(0) : y;
 }
 
 template <typename T> __device__ __forceinline__ T min_image(T d, T L, T inv_L) { return d - L * rint(d * inv_L); }
@@ -724,11 +727,15 @@ static __global__ void scan_add(int* __restrict__ out, const int* __restrict__ b
 // In: AoS [n][3] by bead id (type TI). Out: SoA slot order = id order.
 template <typename T, typename TI>
 __global__ void load_positions(int n_beads, const TI* __restrict__ in, T L, T inv_L, T* __restrict__ pos /*[3][N]*/,
-                               int* __restrict__ id) {
+                               int* __restrict__ id, unsigned int* __restrict__ err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_beads) return;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) pos[(size_t)d * n_beads + i] = wrap_coord((T)in[3 * (size_t)i + d], L, inv_L);
+    for (int d = 0; d < 3; ++d) {
+        const T x = (T)in[3 * (size_t)i + d];
+        if (!isfinite(x)) atomicOr(err, kErrNonFinite);
+        pos[(size_t)d * n_beads + i] = wrap_coord(x, L, inv_L);
+    }
     id[i] = i;
 }
 

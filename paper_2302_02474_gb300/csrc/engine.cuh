@@ -108,13 +108,14 @@ template <typename T> class Engine final : public EngineBase {
         cur_pos_ = cur_u_ = cur_id_ = 0;
         const T L = (T)cfg_->L;
         if (dtype == TILD_DTYPE_F32)
-            load_positions<T, float><<<blocks(N), 256, 0, stream_>>>(N, (const float*)src, L, (T)(1.0 / cfg_->L), pos_[0], id_[0]);
+            load_positions<T, float><<<blocks(N), 256, 0, stream_>>>(N, (const float*)src, L, (T)(1.0 / cfg_->L), pos_[0], id_[0], err_ptr());
         else
-            load_positions<T, double><<<blocks(N), 256, 0, stream_>>>(N, (const double*)src, L, (T)(1.0 / cfg_->L), pos_[0], id_[0]);
+            load_positions<T, double><<<blocks(N), 256, 0, stream_>>>(N, (const double*)src, L, (T)(1.0 / cfg_->L), pos_[0], id_[0], err_ptr());
         TILD_CUDA(cudaGetLastError());
         if ((st = enqueue_sort())) return st;
         if ((st = respread())) return st;
         TILD_CUDA(cudaStreamSynchronize(stream_));
+        if ((st = check_err())) return st;
         have_pos_ = true;
         have_vel_ = false;
         return TILD_OK;
@@ -354,7 +355,7 @@ template <typename T> class Engine final : public EngineBase {
         T* d = (T*)aux_;
         TILD_CUDA(cudaMemcpyAsync(d, h + 5, 6 * N * sizeof(T), cudaMemcpyHostToDevice, stream_));
         cur_pos_ = cur_u_ = cur_id_ = 0;
-        load_positions<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, d, (T)cfg_->L, (T)(1.0 / cfg_->L), pos_[0], id_[0]);
+        load_positions<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, d, (T)cfg_->L, (T)(1.0 / cfg_->L), pos_[0], id_[0], err_ptr());
         load_by_id<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, d + 3 * N, id_[0], u_[0]);
         TILD_CUDA(cudaGetLastError());
         if ((st = enqueue_sort())) return st;
@@ -554,7 +555,7 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(cudaMemcpy(&h, err_ptr(), sizeof(h), cudaMemcpyDeviceToHost));
         if (h & kErrNonFinite) {
             TILD_CUDA(cudaMemset(err_ptr(), 0, sizeof(unsigned int)));
-            err = "non-finite force detected on the device";
+            err = "non-finite position or force detected on the device";
             return TILD_ENAN;
         }
         return TILD_OK;

@@ -295,6 +295,18 @@ def test_invalid_calls_return_errors(B):
         t.set_interactions(1.0, -1.0, 0.5)
     with pytest.raises(ValueError):
         t.set_positions(np.zeros((5, 3)))
+    # a non-finite coordinate is reported; the context stays usable
+    bad = 1.0 + 0.5 * np.arange(18, dtype=np.float64).reshape(6, 3)
+    bad[2, 1] = np.nan
+    bad[4, 0] = np.inf
+    with pytest.raises(B.TildError, match="ENAN"):
+        t.set_positions(bad)
+    good = 1.0 + 0.25 * np.arange(18, dtype=np.float64).reshape(6, 3)
+    t.set_positions(good)
+    t.init_velocities()
+    t.step(2)
+    t.synchronize()
+    assert np.isfinite(t.positions()).all()
 
 
 # --------------------------------------------------- named workloads
