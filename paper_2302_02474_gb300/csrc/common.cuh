@@ -100,12 +100,15 @@ __device__ __forceinline__ normal3<float> gaussian3(uint32_t id, uint64_t step, 
     const float u1 = fmaf((float)r.y, s, 0.5f * s);
     const float u2 = fmaf((float)r.z, s, 0.5f * s);
     const float u3 = fmaf((float)r.w, s, 0.5f * s);
-    const float m1 = sqrtf(-2.0f * logf(u0));
-    const float m2 = sqrtf(-2.0f * logf(u2));
+    // CUDA's fast log and sine/cosine intrinsics (absolute errors near
+    // 1e-6); the angle 2 pi u - pi lies in their accurate range [-pi, pi],
+    // and sin, cos of 2 pi u are minus those of 2 pi u - pi
+    const float m1 = sqrtf(fmaxf(-2.0f * __logf(u0), 0.0f));
+    const float m2 = sqrtf(fmaxf(-2.0f * __logf(u2), 0.0f));
     float s1, c1, s3, c3;
-    sincospif(2.0f * u1, &s1, &c1);
-    sincospif(2.0f * u3, &s3, &c3);
-    return {m1 * c1, m1 * s1, m2 * c3};
+    __sincosf(fmaf(6.28318530717958648f, u1, -3.14159265358979324f), &s1, &c1);
+    __sincosf(fmaf(6.28318530717958648f, u3, -3.14159265358979324f), &s3, &c3);
+    return {-m1 * c1, -m1 * s1, -m2 * c3};
 }
 
 __device__ __forceinline__ normal3<double> gaussian3(uint32_t id, uint64_t step, uint64_t seed, double) {
