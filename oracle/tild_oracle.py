@@ -19,7 +19,8 @@ Sec. "Long-range interactions"):
 * the harmonic bond energy with spring constant 3/b^2 (Eq. bonds);
 * the Gronbech-Jensen-Farago Langevin integrator (named in the Integrator
   Class list and used by Listing infile), with Philox4x32-10 random numbers
-  and Box-Muller normals.
+  and Box-Muller normals, and the two other integrators of that list:
+  Euler-Maruyama and velocity-Verlet with a Langevin thermostat force.
 
 Readings where the paper is silent are listed with each function.
 Everything here is FP64; the only library primitives are numpy's FFT and
@@ -474,3 +475,75 @@ def run(m: Model, st: State, n_steps: int, force_fn=None) -> State:
 
 def kinetic_energy(m: Model, vel: np.ndarray) -> float:
     return float(0.5 * m.mass * np.sum(vel * vel))
+
+
+# ---------------------------------------------------------------------------
+# The other integrators of the Integrator Class list (Sec. "Integrator
+# Class"): Euler-Maruyama (EM) and velocity-Verlet (VV) coupled to the
+# Langevin thermostat force of the ExtraForce list.
+# ---------------------------------------------------------------------------
+
+
+def em_step(m: Model, st: State, force_fn=None) -> State:
+    """One Euler-Maruyama step of overdamped Langevin (Brownian) dynamics:
+      r^{n+1} = r^n + (dt / alpha) F^n + sqrt(2 kT dt / alpha) xi^{n+1}
+    with xi^{n+1} ~ N(0, 1) per component (counter step n+1) and alpha the
+    friction coefficient. Reading: the paper names EM as the scheme that
+    draws its noise during the update; for particles that is the EM
+    discretisation of dr = F/alpha dt + sqrt(2 kT/alpha) dW. There is no
+    velocity in this dynamics; ``vel`` stays zero.
+    """
+    dt, alpha = m.dt, m.friction
+    xi = gaussian_triplets(np.arange(m.n_beads), st.step + 1, m.seed)
+    r_new = wrap(st.pos + dt / alpha * st.force + np.sqrt(2.0 * m.kT * dt / alpha) * xi, m.L)
+    f_new = (forces if force_fn is None else force_fn)(m, r_new)
+    return State(r_new, np.zeros_like(st.vel), f_new, st.step + 1)
+
+
+def em_initial_state(m: Model, pos: np.ndarray, force_fn=None) -> State:
+    force_fn = forces if force_fn is None else force_fn
+    p = wrap(pos, m.L)
+    return State(p, np.zeros((m.n_beads, 3)), force_fn(m, p), 0)
+
+
+def langevin_force(m: Model, v_half: np.ndarray, step: int) -> np.ndarray:
+    """Langevin thermostat force of step n: -alpha v + sqrt(2 alpha kT / dt)
+    xi^n, xi^n ~ N(0, 1) per component (counter step n). Reading: the force
+    acts on the half-step velocity v^{n-1/2} = v^n - (dt/2m) F^n, the
+    velocity a velocity-Verlet step holds when forces are evaluated."""
+    sigma = np.sqrt(2.0 * m.friction * m.kT / m.dt)
+    return -m.friction * v_half + sigma * gaussian_triplets(np.arange(m.n_beads), step, m.seed)
+
+
+def vv_initial_state(m: Model, pos: np.ndarray, vel: np.ndarray, force_fn=None) -> State:
+    """Velocity-Verlet state at n = 0 from r^0, v^0. F^0 = F_c(r^0) +
+    Langevin force on v^{-1/2} = v^0 - (dt/2m) F^0, which is linear in F^0:
+      v^{-1/2} = (v^0 - (dt/2m)(F_c + sigma xi^0)) / (1 - alpha dt/2m)."""
+    force_fn = forces if force_fn is None else force_fn
+    p = wrap(pos, m.L)
+    fc = force_fn(m, p)
+    h = m.dt / (2.0 * m.mass)
+    noise = langevin_force(m, np.zeros_like(vel), 0)
+    v_half = (vel - h * (fc + noise)) / (1.0 - m.friction * h)
+    return State(p, vel.copy(), fc + langevin_force(m, v_half, 0), 0)
+
+
+def vv_step(m: Model, st: State, force_fn=None) -> State:
+    """One velocity-Verlet step with the Langevin force (friction alpha,
+    temperature kT; alpha = 0 gives plain NVE velocity-Verlet):
+      v^{n+1/2} = v^n + (dt/2m) F^n
+      r^{n+1}   = r^n + dt v^{n+1/2}
+      F^{n+1}   = F_c(r^{n+1}) - alpha v^{n+1/2} + sqrt(2 alpha kT/dt) xi^{n+1}
+      v^{n+1}   = v^{n+1/2} + (dt/2m) F^{n+1}
+    """
+    h = m.dt / (2.0 * m.mass)
+    v_half = st.vel + h * st.force
+    r_new = wrap(st.pos + m.dt * v_half, m.L)
+    f_new = (forces if force_fn is None else force_fn)(m, r_new) + langevin_force(m, v_half, st.step + 1)
+    return State(r_new, v_half + h * f_new, f_new, st.step + 1)
+
+
+def run_with(step_fn, m: Model, st: State, n_steps: int, force_fn=None) -> State:
+    for _ in range(n_steps):
+        st = step_fn(m, st, force_fn)
+    return st

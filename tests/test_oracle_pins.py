@@ -358,3 +358,120 @@ def test_gjf_free_particle_velocity_variance():
     for _ in range(50):
         st = O.gjf_step(m, st, force)
     assert abs(np.mean(st.vel ** 2) - 0.7) < 0.02
+
+
+# ----------------------------------------- Euler-Maruyama and velocity-Verlet
+
+
+def _free_or_bonded(n_beads, bonds, **kw):
+    return O.Model(L=kw.pop("L", 50.0), n=8, P=2, species=np.zeros(n_beads, np.int64), n_species=1,
+                   bonds=bonds, b=1.0, chi=np.zeros((1, 1)), kappa=0.0, a=0.5, **kw)
+
+
+def test_em_free_particle_diffusion_coefficient():
+    """Brownian dynamics of free particles: <|r(t) - r(0)|^2> = 6 D t with
+    the Einstein relation D = kT / alpha (exact for the EM discretisation)."""
+    n, K = 20000, 50
+    m = _free_or_bonded(n, np.zeros((0, 2), np.int64), dt=0.01, friction=2.0, kT=0.7, seed=4)
+
+    def force(mm, p):
+        return np.zeros_like(p)
+
+    st = O.em_initial_state(m, np.full((n, 3), 25.0), force_fn=force)
+    disp = np.zeros((n, 3))
+    for _ in range(K):
+        new = O.em_step(m, st, force)
+        disp += O.minimum_image(new.pos - st.pos, m.L)
+        st = new
+    msd = np.mean(np.sum(disp * disp, axis=1))
+    assert abs(msd - 6.0 * (0.7 / 2.0) * K * m.dt) < 0.03 * 6.0 * (0.7 / 2.0) * K * m.dt
+    assert not np.any(st.vel)
+
+
+def test_em_dimer_bond_length_closed_form():
+    """Dimers with the bond force of Eq. bonds (k = 3/b^2) under EM: the
+    bond vector is an AR(1) process d' = (1 - 2 k dt/alpha) d + noise of
+    variance 4 kT dt/alpha per component, whose stationary mean square is
+    <|d|^2> = 3 (kT/k) / (1 - k dt/alpha) (= b^2 as dt -> 0)."""
+    nd = 10000
+    bonds = np.stack([2 * np.arange(nd), 2 * np.arange(nd) + 1], axis=1).astype(np.int64)
+    m = _free_or_bonded(2 * nd, bonds, L=400.0, dt=0.03, friction=1.0, kT=1.0, seed=8)
+
+    def force(mm, p):
+        return O.bond_forces(mm, p)
+
+    rng = np.random.default_rng(3)
+    pos = np.repeat(rng.uniform(10, 390, size=(nd, 3)), 2, axis=0)
+    pos[1::2] += rng.normal(size=(nd, 3)) / np.sqrt(3.0)
+    st = O.em_initial_state(m, pos, force_fn=force)
+    d2 = []
+    for it in range(400):
+        st = O.em_step(m, st, force)
+        if it >= 100 and it % 10 == 0:
+            d = O.bond_vectors(m, st.pos)
+            d2.append(np.mean(np.sum(d * d, axis=1)))
+    expect = 3.0 * (1.0 / 3.0) / (1.0 - 3.0 * m.dt / m.friction)
+    assert abs(np.mean(d2) - expect) < 0.015 * expect
+    assert abs(expect - 1.0) > 0.08  # the pin distinguishes the discrete process from its continuum limit
+
+
+def test_vv_is_time_reversible_without_friction():
+    """alpha = 0: velocity-Verlet is time reversible for any position-only
+    force (here the full field + bond force): n steps, reverse velocities,
+    n steps returns to the start."""
+    m, pos = _model(friction=0.0, dt=0.01)
+    vel = np.random.default_rng(2).normal(size=pos.shape)
+    st0 = O.vv_initial_state(m, pos, vel)
+    st = O.run_with(O.vv_step, m, st0, 30)
+    assert np.abs(O.minimum_image(st.pos - st0.pos, m.L)).max() > 0.1
+    back = O.run_with(O.vv_step, m, O.State(st.pos, -st.vel, st.force, st.step), 30)
+    assert np.abs(O.minimum_image(back.pos - st0.pos, m.L)).max() < 1e-9
+    np.testing.assert_allclose(-back.vel, vel, atol=1e-8)
+
+
+def test_vv_conserves_energy_without_friction():
+    """alpha = 0, bonds only: E = kinetic + bond energy stays within the
+    O((omega dt)^2) shadow-Hamiltonian band and does not drift."""
+    mt = (I.MolType(200, 10, 10),)
+    m = O.Model(L=40.0, n=8, P=2, species=I.species_of_beads(mt).astype(np.int64), n_species=1,
+                bonds=I.bond_pairs(mt), b=1.0, chi=np.zeros((1, 1)), kappa=0.0, a=0.5, dt=0.01, friction=0.0,
+                kT=1.0, seed=9)
+    pos = I.random_walk_positions(mt, m.L, 1.0, 4)
+    vel = np.random.default_rng(6).normal(size=pos.shape)
+
+    def force(mm, p):
+        return O.bond_forces(mm, p)
+
+    st = O.vv_initial_state(m, pos, vel, force_fn=force)
+    e = []
+    for _ in range(500):
+        st = O.vv_step(m, st, force)
+        e.append(O.kinetic_energy(m, st.vel) + O.bond_energy(m, st.pos))
+    e = np.array(e)
+    assert np.abs(e - e[0]).max() < 1e-3 * abs(e[0])
+    assert abs(e[-50:].mean() - e[:50].mean()) < 2e-4 * abs(e[0])
+
+
+def test_vv_langevin_free_particle_velocity_variances():
+    """Free particles under VV + Langevin force: the half-step velocity is
+    an AR(1) process u' = (1 - alpha dt/m) u + (dt/m) sigma xi with
+    stationary variance (kT/m) / (1 - alpha dt/2m), and the full-step
+    velocity v = u + (dt/2m) F then has variance exactly kT/m."""
+    n = 20000
+    m = _free_or_bonded(n, np.zeros((0, 2), np.int64), dt=0.1, friction=2.0, kT=0.7, seed=12)
+
+    def force(mm, p):
+        return np.zeros_like(p)
+
+    vel = np.sqrt(0.7) * np.random.default_rng(1).normal(size=(n, 3))
+    st = O.vv_initial_state(m, np.full((n, 3), 25.0), vel, force_fn=force)
+    v2, u2 = [], []
+    for it in range(120):
+        st = O.vv_step(m, st, force)
+        if it >= 40 and it % 4 == 0:
+            v2.append(np.mean(st.vel ** 2))
+            u2.append(np.mean((st.vel - m.dt / 2 * st.force) ** 2))
+    assert abs(np.mean(v2) - 0.7) < 0.01 * 0.7
+    expect_u = 0.7 / (1.0 - 2.0 * 0.1 / 2.0)
+    assert abs(np.mean(u2) - expect_u) < 0.01 * expect_u
+    assert expect_u / 0.7 > 1.1  # distinguishes the half-step from the full-step variance
