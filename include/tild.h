@@ -158,10 +158,32 @@ tild_status tild_set_chains(tild_ctx* ctx, int n_types, const tild_moltype* type
  * new forces. */
 tild_status tild_set_interactions(tild_ctx* ctx, double chi_ab, double kappa, double a);
 
-/* GJF integrator (Sec. "Integrator Class"): time step dt > 0, friction
- * alpha >= 0, temperature kT >= 0, bead mass > 0. Defaults: dt = 0.005,
- * alpha = 1, kT = 1, mass = 1. If velocities exist, v^n is kept. */
+/* Integrator parameters (Sec. "Integrator Class"): time step dt > 0,
+ * friction alpha >= 0, temperature kT >= 0, bead mass > 0. Defaults:
+ * dt = 0.005, alpha = 1, kT = 1, mass = 1. If velocities exist, v^n is
+ * kept. The scheme in use may add limits (see tild_set_integrator_scheme);
+ * values it cannot take return TILD_EINVAL and change nothing. */
 tild_status tild_set_integrator(tild_ctx* ctx, double dt, double friction, double kT, double mass);
+
+/* The three integrators of Sec. "Integrator Class". Random numbers of all
+ * three come from the same Philox stream (counter = bead id and step).
+ *   TILD_SCHEME_GJF  Gronbech-Jensen-Farago Langevin (the default).
+ *   TILD_SCHEME_EM   Euler-Maruyama for overdamped Langevin (Brownian)
+ *                    dynamics: r^{n+1} = r^n + (dt/alpha) F^n
+ *                    + sqrt(2 kT dt/alpha) xi^{n+1}. Needs alpha > 0. There
+ *                    is no velocity: velocities read back as 0 and the
+ *                    kinetic energy is 0.
+ *   TILD_SCHEME_VV   velocity-Verlet with the Langevin thermostat force
+ *                    -alpha v^{n-1/2} + sqrt(2 alpha kT/dt) xi^n acting on the
+ *                    half-step velocity (alpha = 0: plain NVE). Needs
+ *                    alpha dt / 2m < 1.
+ * Forces reported by tild_compute are the field and bond forces only.
+ * Switching keeps v^n (zero when leaving EM). Unknown schemes return
+ * TILD_EINVAL. */
+#define TILD_SCHEME_GJF 0
+#define TILD_SCHEME_EM 1
+#define TILD_SCHEME_VV 2
+tild_status tild_set_integrator_scheme(tild_ctx* ctx, int scheme);
 
 /* Order all work of this context on `stream` (a cudaStream_t; NULL = the
  * context's own stream). The stream must belong to the context's device and

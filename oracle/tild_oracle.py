@@ -515,17 +515,18 @@ def langevin_force(m: Model, v_half: np.ndarray, step: int) -> np.ndarray:
     return -m.friction * v_half + sigma * gaussian_triplets(np.arange(m.n_beads), step, m.seed)
 
 
-def vv_initial_state(m: Model, pos: np.ndarray, vel: np.ndarray, force_fn=None) -> State:
-    """Velocity-Verlet state at n = 0 from r^0, v^0. F^0 = F_c(r^0) +
-    Langevin force on v^{-1/2} = v^0 - (dt/2m) F^0, which is linear in F^0:
-      v^{-1/2} = (v^0 - (dt/2m)(F_c + sigma xi^0)) / (1 - alpha dt/2m)."""
+def vv_initial_state(m: Model, pos: np.ndarray, vel: np.ndarray, force_fn=None, step: int = 0) -> State:
+    """Velocity-Verlet state at step n (default 0) from r^n, v^n. F^n =
+    F_c(r^n) + Langevin force on v^{n-1/2} = v^n - (dt/2m) F^n, which is
+    linear in F^n:
+      v^{n-1/2} = (v^n - (dt/2m)(F_c + sigma xi^n)) / (1 - alpha dt/2m)."""
     force_fn = forces if force_fn is None else force_fn
     p = wrap(pos, m.L)
     fc = force_fn(m, p)
     h = m.dt / (2.0 * m.mass)
-    noise = langevin_force(m, np.zeros_like(vel), 0)
+    noise = langevin_force(m, np.zeros_like(vel), step)
     v_half = (vel - h * (fc + noise)) / (1.0 - m.friction * h)
-    return State(p, vel.copy(), fc + langevin_force(m, v_half, 0), 0)
+    return State(p, vel.copy(), fc + langevin_force(m, v_half, step), step)
 
 
 def vv_step(m: Model, st: State, force_fn=None) -> State:

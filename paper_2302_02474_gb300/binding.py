@@ -60,6 +60,7 @@ _SIGS = {
     "tild_set_chains": [_P, _I, ctypes.POINTER(tild_moltype), ctypes.c_double],
     "tild_set_interactions": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double],
     "tild_set_integrator": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+    "tild_set_integrator_scheme": [_P, ctypes.c_int],
     "tild_set_stream": [_P, _P],
     "tild_set_positions": [_P, _P, _I, _I],
     "tild_init_velocities": [_P],
@@ -222,6 +223,13 @@ class Tild:
 
     def set_integrator(self, dt: float, friction: float, kT: float, mass: float = 1.0) -> None:
         self._chk(self.lib.tild_set_integrator(self.ctx, dt, friction, kT, mass))
+
+    SCHEMES = {"gjf": 0, "em": 1, "vv": 2}
+
+    def set_scheme(self, scheme: str) -> None:
+        """Integrator of Sec. "Integrator Class": "gjf" (default), "em"
+        (Euler-Maruyama, overdamped) or "vv" (velocity-Verlet + Langevin force)."""
+        self._chk(self.lib.tild_set_integrator_scheme(self.ctx, self.SCHEMES[scheme]))
 
     def set_stream(self, stream) -> None:
         handle = getattr(stream, "cuda_stream", stream)

@@ -131,6 +131,14 @@ tild_status tild_set_chains(tild_ctx* c, int n_types, const tild_moltype* t, dou
     return TILD_OK;
 }
 
+// Parameter limits of the integrator schemes (NULL: acceptable).
+static const char* scheme_limits(const HostConfig& h) {
+    if (h.scheme == TILD_SCHEME_EM && !(h.friction > 0)) return "Euler-Maruyama needs friction > 0";
+    if (h.scheme == TILD_SCHEME_VV && !(h.friction * h.dt / (2.0 * h.mass) < 1.0))
+        return "velocity-Verlet with the Langevin force needs friction * dt / (2 mass) < 1";
+    return nullptr;
+}
+
 static tild_status reparam(tild_ctx* c, const HostConfig& next) {
     // keep v^n = u^n + (dt/2m) F^n across the change
     const bool keep = c->eng->has_velocities();
@@ -164,6 +172,17 @@ tild_status tild_set_integrator(tild_ctx* c, double dt, double friction, double 
     next.friction = friction;
     next.kT = kT;
     next.mass = mass;
+    if (const char* why = scheme_limits(next)) return fail(c, TILD_EINVAL, why);
+    return reparam(c, next);
+}
+
+tild_status tild_set_integrator_scheme(tild_ctx* c, int scheme) {
+    if (!c) return TILD_EINVAL;
+    if (scheme != TILD_SCHEME_GJF && scheme != TILD_SCHEME_EM && scheme != TILD_SCHEME_VV)
+        return fail(c, TILD_EINVAL, "set_integrator_scheme: unknown scheme");
+    HostConfig next = c->cfg;
+    next.scheme = scheme;
+    if (const char* why = scheme_limits(next)) return fail(c, TILD_EINVAL, why);
     return reparam(c, next);
 }
 

@@ -18,6 +18,13 @@
 // which is the GJF update with a = (1 - alpha dt/2m)/(1 + alpha dt/2m),
 // b = 1/(1 + alpha dt/2m), beta ~ N(0, 2 alpha kT dt).
 //
+// The other integrators of Sec. "Integrator Class":
+//   EM (overdamped Langevin, Euler-Maruyama): r^{n+1} = r^n + (dt/alpha) F^n
+//       + sqrt(2 kT dt/alpha) xi^{n+1}; no velocity (u = 0).
+//   VV (velocity-Verlet with the Langevin thermostat force): u^n = v^{n-1/2},
+//       F^n = F_c^n - alpha u^n + sqrt(2 alpha kT/dt) xi^n, v^n = u^n + (dt/2m) F^n,
+//       u^{n+1} = v^{n+1/2} = u^n + (dt/m) F^n, r^{n+1} = r^n + dt u^{n+1}.
+//
 // Bead arrays are SoA in "slot" order: beads binned by cell (tile-major)
 // every few steps. Slot -> bead id in `id`; bonded neighbours by slot in
 // `nbr`. All results are independent of the slot order.
@@ -28,6 +35,8 @@
 namespace tild {
 
 enum BeadMode : int { kModeSpread = 0, kModeForce = 1, kModeSetVel = 2, kModeStep = 3 };
+// Integrators of Sec. "Integrator Class" (values as TILD_SCHEME_* in tild.h).
+enum Scheme : int { kSchemeGJF = 0, kSchemeEM = 1, kSchemeVV = 2 };
 
 template <typename T> struct BeadParams {
     int n_beads;
@@ -35,13 +44,13 @@ template <typename T> struct BeadParams {
     int tiles;        // tiles per edge
     T L, inv_L, inv_dx;
     T k_bond;         // 3 / b^2
-    // GJF constants
-    T hdm;            // dt / (2m)
-    T gb_dt;          // b dt
-    T inv_2m;         // 1 / (2m)
-    T ga;             // a
-    T gb_m;           // b / m
-    T sigma_beta;     // sqrt(2 alpha kT dt)
+    // Integrator (scheme-specific constants, see integrator_constants):
+    //   step   h = su u + sf F + sg xi,  r' = r + sd h + se xi,  u' = sh h + sk xi
+    //          with xi the normals of counter (n+1) - noise_lag;
+    //   report v^n = vu u + vf F + vg xi^n;  set u from v^n: u = wu v + wf F + wg xi^n.
+    T su, sf, sg, sd, se, sh, sk;
+    T vu, vf, vg, wu, wf, wg;
+    int noise_lag;
     T sigma_v;        // sqrt(kT / m) (initial velocities)
     T mass;
     uint64_t seed;
@@ -389,7 +398,12 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
                 }
                 if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(bf.err, kErrNonFinite);
                 if (MODE == kModeForce) {
-                    const T vx = ux + p.hdm * fx, vy = uy + p.hdm * fy, vz = uz + p.hdm * fz;
+                    // v^n = vu u + vf F + vg xi^n (the integrator's total force enters)
+                    normal3<T> g = {T(0), T(0), T(0)};
+                    if (p.vg != T(0)) g = gaussian3((uint32_t)bid, *bf.step, p.seed, T(0));
+                    const T vx = p.vu * ux + p.vf * fx + p.vg * g.a;
+                    const T vy = p.vu * uy + p.vf * fy + p.vg * g.b;
+                    const T vz = p.vu * uz + p.vf * fz + p.vg * g.c;
                     acc[1] += 0.5 * (double)p.mass * ((double)vx * vx + (double)vy * vy + (double)vz * vz);
                     acc[2] += fx;
                     acc[3] += fy;
@@ -416,25 +430,25 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
                         vy = p.sigma_v * g.b;
                         vz = p.sigma_v * g.c;
                     }
-                    bf.ux[i] = vx - p.hdm * fx;
-                    bf.uy[i] = vy - p.hdm * fy;
-                    bf.uz[i] = vz - p.hdm * fz;
+                    normal3<T> g = {T(0), T(0), T(0)};
+                    if (p.wg != T(0)) g = gaussian3((uint32_t)bid, *bf.step, p.seed, T(0));
+                    bf.ux[i] = p.wu * vx + p.wf * fx + p.wg * g.a;
+                    bf.uy[i] = p.wu * vy + p.wf * fy + p.wg * g.b;
+                    bf.uz[i] = p.wu * vz + p.wf * fz + p.wg * g.c;
                 } else if (MODE == kModeStep) {
-                    const normal3<T> g = gaussian3((uint32_t)bid, step_next, p.seed, T(0));
-                    const T bx = p.sigma_beta * g.a, by = p.sigma_beta * g.b, bz = p.sigma_beta * g.c;
-                    // v^n + (dt/2m) F^n
-                    const T hx = ux + T(2) * p.hdm * fx;
-                    const T hy = uy + T(2) * p.hdm * fy;
-                    const T hz = uz + T(2) * p.hdm * fz;
-                    x = wrap_coord(x + p.gb_dt * (hx + p.inv_2m * bx), p.L, p.inv_L);
-                    y = wrap_coord(y + p.gb_dt * (hy + p.inv_2m * by), p.L, p.inv_L);
-                    z = wrap_coord(z + p.gb_dt * (hz + p.inv_2m * bz), p.L, p.inv_L);
+                    const normal3<T> g = gaussian3((uint32_t)bid, step_next - (uint64_t)p.noise_lag, p.seed, T(0));
+                    const T hx = p.su * ux + p.sf * fx + p.sg * g.a;
+                    const T hy = p.su * uy + p.sf * fy + p.sg * g.b;
+                    const T hz = p.su * uz + p.sf * fz + p.sg * g.c;
+                    x = wrap_coord(x + p.sd * hx + p.se * g.a, p.L, p.inv_L);
+                    y = wrap_coord(y + p.sd * hy + p.se * g.b, p.L, p.inv_L);
+                    z = wrap_coord(z + p.sd * hz + p.se * g.c, p.L, p.inv_L);
                     bf.qx[i] = x;
                     bf.qy[i] = y;
                     bf.qz[i] = z;
-                    bf.ux[i] = p.ga * hx + p.gb_m * bx;
-                    bf.uy[i] = p.ga * hy + p.gb_m * by;
-                    bf.uz[i] = p.ga * hz + p.gb_m * bz;
+                    bf.ux[i] = p.sh * hx + p.sk * g.a;
+                    bf.uy[i] = p.sh * hy + p.sk * g.b;
+                    bf.uz[i] = p.sh * hz + p.sk * g.c;
                     st.set(x, y, z, p.inv_dx);
                     inside = patch_local(st, org, l);
                 }

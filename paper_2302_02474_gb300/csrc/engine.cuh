@@ -802,6 +802,46 @@ template <typename T> class Engine final : public EngineBase {
         return enqueue_inverse(with_potential);
     }
 
+    // Constants of the integrator update (see BeadParams), from FP64.
+    static void integrator_constants(const HostConfig& c, BeadParams<T>& p) {
+        const double dt = c.dt, m = c.mass, al = c.friction, kT = c.kT;
+        const double hdm = dt / (2.0 * m);
+        double su = 1, sf = 2 * hdm, sg = 0, sd = dt, se = 0, sh = 1, sk = 0;
+        double vu = 1, vf = hdm, vg = 0, wu = 1, wf = -hdm, wg = 0;
+        int lag = 0;
+        if (c.scheme == kSchemeGJF) {
+            // GJF: a = (1 - alpha dt/2m)/(1 + alpha dt/2m), b = 1/(1 + alpha dt/2m), beta = sigma xi
+            const double den = 1.0 + al * hdm, ga = (1.0 - al * hdm) / den, gb = 1.0 / den;
+            const double sb = std::sqrt(2.0 * al * kT * dt);
+            sd = gb * dt;
+            se = gb * dt * sb / (2.0 * m);
+            sh = ga;
+            sk = gb * sb / m;
+        } else if (c.scheme == kSchemeEM) {
+            // r' = r + (dt/alpha) F + sqrt(2 kT dt/alpha) xi; no velocity
+            su = 0;
+            sf = al > 0 ? dt / al : 0;
+            sg = al > 0 ? std::sqrt(2.0 * kT * dt / al) : 0;
+            sd = 1;
+            sh = 0;
+            vu = vf = wu = wf = 0;
+        } else {
+            // VV: F = F_c - alpha u + s xi^n (s = sqrt(2 alpha kT/dt)), h = u + (dt/m) F
+            const double s = std::sqrt(2.0 * al * kT / dt), inv = 1.0 / (1.0 - al * hdm);
+            su = 1.0 - 2.0 * hdm * al;
+            sg = 2.0 * hdm * s;
+            lag = 1;
+            vu = 1.0 - hdm * al;
+            vg = hdm * s;
+            wu = inv;
+            wf = -inv * hdm;
+            wg = -inv * hdm * s;
+        }
+        p.su = (T)su; p.sf = (T)sf; p.sg = (T)sg; p.sd = (T)sd; p.se = (T)se; p.sh = (T)sh; p.sk = (T)sk;
+        p.vu = (T)vu; p.vf = (T)vf; p.vg = (T)vg; p.wu = (T)wu; p.wf = (T)wf; p.wg = (T)wg;
+        p.noise_lag = lag;
+    }
+
     BeadParams<T> bead_params() const {
         BeadParams<T> p;
         const HostConfig& c = *cfg_;
@@ -812,16 +852,7 @@ template <typename T> class Engine final : public EngineBase {
         p.inv_L = (T)(1.0 / c.L);
         p.inv_dx = (T)((double)n_ / c.L);
         p.k_bond = (T)(3.0 / (c.b * c.b));
-        const double hdm = c.dt / (2.0 * c.mass);
-        const double den = 1.0 + c.friction * c.dt / (2.0 * c.mass);
-        const double ga = (1.0 - c.friction * c.dt / (2.0 * c.mass)) / den;
-        const double gb = 1.0 / den;
-        p.hdm = (T)hdm;
-        p.gb_dt = (T)(gb * c.dt);
-        p.inv_2m = (T)(1.0 / (2.0 * c.mass));
-        p.ga = (T)ga;
-        p.gb_m = (T)(gb / c.mass);
-        p.sigma_beta = (T)std::sqrt(2.0 * c.friction * c.kT * c.dt);
+        integrator_constants(c, p);
         p.sigma_v = (T)std::sqrt(c.kT / c.mass);
         p.mass = (T)c.mass;
         p.seed = c.seed;

@@ -27,6 +27,7 @@ struct HostConfig {
     bool have_interactions = false;
     // integrator
     double dt = 0.005, friction = 1.0, kT = 1.0, mass = 1.0;
+    int scheme = 0;  // TILD_SCHEME_*
 };
 
 class EngineBase {
