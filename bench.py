@@ -308,6 +308,7 @@ def main():
     ap.add_argument("--cpu-baseline-steps", type=int, default=3)
     ap.add_argument("--reference-budget", type=float, default=150.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip timing the step variants")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256"],
                     help="batch256: 256 uneven replicas stepped with tild_batch_* (extra measurement)")
     ap.add_argument("--mode", default="bench", choices=["bench", "run"],
@@ -387,6 +388,37 @@ def main():
     h2d = len(blob)
     d2h = host_pos.nbytes
 
+    # the step's variants (Sec. "Integrator Class"; analytic-differentiation
+    # force) on the same system, timed the same way; the headline above is
+    # the paper's ik force with GJF
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = {}
+        vsteps = max(args.steps // 4, 100)
+
+        def timed(name, note):
+            t.step(20)
+            t.synchronize()
+            st_ms = t.profile_steps(prof_steps)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            t.step(vsteps)
+            b.record(stream)
+            b.synchronize()
+            t.synchronize()
+            variants[name] = {"value": vsteps / (a.elapsed_time(b) / 1000.0), "unit": "steps/s", "steps": vsteps,
+                              "stage_ms": {s_: st_ms[i] for i, s_ in enumerate(STAGES)}, "note": note}
+
+        t.set_force_method("analytic")
+        timed("analytic_force", "F = -sum grad W w_K: one inverse transform of the potentials, GJF")
+        t.set_force_method("ik")
+        t.set_scheme("vv")
+        timed("velocity_verlet", "ik force, velocity-Verlet + Langevin thermostat force")
+        t.set_scheme("em")
+        timed("euler_maruyama", "ik force, Euler-Maruyama (overdamped)")
+        t.set_scheme("gjf")
+
     n_points = spec.n ** 3
     peak, peak_kind = measured_peaks()
     stage_time = {s: stage_ms[i] for i, s in enumerate(STAGES)}
@@ -429,6 +461,7 @@ def main():
                     "d2h_bytes_per_step": d2h / args.steps},
             "gpu_launches": launches,
             "clocks": clk.summary(),
+            "variants": variants,
         }
         print(json.dumps(out))
     t.close()

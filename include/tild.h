@@ -180,6 +180,21 @@ tild_status tild_set_integrator(tild_ctx* ctx, double dt, double friction, doubl
  * Forces reported by tild_compute are the field and bond forces only.
  * Switching keeps v^n (zero when leaving EM). Unknown schemes return
  * TILD_EINVAL. */
+/* How the particle-mesh force is taken from the potentials (Sec. "Long-range
+ * interactions", Eq. PMM):
+ *   TILD_FORCE_IK        the default: the field gradient by spectral (i k)
+ *                        differentiation, interpolated back with the
+ *                        assignment weights (three inverse transforms).
+ *   TILD_FORCE_ANALYTIC  F_i = -sum_g grad W(r_i - g) w_K(g): the exact
+ *                        gradient of the gridded energy, from the potentials
+ *                        (one inverse transform) and the derivatives of the
+ *                        assignment weights. Not momentum conserving.
+ * If velocities exist, v^n is kept. Batches (tild_batch_create) take
+ * TILD_FORCE_IK contexts only. Unknown methods return TILD_EINVAL. */
+#define TILD_FORCE_IK 0
+#define TILD_FORCE_ANALYTIC 1
+tild_status tild_set_force_method(tild_ctx* ctx, int method);
+
 #define TILD_SCHEME_GJF 0
 #define TILD_SCHEME_EM 1
 #define TILD_SCHEME_VV 2

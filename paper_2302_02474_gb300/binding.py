@@ -61,6 +61,7 @@ _SIGS = {
     "tild_set_interactions": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double],
     "tild_set_integrator": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
     "tild_set_integrator_scheme": [_P, ctypes.c_int],
+    "tild_set_force_method": [_P, ctypes.c_int],
     "tild_set_stream": [_P, _P],
     "tild_set_positions": [_P, _P, _I, _I],
     "tild_init_velocities": [_P],
@@ -223,6 +224,13 @@ class Tild:
 
     def set_integrator(self, dt: float, friction: float, kT: float, mass: float = 1.0) -> None:
         self._chk(self.lib.tild_set_integrator(self.ctx, dt, friction, kT, mass))
+
+    FORCE_METHODS = {"ik": 0, "analytic": 1}
+
+    def set_force_method(self, method: str) -> None:
+        """Particle-mesh force: "ik" (spectral gradient, default) or
+        "analytic" (gradient of the assignment weights on the potentials)."""
+        self._chk(self.lib.tild_set_force_method(self.ctx, self.FORCE_METHODS[method]))
 
     SCHEMES = {"gjf": 0, "em": 1, "vv": 2}
 

@@ -176,6 +176,15 @@ tild_status tild_set_integrator(tild_ctx* c, double dt, double friction, double 
     return reparam(c, next);
 }
 
+tild_status tild_set_force_method(tild_ctx* c, int method) {
+    if (!c) return TILD_EINVAL;
+    if (method != TILD_FORCE_IK && method != TILD_FORCE_ANALYTIC)
+        return fail(c, TILD_EINVAL, "set_force_method: unknown method");
+    HostConfig next = c->cfg;
+    next.force_method = method;
+    return reparam(c, next);
+}
+
 tild_status tild_set_integrator_scheme(tild_ctx* c, int scheme) {
     if (!c) return TILD_EINVAL;
     if (scheme != TILD_SCHEME_GJF && scheme != TILD_SCHEME_EM && scheme != TILD_SCHEME_VV)
@@ -335,6 +344,10 @@ tild_status tild_batch_create(int n, tild_ctx* const* ctxs, tild_batch** out) {
         if (ctxs[i]->cfg.precision != prec) {
             g_create_error = "batch_create: all contexts must have the same precision";
             return TILD_EINVAL;
+        }
+        if (ctxs[i]->cfg.force_method != TILD_FORCE_IK) {
+            g_create_error = "batch_create: batched steps use the ik force only";
+            return TILD_EUNSUPPORTED;
         }
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) {

@@ -217,7 +217,7 @@ template <typename T> class BatchEngine final : public BatchBase {
                 if (st) return fail_from(e);
             }
             z.push_back(ZArgs<T>{e->Zxy_, e->H_, e->tw_, e->spectral_params(), nullptr, nullptr});
-            inv.push_back(InverseArgs<T>{e->H_, e->grad_, e->tw_, e->two_pi_L()});
+            inv.push_back(InverseArgs<T>{e->H_, e->grad_, e->tw_, e->two_pi_L(), 0});
         }
         tild_status st;
         if ((st = upload(&g.d_fwd, f)) || (st = upload(&g.d_z, z)) || (st = upload(&g.d_inv, inv))) return st;

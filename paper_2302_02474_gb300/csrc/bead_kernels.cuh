@@ -118,7 +118,7 @@ template <int P, typename T> struct Stencil {
 
 template <typename T> struct vec4_of;
 template <> struct vec4_of<float> { using type = float4; };
-template <> struct vec4_of<double> { using type = double4; };
+template <> struct vec4_of<double> { using type = double4_16a; };
 
 // -grad w_K interpolated at a bead, from the staged patch (in_patch: one
 // (gx, gy, gz) record per point and species) or from global memory.
@@ -174,6 +174,57 @@ __device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_pa
     fz = -gz;
 }
 
+// Analytic-differentiation force: F_i = -sum_g grad_r W(r_i - g) w_K(g),
+// the exact gradient of the gridded energy. The potentials come from the
+// staged patch (in_patch: w_A then w_B, one value per point) or from the
+// global field pot = i (w_A + i w_B). dw*: d/ds of the weights (s = x/dx).
+template <int P, typename T>
+__device__ __forceinline__ void gather_force_an(const Stencil<P, T>& st, const T (&dwx)[P], const T (&dwy)[P],
+                                                const T (&dwz)[P], bool in_patch, int3 l, const T* s_pot,
+                                                const cplx_t<T>* __restrict__ pot, int n, int species, T inv_dx,
+                                                T& fx, T& fy, T& fz) {
+    using PT = Patch<P>;
+    T gx = 0, gy = 0, gz = 0;
+    if (in_patch) {
+        const T* sp = s_pot + species * PT::W3;
+#pragma unroll
+        for (int c = 0; c < P; ++c)
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const T wyz = st.wy[b] * st.wz[c], dyz = dwy[b] * st.wz[c], ydz = st.wy[b] * dwz[c];
+                const int row = ((l.z + c) * PT::W + (l.y + b)) * PT::W + l.x;
+#pragma unroll
+                for (int a = 0; a < P; ++a) {
+                    const T w = sp[row + a];
+                    gx += dwx[a] * wyz * w;
+                    gy += st.wx[a] * dyz * w;
+                    gz += st.wx[a] * ydz * w;
+                }
+            }
+    } else {
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+            const size_t oz = (size_t)pwrap(st.jz + c, n) * n * n;
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const size_t oy = oz + (size_t)pwrap(st.jy + b, n) * n;
+                const T wyz = st.wy[b] * st.wz[c], dyz = dwy[b] * st.wz[c], ydz = st.wy[b] * dwz[c];
+#pragma unroll
+                for (int a = 0; a < P; ++a) {
+                    const cplx_t<T> v = __ldg(pot + oy + pwrap(st.jx + a, n));
+                    const T w = species ? -v.x : v.y;
+                    gx += dwx[a] * wyz * w;
+                    gy += st.wx[a] * dyz * w;
+                    gz += st.wx[a] * ydz * w;
+                }
+            }
+        }
+    }
+    fx = -gx * inv_dx;
+    fy = -gy * inv_dx;
+    fz = -gz * inv_dx;
+}
+
 // Spread one bead of species K into the fixed-point patch (in_patch) or
 // straight into the global grid.
 template <int P, typename T>
@@ -219,22 +270,24 @@ template <int P, typename T> __device__ __forceinline__ bool patch_local(const S
 // Beads of a tile are staged in shared memory in chunks of up to kBeadChunk.
 constexpr int kBeadChunk = 512;
 
-template <int P, typename T> struct BeadSmem {
+template <int P, typename T, bool AN = false> struct BeadSmem {
     using patch_t = typename FixedPoint<T>::patch_t;
     static constexpr int W3 = Patch<P>::W3;
-    // the gradient patch ([2 species][W3] of (gx, gy, gz, -)) is staged when
-    // it is small (else gathered from global memory)
-    static constexpr bool stage_grad = 2 * W3 * sizeof(typename vec4_of<T>::type) <= 48 * 1024;
+    // the force patch is staged when it is small (else gathered from global
+    // memory): [2 species][W3] of (gx, gy, gz, -) records, or with the
+    // analytic force [2 species][W3] potentials
+    static constexpr size_t field_bytes = AN ? 2 * W3 * sizeof(T) : 2 * W3 * sizeof(typename vec4_of<T>::type);
+    static constexpr bool stage_grad = field_bytes <= 48 * 1024;
     static constexpr int patches = 2;
     static constexpr size_t patch_off = 0;                                                       // patch_t [patches][W3]
-    static constexpr size_t grad_off = (patch_off + patches * W3 * sizeof(patch_t) + 31) / 32 * 32;  // vec4 [2][W3]
-    static constexpr size_t pos_off = grad_off + (stage_grad ? 2 * W3 * sizeof(typename vec4_of<T>::type) : 0);
+    static constexpr size_t grad_off = (patch_off + patches * W3 * sizeof(patch_t) + 31) / 32 * 32;
+    static constexpr size_t pos_off = grad_off + (stage_grad ? (field_bytes + 15) / 16 * 16 : 0);
     static constexpr size_t nbr_off = pos_off + 3 * kBeadChunk * sizeof(T);                       // int2 [chunk]
     static constexpr size_t tag_off = nbr_off + kBeadChunk * sizeof(int2);                        // int [chunk]
     static constexpr size_t bytes = tag_off + kBeadChunk * sizeof(int);
 };
 
-template <int P, typename T> constexpr size_t bead_smem_bytes() { return BeadSmem<P, T>::bytes; }
+template <int P, typename T, bool AN = false> constexpr size_t bead_smem_bytes() { return BeadSmem<P, T, AN>::bytes; }
 
 // Grid offset (within one field) of the first point of patch row `row`,
 // row = (plane * W + lz) * W + ly over stacked patches; sets the plane.
@@ -246,10 +299,10 @@ template <int P> __device__ __forceinline__ size_t patch_row_base(int row, int3 
     return ((size_t)pwrap(org.z + lz, n) * n + pwrap(org.y + ly, n)) * n;
 }
 
-template <int P, int MODE, typename T>
+template <int P, int MODE, typename T, bool AN = false>
 __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const BeadBuffers<T>& bf, int t) {
     using PT = Patch<P>;
-    using SM = BeadSmem<P, T>;
+    using SM = BeadSmem<P, T, AN>;
     using FP = FixedPoint<T>;
     using patch_t = typename FP::patch_t;
     using V = cplx_t<T>;
@@ -260,6 +313,7 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
     patch_t* patch = reinterpret_cast<patch_t*>(smem_raw + SM::patch_off);
     using V4 = typename vec4_of<T>::type;
     V4* s_grad = reinterpret_cast<V4*>(smem_raw + SM::grad_off);
+    T* s_pot = reinterpret_cast<T*>(smem_raw + SM::grad_off);  // analytic force: [2][W3] potentials
     T* s_pos = reinterpret_cast<T*>(smem_raw + SM::pos_off);
     int2* s_nbr = reinterpret_cast<int2*>(smem_raw + SM::nbr_off);
     int* s_tag = reinterpret_cast<int*>(smem_raw + SM::tag_off);
@@ -278,7 +332,29 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
     if (kSpread) {
         for (int i = threadIdx.x; i < SM::patches * PT::W3; i += blockDim.x) patch[i] = 0;
     }
-    if (kForce && SM::stage_grad && row_lane) {
+    if (AN && kForce && row_lane) {
+        // stage w_A, w_B of the patch from pot = i (w_A + i w_B) (field 3)
+        constexpr int NWARP = 8;
+        constexpr int ROWS_PER_LANE = (W * W + NWARP * RPW - 1) / (NWARP * RPW);
+        V v[ROWS_PER_LANE];
+#pragma unroll
+        for (int k = 0; k < ROWS_PER_LANE; ++k) {
+            const int row = row0 + k * rstride;
+            if (row < W * W) {
+                int unused;
+                v[k] = __ldg(bf.grad + 3 * M + patch_row_base<P>(row, org, p.n, unused) + gx);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < ROWS_PER_LANE; ++k) {
+            const int row = row0 + k * rstride;
+            if (row < W * W) {
+                s_pot[row * W + lx] = v[k].y;
+                s_pot[PT::W3 + row * W + lx] = -v[k].x;
+            }
+        }
+    }
+    if (!AN && kForce && SM::stage_grad && row_lane) {
         // stage the gradient fields of the patch as per-species (gx, gy, gz);
         // every row's loads are issued before any is used
         constexpr int NWARP = 8;  // 256 threads
@@ -382,7 +458,16 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
                     }
                 }
                 T fx, fy, fz;
-                gather_force<P>(st, staged, l, s_grad, bf.grad, p.n, species, fx, fy, fz);
+                if (AN) {
+                    T dwx[P], dwy[P], dwz[P];
+                    dh_weight_derivs<P>(x * p.inv_dx, dwx);
+                    dh_weight_derivs<P>(y * p.inv_dx, dwy);
+                    dh_weight_derivs<P>(z * p.inv_dx, dwz);
+                    gather_force_an<P>(st, dwx, dwy, dwz, inside, l, s_pot, bf.grad + 3 * M, p.n, species, p.inv_dx, fx,
+                                       fy, fz);
+                } else {
+                    gather_force<P>(st, staged, l, s_grad, bf.grad, p.n, species, fx, fy, fz);
+                }
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if ((k == 0 ? nb.x : nb.y) >= 0) {
@@ -488,9 +573,9 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
     }
 }
 
-template <int P, int MODE, typename T>
+template <int P, int MODE, typename T, bool AN = false>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
-    bead_kernel_body<P, MODE, T>(p, bf, blockIdx.x);
+    bead_kernel_body<P, MODE, T, AN>(p, bf, blockIdx.x);
 }
 
 // Batched form: blocks [r * tiles^3, (r + 1) * tiles^3) serve replica r.

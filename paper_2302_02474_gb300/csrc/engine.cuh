@@ -223,7 +223,7 @@ template <typename T> class Engine final : public EngineBase {
 
     tild_status energy_gradient(tild_energy_grad* g, void* dUdr, int dtype, int where) override {
         tild_status st;
-        if ((st = enqueue_fields(true, partials_, nullptr, true))) return st;
+        if ((st = enqueue_fields(true, partials_, nullptr, kInvGradPot))) return st;
         std::vector<double> zpart(4 * n_z_blocks_);
         TILD_CUDA(cudaMemcpyAsync(zpart.data(), partials_, zpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
         BeadBuffers<T> bf = bead_buffers();
@@ -312,7 +312,7 @@ template <typename T> class Engine final : public EngineBase {
 
     tild_status get_field_gradient(void* out, int dtype, int where) override {
         tild_status st;
-        if ((st = enqueue_fields(false, nullptr, nullptr))) return st;
+        if ((st = enqueue_fields(false, nullptr, nullptr, kInvGrad))) return st;
         if ((st = stage_out_vec((T*)grad_, 6 * M_, out, dtype, where))) return st;
         TILD_CUDA(cudaStreamSynchronize(stream_));
         return TILD_OK;
@@ -383,9 +383,9 @@ template <typename T> class Engine final : public EngineBase {
             TILD_CUDA(cudaEventRecord(ev[1], stream_));
             if ((st = enqueue_forward(true))) return st;
             TILD_CUDA(cudaEventRecord(ev[2], stream_));
-            if ((st = enqueue_zpass(nullptr, nullptr))) return st;
+            if ((st = enqueue_zpass(nullptr, nullptr, analytic()))) return st;
             TILD_CUDA(cudaEventRecord(ev[3], stream_));
-            if ((st = enqueue_inverse())) return st;
+            if ((st = enqueue_inverse(force_fields()))) return st;
             TILD_CUDA(cudaEventRecord(ev[4], stream_));
             BeadBuffers<T> bf = bead_buffers();
             bf.qx = pos_[1 - cur_pos_];
@@ -507,12 +507,14 @@ template <typename T> class Engine final : public EngineBase {
     size_t rows_smem() const { return ((size_t)n_ + (size_t)16 * row_pitch(n_)) * sizeof(V); }
     size_t ycol_smem() const { return ((size_t)n_ + 2 * (size_t)n_ * C_) * sizeof(V); }
     size_t zpass_smem() const { return ((size_t)n_ + 4 * (size_t)n_ * CZ_) * sizeof(V); }
-    size_t bead_smem() const {
+    bool analytic() const { return cfg_->force_method == TILD_FORCE_ANALYTIC; }
+    size_t bead_smem() const { return bead_smem(analytic()); }
+    size_t bead_smem(bool an) const {
         switch (P_) {
-            case 2: return bead_smem_bytes<2, T>();
-            case 3: return bead_smem_bytes<3, T>();
-            case 4: return bead_smem_bytes<4, T>();
-            default: return bead_smem_bytes<5, T>();
+            case 2: return an ? bead_smem_bytes<2, T, true>() : bead_smem_bytes<2, T>();
+            case 3: return an ? bead_smem_bytes<3, T, true>() : bead_smem_bytes<3, T>();
+            case 4: return an ? bead_smem_bytes<4, T, true>() : bead_smem_bytes<4, T>();
+            default: return an ? bead_smem_bytes<5, T, true>() : bead_smem_bytes<5, T>();
         }
     }
 
@@ -649,15 +651,20 @@ template <typename T> class Engine final : public EngineBase {
         }
         constexpr int CC = zpass_cols(NN);
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
+        TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
         return TILD_OK;
     }
 
     template <int P> tild_status attrs_p() {
-        const int s = (int)bead_smem();
+        const int s = (int)bead_smem(false);
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSpread, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeForce, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSetVel, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeStep, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
+        const int sa = (int)bead_smem(true);
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeForce, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSetVel, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeStep, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
         return TILD_OK;
     }
 
@@ -717,7 +724,7 @@ template <typename T> class Engine final : public EngineBase {
             if constexpr (NN >= 16 && NN >= CC) {
                 x_forward_rows<T, NN, 16><<<(unsigned)((size_t)NN * NN / 16), 256, rows_smem(), stream_>>>(
                     rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0, zero_after ? counters_ : nullptr);
-                y_columns<T, NN, CC, -1><<<dim3(NN / CC, NN, 1), 256, ycol_smem(), stream_>>>(Zxy_, tw_, two_pi_L());
+                y_columns<T, NN, CC, -1><<<dim3(NN / CC, NN, 1), 256, ycol_smem(), stream_>>>(Zxy_, tw_, two_pi_L(), 0);
             }
         }
         TILD_CUDA(cudaGetLastError());
@@ -749,13 +756,18 @@ template <typename T> class Engine final : public EngineBase {
         return sp;
     }
 
-    template <int NN> tild_status zpass_n(double* partials, V* spec_out) {
+    template <int NN> tild_status zpass_n(double* partials, V* spec_out, bool g_only) {
         constexpr int CC = zpass_cols(NN);
-        z_spectral<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1), 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, spectral_params(), partials, spec_out);
+        if (g_only)
+            z_spectral<T, NN, CC, true><<<dim3(NN / CC, NN / 2 + 1), 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, spectral_params(),
+                                                                                                    partials, spec_out);
+        else
+            z_spectral<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1), 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, spectral_params(),
+                                                                                              partials, spec_out);
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
     }
-    tild_status enqueue_zpass(double* partials, V* spec_out) {
+    tild_status enqueue_zpass(double* partials, V* spec_out, bool g_only = false) {
         if (kernel_a_ != cfg_->a) {
             // exp(-a^2 k_m^2), k_m = 2 pi m / L with m in FFT index order
             std::vector<T> e(n_);
@@ -768,38 +780,46 @@ template <typename T> class Engine final : public EngineBase {
             TILD_CUDA(cudaMemcpy(kernel1d_, e.data(), n_ * sizeof(T), cudaMemcpyHostToDevice));
             kernel_a_ = cfg_->a;
         }
-        return dispatch_n([&](auto nn) { return this->template zpass_n<decltype(nn)::value>(partials, spec_out); });
+        return dispatch_n([&](auto nn) { return this->template zpass_n<decltype(nn)::value>(partials, spec_out, g_only); });
     }
 
-    template <int NN> tild_status inverse_n(bool with_potential) {
-        const unsigned nd = with_potential ? 4 : 3;
+    // what the inverse xy pass produces
+    static constexpr int kInvGrad = 0, kInvGradPot = 1, kInvPot = 2;
+    template <int NN> tild_status inverse_n(int what) {
+        const unsigned nd = what == kInvGrad ? 3 : what == kInvGradPot ? 4 : 1;
+        const int d0 = what == kInvPot ? 3 : 0;
         if (plane_fits_) {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
-                xy_inverse_plane<T, NN><<<dim3(NN, nd), 512, plane_smem(), stream_>>>(H_, grad_, tw_, two_pi_L());
+                xy_inverse_plane<T, NN><<<dim3(NN, nd), 512, plane_smem(), stream_>>>(H_, grad_, tw_, two_pi_L(), d0);
             }
         } else {
             constexpr int CC = 128 / sizeof(V);
             if constexpr (NN >= 16 && NN >= CC) {
-                y_columns<T, NN, CC, +1><<<dim3(NN / CC, NN, 2), 256, ycol_smem(), stream_>>>(H_, tw_, two_pi_L());
-                x_inverse_rows<T, NN, 16><<<dim3((unsigned)((size_t)NN * NN / 16), nd), 256, rows_smem(), stream_>>>(H_, grad_, tw_, two_pi_L());
+                y_columns<T, NN, CC, +1><<<dim3(NN / CC, NN, what == kInvPot ? 1 : 2), 256, ycol_smem(), stream_>>>(
+                    H_, tw_, two_pi_L(), what == kInvPot ? 1 : 0);
+                x_inverse_rows<T, NN, 16><<<dim3((unsigned)((size_t)NN * NN / 16), nd), 256, rows_smem(), stream_>>>(
+                    H_, grad_, tw_, two_pi_L(), d0);
             }
         }
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
     }
-    tild_status enqueue_inverse(bool with_potential = false) {
-        return dispatch_n([&](auto nn) { return this->template inverse_n<decltype(nn)::value>(with_potential); });
+    tild_status enqueue_inverse(int what) {
+        return dispatch_n([&](auto nn) { return this->template inverse_n<decltype(nn)::value>(what); });
     }
+    // the fields the bead kernel's force needs: ik gradients or the potentials
+    int force_fields() const { return analytic() ? kInvPot : kInvGrad; }
 
-    tild_status enqueue_fields(bool energy, double* partials, V* spec_out, bool with_potential = false) {
+    tild_status enqueue_fields(bool energy, double* partials, V* spec_out, int what = -1) {
+        if (what < 0) what = force_fields();
         tild_status st;
         if (!have_pos_) {
             err = "positions have not been set";
             return TILD_ESTATE;
         }
         if ((st = enqueue_forward(false))) return st;
-        if ((st = enqueue_zpass(energy ? partials : nullptr, spec_out))) return st;
-        return enqueue_inverse(with_potential);
+        if ((st = enqueue_zpass(energy ? partials : nullptr, spec_out, what == kInvPot))) return st;
+        return enqueue_inverse(what);
     }
 
     // Constants of the integrator update (see BeadParams), from FP64.
@@ -886,13 +906,22 @@ template <typename T> class Engine final : public EngineBase {
 
     template <int P> tild_status bead_p(int mode, const BeadBuffers<T>& bf) {
         const unsigned grid = (unsigned)tiles_ * tiles_ * tiles_;
-        const size_t sm = bead_smem();
         const BeadParams<T> p = bead_params();
-        switch (mode) {
-            case kModeSpread: bead_kernel<P, kModeSpread, T><<<grid, 256, sm, stream_>>>(p, bf); break;
-            case kModeForce: bead_kernel<P, kModeForce, T><<<grid, 256, sm, stream_>>>(p, bf); break;
-            case kModeSetVel: bead_kernel<P, kModeSetVel, T><<<grid, 256, sm, stream_>>>(p, bf); break;
-            default: bead_kernel<P, kModeStep, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+        if (analytic() && mode != kModeSpread) {
+            const size_t sm = bead_smem(true);
+            switch (mode) {
+                case kModeForce: bead_kernel<P, kModeForce, T, true><<<grid, 256, sm, stream_>>>(p, bf); break;
+                case kModeSetVel: bead_kernel<P, kModeSetVel, T, true><<<grid, 256, sm, stream_>>>(p, bf); break;
+                default: bead_kernel<P, kModeStep, T, true><<<grid, 256, sm, stream_>>>(p, bf); break;
+            }
+        } else {
+            const size_t sm = bead_smem(false);
+            switch (mode) {
+                case kModeSpread: bead_kernel<P, kModeSpread, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+                case kModeForce: bead_kernel<P, kModeForce, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+                case kModeSetVel: bead_kernel<P, kModeSetVel, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+                default: bead_kernel<P, kModeStep, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+            }
         }
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
@@ -909,8 +938,8 @@ template <typename T> class Engine final : public EngineBase {
     tild_status enqueue_step() {
         tild_status st;
         if ((st = enqueue_forward(true))) return st;
-        if ((st = enqueue_zpass(nullptr, nullptr))) return st;
-        if ((st = enqueue_inverse())) return st;
+        if ((st = enqueue_zpass(nullptr, nullptr, analytic()))) return st;
+        if ((st = enqueue_inverse(force_fields()))) return st;
         BeadBuffers<T> bf = bead_buffers();
         bf.qx = pos_[1 - cur_pos_];
         bf.qy = bf.qx + cfg_->n_beads;

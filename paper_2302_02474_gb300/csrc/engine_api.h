@@ -28,6 +28,7 @@ struct HostConfig {
     // integrator
     double dt = 0.005, friction = 1.0, kT = 1.0, mass = 1.0;
     int scheme = 0;  // TILD_SCHEME_*
+    int force_method = 0;  // TILD_FORCE_*
 };
 
 class EngineBase {

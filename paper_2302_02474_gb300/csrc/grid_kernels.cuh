@@ -184,6 +184,7 @@ template <typename T> struct InverseArgs {
     cplx_t<T>* grad;
     const cplx_t<T>* tw;
     T two_pi_over_L;
+    int d0;  // first direction (blockIdx.y + d0); 3 alone: the potentials only
 };
 
 template <typename T, int N> __device__ __forceinline__ void xy_inverse_plane_body(const InverseArgs<T>& args, int bx, int by) {
@@ -200,7 +201,7 @@ template <typename T, int N> __device__ __forceinline__ void xy_inverse_plane_bo
 
     // direction d: x from i k_x G, y from i k_y G, z from G_z (field 2);
     // d = 3 (optional): the potentials themselves, i (w_A + i w_B), from G
-    const int d = by;
+    const int d = by + args.d0;
     const size_t M = (size_t)N * N * N;
     const size_t src = (d == 2 ? 2 * M : 0) + (size_t)bx * N * N;
     batched_load<N * N, 512, V>([&](int i) { return H[src + i]; },
@@ -226,8 +227,8 @@ template <typename T, int N> __device__ __forceinline__ void xy_inverse_plane_bo
 template <typename T, int N>
 __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restrict__ H,
                                                          cplx_t<T>* __restrict__ grad,
-                                                         const cplx_t<T>* __restrict__ tw_g, T two_pi_over_L) {
-    xy_inverse_plane_body<T, N>(InverseArgs<T>{H, grad, tw_g, two_pi_over_L}, blockIdx.x, blockIdx.y);
+                                                         const cplx_t<T>* __restrict__ tw_g, T two_pi_over_L, int d0) {
+    xy_inverse_plane_body<T, N>(InverseArgs<T>{H, grad, tw_g, two_pi_over_L, d0}, blockIdx.x, blockIdx.y);
 }
 
 // Batched form: replica blockIdx.z.
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(256) x_forward_rows(unsigned long long* __rest
 
 template <typename T, int N, int R>
 __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restrict__ H, cplx_t<T>* __restrict__ grad,
-                                                       const cplx_t<T>* __restrict__ tw_g, T two_pi_over_L) {
+                                                       const cplx_t<T>* __restrict__ tw_g, T two_pi_over_L, int d0) {
     using V = cplx_t<T>;
     constexpr int PITCH = row_pitch(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -270,10 +271,11 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
     V* rows = tw + N;
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
-    const size_t base = (size_t)blockIdx.y * M + (size_t)blockIdx.x * R * N;
+    const int d = (int)blockIdx.y + d0;
+    const size_t base = (size_t)d * M + (size_t)blockIdx.x * R * N;
     // field 3 (optional, the potentials) is the plain transform of field 0
-    const size_t src = (size_t)(blockIdx.y == 3 ? 0 : blockIdx.y) * M + (size_t)blockIdx.x * R * N;
-    const bool kx_mult = blockIdx.y == 0;  // d_x: multiply by k_x before the x transform
+    const size_t src = (size_t)(d == 3 ? 0 : d) * M + (size_t)blockIdx.x * R * N;
+    const bool kx_mult = d == 0;  // d_x: multiply by k_x before the x transform
     batched_load<R * N, 256, V>([&](int i) { return H[src + i]; },
                                 [&](int i, V v) {
                                     const int kx = kx_of_pos<N>(i % N);
@@ -289,10 +291,11 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
 // Forward (DIR = -1, part 0): Zxy in place.
 // Inverse (DIR = +1) on H: part 0 loads a tile of G (field 0) and writes
 // the transforms of G (field 0) and of i k_y G (field 1) from the same
-// load; part 1 transforms G_z (field 2) in place.
+// load; part 1 transforms G_z (field 2) in place. With only_g, one part
+// transforms G alone.
 template <typename T, int N, int C, int DIR>
 __global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, const cplx_t<T>* __restrict__ tw_g,
-                                                 T two_pi_over_L) {
+                                                 T two_pi_over_L, int only_g) {
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, c
     constexpr int TS = N * C;
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
-    const bool two = DIR > 0 && blockIdx.z == 0;
+    const bool two = DIR > 0 && blockIdx.z == 0 && !only_g;  // only_g: G alone (one part)
     const size_t off = (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * C;
     const size_t src = (DIR > 0 && blockIdx.z == 1 ? 2 * M : 0) + off;
     batched_load<TS, 256, V>([&](int i) { return data[src + (size_t)(i / C) * N + i % C]; },
@@ -350,7 +353,7 @@ template <typename T> __device__ __forceinline__ int freq_index(int i, int n) { 
 // with Q = w~_A + i w~_B. Buffers [2R][N][C]: G of row r in buffer r
 // (overwriting the input), G_z in buffer R + r.
 // --------------------------------------------------------------------------
-template <typename T, int N, int C, int R>
+template <typename T, int N, int C, int R, bool G_ONLY>
 __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, const T* e1, const SpectralParams<T>& sp,
                                        int p0, const int (&ky)[2], bool want_e, double (&acc)[4]) {
     using V = cplx_t<T>;
@@ -408,12 +411,13 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
         }
 #pragma unroll
         for (int d = 0; d < 2; ++d) {
+            if (d == 1 && G_ONLY) break;
             buf[(d * R) * TS + kz * C + c] = out[0][d];
             if (!same) buf[(d * R + rB) * TS + kzB * C + cB] = out[1][d];
         }
     }
     __syncthreads();
-    smem_fft_lines<N, +1, 2 * R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+    smem_fft_lines<N, +1, (G_ONLY ? 1 : 2) * R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
 }
 
 template <typename T> struct ZArgs {
@@ -425,7 +429,7 @@ template <typename T> struct ZArgs {
     cplx_t<T>* spectrum_out;
 };
 
-template <typename T, int N, int C>
+template <typename T, int N, int C, bool G_ONLY = false>
 __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, int by, int gdx) {
     using V = cplx_t<T>;
     const cplx_t<T>* __restrict__ Zxy = args.Zxy;
@@ -474,9 +478,9 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
         return;
     }
     if (R == 1)
-        z_tile<T, N, C, 1>(buf, tw, e1, sp, p0, ky, want_e, acc);
+        z_tile<T, N, C, 1, G_ONLY>(buf, tw, e1, sp, p0, ky, want_e, acc);
     else
-        z_tile<T, N, C, 2>(buf, tw, e1, sp, p0, ky, want_e, acc);
+        z_tile<T, N, C, 2, G_ONLY>(buf, tw, e1, sp, p0, ky, want_e, acc);
     if (want_e) {
         // block reduction in a fixed order (deterministic)
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -495,7 +499,8 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
         }
     }
     const size_t M = NN * N;
-    for (int i = threadIdx.x; i < 2 * R * TS; i += blockDim.x) {
+    const int nbuf = (G_ONLY ? 1 : 2) * R * TS;
+    for (int i = threadIdx.x; i < nbuf; i += blockDim.x) {
         const int b = i / TS, rem = i % TS;
         const int f = (b / R) * 2, r = b % R;  // fields 0 (G) and 2 (G_z)
         const int z = rem / C, c = rem % C;
@@ -503,13 +508,14 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
     }
 }
 
-template <typename T, int N, int C>
+// G_ONLY: write G alone (the potentials' path of the analytic force).
+template <typename T, int N, int C, bool G_ONLY = false>
 __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ Zxy, cplx_t<T>* __restrict__ H,
                                                   const cplx_t<T>* __restrict__ tw_g, SpectralParams<T> sp,
                                                   double* __restrict__ energy_partials,
                                                   cplx_t<T>* __restrict__ spectrum_out) {
-    z_spectral_body<T, N, C>(ZArgs<T>{Zxy, H, tw_g, sp, energy_partials, spectrum_out}, blockIdx.x, blockIdx.y,
-                             gridDim.x);
+    z_spectral_body<T, N, C, G_ONLY>(ZArgs<T>{Zxy, H, tw_g, sp, energy_partials, spectrum_out}, blockIdx.x,
+                                     blockIdx.y, gridDim.x);
 }
 
 // Batched form: replica blockIdx.z.
