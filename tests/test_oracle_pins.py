@@ -475,3 +475,82 @@ def test_vv_langevin_free_particle_velocity_variances():
     expect_u = 0.7 / (1.0 - 2.0 * 0.1 / 2.0)
     assert abs(np.mean(u2) - expect_u) < 0.01 * expect_u
     assert expect_u / 0.7 > 1.1  # distinguishes the half-step from the full-step variance
+
+
+# ------------------------------------------------------------ electrostatics
+
+
+def _charged_pair(r, n, L=24.0, ae=1.0, lb=1.0, P=4):
+    """A +1 (species A) and a -1 (species B) charge at separation r along x."""
+    m = O.Model(L=L, n=n, P=P, species=np.array([0, 1]), n_species=2, bonds=np.zeros((0, 2), np.int64), b=1.0,
+                chi=np.zeros((2, 2)), kappa=0.0, a=0.5, charges=np.array([1.0, -1.0]), bjerrum=lb, charge_smear=ae)
+    c = np.array([L / 2 + 0.13, L / 2 - 0.21, L / 2 + 0.07])
+    return m, np.stack([c - [r / 2, 0, 0], c + [r / 2, 0, 0]])
+
+
+def test_coulomb_pair_converges_to_the_smeared_closed_form():
+    """Two opposite charges smeared over unit Gaussians of width a_e interact
+    through -l_B erf(r / 2 a_e) / r (the convolution of two such Gaussians
+    has variance 2 a_e^2 per axis). Differences of the gridded energy and the
+    gridded force along the pair axis approach that closed form as the grid
+    is refined (the particle-mesh smoothing of order-P splines is the
+    method's own error): the error falls at least twofold from dx = 0.5 to
+    dx = 0.25, where it is below 3% (the images of the neutral pair in
+    L = 24 contribute about 1e-3). A wrong 4 pi, a missing 1/2, the smearing
+    exponent a_e^2/2 or a flipped sign each miss by 20% or more."""
+    from math import erf, exp, pi, sqrt
+
+    def closed_e(r):
+        return -erf(r / 2.0) / r
+
+    def closed_f(r):  # force on the +1 charge along +x (attractive: towards the -1 charge)
+        return -(erf(r / 2.0) / r ** 2 - exp(-r * r / 4.0) / (sqrt(pi) * r))
+
+    errs = []
+    for n in (48, 96):
+        e = {}
+        for r in (1.5, 3.0):
+            m, pos = _charged_pair(r, n)
+            e[r] = O.energies(m, pos)["elec"]
+        de = e[1.5] - e[3.0]
+        ref = closed_e(1.5) - closed_e(3.0)
+        m, pos = _charged_pair(2.0, n)
+        fx = O.nonbonded_forces(m, pos, "analytic")[0, 0]
+        errs.append((abs(de / ref - 1.0), abs(fx / -closed_f(2.0) - 1.0)))
+    assert errs[1][0] < 0.5 * errs[0][0] and errs[1][1] < 0.5 * errs[0][1]
+    assert errs[1][0] < 0.03 and errs[1][1] < 0.03
+
+
+def test_charged_forces_are_energy_gradient():
+    """With charges, central differences of the total energy (bond, chi,
+    kappa and electrostatic) equal the analytic force."""
+    m, pos = _model(P=3, n_chains=4, N=4, n_a=2, L=4.0, n=8, a=0.5, charges=np.array([0.7, -1.1]), bjerrum=2.0,
+                    charge_smear=0.4)
+    f = O.forces(m, pos, variant="analytic")
+
+    def etot(p):
+        e = O.energies(m, p)
+        return e["bond"] + e["chi"] + e["kappa"] + e["elec"]
+
+    assert abs(O.energies(m, pos)["elec"]) > 1e-3
+    h = 1e-5
+    for i in (0, 5, 10):
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            fd = -(etot(pp) - etot(pm)) / (2 * h)
+            assert abs(fd - f[i, d]) < 1e-7 * max(1.0, np.abs(f).max())
+
+
+def test_neutral_homogeneous_melt_has_no_electrostatics():
+    """A +1 and a -1 bead on every node: zero charge density, no
+    electrostatic energy or force."""
+    L, n = 4.0, 8
+    g = np.stack(np.meshgrid(*[np.arange(n) * (L / n)] * 3, indexing="ij"), axis=-1).reshape(-1, 3)
+    pos = np.concatenate([g, g])
+    sp = np.concatenate([np.zeros(len(g), np.int64), np.ones(len(g), np.int64)])
+    m = O.Model(L=L, n=n, P=2, species=sp, n_species=2, bonds=np.zeros((0, 2), np.int64), b=1.0,
+                chi=np.zeros((2, 2)), kappa=0.0, a=0.5, charges=np.array([1.0, -1.0]), bjerrum=3.0, charge_smear=0.5)
+    assert abs(O.energies(m, pos)["elec"]) < 1e-12
+    assert np.abs(O.nonbonded_forces(m, pos)).max() < 1e-12
