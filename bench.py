@@ -413,6 +413,10 @@ def main():
         t.set_force_method("analytic")
         timed("analytic_force", "F = -sum grad W w_K: one inverse transform of the potentials, GJF")
         t.set_force_method("ik")
+        t.set_electrostatics(1.5, -1.0, 1.0, 0.5)
+        timed("electrostatics", "ik force, GJF, smeared-charge Coulomb term: q_A = 1.5, q_B = -1 (neutral A8B12 "
+                                "chains), l_B = 1, a_e = 0.5")
+        t.set_electrostatics(0.0, 0.0, 0.0, 0.5)
         t.set_scheme("vv")
         timed("velocity_verlet", "ik force, velocity-Verlet + Langevin thermostat force")
         t.set_scheme("em")

@@ -73,8 +73,9 @@ typedef struct tild_ctx tild_ctx;
 /*
  * Box, grid and numerics (Listing infile: box and grid size, pmeorder).
  *   L[3]        box edges; this build requires a cubic box (L[0]=L[1]=L[2] > 0).
- *   n[3]        grid points per edge; cubic, a power of two in [8, 256]
- *               (FP64 grids up to 128). Others give TILD_EUNSUPPORTED.
+ *   n[3]        grid points per edge; cubic: a power of two in [8, 256]
+ *               (FP64 grids up to 128) or one of the 5-smooth sizes 24,
+ *               40, 48, 80. Others give TILD_EUNSUPPORTED.
  *   pmeorder    assignment order p in 1..4: p+1 grid points per dimension
  *               (order 1 = the two nearest points, Fig. pmm).
  *   precision   TILD_FP32 (grids, FFT and bead state in FP32; energies in
@@ -106,13 +107,16 @@ typedef struct {
 /* Energies in kT (Eqs. bonds, fh, HelfandP) and diagnostics of the current
  * configuration. e_chi keeps the k=0 Fourier term of Eq. fh; e_kappa drops
  * the k=0 term, which cancels the -rho_0 shift of Eq. HelfandP exactly.
- * kinetic = sum_i m |v_i|^2 / 2. net_force = sum_i F_i. */
+ * kinetic = sum_i m |v_i|^2 / 2. net_force = sum_i F_i. e_elec is the
+ * smeared-charge electrostatic energy (0 without charges; see
+ * tild_set_electrostatics). */
 typedef struct {
     double e_bond;
     double e_chi;
     double e_kappa;
     double kinetic;
     double net_force[3];
+    double e_elec;
 } tild_energy;
 
 /* Energy of the current configuration and its derivatives with respect to
@@ -130,6 +134,7 @@ typedef struct {
     double dU_dchi;
     double dU_dkappa;
     double dU_da;
+    double e_elec;  /* included in energy; a does not enter it */
 } tild_energy_grad;
 
 #define TILD_COMPUTE_ENERGY 1u
@@ -191,6 +196,19 @@ tild_status tild_set_integrator(tild_ctx* ctx, double dt, double friction, doubl
  *                        assignment weights. Not momentum conserving.
  * If velocities exist, v^n is kept. Batches (tild_batch_create) take
  * TILD_FORCE_IK contexts only. Unknown methods return TILD_EINVAL. */
+/* Electrostatics (Sec. "Long-range interactions": charged monomers interact
+ * through Coulomb forces computed with the same particle-mesh scheme;
+ * charges are spread over a unit Gaussian with a charge spreading length,
+ * and the Bjerrum length sets the strength). q_a, q_b = charge of every A
+ * and every B bead (units of e); bjerrum = l_B in units of length (0 turns
+ * electrostatics off); smear = a_e > 0. The pair kernel of two smeared
+ * charges is 4 pi l_B exp(-|k|^2 a_e^2) / |k|^2 in Fourier space (k = 0
+ * dropped: a neutralising background), so w_K gains q_K phi and
+ * E_elec = (1/2) int rho_q phi. Applies to both force methods and to
+ * tild_energy_gradient. If velocities exist, v^n is kept. Non-finite values,
+ * bjerrum < 0 or smear <= 0 return TILD_EINVAL. */
+tild_status tild_set_electrostatics(tild_ctx* ctx, double q_a, double q_b, double bjerrum, double smear);
+
 #define TILD_FORCE_IK 0
 #define TILD_FORCE_ANALYTIC 1
 tild_status tild_set_force_method(tild_ctx* ctx, int method);

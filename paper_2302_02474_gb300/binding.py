@@ -43,12 +43,13 @@ class tild_moltype(ctypes.Structure):
 
 
 class tild_energy_grad(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_double) for k in ("energy", "e_bond", "e_chi", "e_kappa", "dU_dchi", "dU_dkappa", "dU_da")]
+    _fields_ = [(k, ctypes.c_double) for k in ("energy", "e_bond", "e_chi", "e_kappa", "dU_dchi", "dU_dkappa", "dU_da",
+                                               "e_elec")]
 
 
 class tild_energy(ctypes.Structure):
     _fields_ = [("e_bond", ctypes.c_double), ("e_chi", ctypes.c_double), ("e_kappa", ctypes.c_double),
-                ("kinetic", ctypes.c_double), ("net_force", ctypes.c_double * 3)]
+                ("kinetic", ctypes.c_double), ("net_force", ctypes.c_double * 3), ("e_elec", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -62,6 +63,7 @@ _SIGS = {
     "tild_set_integrator": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
     "tild_set_integrator_scheme": [_P, ctypes.c_int],
     "tild_set_force_method": [_P, ctypes.c_int],
+    "tild_set_electrostatics": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
     "tild_set_stream": [_P, _P],
     "tild_set_positions": [_P, _P, _I, _I],
     "tild_init_velocities": [_P],
@@ -225,6 +227,11 @@ class Tild:
     def set_integrator(self, dt: float, friction: float, kT: float, mass: float = 1.0) -> None:
         self._chk(self.lib.tild_set_integrator(self.ctx, dt, friction, kT, mass))
 
+    def set_electrostatics(self, q_a: float, q_b: float, bjerrum: float, smear: float) -> None:
+        """Per-species charges, Bjerrum length (0: off) and charge spreading
+        length of the smeared-charge Coulomb interaction."""
+        self._chk(self.lib.tild_set_electrostatics(self.ctx, q_a, q_b, bjerrum, smear))
+
     FORCE_METHODS = {"ik": 0, "analytic": 1}
 
     def set_force_method(self, method: str) -> None:
@@ -299,7 +306,7 @@ class Tild:
             f = np.empty(3 * self.n_beads, dtype=dtype) if out is None else out
             ptr, code, where, _keep = _buffer(f, 3 * self.n_beads)
         self._chk(self.lib.tild_compute(self.ctx, what, ctypes.byref(e), ptr, code, where))
-        en = {"bond": e.e_bond, "chi": e.e_chi, "kappa": e.e_kappa, "kinetic": e.kinetic,
+        en = {"bond": e.e_bond, "chi": e.e_chi, "kappa": e.e_kappa, "elec": e.e_elec, "kinetic": e.kinetic,
               "net_force": np.array(e.net_force[:])}
         if f is not None and isinstance(f, np.ndarray):
             f = f.reshape(-1, 3)

@@ -176,6 +176,19 @@ tild_status tild_set_integrator(tild_ctx* c, double dt, double friction, double 
     return reparam(c, next);
 }
 
+tild_status tild_set_electrostatics(tild_ctx* c, double q_a, double q_b, double bjerrum, double smear) {
+    if (!c) return TILD_EINVAL;
+    if (!std::isfinite(q_a) || !std::isfinite(q_b) || !std::isfinite(bjerrum) || !std::isfinite(smear) ||
+        !(bjerrum >= 0) || !(smear > 0))
+        return fail(c, TILD_EINVAL, "set_electrostatics: need finite charges, bjerrum >= 0 and smear > 0");
+    HostConfig next = c->cfg;
+    next.q_a = q_a;
+    next.q_b = q_b;
+    next.bjerrum = bjerrum;
+    next.charge_smear = smear;
+    return reparam(c, next);
+}
+
 tild_status tild_set_force_method(tild_ctx* c, int method) {
     if (!c) return TILD_EINVAL;
     if (method != TILD_FORCE_IK && method != TILD_FORCE_ANALYTIC)

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <map>
+#include <tuple>
 #include <utility>
 
 #include "engine.cuh"
@@ -23,6 +24,7 @@ template <typename T> class BatchEngine final : public BatchBase {
 
     struct Group {
         int n = 0, P = 2, C = 16, tiles3 = 0;
+        bool el = false;  // charges on (z pass with the Coulomb term)
         std::vector<E*> reps;
         cudaStream_t s = nullptr;   // the group's stream (forked from the batch stream)
         cudaEvent_t done = nullptr;
@@ -95,15 +97,16 @@ template <typename T> class BatchEngine final : public BatchBase {
         }
         cur_pos_ = cur_uid_ = 0;
         steps_since_sort_ = 0;
-        // groups by (grid, order)
-        std::map<std::pair<int, int>, size_t> index;
+        // groups by (grid, order, charges on)
+        std::map<std::tuple<int, int, bool>, size_t> index;
         for (E* e : reps_) {
-            const auto key = std::make_pair(e->n_, e->P_);
+            const auto key = std::make_tuple(e->n_, e->P_, e->c_el_on());
             if (!index.count(key)) {
                 index[key] = groups_.size();
                 Group g;
                 g.n = e->n_;
                 g.P = e->P_;
+                g.el = e->c_el_on();
                 g.C = E::zpass_cols(e->n_);
                 g.tiles3 = e->n_tiles_;
                 groups_.push_back(g);
@@ -211,11 +214,8 @@ template <typename T> class BatchEngine final : public BatchBase {
         std::vector<InverseArgs<T>> inv;
         for (E* e : g.reps) {
             f.push_back(ForwardArgs<T>{e->rho_fx_, e->Zxy_, e->tw_, e->density_scale(), 1, e->counters_});
-            // the z pass needs the kernel table of the replica's current a
-            if (e->kernel_a_ != e->cfg_->a) {
-                tild_status st = e->enqueue_zpass(nullptr, nullptr);  // refreshes the table
-                if (st) return fail_from(e);
-            }
+            // the z pass needs the kernel tables of the replica's current a (and a_e)
+            if (e->refresh_tables()) return fail_from(e);
             z.push_back(ZArgs<T>{e->Zxy_, e->H_, e->tw_, e->spectral_params(), nullptr, nullptr});
             inv.push_back(InverseArgs<T>{e->H_, e->grad_, e->tw_, e->two_pi_L(), 0});
         }
@@ -255,6 +255,8 @@ template <typename T> class BatchEngine final : public BatchBase {
                                                (int)e0->plane_smem()));
                 TILD_CUDA(cudaFuncSetAttribute(z_spectral_batched<T, NN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)e0->zpass_smem()));
+                TILD_CUDA(cudaFuncSetAttribute(z_spectral_batched<T, NN, CC, true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e0->zpass_smem()));
                 TILD_CUDA(cudaFuncSetAttribute(bead_kernel_batched<PP, kModeStep, T>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e0->bead_smem()));
             }
@@ -302,7 +304,10 @@ template <typename T> class BatchEngine final : public BatchBase {
                 if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
                     constexpr int CC = E::zpass_cols(NN);
                     xy_forward_plane_batched<T, NN><<<dim3(NN, R), 512, e0->plane_smem(), g.s>>>(g.d_fwd);
-                    z_spectral_batched<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1, R), 256, e0->zpass_smem(), g.s>>>(g.d_z);
+                    if (g.el)
+                        z_spectral_batched<T, NN, CC, true><<<dim3(NN / CC, NN / 2 + 1, R), 256, e0->zpass_smem(), g.s>>>(g.d_z);
+                    else
+                        z_spectral_batched<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1, R), 256, e0->zpass_smem(), g.s>>>(g.d_z);
                     xy_inverse_plane_batched<T, NN><<<dim3(NN, 3, R), 512, e0->plane_smem(), g.s>>>(g.d_inv);
                     bead_kernel_batched<PP, kModeStep, T><<<(unsigned)g.tiles3 * R, 256, e0->bead_smem(), g.s>>>(
                         g.d_bead[cur_pos_][cur_uid_], g.tiles3);

@@ -53,7 +53,7 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(cudaMalloc(&H_, 3 * M_ * sizeof(V)));
         TILD_CUDA(cudaMalloc(&grad_, 4 * M_ * sizeof(V)));  // 3 gradients + (optional) potentials
         TILD_CUDA(cudaMalloc(&tw_, n_ * sizeof(V)));
-        TILD_CUDA(cudaMalloc(&kernel1d_, n_ * sizeof(T)));
+        TILD_CUDA(cudaMalloc(&kernel1d_, 2 * n_ * sizeof(T)));  // exp(-a^2 k_m^2), then exp(-a_e^2 k_m^2)
         TILD_CUDA(cudaMalloc(&counters_, 4 * sizeof(unsigned long long)));
         TILD_CUDA(cudaMemset(counters_, 0, 4 * sizeof(unsigned long long)));
         TILD_CUDA(cudaMemset(rho_fx_, 0, 2 * M_ * sizeof(unsigned long long)));
@@ -64,7 +64,7 @@ template <typename T> class Engine final : public EngineBase {
         scan_blocks_ = (int)((n_tiles_ + 1 + 1023) / 1024);
         TILD_CUDA(cudaMalloc(&block_sums_, scan_blocks_ * sizeof(int)));
         n_z_blocks_ = (size_t)(n_ / CZ_) * (n_ / 2 + 1);
-        n_partials_ = std::max(4 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
+        n_partials_ = std::max(5 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
         TILD_CUDA(cudaMalloc(&partials_, n_partials_ * sizeof(double)));
         // twiddles W_n^m = exp(-2 pi i m / n) in FP64, rounded to T
         std::vector<V> tw(n_);
@@ -181,7 +181,7 @@ template <typename T> class Engine final : public EngineBase {
         if ((st = enqueue_fields(want_e, partials_, nullptr))) return st;
         std::vector<double> zpart;
         if (want_e) {
-            zpart.resize(4 * n_z_blocks_);
+            zpart.resize(5 * n_z_blocks_);
             TILD_CUDA(cudaMemcpyAsync(zpart.data(), partials_, zpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
         }
         BeadBuffers<T> bf = bead_buffers();
@@ -198,16 +198,18 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(cudaStreamSynchronize(stream_));
         if ((st = check_err())) return st;
         if (want_e && e) {
-            double s0 = 0, s1 = 0;
+            double s0 = 0, s1 = 0, s4 = 0;
             for (size_t b = 0; b < n_z_blocks_; ++b) {
-                s0 += zpart[4 * b];
-                s1 += zpart[4 * b + 1];
+                s0 += zpart[5 * b];
+                s1 += zpart[5 * b + 1];
+                s4 += zpart[5 * b + 4];
             }
             const double V = cfg_->L * cfg_->L * cfg_->L;
             const double dV = V / (double)M_;
             const double rho0 = cfg_->n_beads / V;
             e->e_chi = cfg_->chi / rho0 * dV * dV / V * s0;
             e->e_kappa = cfg_->kappa / (2.0 * rho0) * dV * dV / V * s1;
+            e->e_elec = e_elec_from(s4);
         }
         if (e) {
             double acc[5] = {0, 0, 0, 0, 0};
@@ -216,7 +218,7 @@ template <typename T> class Engine final : public EngineBase {
             e->e_bond = acc[0];
             e->kinetic = acc[1];
             for (int d = 0; d < 3; ++d) e->net_force[d] = acc[2 + d];
-            if (!want_e) e->e_chi = e->e_kappa = 0.0;
+            if (!want_e) e->e_chi = e->e_kappa = e->e_elec = 0.0;
         }
         return TILD_OK;
     }
@@ -224,7 +226,7 @@ template <typename T> class Engine final : public EngineBase {
     tild_status energy_gradient(tild_energy_grad* g, void* dUdr, int dtype, int where) override {
         tild_status st;
         if ((st = enqueue_fields(true, partials_, nullptr, kInvGradPot))) return st;
-        std::vector<double> zpart(4 * n_z_blocks_);
+        std::vector<double> zpart(5 * n_z_blocks_);
         TILD_CUDA(cudaMemcpyAsync(zpart.data(), partials_, zpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
         BeadBuffers<T> bf = bead_buffers();
         if ((st = launch_bead(kModeForce, bf))) return st;  // bond energy partials
@@ -245,9 +247,9 @@ template <typename T> class Engine final : public EngineBase {
         }
         TILD_CUDA(cudaStreamSynchronize(stream_));
         if ((st = check_err())) return st;
-        double s[4] = {0, 0, 0, 0};
+        double s[5] = {0, 0, 0, 0, 0};
         for (size_t b = 0; b < n_z_blocks_; ++b)
-            for (int k = 0; k < 4; ++k) s[k] += zpart[4 * b + k];
+            for (int k = 0; k < 5; ++k) s[k] += zpart[5 * b + k];
         double eb = 0;
         for (size_t b = 0; b < bpart.size() / 5; ++b) eb += bpart[5 * b];
         const double V = cfg_->L * cfg_->L * cfg_->L;
@@ -258,7 +260,8 @@ template <typename T> class Engine final : public EngineBase {
         g->e_bond = eb;
         g->e_chi = cfg_->chi / rho0 * f * s[0];
         g->e_kappa = cfg_->kappa / (2.0 * rho0) * f * s[1];
-        g->energy = g->e_bond + g->e_chi + g->e_kappa;
+        g->e_elec = e_elec_from(s[4]);
+        g->energy = g->e_bond + g->e_chi + g->e_kappa + g->e_elec;
         g->dU_dchi = f * s[0] / rho0;
         g->dU_dkappa = f * s[1] / (2.0 * rho0);
         g->dU_da = -2.0 * cfg_->a * (cfg_->chi / rho0 * f * s[2] + cfg_->kappa / (2.0 * rho0) * f * s[3]);
@@ -467,7 +470,7 @@ template <typename T> class Engine final : public EngineBase {
     V* grad_ = nullptr;
     V* tw_ = nullptr;
     T* kernel1d_ = nullptr;
-    double kernel_a_ = -1.0;
+    double kernel_a_ = -1.0, kernel_ae_ = -1.0;
     V* spec_ = nullptr;
     unsigned long long* counters_ = nullptr;  // [0] noise step counter, [1] error flags
     double* partials_ = nullptr;
@@ -508,6 +511,12 @@ template <typename T> class Engine final : public EngineBase {
     size_t ycol_smem() const { return ((size_t)n_ + 2 * (size_t)n_ * C_) * sizeof(V); }
     size_t zpass_smem() const { return ((size_t)n_ + 4 * (size_t)n_ * CZ_) * sizeof(V); }
     bool analytic() const { return cfg_->force_method == TILD_FORCE_ANALYTIC; }
+    bool c_el_on() const { return cfg_->bjerrum > 0 && (cfg_->q_a != 0 || cfg_->q_b != 0); }
+    // E_el = (4 pi l_B) dV^2 / (2 V) sum_k exp(-a_e^2 k^2)/k^2 |q_A rho^_A + q_B rho^_B|^2
+    double e_elec_from(double s4) const {
+        const double V = cfg_->L * cfg_->L * cfg_->L, dV = V / (double)M_;
+        return c_el_on() ? 4.0 * 3.14159265358979323846 * cfg_->bjerrum * dV * dV / (2.0 * V) * s4 : 0.0;
+    }
     size_t bead_smem() const { return bead_smem(analytic()); }
     size_t bead_smem(bool an) const {
         switch (P_) {
@@ -652,6 +661,8 @@ template <typename T> class Engine final : public EngineBase {
         constexpr int CC = zpass_cols(NN);
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
+        TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
+        TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
         return TILD_OK;
     }
 
@@ -753,33 +764,55 @@ template <typename T> class Engine final : public EngineBase {
         sp.eBB = sp.eAA;
         sp.eAB = (T)((cfg_->chi + cfg_->kappa) / rho0 / (double)M_);
         sp.kernel1d = kernel1d_;
+        const bool charged = c_el_on();
+        sp.el_scale = charged ? (T)(4.0 * 3.14159265358979323846 * cfg_->bjerrum / (double)M_) : T(0);
+        sp.qA = (T)cfg_->q_a;
+        sp.qB = (T)cfg_->q_b;
+        sp.kernel1d_el = kernel1d_ + n_;
         return sp;
     }
 
     template <int NN> tild_status zpass_n(double* partials, V* spec_out, bool g_only) {
         constexpr int CC = zpass_cols(NN);
-        if (g_only)
-            z_spectral<T, NN, CC, true><<<dim3(NN / CC, NN / 2 + 1), 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, spectral_params(),
-                                                                                                    partials, spec_out);
+        const dim3 grid(NN / CC, NN / 2 + 1);
+        const SpectralParams<T> sp = spectral_params();
+        const bool el = c_el_on();
+        if (g_only && el)
+            z_spectral<T, NN, CC, true, true><<<grid, 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, sp, partials, spec_out);
+        else if (g_only)
+            z_spectral<T, NN, CC, true><<<grid, 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, sp, partials, spec_out);
+        else if (el)
+            z_spectral<T, NN, CC, false, true><<<grid, 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, sp, partials, spec_out);
         else
-            z_spectral<T, NN, CC><<<dim3(NN / CC, NN / 2 + 1), 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, spectral_params(),
-                                                                                              partials, spec_out);
+            z_spectral<T, NN, CC><<<grid, 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, sp, partials, spec_out);
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
     }
-    tild_status enqueue_zpass(double* partials, V* spec_out, bool g_only = false) {
-        if (kernel_a_ != cfg_->a) {
-            // exp(-a^2 k_m^2), k_m = 2 pi m / L with m in FFT index order
+    // separable Gaussian tables exp(-s^2 k_m^2), k_m = 2 pi m / L, m in FFT
+    // index order: the pair kernel's (s = a) and, with charges, the charge
+    // smearing's (s = a_e); rebuilt when the parameter changes
+    tild_status refresh_tables() {
+        auto refresh = [&](double s, double& cached, T* dst) -> tild_status {
+            if (cached == s) return TILD_OK;
             std::vector<T> e(n_);
             for (int i = 0; i < n_; ++i) {
                 const double m = i < n_ / 2 ? i : i - n_;
                 const double k = 2.0 * 3.14159265358979323846 * m / cfg_->L;
-                e[i] = (T)std::exp(-cfg_->a * cfg_->a * k * k);
+                e[i] = (T)std::exp(-s * s * k * k);
             }
             TILD_CUDA(cudaStreamSynchronize(stream_));  // no z pass may still read the old table
-            TILD_CUDA(cudaMemcpy(kernel1d_, e.data(), n_ * sizeof(T), cudaMemcpyHostToDevice));
-            kernel_a_ = cfg_->a;
-        }
+            TILD_CUDA(cudaMemcpy(dst, e.data(), n_ * sizeof(T), cudaMemcpyHostToDevice));
+            cached = s;
+            return TILD_OK;
+        };
+        tild_status st;
+        if ((st = refresh(cfg_->a, kernel_a_, kernel1d_))) return st;
+        if (c_el_on() && (st = refresh(cfg_->charge_smear, kernel_ae_, kernel1d_ + n_))) return st;
+        return TILD_OK;
+    }
+    tild_status enqueue_zpass(double* partials, V* spec_out, bool g_only = false) {
+        tild_status st;
+        if ((st = refresh_tables())) return st;
         return dispatch_n([&](auto nn) { return this->template zpass_n<decltype(nn)::value>(partials, spec_out, g_only); });
     }
 

@@ -29,6 +29,8 @@ struct HostConfig {
     double dt = 0.005, friction = 1.0, kT = 1.0, mass = 1.0;
     int scheme = 0;  // TILD_SCHEME_*
     int force_method = 0;  // TILD_FORCE_*
+    // electrostatics: charge per species, Bjerrum length (0: off), charge spreading length
+    double q_a = 0.0, q_b = 0.0, bjerrum = 0.0, charge_smear = 0.5;
 };
 
 class EngineBase {

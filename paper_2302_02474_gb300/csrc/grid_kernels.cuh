@@ -28,6 +28,11 @@ template <typename T> struct SpectralParams {
     T two_pi_over_L;   // 2 pi / L
     T eAA, eAB, eBB;   // eps matrix / M (the 1/M of the inverse DFT folded in)
     const T* kernel1d; // exp(-a^2 k_m^2) per 1-D frequency index m (FP64 on the host)
+    // smeared-charge electrostatics: w_K += q_K c(k) (q_A rho~_A + q_B rho~_B) with
+    // c(k) = el_scale exp(-a_e^2 |k|^2) / |k|^2 (0 at k = 0); el_scale = 4 pi l_B / M
+    // (0: no charges); kernel1d_el = exp(-a_e^2 k_m^2)
+    T el_scale, qA, qB;
+    const T* kernel1d_el;
 };
 
 template <int N> __host__ __device__ __forceinline__ int kx_of_pos(int p);
@@ -353,9 +358,9 @@ template <typename T> __device__ __forceinline__ int freq_index(int i, int n) { 
 // with Q = w~_A + i w~_B. Buffers [2R][N][C]: G of row r in buffer r
 // (overwriting the input), G_z in buffer R + r.
 // --------------------------------------------------------------------------
-template <typename T, int N, int C, int R, bool G_ONLY>
+template <typename T, int N, int C, int R, bool G_ONLY, bool EL>
 __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, const T* e1, const SpectralParams<T>& sp,
-                                       int p0, const int (&ky)[2], bool want_e, double (&acc)[4]) {
+                                       int p0, const int (&ky)[2], bool want_e, double (&acc)[5], const T* e2) {
     using V = cplx_t<T>;
     constexpr int TS = N * C;
     smem_fft_lines<N, -1, R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
@@ -371,6 +376,7 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
     const T qxA = raw_k<T, N>(kxA, sp.two_pi_over_L), qyA = raw_k<T, N>(ky[0], sp.two_pi_over_L);
     const T qxB = raw_k<T, N>(kxB, sp.two_pi_over_L), qyB = raw_k<T, N>(ky[rB], sp.two_pi_over_L);
     const double kxy2A = (double)qxA * qxA + (double)qyA * qyA, kxy2B = (double)qxB * qxB + (double)qyB * qyB;
+    const T exy2A = EL ? e2[kxA] * e2[ky[0]] : T(0), exy2B = EL ? e2[kxB] * e2[ky[rB]] : T(0);
     for (int kz = threadIdx.x / C; kz < N; kz += 256 / C) {
         const int kzB = kz == 0 ? 0 : N - kz;
         if (R == 1 && kzB * C + cB < kz * C + c) continue;  // the mirror element owns this pair
@@ -403,8 +409,21 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
                     acc[3] += k2 * fkap;
                 }
             }
-            const V wA = {uh * (sp.eAA * A.x + sp.eAB * B.x), uh * (sp.eAA * A.y + sp.eAB * B.y)};
-            const V wB = {uh * (sp.eAB * A.x + sp.eBB * B.x), uh * (sp.eAB * A.y + sp.eBB * B.y)};
+            V wA = {uh * (sp.eAA * A.x + sp.eAB * B.x), uh * (sp.eAA * A.y + sp.eAB * B.y)};
+            V wB = {uh * (sp.eAB * A.x + sp.eBB * B.x), uh * (sp.eAB * A.y + sp.eBB * B.y)};
+            if (EL) {
+                // w_K += q_K c(k) rho~_q with rho~_q = q_A rho~_A + q_B rho~_B
+                const T qzv = raw_k<T, N>(kzi, sp.two_pi_over_L);
+                const T k2 = (T)(s == 0 ? kxy2A : kxy2B) + qzv * qzv;
+                const T g = k2 > T(0) ? (s == 0 ? exy2A : exy2B) * e2[kzi] / k2 : T(0);
+                const V rq = {sp.qA * A.x + sp.qB * B.x, sp.qA * A.y + sp.qB * B.y};
+                const T c = sp.el_scale * g;
+                wA.x += c * sp.qA * rq.x;
+                wA.y += c * sp.qA * rq.y;
+                wB.x += c * sp.qB * rq.x;
+                wB.y += c * sp.qB * rq.y;
+                if (want_e) acc[4] += (double)g * ((double)rq.x * rq.x + (double)rq.y * rq.y);
+            }
             const V iQ = {-(wA.y + wB.x), wA.x - wB.y};  // i (w~_A + i w~_B)
             out[s][0] = iQ;                               // x, y: k_x, k_y applied in the xy pass
             out[s][1] = {kzv * iQ.x, kzv * iQ.y};         // z
@@ -429,7 +448,7 @@ template <typename T> struct ZArgs {
     cplx_t<T>* spectrum_out;
 };
 
-template <typename T, int N, int C, bool G_ONLY = false>
+template <typename T, int N, int C, bool G_ONLY = false, bool EL = false>
 __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, int by, int gdx) {
     using V = cplx_t<T>;
     const cplx_t<T>* __restrict__ Zxy = args.Zxy;
@@ -442,10 +461,13 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* buf = tw + N;
     constexpr int TS = N * C;
-    __shared__ double red[4][8];
+    __shared__ double red[5][8];
     __shared__ T e1[N];  // separable Gaussian kernel: u_hat = e1[kx] e1[ky] e1[kz]
+    __shared__ T e2[N];  // charge smearing exp(-a_e^2 k_m^2), when charges are on
     load_twiddles(tw, tw_g, N);
     for (int i = threadIdx.x; i < N; i += blockDim.x) e1[i] = sp.kernel1d[i];
+    if (EL)
+        for (int i = threadIdx.x; i < N; i += blockDim.x) e2[i] = sp.kernel1d_el[i];
 
     const int p0 = bx * C;
     const int ky[2] = {by, by == 0 ? 0 : N - by};
@@ -462,7 +484,7 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
     else
         batched_load<2 * TS, 256, V>(zsrc, zdst);
     __syncthreads();
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     const bool want_e = energy_partials != nullptr;
     if (spectrum_out) {
         // forward transform only, written out in natural kx order
@@ -478,24 +500,24 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
         return;
     }
     if (R == 1)
-        z_tile<T, N, C, 1, G_ONLY>(buf, tw, e1, sp, p0, ky, want_e, acc);
+        z_tile<T, N, C, 1, G_ONLY, EL>(buf, tw, e1, sp, p0, ky, want_e, acc, e2);
     else
-        z_tile<T, N, C, 2, G_ONLY>(buf, tw, e1, sp, p0, ky, want_e, acc);
+        z_tile<T, N, C, 2, G_ONLY, EL>(buf, tw, e1, sp, p0, ky, want_e, acc, e2);
     if (want_e) {
         // block reduction in a fixed order (deterministic)
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 5; ++k) {
             double v = acc[k];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if (lane == 0) red[k][wid] = v;
         }
         __syncthreads();
-        if (threadIdx.x < 4) {
+        if (threadIdx.x < 5) {
             double sum = 0;
             for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) sum += red[threadIdx.x][w];
             const size_t b = (size_t)by * gdx + bx;
-            energy_partials[4 * b + threadIdx.x] = sum;
+            energy_partials[5 * b + threadIdx.x] = sum;
         }
     }
     const size_t M = NN * N;
@@ -509,19 +531,20 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
 }
 
 // G_ONLY: write G alone (the potentials' path of the analytic force).
-template <typename T, int N, int C, bool G_ONLY = false>
+// EL: add the smeared-charge Coulomb term (charges on).
+template <typename T, int N, int C, bool G_ONLY = false, bool EL = false>
 __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ Zxy, cplx_t<T>* __restrict__ H,
                                                   const cplx_t<T>* __restrict__ tw_g, SpectralParams<T> sp,
                                                   double* __restrict__ energy_partials,
                                                   cplx_t<T>* __restrict__ spectrum_out) {
-    z_spectral_body<T, N, C, G_ONLY>(ZArgs<T>{Zxy, H, tw_g, sp, energy_partials, spectrum_out}, blockIdx.x,
+    z_spectral_body<T, N, C, G_ONLY, EL>(ZArgs<T>{Zxy, H, tw_g, sp, energy_partials, spectrum_out}, blockIdx.x,
                                      blockIdx.y, gridDim.x);
 }
 
 // Batched form: replica blockIdx.z.
-template <typename T, int N, int C>
+template <typename T, int N, int C, bool EL = false>
 __global__ void __launch_bounds__(256) z_spectral_batched(const ZArgs<T>* __restrict__ args) {
-    z_spectral_body<T, N, C>(args[blockIdx.z], blockIdx.x, blockIdx.y, gridDim.x);
+    z_spectral_body<T, N, C, false, EL>(args[blockIdx.z], blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 }  // namespace tild
