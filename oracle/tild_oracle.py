@@ -586,3 +586,137 @@ def run_with(step_fn, m: Model, st: State, n_steps: int, force_fn=None) -> State
     for _ in range(n_steps):
         st = step_fn(m, st, force_fn)
     return st
+
+
+# ---------------------------------------------------------------------------
+# Differentiable form: vector-Jacobian product of the ik force
+# ---------------------------------------------------------------------------
+
+
+def force_vjp(m: Model, pos: np.ndarray, lam: np.ndarray) -> Dict[str, object]:
+    """J^T lam for the ik particle-mesh + bond force F(r; chi, kappa, a):
+    d/dr_j of sum_i lam_i . F_i, and the derivatives of sum_i lam_i . F_i with
+    respect to chi, kappa and a.
+
+    With W_i(g) = W(r_i - g), mu_K(g) = sum_{i in K} W_i(g) lam_i, C the
+    convolution with the smeared kernel (u_hat), D the i k~ derivative (anti-
+    self-adjoint; Nyquist zeroed) and psi_K = sum_K' eps_KK' C (D . mu_K'):
+      (J^T lam)_j = - sum_g grad W_j(g) (lam_j . D w_{K_j})(g)
+                    + (1/dV) sum_g grad W_j(g) psi_{K_j}(g)
+                    - (3/b^2) sum_{i ~ j} (lam_j - lam_i),
+      d/dchi   = sum_K sum_g (D . mu_K)(g) dw_K/dchi(g)  (dw_A/dchi = C rho_B / rho0),
+      d/dkappa = ... with dw_K/dkappa = C (rho_A + rho_B) / rho0,
+      d/da     = ... with dw_K/da = sum_K' eps_KK' C_a rho_K', C_a: -2 a |k|^2 u_hat.
+    Charges add their Coulomb term to C for the position part (the parameter
+    part covers chi, kappa, a only)."""
+    n, L, P, dx = m.n, m.L, m.P, m.dx
+    S = m.n_species
+    rho = spread(m, pos)
+    f = potential_fields(m, rho)
+    s = wrap(pos, L) / dx
+    js, ws, dws = [], [], []
+    for d in range(3):
+        j, w = stencil(s[:, d], P)
+        _, dw = stencil_derivative(s[:, d], P)
+        js.append(j % n)
+        ws.append(w)
+        dws.append(dw / dx)
+    # mu_K (vector field per species, no 1/dV)
+    mu = np.zeros((S, 3, n * n * n))
+    for a in range(P):
+        for b in range(P):
+            for c in range(P):
+                flat = (js[0][:, a] * n + js[1][:, b]) * n + js[2][:, c]
+                w = ws[0][:, a] * ws[1][:, b] * ws[2][:, c]
+                for K in range(S):
+                    sel = m.species == K
+                    for d in range(3):
+                        mu[K, d] += np.bincount(flat[sel], weights=w[sel] * lam[sel, d], minlength=n ** 3)
+    mu = mu.reshape(S, 3, n, n, n)
+    kt = gradient_wavenumbers(n, L)
+    kvec = (kt[:, None, None], kt[None, :, None], kt[None, None, :])
+    div_hat = np.zeros((S, n, n, n), dtype=complex)  # DFT of D . mu_K
+    for K in range(S):
+        for d in range(3):
+            div_hat[K] += 1j * kvec[d] * np.fft.fftn(mu[K, d])
+    u_hat = f["u_hat"]
+    kernel = m.eps()[:, :, None, None, None] * u_hat[None, None]
+    if _has_charges(m):
+        q = np.asarray(m.charges, dtype=float)[:S]
+        kernel = kernel + q[:, None, None, None, None] * q[None, :, None, None, None] * \
+            coulomb_kernel_hat(n, L, m.bjerrum, m.charge_smear)[None, None]
+    psi = np.fft.ifftn(np.einsum("kl...,l...->k...", kernel, div_hat), axes=(1, 2, 3)).real
+    dV = dx ** 3
+    # lam_j . D w_{K_j} at every grid point, per bead
+    gw = f["grad_w"]  # (S, 3, n, n, n)
+    out = np.zeros((m.n_beads, 3))
+    rows = np.arange(m.n_beads)
+    K = m.species
+    for a in range(P):
+        for b in range(P):
+            for c in range(P):
+                gx, gy, gz = js[0][:, a], js[1][:, b], js[2][:, c]
+                ldw = sum(lam[:, d] * gw[K, d, gx, gy, gz] for d in range(3))
+                val = psi[K, gx, gy, gz] / dV - ldw
+                out[:, 0] += dws[0][:, a] * ws[1][:, b] * ws[2][:, c] * val
+                out[:, 1] += ws[0][:, a] * dws[1][:, b] * ws[2][:, c] * val
+                out[:, 2] += ws[0][:, a] * ws[1][:, b] * dws[2][:, c] * val
+    # bonds
+    kb = 3.0 / m.b ** 2
+    dl = lam[m.bonds[:, 0]] - lam[m.bonds[:, 1]]
+    np.add.at(out, m.bonds[:, 0], -kb * dl)
+    np.add.at(out, m.bonds[:, 1], kb * dl)
+    # parameters (Parseval: sum_g f h = (1/M) sum_k conj(f~) h~ for real f, h)
+    M = n ** 3
+    rho_hat = f["rho_hat"]
+    k = wavenumbers(n, L)
+    k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2
+    out_t = {"chi": 0.0, "kappa": 0.0, "a": 0.0}
+    if S == 2:
+        out_t["chi"] = float(np.real(np.sum(np.conj(div_hat[0]) * u_hat * rho_hat[1] +
+                                            np.conj(div_hat[1]) * u_hat * rho_hat[0]))) / (m.rho0 * M)
+    tot = rho_hat.sum(axis=0)
+    out_t["kappa"] = float(np.real(np.sum(np.conj(div_hat.sum(axis=0)) * u_hat * tot))) / (m.rho0 * M)
+    eps_rho = np.einsum("kl,l...->k...", m.eps(), rho_hat)
+    out_t["a"] = float(np.real(np.sum(np.conj(div_hat) * (-2.0 * m.a * k2 * u_hat)[None] * eps_rho))) / M
+    return {"r": out, **out_t}
+
+
+def gjf_trajectory_vjp(m: Model, pos0: np.ndarray, vel0: np.ndarray, n_steps: int, r_bar: np.ndarray,
+                       v_bar: Optional[np.ndarray] = None) -> Dict[str, object]:
+    """Reverse-mode derivative of L(r^K, v^K) through K GJF steps (noise held
+    fixed: the same Philox counters), given dL/dr^K = r_bar and dL/dv^K =
+    v_bar. Returns dL/dr^0, dL/dv^0 and dL/dchi, dL/dkappa, dL/da.
+
+    One step maps (r, v, F) to (r', v', F') with F' = F(r') and
+      r' = r + b dt v + (b dt^2/2m) F + (b dt/2m) beta,
+      v' = a v + (dt/2m)(a F + F'),
+    so with h = dt/2m its adjoint is
+      Fb'_tot = Fb' + h vb',  rb'_tot = rb' + J(r')^T Fb'_tot,
+      rb = rb'_tot,  vb = b dt rb'_tot + a vb',  Fb = (b dt^2/2m) rb'_tot + h a vb',
+    and the parameters collect (dF/dtheta)(r')^T Fb'_tot at every step and at
+    r^0 (F^0 = F(r^0))."""
+    dt, mass, alpha = m.dt, m.mass, m.friction
+    h = dt / (2 * mass)
+    ga = (1.0 - alpha * h) / (1.0 + alpha * h)
+    gb = 1.0 / (1.0 + alpha * h)
+    st = State(wrap(pos0, m.L), vel0.copy(), forces(m, wrap(pos0, m.L)), 0)
+    traj = [st]
+    for _ in range(n_steps):
+        st = gjf_step(m, st)
+        traj.append(st)
+    rb = r_bar.copy()
+    vb = np.zeros_like(rb) if v_bar is None else v_bar.copy()
+    fb = np.zeros_like(rb)
+    tb = {"chi": 0.0, "kappa": 0.0, "a": 0.0}
+    for n in range(n_steps, 0, -1):
+        ft = fb + h * vb
+        v = force_vjp(m, traj[n].pos, ft)
+        rt = rb + v["r"]
+        for k in tb:
+            tb[k] += v[k]
+        rb, vb, fb = rt, gb * dt * rt + ga * vb, gb * dt * dt / (2 * mass) * rt + h * ga * vb
+    v = force_vjp(m, traj[0].pos, fb)
+    for k in tb:
+        tb[k] += v[k]
+    return {"r0": rb + v["r"], "v0": vb, **tb}

@@ -554,3 +554,80 @@ def test_neutral_homogeneous_melt_has_no_electrostatics():
                 chi=np.zeros((2, 2)), kappa=0.0, a=0.5, charges=np.array([1.0, -1.0]), bjerrum=3.0, charge_smear=0.5)
     assert abs(O.energies(m, pos)["elec"]) < 1e-12
     assert np.abs(O.nonbonded_forces(m, pos)).max() < 1e-12
+
+
+# ------------------------------------------------------- force vector-Jacobian
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_force_vjp_matches_finite_differences(P):
+    """J^T lam of the ik force equals central differences of sum_i lam_i . F_i
+    with respect to positions, chi, kappa and a (with charges on)."""
+    m, pos = _model(P=P, n_chains=4, N=4, n_a=2, L=4.0, n=8, a=0.6, charges=np.array([0.5, -0.8]), bjerrum=1.5,
+                    charge_smear=0.5)
+    lam = np.random.default_rng(7).normal(size=pos.shape)
+    v = O.force_vjp(m, pos, lam)
+
+    def lf(mm, p):
+        return float(np.sum(lam * O.forces(mm, p)))
+
+    h = 1e-5
+    scale = max(1.0, np.abs(v["r"]).max())
+    for i in (0, 5, 11):
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            fd = (lf(m, pp) - lf(m, pm)) / (2 * h)
+            assert abs(fd - v["r"][i, d]) < 1e-6 * scale
+    import dataclasses
+    for name, attr, get in (("chi", "chi", lambda mm: mm.chi[0, 1]), ("kappa", "kappa", None), ("a", "a", None)):
+        mp, mm_ = dataclasses.replace(m), dataclasses.replace(m)
+        if name == "chi":
+            mp.chi = m.chi + h * np.array([[0, 1], [1, 0]])
+            mm_.chi = m.chi - h * np.array([[0, 1], [1, 0]])
+        else:
+            setattr(mp, attr, getattr(m, attr) + h)
+            setattr(mm_, attr, getattr(m, attr) - h)
+        fd = (lf(mp, pos) - lf(mm_, pos)) / (2 * h)
+        assert fd == pytest.approx(v[name], rel=1e-6, abs=1e-8)
+
+
+def test_gjf_trajectory_vjp_matches_finite_differences():
+    """Reverse-mode derivatives of L = sum w . r^K after K GJF steps (noise
+    fixed) equal central differences of L with respect to chi, kappa, a, an
+    initial position and an initial velocity."""
+    import dataclasses
+
+    m, pos = _model(P=2, n_chains=4, N=4, n_a=2, L=4.0, n=8, a=0.6, dt=0.02)
+    vel = O.initial_state(m, pos).vel
+    K = 6
+    w = np.random.default_rng(9).normal(size=pos.shape)
+    g = O.gjf_trajectory_vjp(m, pos, vel, K, w)
+
+    def loss(mm, p, v):
+        st = O.State(O.wrap(p, mm.L), v, O.forces(mm, O.wrap(p, mm.L)), 0)
+        st = O.run(mm, st, K)
+        r = st.pos
+        # unwrap against the start so a boundary crossing does not jump
+        return float(np.sum(w * (O.wrap(pos, mm.L) + O.minimum_image(r - O.wrap(pos, mm.L), mm.L))))
+
+    h = 1e-6
+    for name in ("chi", "kappa", "a"):
+        mp, mm_ = dataclasses.replace(m), dataclasses.replace(m)
+        if name == "chi":
+            mp.chi, mm_.chi = m.chi + h * np.array([[0, 1], [1, 0]]), m.chi - h * np.array([[0, 1], [1, 0]])
+        else:
+            setattr(mp, name, getattr(m, name) + h)
+            setattr(mm_, name, getattr(m, name) - h)
+        fd = (loss(mp, pos, vel) - loss(mm_, pos, vel)) / (2 * h)
+        assert fd == pytest.approx(g[name], rel=1e-5, abs=1e-9), name
+    for i, d in ((0, 1), (7, 2)):
+        pp, pm = pos.copy(), pos.copy()
+        pp[i, d] += h
+        pm[i, d] -= h
+        assert (loss(m, pp, vel) - loss(m, pm, vel)) / (2 * h) == pytest.approx(g["r0"][i, d], rel=1e-5, abs=1e-9)
+        vp, vm = vel.copy(), vel.copy()
+        vp[i, d] += h
+        vm[i, d] -= h
+        assert (loss(m, pos, vp) - loss(m, pos, vm)) / (2 * h) == pytest.approx(g["v0"][i, d], rel=1e-5, abs=1e-9)
