@@ -264,6 +264,18 @@ tild_status tild_compute(tild_ctx* ctx, unsigned what, tild_energy* e, void* for
  * refined.) Does not change the state. */
 tild_status tild_energy_gradient(tild_ctx* ctx, tild_energy_grad* g, void* dU_dr, int dtype, int where);
 
+/* Vector-Jacobian product of the force (differentiable form): for an
+ * adjoint vector lam [n_beads][3] (by bead id, dtype/where as for
+ * positions), out [n_beads][3] receives sum_i lam_i . dF_i/dr_j for every
+ * bead j, where F is the ik particle-mesh force of Eq. PMM plus the bond
+ * force of Eq. bonds (charges included) at the current positions. dtheta
+ * (NULL to skip) receives d(sum_i lam_i . F_i)/d(chi, kappa, a). Chained
+ * through the integrator this gives derivatives of trajectories; the
+ * Python package has the GJF chain with checkpoints. Returns
+ * TILD_EUNSUPPORTED with the analytic force method or for grids whose
+ * planes do not fit one CTA (FP32 above 128^3, FP64 above 64^3). */
+tild_status tild_force_vjp(tild_ctx* ctx, const void* lam, void* out, int dtype, int where, double* dtheta);
+
 /* Current positions (wrapped into [0, L)), [n_beads][3]. */
 tild_status tild_get_positions(tild_ctx* ctx, void* out, int dtype, int where);
 

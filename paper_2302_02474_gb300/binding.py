@@ -64,6 +64,7 @@ _SIGS = {
     "tild_set_integrator_scheme": [_P, ctypes.c_int],
     "tild_set_force_method": [_P, ctypes.c_int],
     "tild_set_electrostatics": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+    "tild_force_vjp": [_P, _P, _P, _I, _I, ctypes.POINTER(ctypes.c_double)],
     "tild_set_stream": [_P, _P],
     "tild_set_positions": [_P, _P, _I, _I],
     "tild_init_velocities": [_P],
@@ -183,6 +184,9 @@ class Tild:
         self.L = L
         self.np_dtype = np.float32 if precision == "fp32" else np.float64
         self.n_beads = 0
+        self.integrator = (0.005, 1.0, 1.0, 1.0)  # dt, friction, kT, mass (the library defaults)
+        self.scheme = "gjf"
+        self.force_method = "ik"
 
     @classmethod
     def from_spec(cls, spec, sort_every: int = 0, precision: Optional[str] = None) -> "Tild":
@@ -226,6 +230,7 @@ class Tild:
 
     def set_integrator(self, dt: float, friction: float, kT: float, mass: float = 1.0) -> None:
         self._chk(self.lib.tild_set_integrator(self.ctx, dt, friction, kT, mass))
+        self.integrator = (float(dt), float(friction), float(kT), float(mass))
 
     def set_electrostatics(self, q_a: float, q_b: float, bjerrum: float, smear: float) -> None:
         """Per-species charges, Bjerrum length (0: off) and charge spreading
@@ -238,6 +243,7 @@ class Tild:
         """Particle-mesh force: "ik" (spectral gradient, default) or
         "analytic" (gradient of the assignment weights on the potentials)."""
         self._chk(self.lib.tild_set_force_method(self.ctx, self.FORCE_METHODS[method]))
+        self.force_method = method
 
     SCHEMES = {"gjf": 0, "em": 1, "vv": 2}
 
@@ -245,6 +251,7 @@ class Tild:
         """Integrator of Sec. "Integrator Class": "gjf" (default), "em"
         (Euler-Maruyama, overdamped) or "vv" (velocity-Verlet + Langevin force)."""
         self._chk(self.lib.tild_set_integrator_scheme(self.ctx, self.SCHEMES[scheme]))
+        self.scheme = scheme
 
     def set_stream(self, stream) -> None:
         handle = getattr(stream, "cuda_stream", stream)
@@ -311,6 +318,23 @@ class Tild:
         if f is not None and isinstance(f, np.ndarray):
             f = f.reshape(-1, 3)
         return f, en
+
+    def force_vjp(self, lam, out=None):
+        """(J^T lam by bead id, {"chi", "kappa", "a"}: d(lam . F)/dtheta) for
+        the ik force at the current positions; lam is a host array or a
+        CUDA tensor of n_beads x 3."""
+        n3 = 3 * self.n_beads
+        lptr, lcode, lwhere, _k1 = _buffer(lam, n3)
+        if out is None:
+            out = np.empty(n3, dtype=np.float64 if lcode == TILD_DTYPE_F64 else np.float32)
+        optr, ocode, owhere, _k2 = _buffer(out, n3)
+        if (ocode, owhere) != (lcode, lwhere):
+            raise ValueError("force_vjp: lam and out must share dtype and memory space")
+        th = (ctypes.c_double * 3)()
+        self._chk(self.lib.tild_force_vjp(self.ctx, lptr, optr, lcode, lwhere, th))
+        if isinstance(out, np.ndarray):
+            out = out.reshape(-1, 3)
+        return out, {"chi": th[0], "kappa": th[1], "a": th[2]}
 
     def energy_gradient(self, with_positions: bool = True, out=None, dtype=np.float64):
         """(dict of U, its terms and dU/dchi, dU/dkappa, dU/da; dU/dr or None)."""

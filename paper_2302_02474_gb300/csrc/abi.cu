@@ -263,6 +263,13 @@ tild_status tild_energy_gradient(tild_ctx* c, tild_energy_grad* g, void* dU_dr, 
     return from_engine(c, c->eng->energy_gradient(g, dU_dr, dtype, where));
 }
 
+tild_status tild_force_vjp(tild_ctx* c, const void* lam, void* out, int dtype, int where, double* dtheta) {
+    if (!c) return TILD_EINVAL;
+    if (!lam || !out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "force_vjp: bad pointer, dtype or where");
+    if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "force_vjp: positions not set");
+    return from_engine(c, c->eng->force_vjp(lam, out, dtype, where, dtheta));
+}
+
 tild_status tild_get_positions(tild_ctx* c, void* out, int dtype, int where) {
     if (!c) return TILD_EINVAL;
     if (!out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "get_positions: bad pointer, dtype or where");

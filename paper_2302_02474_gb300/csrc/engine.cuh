@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "bead_kernels.cuh"
+#include "vjp_kernels.cuh"
 #include "engine_api.h"
 #include "grid_kernels.cuh"
 
@@ -65,6 +66,7 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(cudaMalloc(&block_sums_, scan_blocks_ * sizeof(int)));
         n_z_blocks_ = (size_t)(n_ / CZ_) * (n_ / 2 + 1);
         n_partials_ = std::max(5 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
+        n_partials_ = std::max(n_partials_, 3 * (size_t)(n_ / vjp_cols(n_)) * (n_ / 2 + 1));
         TILD_CUDA(cudaMalloc(&partials_, n_partials_ * sizeof(double)));
         // twiddles W_n^m = exp(-2 pi i m / n) in FP64, rounded to T
         std::vector<V> tw(n_);
@@ -265,6 +267,77 @@ template <typename T> class Engine final : public EngineBase {
         g->dU_dchi = f * s[0] / rho0;
         g->dU_dkappa = f * s[1] / (2.0 * rho0);
         g->dU_da = -2.0 * cfg_->a * (cfg_->chi / rho0 * f * s[2] + cfg_->kappa / (2.0 * rho0) * f * s[3]);
+        return TILD_OK;
+    }
+
+    // J^T lam of the ik force at the current positions (see vjp_kernels.cuh);
+    // dtheta (optional): d(lam . F)/d(chi, kappa, a).
+    tild_status force_vjp(const void* lam, void* out, int dtype, int where, double* dtheta) override {
+        if (analytic()) {
+            err = "force_vjp: implemented for the ik force";
+            return TILD_EUNSUPPORTED;
+        }
+        if (!plane_fits_) {
+            err = "force_vjp: the grid must fit the single-plane xy passes (FP32 up to 128^3, FP64 up to 64^3)";
+            return TILD_EUNSUPPORTED;
+        }
+        const size_t N = cfg_->n_beads;
+        tild_status st;
+        const void* src = lam;
+        if ((st = stage_in(&src, lam, 3 * N, dtype, where))) return st;
+        if ((st = ensure_aux(6 * N * sizeof(T)))) return st;
+        T* lam_d = (T*)aux_;
+        T* out_d = lam_d + 3 * N;
+        if (dtype == TILD_DTYPE_F32)
+            convert_copy<float, T><<<blocks(3 * N), 256, 0, stream_>>>(3 * N, (const float*)src, lam_d);
+        else
+            convert_copy<double, T><<<blocks(3 * N), 256, 0, stream_>>>(3 * N, (const double*)src, lam_d);
+        TILD_CUDA(cudaGetLastError());
+        if ((st = enqueue_fields(false, nullptr, nullptr, kInvGrad))) return st;  // D w at r; Zxy = xy(rho)
+        TILD_CUDA(cudaMemsetAsync(H_, 0, 3 * M_ * sizeof(V), stream_));
+        const BeadParams<T> p = bead_params();
+        const BeadBuffers<T> bf = bead_buffers();
+        if ((st = dispatch_p([&](auto pp) -> tild_status {
+                 vjp_spread<decltype(pp)::value, T><<<blocks(N), 256, 0, stream_>>>(p, bf, lam_d, (T*)H_);
+                 return TILD_OK;
+             })))
+            return st;
+        const SpectralParams<T> sp = spectral_params();
+        const int el = c_el_on() ? 1 : 0;
+        if ((st = dispatch_n([&](auto nn) -> tild_status {
+                 constexpr int NN = decltype(nn)::value;
+                 if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
+                     constexpr int CV = vjp_cols(NN);
+                     xy_forward_cplx<T, NN><<<dim3(NN, 3), 512, plane_smem(), stream_>>>(H_, tw_);
+                     z_vjp<T, NN, CV><<<dim3(NN / CV, NN / 2 + 1), 256, vjp_smem(), stream_>>>(H_, Zxy_, tw_, sp, partials_, el);
+                 }
+                 return TILD_OK;
+             })))
+            return st;
+        TILD_CUDA(cudaGetLastError());
+        if ((st = enqueue_inverse(kInvPot))) return st;  // psi into the potential slot
+        const double dV = cfg_->L * cfg_->L * cfg_->L / (double)M_;
+        if ((st = dispatch_p([&](auto pp) -> tild_status {
+                 vjp_beads<decltype(pp)::value, T><<<blocks(N), 256, 0, stream_>>>(p, bf, grad_, lam_d, (T)(1.0 / dV), out_d);
+                 return TILD_OK;
+             })))
+            return st;
+        TILD_CUDA(cudaGetLastError());
+        const size_t nb = (size_t)(n_ / vjp_cols(n_)) * (n_ / 2 + 1);
+        std::vector<double> part(3 * nb);
+        TILD_CUDA(cudaMemcpyAsync(part.data(), partials_, part.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        if ((st = stage_out_vec(out_d, 3 * N, out, dtype, where))) return st;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        if ((st = check_err())) return st;
+        if (dtheta) {
+            double s[3] = {0, 0, 0};
+            for (size_t b = 0; b < nb; ++b)
+                for (int k = 0; k < 3; ++k) s[k] += part[3 * b + k];
+            const double rho0 = cfg_->n_beads / (cfg_->L * cfg_->L * cfg_->L);
+            dtheta[0] = s[0] / (rho0 * (double)M_);
+            dtheta[1] = s[1] / (rho0 * (double)M_);
+            dtheta[2] = -2.0 * cfg_->a * s[2];
+        }
         return TILD_OK;
     }
 
@@ -651,6 +724,8 @@ template <typename T> class Engine final : public EngineBase {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
                 TILD_CUDA(cudaFuncSetAttribute(xy_forward_plane<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
                 TILD_CUDA(cudaFuncSetAttribute(xy_inverse_plane<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+                TILD_CUDA(cudaFuncSetAttribute(xy_forward_cplx<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+                TILD_CUDA(cudaFuncSetAttribute(z_vjp<T, NN, vjp_cols(NN)>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vjp_smem()));
             }
         } else {
             TILD_CUDA(cudaFuncSetAttribute(x_forward_rows<T, NN, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem()));
@@ -747,6 +822,10 @@ template <typename T> class Engine final : public EngineBase {
 
     // z-pass column tile: 128 bytes of complex values, or the largest power of
     // two dividing n when that is smaller
+    // force-VJP z pass column tile: half the z pass's, at least 2
+    static constexpr int vjp_cols(int n) { return zpass_cols(n) / 2 < 2 ? 2 : zpass_cols(n) / 2; }
+    size_t vjp_smem() const { return ((size_t)n_ + 8 * (size_t)n_ * vjp_cols(n_)) * sizeof(V); }
+
     static constexpr int zpass_cols(int n) {
         int c = (int)(128 / sizeof(V));
         while (c > 1 && (n % c) != 0) c /= 2;

@@ -61,6 +61,7 @@ class EngineBase {
     virtual bool has_positions() const = 0;
     virtual bool has_velocities() const = 0;
     // Parameter changes: keep v^n while F^n changes (u = v - dt/2m F).
+    virtual tild_status force_vjp(const void* lam, void* out, int dtype, int where, double* dtheta) = 0;
     virtual tild_status save_velocities() = 0;
     virtual tild_status restore_velocities() = 0;
     virtual void params_changed() = 0;

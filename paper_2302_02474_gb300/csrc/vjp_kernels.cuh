@@ -1,0 +1,274 @@
+// Differentiable form: the vector-Jacobian product of the ik particle-mesh +
+// bond force (Eq. PMM with the gradient taken by i k differentiation; Eq.
+// bonds), J^T lam = d/dr of sum_i lam_i . F_i, and the derivatives of
+// sum_i lam_i . F_i with respect to chi, kappa and a.
+//
+// With W_i(g) = W(r_i - g), mu_K(g) = sum_{i in K} W_i(g) lam_i, C the
+// convolution with the smeared kernel (u_hat, plus the Coulomb term with
+// charges), D the i k~ derivative (anti-self-adjoint) and
+// psi_K = sum_K' eps_KK' C (D . mu_K'):
+//   (J^T lam)_j = sum_g grad W_j(g) [psi_{K_j}(g) / dV - (lam_j . D w_{K_j})(g)]
+//                 - (3/b^2) sum_{i ~ j} (lam_j - lam_i).
+// The pipeline: spread mu (three complex grids: component d of mu_A in the
+// real and of mu_B in the imaginary part), xy transforms in place, a z pass
+// that forms D . mu per species, psi and the parameter sums, the inverse
+// transforms of psi (the potential slot of the gradient buffer), and a
+// per-bead gather with the derivatives of the assignment weights.
+#pragma once
+
+#include "bead_kernels.cuh"
+#include "grid_kernels.cuh"
+
+namespace tild {
+
+// mu_d += W_i lam_{i,d}; lam by bead id ([N][3]); mu as T pairs [3][M].
+template <int P, typename T>
+__global__ void __launch_bounds__(256) vjp_spread(BeadParams<T> p, BeadBuffers<T> bf, const T* __restrict__ lam,
+                                                  T* __restrict__ mu) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n_beads) return;
+    const int tag = bf.id[i];
+    const int bid = slot_bead_id(tag), K = slot_species(tag);
+    const T l0 = lam[3 * (size_t)bid], l1 = lam[3 * (size_t)bid + 1], l2 = lam[3 * (size_t)bid + 2];
+    Stencil<P, T> st;
+    st.set(bf.px[i], bf.py[i], bf.pz[i], p.inv_dx);
+    const int n = p.n;
+    const size_t M = (size_t)n * n * n;
+#pragma unroll
+    for (int c = 0; c < P; ++c)
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            const T wyz = st.wy[b] * st.wz[c];
+            const size_t row = ((size_t)pwrap(st.jz + c, n) * n + pwrap(st.jy + b, n)) * n;
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                const size_t g = row + pwrap(st.jx + a, n);
+                const T w = st.wx[a] * wyz;
+                atomicAdd(mu + 2 * g + K, w * l0);
+                atomicAdd(mu + 2 * (M + g) + K, w * l1);
+                atomicAdd(mu + 2 * (2 * M + g) + K, w * l2);
+            }
+        }
+}
+
+// Forward DFT along x and y of plane blockIdx.x of field blockIdx.y of a
+// complex [3][M] array, in place, stored in mirror-paired column order.
+template <typename T, int N>
+__global__ void __launch_bounds__(512) xy_forward_cplx(cplx_t<T>* __restrict__ data, const cplx_t<T>* __restrict__ tw_g) {
+    using V = cplx_t<T>;
+    constexpr int PITCH = row_pitch(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* tw = reinterpret_cast<V*>(smem_raw);
+    V* plane = tw + N;
+    load_twiddles(tw, tw_g, N);
+    const size_t base = (size_t)blockIdx.y * N * N * N + (size_t)blockIdx.x * N * N;
+    batched_load<N * N, 512, V>([&](int i) { return data[base + i]; },
+                                [&](int i, V v) { plane[(i / N) * PITCH + i % N] = v; });
+    __syncthreads();
+    smem_fft_lines<N, -1, N, 512>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
+    smem_fft_lines<N, -1, N, 512>(plane, StridedLines<1>{}, PITCH, tw);  // along y
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) data[base + i] = plane[(i / N) * PITCH + kx_of_pos<N>(i % N)];
+}
+
+// z pass of the VJP. CTA (C column positions, rows ky and -ky) as in
+// z_spectral. Buffers [4R][N][C]: sets 0..2 = the xy-transformed mu_d rows,
+// set 3 = the xy-transformed density rows (Zxy). Writes i (psi~_A + i psi~_B)
+// transformed back along z into field 0 of H, and per block the sums
+//   0: sum_k Re[conj(s_A) u_hat rho~_B + conj(s_B) u_hat rho~_A]
+//   1: sum_k Re[(conj(s_A) + conj(s_B)) u_hat (rho~_A + rho~_B)]
+//   2: sum_k Re[sum_K conj(s_K) |k|^2 u_hat sum_K' (eps_KK'/M) rho~_K']
+// with s_K = (D . mu_K)~.
+template <typename T, int N, int C, int R>
+__device__ __forceinline__ void z_vjp_tile(cplx_t<T>* buf, const cplx_t<T>* tw, const T* e1, const T* e2,
+                                           const SpectralParams<T>& sp, bool el, int p0, const int (&ky)[2],
+                                           double (&acc)[3]) {
+    using V = cplx_t<T>;
+    constexpr int TS = N * C;
+    smem_fft_lines<N, -1, 4 * R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+    constexpr int rB = R - 1;
+    const int c = threadIdx.x % C;
+    const int cB = mirror_pos(p0 + c) - p0;
+    const int kxA = kx_of_pos<N>(p0 + c), kxB = kx_of_pos<N>(p0 + cB);
+    const T exyA = e1[kxA] * e1[ky[0]], exyB = e1[kxB] * e1[ky[rB]];
+    const T exy2A = el ? e2[kxA] * e2[ky[0]] : T(0), exy2B = el ? e2[kxB] * e2[ky[rB]] : T(0);
+    const T tp = sp.two_pi_over_L;
+    const T qxA = raw_k<T, N>(kxA, tp), qyA = raw_k<T, N>(ky[0], tp);
+    const T qxB = raw_k<T, N>(kxB, tp), qyB = raw_k<T, N>(ky[rB], tp);
+    const T gxA = grad_k<T, N>(kxA, tp), gyA = grad_k<T, N>(ky[0], tp);
+    const T gxB = grad_k<T, N>(kxB, tp), gyB = grad_k<T, N>(ky[rB], tp);
+    for (int kz = threadIdx.x / C; kz < N; kz += 256 / C) {
+        const int kzB = kz == 0 ? 0 : N - kz;
+        if (R == 1 && kzB * C + cB < kz * C + c) continue;  // the mirror element owns this pair
+        const bool same = (R == 1) && (kzB == kz) && (cB == c);
+        V zA[4], zB[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            zA[d] = buf[(d * R) * TS + kz * C + c];
+            zB[d] = buf[(d * R + rB) * TS + kzB * C + cB];
+        }
+        V out[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (s == 1 && same) break;
+            const int kzi = s == 0 ? kz : kzB;
+            const T kd[3] = {s == 0 ? gxA : gxB, s == 0 ? gyA : gyB, grad_k<T, N>(kzi, tp)};
+            // s_K = sum_d i k~_d mu~_{K,d}, mu~_A = (Z + conj Zm)/2, mu~_B = -i (Z - conj Zm)/2
+            V sA = {T(0), T(0)}, sB = {T(0), T(0)};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const V Z = s == 0 ? zA[d] : zB[d];
+                const V Zm = s == 0 ? zB[d] : zA[d];
+                const V mA = {T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y)};
+                const V mB = {T(0.5) * (Z.y + Zm.y), -T(0.5) * (Z.x - Zm.x)};
+                sA.x -= kd[d] * mA.y;
+                sA.y += kd[d] * mA.x;
+                sB.x -= kd[d] * mB.y;
+                sB.y += kd[d] * mB.x;
+            }
+            const V Z = s == 0 ? zA[3] : zB[3];
+            const V Zm = s == 0 ? zB[3] : zA[3];
+            const V rA = {T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y)};
+            const V rBv = {T(0.5) * (Z.y + Zm.y), -T(0.5) * (Z.x - Zm.x)};
+            const T uh = (s == 0 ? exyA : exyB) * e1[kzi];
+            V pA = {uh * (sp.eAA * sA.x + sp.eAB * sB.x), uh * (sp.eAA * sA.y + sp.eAB * sB.y)};
+            V pB = {uh * (sp.eAB * sA.x + sp.eBB * sB.x), uh * (sp.eAB * sA.y + sp.eBB * sB.y)};
+            const T qz = raw_k<T, N>(kzi, tp);
+            const T k2 = (s == 0 ? qxA * qxA + qyA * qyA : qxB * qxB + qyB * qyB) + qz * qz;
+            if (el) {
+                const T g = k2 > T(0) ? (s == 0 ? exy2A : exy2B) * e2[kzi] / k2 : T(0);
+                const T cq = sp.el_scale * g;
+                const V sq = {sp.qA * sA.x + sp.qB * sB.x, sp.qA * sA.y + sp.qB * sB.y};
+                pA.x += cq * sp.qA * sq.x;
+                pA.y += cq * sp.qA * sq.y;
+                pB.x += cq * sp.qB * sq.x;
+                pB.y += cq * sp.qB * sq.y;
+            }
+            out[s] = {-(pA.y + pB.x), pA.x - pB.y};  // i (psi~_A + i psi~_B)
+            const double sar = sA.x, sai = sA.y, sbr = sB.x, sbi = sB.y;
+            const double ar = rA.x, ai = rA.y, br = rBv.x, bi = rBv.y, u = uh;
+            acc[0] += u * ((sar * br + sai * bi) + (sbr * ar + sbi * ai));
+            acc[1] += u * ((sar + sbr) * (ar + br) + (sai + sbi) * (ai + bi));
+            const double wAr = (double)sp.eAA * ar + (double)sp.eAB * br, wAi = (double)sp.eAA * ai + (double)sp.eAB * bi;
+            const double wBr = (double)sp.eAB * ar + (double)sp.eBB * br, wBi = (double)sp.eAB * ai + (double)sp.eBB * bi;
+            acc[2] += u * (double)k2 * ((sar * wAr + sai * wAi) + (sbr * wBr + sbi * wBi));
+        }
+        buf[kz * C + c] = out[0];
+        if (!same) buf[rB * TS + kzB * C + cB] = out[1];
+    }
+    __syncthreads();
+    smem_fft_lines<N, +1, R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+}
+
+template <typename T, int N, int C>
+__global__ void __launch_bounds__(256) z_vjp(cplx_t<T>* __restrict__ H, const cplx_t<T>* __restrict__ Zxy,
+                                             const cplx_t<T>* __restrict__ tw_g, SpectralParams<T> sp,
+                                             double* __restrict__ partials, int el) {
+    using V = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* tw = reinterpret_cast<V*>(smem_raw);
+    V* buf = tw + N;
+    constexpr int TS = N * C;
+    __shared__ double red[3][8];
+    __shared__ T e1[N];
+    __shared__ T e2[N];
+    load_twiddles(tw, tw_g, N);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        e1[i] = sp.kernel1d[i];
+        if (el) e2[i] = sp.kernel1d_el[i];
+    }
+    const int p0 = blockIdx.x * C;
+    const int ky[2] = {(int)blockIdx.y, blockIdx.y == 0 ? 0 : N - (int)blockIdx.y};
+    const int R = (ky[0] == ky[1]) ? 1 : 2;
+    const size_t NN = (size_t)N * N, M = NN * N;
+    for (int i = threadIdx.x; i < 4 * R * TS; i += blockDim.x) {
+        const int set = i / (R * TS), rem = i % (R * TS);
+        const int r = rem / TS, zc = rem % TS;
+        const int z = zc / C, cc = zc % C;
+        const size_t off = z * NN + (size_t)ky[r] * N + p0 + cc;
+        buf[i] = set < 3 ? H[set * M + off] : Zxy[off];
+    }
+    __syncthreads();
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (R == 1)
+        z_vjp_tile<T, N, C, 1>(buf, tw, e1, e2, sp, el != 0, p0, ky, acc);
+    else
+        z_vjp_tile<T, N, C, 2>(buf, tw, e1, e2, sp, el != 0, p0, ky, acc);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double sum = 0;
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) sum += red[threadIdx.x][w];
+        partials[3 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x) + threadIdx.x] = sum;
+    }
+    for (int i = threadIdx.x; i < R * TS; i += blockDim.x) {
+        const int r = i / TS, zc = i % TS;
+        const int z = zc / C, cc = zc % C;
+        H[z * NN + (size_t)ky[r] * N + p0 + cc] = buf[i];
+    }
+}
+
+// Per bead: sum_g grad W_j(g) [psi_{K_j}(g)/dV - lam_j . D w_{K_j}(g)] and the
+// bond term. fields = the gradient buffer: [0..2] (d_x, d_y, d_z)(w_A, w_B),
+// [3] i (psi_A + i psi_B). lam and out by bead id ([N][3]).
+template <int P, typename T>
+__global__ void __launch_bounds__(256) vjp_beads(BeadParams<T> p, BeadBuffers<T> bf, const cplx_t<T>* __restrict__ fields,
+                                                 const T* __restrict__ lam, T inv_dV, T* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n_beads) return;
+    const T x = bf.px[i], y = bf.py[i], z = bf.pz[i];
+    const int tag = bf.id[i];
+    const int bid = slot_bead_id(tag), K = slot_species(tag);
+    const T l0 = lam[3 * (size_t)bid], l1 = lam[3 * (size_t)bid + 1], l2 = lam[3 * (size_t)bid + 2];
+    Stencil<P, T> st;
+    st.set(x, y, z, p.inv_dx);
+    T dwx[P], dwy[P], dwz[P];
+    dh_weight_derivs<P>(x * p.inv_dx, dwx);
+    dh_weight_derivs<P>(y * p.inv_dx, dwy);
+    dh_weight_derivs<P>(z * p.inv_dx, dwz);
+    const int n = p.n;
+    const size_t M = (size_t)n * n * n;
+    T ox = 0, oy = 0, oz = 0;
+#pragma unroll
+    for (int c = 0; c < P; ++c)
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            const size_t row = ((size_t)pwrap(st.jz + c, n) * n + pwrap(st.jy + b, n)) * n;
+            const T wyz = st.wy[b] * st.wz[c], dyz = dwy[b] * st.wz[c], ydz = st.wy[b] * dwz[c];
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                const size_t g = row + pwrap(st.jx + a, n);
+                const cplx_t<T> f0 = fields[g], f1 = fields[M + g], f2 = fields[2 * M + g], f3 = fields[3 * M + g];
+                const T ldw = l0 * (K ? f0.y : f0.x) + l1 * (K ? f1.y : f1.x) + l2 * (K ? f2.y : f2.x);
+                const T psi = K ? -f3.x : f3.y;
+                const T val = psi * inv_dV - ldw;
+                ox += dwx[a] * wyz * val;
+                oy += st.wx[a] * dyz * val;
+                oz += st.wx[a] * ydz * val;
+            }
+        }
+    ox *= p.inv_dx;
+    oy *= p.inv_dx;
+    oz *= p.inv_dx;
+    const int2 nb = bf.nbr[i];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int s = k == 0 ? nb.x : nb.y;
+        if (s >= 0) {
+            const int nid = slot_bead_id(bf.id[s]);
+            ox -= p.k_bond * (l0 - lam[3 * (size_t)nid]);
+            oy -= p.k_bond * (l1 - lam[3 * (size_t)nid + 1]);
+            oz -= p.k_bond * (l2 - lam[3 * (size_t)nid + 2]);
+        }
+    }
+    out[3 * (size_t)bid] = ox;
+    out[3 * (size_t)bid + 1] = oy;
+    out[3 * (size_t)bid + 2] = oz;
+}
+
+}  // namespace tild

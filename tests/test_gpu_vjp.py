@@ -1,0 +1,85 @@
+"""Differentiable form on the GPU: the force vector-Jacobian product
+(tild_force_vjp) and derivatives through GJF trajectories with checkpoints,
+against the oracle's force_vjp and gjf_trajectory_vjp (themselves pinned by
+finite differences)."""
+import numpy as np
+import pytest
+
+from oracle import tild_oracle as O
+from paper_2302_02474_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_02474_gb300 import _build, binding
+
+    _build.build()
+    return binding
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def _setup(B, spec, charges=None):
+    pos = I.initial_positions(spec)
+    if spec.precision == "fp32":
+        pos = pos.astype(np.float32).astype(np.float64)
+    t = B.Tild.from_spec(spec, sort_every=3)
+    m = O.model_from_spec(spec, I.species_of_beads(spec.moltypes), I.bond_pairs(spec.moltypes))
+    if charges is not None:
+        t.set_electrostatics(charges[0], charges[1], 1.5, 0.6)
+        m.charges, m.bjerrum, m.charge_smear = np.array(charges), 1.5, 0.6
+    t.set_positions(pos)
+    return t, m, pos
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("order,charges", [(1, None), (2, (0.7, -1.2)), (4, None)])
+def test_force_vjp_matches_oracle(B, prec, order, charges):
+    spec = I.small_system(n_chains=70, N=10, n_a=4, L=8.0, n=16, pmeorder=order, precision=prec, chi=1.1, kappa=6.0)
+    t, m, pos = _setup(B, spec, charges)
+    lam = np.random.default_rng(3).normal(size=pos.shape)
+    if prec == "fp32":
+        lam = lam.astype(np.float32)
+    got, th = t.force_vjp(lam)
+    ref = O.force_vjp(m, pos, lam.astype(np.float64))
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    assert _rel(got, ref["r"]) < tol
+    for k in ("chi", "kappa", "a"):
+        assert th[k] == pytest.approx(ref[k], rel=tol, abs=tol * 1e-3 * abs(ref["a"])), k
+
+
+def test_trajectory_vjp_matches_oracle(B):
+    from paper_2302_02474_gb300.trajectory import gjf_trajectory_vjp
+
+    spec = I.small_system(n_chains=40, N=10, n_a=4, L=7.0, n=16, pmeorder=1, precision="fp64", chi=1.0, kappa=6.0,
+                          dt=0.01)
+    t, m, pos = _setup(B, spec)
+    t.init_velocities()
+    vel0 = O.initial_state(m, pos).vel
+    K = 7
+    w = np.random.default_rng(5).normal(size=pos.shape)
+    g = gjf_trajectory_vjp(t, K, w, checkpoint_every=3)
+    ref = O.gjf_trajectory_vjp(m, pos, vel0, K, w)
+    assert t.step_count() == K
+    st = O.run(m, O.initial_state(m, pos), K)
+    assert np.abs(O.minimum_image(t.positions() - st.pos, m.L)).max() < 1e-10
+    assert _rel(g["r0"], ref["r0"]) < 1e-9
+    assert _rel(g["v0"], ref["v0"]) < 1e-9
+    for k in ("chi", "kappa", "a"):
+        assert g[k] == pytest.approx(ref[k], rel=1e-9), k
+
+
+def test_force_vjp_needs_the_ik_force(B):
+    spec = I.small_system(n_chains=20, N=10, n_a=4, L=6.0, n=16, precision="fp64")
+    t, m, pos = _setup(B, spec)
+    t.set_force_method("analytic")
+    with pytest.raises(B.TildError, match="EUNSUPPORTED"):
+        t.force_vjp(np.zeros(pos.shape))
