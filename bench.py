@@ -341,8 +341,8 @@ def run_diff(args):
                 "config": {"workload": "diff200k", "beads": spec.n_beads, "grid": spec.n, "checkpoint_every": 20},
                 "force_vjp_ms": a.elapsed_time(b) / 20,
                 "gradients": {k: g[k] for k in ("chi", "kappa", "a")},
-                "note": "wall time of forward + recomputation + reverse sweep through the public API; the reverse "
-                        "sweep restores each state from a host checkpoint blob"}
+                "note": "wall time of forward + recomputation + reverse sweep through the public API, with "
+                        "device-memory checkpoints; one force vector-Jacobian product per reverse step"}
     print(json.dumps(out_json))
     t.close()
 

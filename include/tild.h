@@ -300,14 +300,15 @@ tild_status tild_get_field_gradient(tild_ctx* ctx, void* out, int dtype, int whe
 /* Number of steps taken since velocities were set. */
 tild_status tild_get_step(tild_ctx* ctx, int64_t* step);
 
-/* Checkpoint: tild_state_bytes gives the size of the opaque host blob that
+/* Checkpoint: tild_state_bytes gives the size of the opaque blob that
  * tild_get_state writes (positions, carried velocities, step counter, seed,
- * in the context's precision). tild_set_state restores it into a context
- * with the same chains and precision; continuing from a restored state
- * reproduces the original trajectory bit for bit. */
+ * in the context's precision) to host (where = TILD_HOST) or device
+ * (TILD_DEVICE, 8-byte aligned) memory owned by the caller. tild_set_state
+ * restores it into a context with the same chains and precision; continuing
+ * from a restored state reproduces the original trajectory bit for bit. */
 tild_status tild_state_bytes(tild_ctx* ctx, size_t* bytes);
-tild_status tild_get_state(tild_ctx* ctx, void* host_blob, size_t bytes);
-tild_status tild_set_state(tild_ctx* ctx, const void* host_blob, size_t bytes);
+tild_status tild_get_state(tild_ctx* ctx, void* blob, size_t bytes, int where);
+tild_status tild_set_state(tild_ctx* ctx, const void* blob, size_t bytes, int where);
 
 /* Time each kernel of the step: runs n_steps steps with CUDA events around
  * every kernel launch (no graph) and writes the mean device time in

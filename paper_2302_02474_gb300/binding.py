@@ -80,8 +80,8 @@ _SIGS = {
     "tild_get_field_gradient": [_P, _P, _I, _I],
     "tild_get_step": [_P, ctypes.POINTER(_I64)],
     "tild_state_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
-    "tild_get_state": [_P, _P, ctypes.c_size_t],
-    "tild_set_state": [_P, _P, ctypes.c_size_t],
+    "tild_get_state": [_P, _P, ctypes.c_size_t, _I],
+    "tild_set_state": [_P, _P, ctypes.c_size_t, _I],
     "tild_profile_steps": [_P, _I, ctypes.POINTER(ctypes.c_double)],
     "tild_launches_per_steps": [_P, _I64, ctypes.POINTER(_I64)],
     "tild_spread_density_noalloc": [_P, _P, _I64, ctypes.c_double, _I, _I, _P, _P],
@@ -354,16 +354,31 @@ class Tild:
         self._chk(self.lib.tild_get_step(self.ctx, ctypes.byref(s)))
         return s.value
 
-    def get_state(self) -> bytes:
+    def state_bytes(self) -> int:
         nb = ctypes.c_size_t()
         self._chk(self.lib.tild_state_bytes(self.ctx, ctypes.byref(nb)))
-        buf = ctypes.create_string_buffer(nb.value)
-        self._chk(self.lib.tild_get_state(self.ctx, buf, nb))
+        return nb.value
+
+    def get_state(self, out=None):
+        """Checkpoint blob: bytes (host), or written into `out`, a CUDA uint8
+        tensor of state_bytes() elements (device)."""
+        nb = self.state_bytes()
+        if out is not None:
+            if not out.is_cuda or out.numel() < nb or out.element_size() != 1:
+                raise ValueError("out must be a CUDA uint8 tensor of state_bytes() elements")
+            self._chk(self.lib.tild_get_state(self.ctx, ctypes.c_void_p(out.data_ptr()), nb, TILD_DEVICE))
+            return out
+        buf = ctypes.create_string_buffer(nb)
+        self._chk(self.lib.tild_get_state(self.ctx, buf, nb, TILD_HOST))
         return buf.raw
 
-    def set_state(self, blob: bytes) -> None:
-        buf = ctypes.create_string_buffer(blob, len(blob))
-        self._chk(self.lib.tild_set_state(self.ctx, buf, len(blob)))
+    def set_state(self, blob) -> None:
+        """Restore a blob from get_state (bytes, or a CUDA uint8 tensor)."""
+        if isinstance(blob, (bytes, bytearray)):
+            buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+            self._chk(self.lib.tild_set_state(self.ctx, buf, len(blob), TILD_HOST))
+        else:
+            self._chk(self.lib.tild_set_state(self.ctx, ctypes.c_void_p(blob.data_ptr()), blob.numel(), TILD_DEVICE))
 
     def profile_steps(self, n: int):
         ms = (ctypes.c_double * 5)()

@@ -318,20 +318,22 @@ tild_status tild_state_bytes(tild_ctx* c, size_t* bytes) {
     return TILD_OK;
 }
 
-tild_status tild_get_state(tild_ctx* c, void* blob, size_t bytes) {
+tild_status tild_get_state(tild_ctx* c, void* blob, size_t bytes, int where) {
     if (!c) return TILD_EINVAL;
     if (!blob) return fail(c, TILD_EINVAL, "get_state: NULL blob");
     if (!c->eng->has_velocities()) return fail(c, TILD_ESTATE, "get_state: velocities not set");
     if (bytes < c->eng->state_bytes()) return fail(c, TILD_EINVAL, "get_state: blob too small");
-    return from_engine(c, c->eng->get_state(blob));
+    if (where != TILD_HOST && where != TILD_DEVICE) return fail(c, TILD_EINVAL, "get_state: bad where");
+    return from_engine(c, c->eng->get_state(blob, where));
 }
 
-tild_status tild_set_state(tild_ctx* c, const void* blob, size_t bytes) {
+tild_status tild_set_state(tild_ctx* c, const void* blob, size_t bytes, int where) {
     if (!c) return TILD_EINVAL;
     if (!blob) return fail(c, TILD_EINVAL, "set_state: NULL blob");
     if (!c->have_chains) return fail(c, TILD_ESTATE, "set_state: chains not set");
     if (bytes < c->eng->state_bytes()) return fail(c, TILD_EINVAL, "set_state: blob too small");
-    return from_engine(c, c->eng->set_state(blob));
+    if (where != TILD_HOST && where != TILD_DEVICE) return fail(c, TILD_EINVAL, "set_state: bad where");
+    return from_engine(c, c->eng->set_state(blob, where));
 }
 
 tild_status tild_profile_steps(tild_ctx* c, int n_steps, double* ms) {

@@ -399,37 +399,54 @@ template <typename T> class Engine final : public EngineBase {
     // blob: magic, n_beads, sizeof(T), step, seed | pos[N][3] | u[N][3] (by id, T)
     size_t state_bytes() const override { return 5 * sizeof(uint64_t) + 6 * (size_t)cfg_->n_beads * sizeof(T); }
 
-    tild_status get_state(void* blob) override {
+    // blob: 5 uint64 (magic, beads, sizeof(T), step, seed), then positions
+    // and carried velocities by bead id ([2][N][3] T); in host or device memory
+    tild_status get_state(void* blob, int where) override {
         const size_t N = cfg_->n_beads;
-        uint64_t* h = (uint64_t*)blob;
-        h[0] = kStateMagic;
-        h[1] = N;
-        h[2] = sizeof(T);
-        h[3] = (uint64_t)host_step_;
-        h[4] = cfg_->seed;
+        uint64_t h[5] = {kStateMagic, N, sizeof(T), (uint64_t)host_step_, cfg_->seed};
         tild_status st;
-        if ((st = ensure_aux(6 * N * sizeof(T)))) return st;
-        T* d = (T*)aux_;
+        T* d;
+        if (where == TILD_DEVICE) {
+            TILD_CUDA(cudaMemcpyAsync(blob, h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+            d = (T*)((char*)blob + sizeof(h));
+        } else {
+            std::memcpy(blob, h, sizeof(h));
+            if ((st = ensure_aux(6 * N * sizeof(T)))) return st;
+            d = (T*)aux_;
+        }
         store_by_id<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, pos_[cur_pos_], id_[cur_id_], d);
         store_by_id<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, u_[cur_u_], id_[cur_id_], d + 3 * N);
         TILD_CUDA(cudaGetLastError());
-        TILD_CUDA(cudaMemcpyAsync(h + 5, d, 6 * N * sizeof(T), cudaMemcpyDeviceToHost, stream_));
+        if (where != TILD_DEVICE)
+            TILD_CUDA(cudaMemcpyAsync((char*)blob + sizeof(h), d, 6 * N * sizeof(T), cudaMemcpyDeviceToHost, stream_));
         TILD_CUDA(cudaStreamSynchronize(stream_));
         return TILD_OK;
     }
 
-    tild_status set_state(const void* blob) override {
+    tild_status set_state(const void* blob, int where) override {
         const size_t N = cfg_->n_beads;
-        const uint64_t* h = (const uint64_t*)blob;
+        uint64_t h[5];
+        if (where == TILD_DEVICE) {
+            TILD_CUDA(cudaMemcpyAsync(h, blob, sizeof(h), cudaMemcpyDeviceToHost, stream_));
+            TILD_CUDA(cudaStreamSynchronize(stream_));
+        } else {
+            std::memcpy(h, blob, sizeof(h));
+        }
         if (h[0] != kStateMagic || h[1] != N || h[2] != sizeof(T) || h[4] != cfg_->seed) {
             err = "state blob does not match this context (beads, precision or seed)";
             return TILD_EINVAL;
         }
         invalidate_graph();
         tild_status st;
-        if ((st = ensure_aux(6 * N * sizeof(T)))) return st;
-        T* d = (T*)aux_;
-        TILD_CUDA(cudaMemcpyAsync(d, h + 5, 6 * N * sizeof(T), cudaMemcpyHostToDevice, stream_));
+        const T* d;
+        if (where == TILD_DEVICE) {
+            d = (const T*)((const char*)blob + sizeof(h));
+        } else {
+            if ((st = ensure_aux(6 * N * sizeof(T)))) return st;
+            TILD_CUDA(cudaMemcpyAsync(aux_, (const char*)blob + sizeof(h), 6 * N * sizeof(T), cudaMemcpyHostToDevice,
+                                      stream_));
+            d = (const T*)aux_;
+        }
         cur_pos_ = cur_u_ = cur_id_ = 0;
         load_positions<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, d, (T)cfg_->L, (T)(1.0 / cfg_->L), pos_[0], id_[0], err_ptr());
         load_by_id<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, d + 3 * N, id_[0], u_[0]);

@@ -54,8 +54,8 @@ class EngineBase {
     virtual tild_status get_field_gradient(void* out, int dtype, int where) = 0;
     virtual int64_t host_step() const = 0;
     virtual size_t state_bytes() const = 0;
-    virtual tild_status get_state(void* blob) = 0;
-    virtual tild_status set_state(const void* blob) = 0;
+    virtual tild_status get_state(void* blob, int where) = 0;
+    virtual tild_status set_state(const void* blob, int where) = 0;
     virtual tild_status profile(int n, double* ms) = 0;
     virtual int64_t launches(int64_t n) const = 0;
     virtual bool has_positions() const = 0;

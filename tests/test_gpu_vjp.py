@@ -83,3 +83,21 @@ def test_force_vjp_needs_the_ik_force(B):
     t.set_force_method("analytic")
     with pytest.raises(B.TildError, match="EUNSUPPORTED"):
         t.force_vjp(np.zeros(pos.shape))
+
+
+def test_device_checkpoints_match_host_blobs(B):
+    import torch
+
+    spec = I.small_system(n_chains=30, N=10, n_a=4, L=6.0, n=16, precision="fp32")
+    t, m, pos = _setup(B, spec)
+    t.init_velocities()
+    t.step(5)
+    host = t.get_state()
+    dev = t.get_state(out=torch.empty(t.state_bytes(), dtype=torch.uint8, device="cuda"))
+    assert dev.cpu().numpy().tobytes() == host
+    t.step(4)
+    r9 = t.positions()
+    t.set_state(dev)
+    assert t.step_count() == 5
+    t.step(4)
+    assert np.array_equal(t.positions(), r9)
