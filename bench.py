@@ -311,11 +311,19 @@ def run_diff(args):
     torch.cuda.set_device(0)
     spec = I.config("diblock_200k_64")
     t = B.Tild.from_spec(spec, sort_every=args.sort_every)
+    stream = torch.cuda.Stream()
+    t.set_stream(stream)
     t.set_positions(I.initial_positions(spec))
     t.init_velocities()
     t.step(args.warmup)
     t.synchronize()
     K = 200
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t.step(K)
+    e1.record(stream)
+    e1.synchronize()
+    plain_ms = e0.elapsed_time(e1) / K
     w = np.random.default_rng(1).normal(size=(spec.n_beads, 3))
     gjf_trajectory_vjp(t, 20, w, checkpoint_every=20)  # warm-up of the reverse path
     torch.cuda.synchronize()
@@ -329,10 +337,10 @@ def run_diff(args):
     for _ in range(3):
         t.force_vjp(lam, out=out)
     torch.cuda.synchronize()
-    a.record()
+    a.record(stream)
     for _ in range(20):
         t.force_vjp(lam, out=out)
-    b.record()
+    b.record(stream)
     b.synchronize()
     out_json = {"metric": "GJF trajectory-gradient windows/s (200 steps, checkpoints every 20; 200k beads, 64^3)",
                 "value": 1.0 / secs, "unit": "windows/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
@@ -340,6 +348,8 @@ def run_diff(args):
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "diff200k", "beads": spec.n_beads, "grid": spec.n, "checkpoint_every": 20},
                 "force_vjp_ms": a.elapsed_time(b) / 20,
+                "plain_step_ms": plain_ms,
+                "ratio_to_plain_step": (1000.0 * secs / K) / plain_ms,
                 "gradients": {k: g[k] for k in ("chi", "kappa", "a")},
                 "note": "wall time of forward + recomputation + reverse sweep through the public API, with "
                         "device-memory checkpoints; one force vector-Jacobian product per reverse step"}
@@ -358,6 +368,7 @@ def main():
     ap.add_argument("--reference-budget", type=float, default=150.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the step variants")
+    ap.add_argument("--no-autotune", action="store_true", help="keep --sort-every instead of autotuning it")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "diff200k"],
                     help="batch256: 256 uneven replicas stepped with tild_batch_*; diff200k: derivatives through a "
                          "200-step GJF window (extra measurements)")
@@ -402,6 +413,12 @@ def main():
     t.init_velocities()
     t.step(args.warmup)
     t.synchronize()
+    autotune = None
+    if args.mode != "run" and not args.no_autotune:
+        # the re-binning period (results do not depend on it) picked by the autotuner
+        k, ms_k = t.autotune(200)
+        autotune = {"sort_every": k, "ms_per_step": {str(p_): v for p_, v in ms_k.items()}}
+        args.sort_every = k
     if args.mode == "run":
         t.step(args.steps)
         t.synchronize()
@@ -519,6 +536,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "variants": variants,
+            "autotune": autotune,
         }
         print(json.dumps(out))
     t.close()

@@ -321,6 +321,16 @@ tild_status tild_profile_steps(tild_ctx* ctx, int n_steps, double* ms);
 /* Number of kernel launches one tild_step(ctx, n) issues for this context. */
 tild_status tild_launches_per_steps(tild_ctx* ctx, int64_t n_steps, int64_t* launches);
 
+/* Autotuner: times whole re-binning cycles for re-binning periods 5, 10, 20
+ * and 40 (each over about trial_steps steps after one untimed cycle, from
+ * the same saved state) and keeps the fastest. Trajectories are
+ * bit-identical for every period, so only speed changes; the context's state
+ * is restored afterwards. sort_every (may be NULL) receives the chosen
+ * period, ms_per_step (may be NULL) four timings in candidate order. Needs
+ * positions and velocities; allocates one state-sized device buffer for the
+ * duration of the call. */
+tild_status tild_autotune(tild_ctx* ctx, int64_t trial_steps, int* sort_every, double* ms_per_step);
+
 /*
  * Batched form: step several independent systems ("replicas": contexts with
  * their own chains, box, grid, chi, kappa, a and seed; same precision and

@@ -65,6 +65,7 @@ _SIGS = {
     "tild_set_force_method": [_P, ctypes.c_int],
     "tild_set_electrostatics": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
     "tild_force_vjp": [_P, _P, _P, _I, _I, ctypes.POINTER(ctypes.c_double)],
+    "tild_autotune": [_P, _I64, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
     "tild_set_stream": [_P, _P],
     "tild_set_positions": [_P, _P, _I, _I],
     "tild_init_velocities": [_P],
@@ -379,6 +380,16 @@ class Tild:
             self._chk(self.lib.tild_set_state(self.ctx, buf, len(blob), TILD_HOST))
         else:
             self._chk(self.lib.tild_set_state(self.ctx, ctypes.c_void_p(blob.data_ptr()), blob.numel(), TILD_DEVICE))
+
+    AUTOTUNE_PERIODS = (5, 10, 20, 40)
+
+    def autotune(self, trial_steps: int = 160):
+        """Pick the fastest re-binning period (results do not depend on it);
+        returns (period, {period: ms per step})."""
+        k = ctypes.c_int()
+        ms = (ctypes.c_double * 4)()
+        self._chk(self.lib.tild_autotune(self.ctx, int(trial_steps), ctypes.byref(k), ms))
+        return k.value, dict(zip(self.AUTOTUNE_PERIODS, list(ms)))
 
     def profile_steps(self, n: int):
         ms = (ctypes.c_double * 5)()

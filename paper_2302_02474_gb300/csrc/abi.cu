@@ -343,6 +343,51 @@ tild_status tild_profile_steps(tild_ctx* c, int n_steps, double* ms) {
     return from_engine(c, c->eng->profile(n_steps, ms));
 }
 
+tild_status tild_autotune(tild_ctx* c, int64_t trial_steps, int* sort_every, double* ms_per_step) {
+    if (!c) return TILD_EINVAL;
+    if (trial_steps < 1) return fail(c, TILD_EINVAL, "autotune: trial_steps must be >= 1");
+    if (!c->eng->has_velocities()) return fail(c, TILD_ESTATE, "autotune: positions and velocities must be set");
+    static const int kCandidates[4] = {5, 10, 20, 40};
+    const size_t nb = c->eng->state_bytes();
+    void* saved = nullptr;
+    if (cudaMalloc(&saved, nb) != cudaSuccess) return fail(c, TILD_ENOMEM, "autotune: cannot allocate the checkpoint");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    tild_status st = c->eng->get_state(saved, TILD_DEVICE);
+    if (!st && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = TILD_EDEVICE;
+    const int original = c->cfg.sort_every;
+    int best = original;
+    double best_ms = 1e300;
+    for (int k = 0; k < 4 && !st; ++k) {
+        const int K = kCandidates[k];
+        c->cfg.sort_every = K;
+        c->eng->params_changed();
+        // whole re-binning cycles, after one untimed cycle
+        const int64_t n = ((trial_steps + 2 * K - 1) / (2 * K)) * (2 * K);
+        if ((st = c->eng->set_state(saved, TILD_DEVICE)) || (st = c->eng->step(2 * K))) break;
+        cudaStream_t s = c->eng->stream();
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = TILD_EDEVICE; break; }
+        if ((st = c->eng->step(n))) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { st = TILD_EDEVICE; break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_per_step) ms_per_step[k] = ms / (double)n;
+        if (ms / (double)n < best_ms) {
+            best_ms = ms / (double)n;
+            best = K;
+        }
+    }
+    // keep the fastest period and the original state (results do not depend on the period)
+    c->cfg.sort_every = st ? original : best;
+    c->eng->params_changed();
+    if (!st) st = c->eng->set_state(saved, TILD_DEVICE);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(saved);
+    if (st) return from_engine(c, st);
+    if (sort_every) *sort_every = best;
+    return TILD_OK;
+}
+
 tild_status tild_launches_per_steps(tild_ctx* c, int64_t n_steps, int64_t* launches) {
     if (!c || !launches || n_steps < 0) return fail(c, TILD_EINVAL, "launches_per_steps: bad argument");
     if (!c->have_chains) return fail(c, TILD_ESTATE, "launches_per_steps: chains not set");

@@ -362,3 +362,22 @@ def test_diblock_1p6M_128_sampled_forces(B):
 def test_blend_6p4M_256_sampled_forces(B):
     """6.4M-bead ternary blend on 256^3 in FP32 (split xy passes)."""
     _sampled_force_check(B, I.config("blend_6p4M_256"), n_sample=3000)
+
+
+def test_autotune_keeps_the_trajectory(B):
+    """The autotuner only changes the re-binning period: state, step count
+    and the following trajectory are bit-identical to an untuned run."""
+    spec = I.small_system(n_chains=150, N=10, n_a=4, L=10.0, n=32, precision="fp32")
+    t, m, pos = _setup(B, spec, sort_every=20)
+    t.init_velocities()
+    t.step(7)
+    r7, v7 = t.positions(), t.velocities()
+    k, ms = t.autotune(80)
+    assert k in B.Tild.AUTOTUNE_PERIODS and all(v > 0 for v in ms.values())
+    assert t.step_count() == 7
+    assert np.array_equal(t.positions(), r7) and np.array_equal(t.velocities(), v7)
+    t.step(30)
+    t2, _, _ = _setup(B, spec, sort_every=20)
+    t2.init_velocities()
+    t2.step(37)
+    assert np.array_equal(t.positions(), t2.positions())
