@@ -50,6 +50,11 @@ template <typename T, int N> __device__ __forceinline__ T grad_k(int i, T two_pi
     return i == N / 2 ? T(0) : two_pi_over_L * (T)(i < N / 2 ? i : i - N);
 }
 
+// 1/x: the correctly rounded reciprocal intrinsic in FP32 (no division
+// slow path), a plain division in FP64.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // Pitch (in complex elements) of a row of n elements in shared memory: odd
 // so that threads on consecutive rows hit distinct banks.
 __host__ __device__ constexpr int row_pitch(int n) { return n + 1; }
@@ -415,7 +420,7 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
                 // w_K += q_K c(k) rho~_q with rho~_q = q_A rho~_A + q_B rho~_B
                 const T qzv = raw_k<T, N>(kzi, sp.two_pi_over_L);
                 const T k2 = (T)(s == 0 ? kxy2A : kxy2B) + qzv * qzv;
-                const T g = k2 > T(0) ? (s == 0 ? exy2A : exy2B) * e2[kzi] / k2 : T(0);
+                const T g = k2 > T(0) ? (s == 0 ? exy2A : exy2B) * e2[kzi] * recip(k2) : T(0);
                 const V rq = {sp.qA * A.x + sp.qB * B.x, sp.qA * A.y + sp.qB * B.y};
                 const T c = sp.el_scale * g;
                 wA.x += c * sp.qA * rq.x;
@@ -533,7 +538,7 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
 // G_ONLY: write G alone (the potentials' path of the analytic force).
 // EL: add the smeared-charge Coulomb term (charges on).
 template <typename T, int N, int C, bool G_ONLY = false, bool EL = false>
-__global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ Zxy, cplx_t<T>* __restrict__ H,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) z_spectral(const cplx_t<T>* __restrict__ Zxy, cplx_t<T>* __restrict__ H,
                                                   const cplx_t<T>* __restrict__ tw_g, SpectralParams<T> sp,
                                                   double* __restrict__ energy_partials,
                                                   cplx_t<T>* __restrict__ spectrum_out) {
@@ -543,7 +548,7 @@ __global__ void __launch_bounds__(256) z_spectral(const cplx_t<T>* __restrict__ 
 
 // Batched form: replica blockIdx.z.
 template <typename T, int N, int C, bool EL = false>
-__global__ void __launch_bounds__(256) z_spectral_batched(const ZArgs<T>* __restrict__ args) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) z_spectral_batched(const ZArgs<T>* __restrict__ args) {
     z_spectral_body<T, N, C, false, EL>(args[blockIdx.z], blockIdx.x, blockIdx.y, gridDim.x);
 }
 

@@ -135,7 +135,7 @@ __device__ __forceinline__ void z_vjp_tile(cplx_t<T>* buf, const cplx_t<T>* tw, 
             const T qz = raw_k<T, N>(kzi, tp);
             const T k2 = (s == 0 ? qxA * qxA + qyA * qyA : qxB * qxB + qyB * qyB) + qz * qz;
             if (el) {
-                const T g = k2 > T(0) ? (s == 0 ? exy2A : exy2B) * e2[kzi] / k2 : T(0);
+                const T g = k2 > T(0) ? (s == 0 ? exy2A : exy2B) * e2[kzi] * recip(k2) : T(0);
                 const T cq = sp.el_scale * g;
                 const V sq = {sp.qA * sA.x + sp.qB * sB.x, sp.qA * sA.y + sp.qB * sB.y};
                 pA.x += cq * sp.qA * sq.x;
