@@ -270,9 +270,7 @@ template <typename T> class Engine final : public EngineBase {
         return TILD_OK;
     }
 
-    // J^T lam of the ik force at the current positions (see vjp_kernels.cuh);
-    // dtheta (optional): d(lam . F)/d(chi, kappa, a).
-    tild_status force_vjp(const void* lam, void* out, int dtype, int where, double* dtheta) override {
+    tild_status vjp_supported() {
         if (analytic()) {
             err = "force_vjp: implemented for the ik force";
             return TILD_EUNSUPPORTED;
@@ -281,18 +279,16 @@ template <typename T> class Engine final : public EngineBase {
             err = "force_vjp: the grid must fit the single-plane xy passes (FP32 up to 128^3, FP64 up to 64^3)";
             return TILD_EUNSUPPORTED;
         }
+        return TILD_OK;
+    }
+    size_t vjp_blocks() const { return (size_t)(n_ / vjp_cols(n_)) * (n_ / 2 + 1); }
+
+    // J^T lam at the current positions into out_d (T, by id), and the
+    // parameter sums added to theta_acc (device, 3 doubles); stream-ordered,
+    // no host synchronisation (see vjp_kernels.cuh).
+    tild_status vjp_core(const T* lam_d, T* out_d, double* theta_acc) {
         const size_t N = cfg_->n_beads;
         tild_status st;
-        const void* src = lam;
-        if ((st = stage_in(&src, lam, 3 * N, dtype, where))) return st;
-        if ((st = ensure_aux(6 * N * sizeof(T)))) return st;
-        T* lam_d = (T*)aux_;
-        T* out_d = lam_d + 3 * N;
-        if (dtype == TILD_DTYPE_F32)
-            convert_copy<float, T><<<blocks(3 * N), 256, 0, stream_>>>(3 * N, (const float*)src, lam_d);
-        else
-            convert_copy<double, T><<<blocks(3 * N), 256, 0, stream_>>>(3 * N, (const double*)src, lam_d);
-        TILD_CUDA(cudaGetLastError());
         if ((st = enqueue_fields(false, nullptr, nullptr, kInvGrad))) return st;  // D w at r; Zxy = xy(rho)
         TILD_CUDA(cudaMemsetAsync(H_, 0, 3 * M_ * sizeof(V), stream_));
         const BeadParams<T> p = bead_params();
@@ -315,6 +311,7 @@ template <typename T> class Engine final : public EngineBase {
              })))
             return st;
         TILD_CUDA(cudaGetLastError());
+        accumulate_partials<<<1, 32, 0, stream_>>>(partials_, (int)vjp_blocks(), theta_acc);
         if ((st = enqueue_inverse(kInvPot))) return st;  // psi into the potential slot
         const double dV = cfg_->L * cfg_->L * cfg_->L / (double)M_;
         if ((st = dispatch_p([&](auto pp) -> tild_status {
@@ -323,20 +320,179 @@ template <typename T> class Engine final : public EngineBase {
              })))
             return st;
         TILD_CUDA(cudaGetLastError());
-        const size_t nb = (size_t)(n_ / vjp_cols(n_)) * (n_ / 2 + 1);
-        std::vector<double> part(3 * nb);
-        TILD_CUDA(cudaMemcpyAsync(part.data(), partials_, part.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        return TILD_OK;
+    }
+    // d(lam . F)/d(chi, kappa, a) from the accumulated sums
+    void theta_from_sums(const double* s, double* dtheta) const {
+        const double rho0 = cfg_->n_beads / (cfg_->L * cfg_->L * cfg_->L);
+        dtheta[0] = s[0] / (rho0 * (double)M_);
+        dtheta[1] = s[1] / (rho0 * (double)M_);
+        dtheta[2] = -2.0 * cfg_->a * s[2];
+    }
+    // a device scratch of `bytes` that lives as long as the context
+    template <class P> tild_status device_buffer(P** ptr, size_t& have, size_t bytes) {
+        if (have >= bytes) return TILD_OK;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        cudaFree(*ptr);
+        *ptr = nullptr;
+        have = 0;
+        TILD_CUDA(cudaMalloc((void**)ptr, bytes));
+        have = bytes;
+        return TILD_OK;
+    }
+
+    // J^T lam of the ik force at the current positions; dtheta (optional):
+    // d(lam . F)/d(chi, kappa, a).
+    tild_status force_vjp(const void* lam, void* out, int dtype, int where, double* dtheta) override {
+        tild_status st;
+        if ((st = vjp_supported())) return st;
+        const size_t N = cfg_->n_beads;
+        const void* src = lam;
+        if ((st = stage_in(&src, lam, 3 * N, dtype, where))) return st;
+        if ((st = ensure_aux(6 * N * sizeof(T)))) return st;
+        if ((st = device_buffer(&theta_, theta_bytes_, 3 * sizeof(double)))) return st;
+        T* lam_d = (T*)aux_;
+        T* out_d = lam_d + 3 * N;
+        if (dtype == TILD_DTYPE_F32)
+            convert_copy<float, T><<<blocks(3 * N), 256, 0, stream_>>>(3 * N, (const float*)src, lam_d);
+        else
+            convert_copy<double, T><<<blocks(3 * N), 256, 0, stream_>>>(3 * N, (const double*)src, lam_d);
+        TILD_CUDA(cudaGetLastError());
+        TILD_CUDA(cudaMemsetAsync(theta_, 0, 3 * sizeof(double), stream_));
+        if ((st = vjp_core(lam_d, out_d, theta_))) return st;
+        double s[3];
+        TILD_CUDA(cudaMemcpyAsync(s, theta_, sizeof(s), cudaMemcpyDeviceToHost, stream_));
         if ((st = stage_out_vec(out_d, 3 * N, out, dtype, where))) return st;
         TILD_CUDA(cudaStreamSynchronize(stream_));
         if ((st = check_err())) return st;
-        if (dtheta) {
-            double s[3] = {0, 0, 0};
-            for (size_t b = 0; b < nb; ++b)
-                for (int k = 0; k < 3; ++k) s[k] += part[3 * b + k];
-            const double rho0 = cfg_->n_beads / (cfg_->L * cfg_->L * cfg_->L);
-            dtheta[0] = s[0] / (rho0 * (double)M_);
-            dtheta[1] = s[1] / (rho0 * (double)M_);
-            dtheta[2] = -2.0 * cfg_->a * s[2];
+        if (dtheta) theta_from_sums(s, dtheta);
+        return TILD_OK;
+    }
+
+    // positions and carried velocities by id ([2][N][3] T) <-> the context
+    void store_state(T* dst) {
+        const int N = cfg_->n_beads;
+        store_by_id<T, T><<<blocks(N), 256, 0, stream_>>>(N, pos_[cur_pos_], id_[cur_id_], dst);
+        store_by_id<T, T><<<blocks(N), 256, 0, stream_>>>(N, u_[cur_u_], id_[cur_id_], dst + 3 * (size_t)N);
+    }
+    tild_status restore_state(const T* src, int64_t step) {
+        const int N = cfg_->n_beads;
+        invalidate_graph();
+        cur_pos_ = cur_u_ = cur_id_ = 0;
+        load_positions<T, T><<<blocks(N), 256, 0, stream_>>>(N, src, (T)cfg_->L, (T)(1.0 / cfg_->L), pos_[0], id_[0], err_ptr());
+        load_by_id<T, T><<<blocks(N), 256, 0, stream_>>>(N, src + 3 * (size_t)N, id_[0], u_[0]);
+        TILD_CUDA(cudaGetLastError());
+        tild_status st;
+        if ((st = enqueue_sort()) || (st = respread())) return st;
+        set_counter<<<1, 1, 0, stream_>>>(counters_, (unsigned long long)step);
+        TILD_CUDA(cudaGetLastError());
+        host_step_ = step;
+        steps_since_sort_ = 0;
+        return TILD_OK;
+    }
+
+    // Reverse-mode derivatives of L(r^K, v^K) through K GJF steps with the
+    // noise held fixed, checkpoints every C steps (see trajectory.py for the
+    // adjoint recursion); leaves the context at step K.
+    tild_status trajectory_vjp(int64_t K, int C, const void* rbar, const void* vbar, int dtype, int where, void* r0,
+                               void* v0, double* dtheta) override {
+        tild_status st;
+        if ((st = vjp_supported())) return st;
+        if (cfg_->scheme != kSchemeGJF) {
+            err = "trajectory_vjp: implemented for the GJF scheme";
+            return TILD_EUNSUPPORTED;
+        }
+        const size_t N = cfg_->n_beads, n3 = 3 * N, sb = 6 * N;  // one state: sb values of T
+        const int64_t n_ckpt = K / C + 1;
+        const size_t need = sizeof(T) * (sb * ((size_t)n_ckpt + (size_t)C + 1) + 2 * n3) + sizeof(double) * (3 * n3 + 3) + 8;
+        if ((st = device_buffer(&traj_, traj_bytes_, need))) return st;
+        T* ckpt = (T*)traj_;                        // [n_ckpt][sb]
+        T* seg = ckpt + sb * n_ckpt;                // [C][sb]
+        T* fin = seg + sb * C;                      // [sb]
+        T* lam = fin + sb;                          // [n3]
+        T* jt = lam + n3;                           // [n3]
+        double* rb = (double*)(((uintptr_t)(jt + n3) + 7) & ~(uintptr_t)7);  // 8-byte aligned
+        double* vb = rb + n3;
+        double* fb = vb + n3;
+        double* acc = fb + n3;
+        const double dt = cfg_->dt, m = cfg_->mass, al = cfg_->friction;
+        const double h = dt / (2.0 * m), ga = (1.0 - al * h) / (1.0 + al * h), gb = 1.0 / (1.0 + al * h);
+        const double c1 = gb * dt, c2 = gb * dt * dt / (2.0 * m);
+        const int64_t step0 = host_step_;
+        // forward with checkpoints
+        store_state(ckpt);
+        for (int64_t s = 0; s < K; ++s) {
+            if ((st = step(1))) return st;
+            if ((s + 1) % C == 0) store_state(ckpt + sb * ((s + 1) / C));
+        }
+        store_state(fin);
+        // adjoint vectors
+        const void* src = rbar;
+        if ((st = stage_in(&src, rbar, n3, dtype, where))) return st;
+        if (dtype == TILD_DTYPE_F32)
+            convert_copy<float, double><<<blocks(n3), 256, 0, stream_>>>(n3, (const float*)src, rb);
+        else
+            convert_copy<double, double><<<blocks(n3), 256, 0, stream_>>>(n3, (const double*)src, rb);
+        if (vbar) {
+            src = vbar;
+            if ((st = stage_in(&src, vbar, n3, dtype, where))) return st;
+            if (dtype == TILD_DTYPE_F32)
+                convert_copy<float, double><<<blocks(n3), 256, 0, stream_>>>(n3, (const float*)src, vb);
+            else
+                convert_copy<double, double><<<blocks(n3), 256, 0, stream_>>>(n3, (const double*)src, vb);
+        } else {
+            TILD_CUDA(cudaMemsetAsync(vb, 0, n3 * sizeof(double), stream_));
+        }
+        TILD_CUDA(cudaMemsetAsync(fb, 0, n3 * sizeof(double), stream_));
+        TILD_CUDA(cudaMemsetAsync(acc, 0, 3 * sizeof(double), stream_));
+        // lam = fb + h vb for the last step
+        scale_copy<T><<<blocks(n3), 256, 0, stream_>>>(n3, vb, h, lam);
+        TILD_CUDA(cudaGetLastError());
+        for (int64_t s0 = ((K - 1) / C) * C; K > 0 && s0 >= 0; s0 -= C) {
+            const int64_t s1 = std::min<int64_t>(s0 + C, K);
+            if ((st = restore_state(ckpt + sb * (s0 / C), step0 + s0))) return st;
+            for (int64_t j = s0; j < s1; ++j) {
+                if ((st = step(1))) return st;
+                store_state(seg + sb * (j - s0));
+            }
+            for (int64_t j = s1 - 1; j >= s0; --j) {
+                if ((st = restore_state(seg + sb * (j - s0), step0 + j + 1))) return st;
+                if ((st = vjp_core(lam, jt, acc))) return st;
+                adjoint_gjf_step<T><<<blocks(n3), 256, 0, stream_>>>(n3, jt, rb, vb, fb, lam, c1, c2, h, ga, j == 0 ? 1 : 0);
+                TILD_CUDA(cudaGetLastError());
+            }
+        }
+        if (K == 0) scale_copy<T><<<blocks(n3), 256, 0, stream_>>>(n3, fb, 1.0, lam);
+        // the force at r^0
+        if ((st = restore_state(ckpt, step0)) || (st = vjp_core(lam, jt, acc))) return st;
+        add_into<T><<<blocks(n3), 256, 0, stream_>>>(n3, rb, jt, rb);
+        TILD_CUDA(cudaGetLastError());
+        if ((st = restore_state(fin, step0 + K))) return st;
+        if ((st = stage_out_double(rb, n3, r0, dtype, where)) || (st = stage_out_double(vb, n3, v0, dtype, where))) return st;
+        double s[3];
+        TILD_CUDA(cudaMemcpyAsync(s, acc, sizeof(s), cudaMemcpyDeviceToHost, stream_));
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        if ((st = check_err())) return st;
+        if (dtheta) theta_from_sums(s, dtheta);
+        return TILD_OK;
+    }
+
+    // Device FP64 array -> caller buffer (dtype, host or device).
+    tild_status stage_out_double(const double* src, size_t count, void* out, int dtype, int where) {
+        tild_status st;
+        void* dst = out;
+        if (where == TILD_HOST) {
+            if ((st = ensure_stage(count * dtype_size(dtype)))) return st;
+            dst = stage_;
+        }
+        if (dtype == TILD_DTYPE_F32)
+            convert_copy<double, float><<<blocks(count), 256, 0, stream_>>>(count, src, (float*)dst);
+        else
+            convert_copy<double, double><<<blocks(count), 256, 0, stream_>>>(count, src, (double*)dst);
+        TILD_CUDA(cudaGetLastError());
+        if (where == TILD_HOST) {
+            TILD_CUDA(cudaMemcpyAsync(out, stage_, count * dtype_size(dtype), cudaMemcpyDeviceToHost, stream_));
+            TILD_CUDA(cudaStreamSynchronize(stream_));
         }
         return TILD_OK;
     }
@@ -585,6 +741,10 @@ template <typename T> class Engine final : public EngineBase {
     // staging
     void* aux_ = nullptr;
     size_t aux_bytes_ = 0;
+    double* theta_ = nullptr;  // force-VJP parameter sums
+    size_t theta_bytes_ = 0;
+    void* traj_ = nullptr;     // trajectory derivatives: checkpoints and adjoint vectors
+    size_t traj_bytes_ = 0;
     void* stage_ = nullptr;
     size_t stage_bytes_ = 0;
     // graph cache
@@ -638,7 +798,7 @@ template <typename T> class Engine final : public EngineBase {
         invalidate_graph();
         free_beads();
         void* ptrs[] = {rho_fx_, Zxy_, H_, grad_, tw_, kernel1d_, spec_, counters_, partials_, counts_,
-                        tile_start_, cursor_, block_sums_, aux_, stage_};
+                        tile_start_, cursor_, block_sums_, aux_, stage_, theta_, traj_};
         for (void* p : ptrs) cudaFree(p);
         rho_fx_ = nullptr;
         if (own_stream_) cudaStreamDestroy(own_stream_);

@@ -62,6 +62,8 @@ class EngineBase {
     virtual bool has_velocities() const = 0;
     // Parameter changes: keep v^n while F^n changes (u = v - dt/2m F).
     virtual tild_status force_vjp(const void* lam, void* out, int dtype, int where, double* dtheta) = 0;
+    virtual tild_status trajectory_vjp(int64_t K, int C, const void* rbar, const void* vbar, int dtype, int where,
+                                       void* r0, void* v0, double* dtheta) = 0;
     virtual tild_status save_velocities() = 0;
     virtual tild_status restore_velocities() = 0;
     virtual void params_changed() = 0;

@@ -271,4 +271,48 @@ __global__ void __launch_bounds__(256) vjp_beads(BeadParams<T> p, BeadBuffers<T>
     out[3 * (size_t)bid + 2] = oz;
 }
 
+// acc[k] += sum_b partials[3 b + k] (k = 0..2), in a fixed order.
+static __global__ void accumulate_partials(const double* __restrict__ partials, int n_blocks, double* __restrict__ acc) {
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int b = 0; b < n_blocks; ++b) s += partials[3 * b + threadIdx.x];
+        acc[threadIdx.x] += s;
+    }
+}
+
+// One reverse GJF step on the adjoint vectors (FP64, [3N] by bead id):
+//   rt = rb + J^T lam;  rb = rt;  vb <- c1 rt + ga vb;  fb <- c2 rt + h ga vb;
+// and the next adjoint vector lam = fb + h vb (or fb alone for the force at r^0).
+template <typename T>
+__global__ void adjoint_gjf_step(size_t n3, const T* __restrict__ jt, double* __restrict__ rb, double* __restrict__ vb,
+                                 double* __restrict__ fb, T* __restrict__ lam_next, double c1, double c2, double h,
+                                 double ga, int last) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const double rt = rb[i] + (double)jt[i];
+    const double v = vb[i];
+    const double vn = c1 * rt + ga * v, fn = c2 * rt + h * ga * v;
+    rb[i] = rt;
+    vb[i] = vn;
+    fb[i] = fn;
+    lam_next[i] = (T)(last ? fn : fn + h * vn);
+}
+
+// y = (T)(a x)
+template <typename T>
+__global__ void scale_copy(size_t n, const double* __restrict__ x, double a, T* __restrict__ y) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (T)(a * x[i]);
+}
+
+// the device step counter (noise counters of the following steps)
+static __global__ void set_counter(unsigned long long* counter, unsigned long long value) { *counter = value; }
+
+// out = a + b (FP64)
+template <typename T>
+__global__ void add_into(size_t n, const double* __restrict__ a, const T* __restrict__ b, double* __restrict__ out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] + (double)b[i];
+}
+
 }  // namespace tild

@@ -6,10 +6,10 @@ velocities and to chi, kappa and a, holding the thermal noise fixed (the same
 Philox counters). Reverse mode needs the states of every step in reverse
 order; they are recomputed segment by segment from checkpoints taken every
 `checkpoint_every` steps (bit-identical, since a step depends only on the
-state and its counters). Checkpoints are device-memory state blobs. Each
-reverse step is one call of the force's vector-Jacobian product
-(tild_force_vjp); the adjoint recursion itself is a few FP64 vector updates
-on device tensors.
+state and its counters). The sweep runs in the library: device
+checkpoints, one force vector-Jacobian product per reverse step and the
+adjoint recursion below on FP64 device vectors, all stream-ordered with one
+host synchronisation at the end.
 
 One GJF step maps (r, v, F) to (r', v', F') with F' = F(r') and
   r' = r + b dt v + (b dt^2 / 2m) F + (b dt / 2m) beta,
@@ -26,65 +26,30 @@ from typing import Dict, Optional
 
 import numpy as np
 
-from .binding import Tild
+import ctypes
+
+from .binding import TILD_DTYPE_F64, TILD_HOST, Tild
 
 
 def gjf_trajectory_vjp(t: Tild, n_steps: int, r_bar, v_bar=None, checkpoint_every: int = 20) -> Dict[str, object]:
     """Derivatives of L through `n_steps` GJF steps of context `t` (positions
     and velocities set). r_bar, v_bar: dL/dr^K, dL/dv^K (n_beads x 3, by bead
-    id; numpy arrays or CUDA tensors). Returns {"r0", "v0"} as numpy arrays
-    and {"chi", "kappa", "a"}; `t` is left at step K. Checkpoints and the
-    adjoint vectors stay in device memory (FP64)."""
-    import torch
-
+    id; numpy arrays or CUDA tensors). Returns {"r0", "v0"} (numpy FP64) and
+    {"chi", "kappa", "a"}; `t` is left at step K. The sweep runs inside the
+    library (tild_gjf_trajectory_vjp)."""
     if t.scheme != "gjf" or t.force_method != "ik":
         raise ValueError("gjf_trajectory_vjp needs the GJF scheme and the ik force")
-    if n_steps < 0 or checkpoint_every < 1:
-        raise ValueError("need n_steps >= 0 and checkpoint_every >= 1")
-    dt, alpha, _kT, mass = t.integrator
-    h = dt / (2.0 * mass)
-    ga = (1.0 - alpha * h) / (1.0 + alpha * h)
-    gb = 1.0 / (1.0 + alpha * h)
-    c1, c2 = gb * dt, gb * dt * dt / (2.0 * mass)
-    nbytes = t.state_bytes()
-
-    def snapshot():
-        return t.get_state(out=torch.empty(nbytes, dtype=torch.uint8, device="cuda"))
-
-    def dev(x):
-        if x is None:
-            return torch.zeros((t.n_beads, 3), dtype=torch.float64, device="cuda")
-        return torch.as_tensor(np.asarray(x) if not torch.is_tensor(x) else x, dtype=torch.float64,
-                               device="cuda").reshape(-1, 3).clone()
-
-    checkpoints = {0: snapshot()}
-    for s in range(n_steps):
-        t.step(1)
-        if (s + 1) % checkpoint_every == 0:
-            checkpoints[s + 1] = snapshot()
-    final = snapshot()
-    rb, vb, fb = dev(r_bar), dev(v_bar), dev(None)
-    jt = torch.empty_like(rb)
-    tb = {"chi": 0.0, "kappa": 0.0, "a": 0.0}
-    for s0 in reversed(range(0, n_steps, checkpoint_every)):
-        s1 = min(s0 + checkpoint_every, n_steps)
-        # states s0 + 1 .. s1 of this segment, recomputed from its checkpoint
-        t.set_state(checkpoints[s0])
-        states = []
-        for _ in range(s0, s1):
-            t.step(1)
-            states.append(snapshot())
-        for k in range(s1 - s0 - 1, -1, -1):
-            t.set_state(states[k])
-            ft = fb + h * vb
-            _, th = t.force_vjp(ft, out=jt)
-            rt = rb + jt
-            for key in tb:
-                tb[key] += th[key]
-            rb, vb, fb = rt, c1 * rt + ga * vb, c2 * rt + h * ga * vb
-    t.set_state(checkpoints[0])
-    _, th = t.force_vjp(fb, out=jt)
-    for key in tb:
-        tb[key] += th[key]
-    t.set_state(final)
-    return {"r0": (rb + jt).cpu().numpy(), "v0": vb.cpu().numpy(), **tb}
+    n3 = 3 * t.n_beads
+    rb = np.ascontiguousarray(np.asarray(r_bar.cpu() if hasattr(r_bar, "cpu") else r_bar, dtype=np.float64)).reshape(-1)
+    vb = None
+    if v_bar is not None:
+        vb = np.ascontiguousarray(np.asarray(v_bar.cpu() if hasattr(v_bar, "cpu") else v_bar, dtype=np.float64)).reshape(-1)
+    if rb.size != n3 or (vb is not None and vb.size != n3):
+        raise ValueError("r_bar and v_bar need n_beads x 3 values")
+    r0 = np.empty(n3, dtype=np.float64)
+    v0 = np.empty(n3, dtype=np.float64)
+    th = (ctypes.c_double * 3)()
+    t._chk(t.lib.tild_gjf_trajectory_vjp(t.ctx, int(n_steps), int(checkpoint_every), rb.ctypes.data,
+                                         None if vb is None else vb.ctypes.data, TILD_DTYPE_F64, TILD_HOST,
+                                         r0.ctypes.data, v0.ctypes.data, th))
+    return {"r0": r0.reshape(-1, 3), "v0": v0.reshape(-1, 3), "chi": th[0], "kappa": th[1], "a": th[2]}
