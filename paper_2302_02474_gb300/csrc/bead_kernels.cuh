@@ -691,9 +691,11 @@ __global__ void bin_scatter_pos(int n_beads, Topology topo, const int* __restric
     slot_of_id[b] = s;
 }
 
-// Within each tile, order the beads by cell (x fastest) so that neighbouring
-// threads of the bead kernel touch neighbouring shared-memory patch points.
-// One CTA per tile; tiles with more than kLocalSortMax beads keep their order.
+// Within each tile, order the beads by (edge class, cell): beads more than
+// half a cell from every tile face first, then the others, each group by
+// cell (x fastest) so that neighbouring threads of the bead kernel touch
+// neighbouring shared-memory patch points. One CTA per tile; tiles with more
+// than kLocalSortMax beads keep their order.
 template <typename T>
 __global__ void __launch_bounds__(256) bin_local_sort(const int* __restrict__ tile_start, int tiles, int n, T inv_dx,
                                                       int n_beads, T* __restrict__ pos /*[3][N]*/,
@@ -703,12 +705,12 @@ __global__ void __launch_bounds__(256) bin_local_sort(const int* __restrict__ ti
     __shared__ T s_v[6][kLocalSortMax];
     __shared__ int s_id[kLocalSortMax];
     __shared__ short s_key[kLocalSortMax];
-    __shared__ int s_cnt[kTileCells];
+    __shared__ int s_cnt[2 * kTileCells];
     const int t = blockIdx.x;
     const int start = tile_start[t], cnt = tile_start[t + 1] - start;
     if (cnt <= 1 || cnt > kLocalSortMax) return;
     const int tx = t % tiles, ty = (t / tiles) % tiles, tz = t / (tiles * tiles);
-    for (int c = threadIdx.x; c < kTileCells; c += blockDim.x) s_cnt[c] = 0;
+    for (int c = threadIdx.x; c < 2 * kTileCells; c += blockDim.x) s_cnt[c] = 0;
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
         const int i = start + j;
@@ -724,13 +726,19 @@ __global__ void __launch_bounds__(256) bin_local_sort(const int* __restrict__ ti
         const int cy = min(max((int)floor(y * inv_dx), 0), n - 1) - ty * kTile;
         const int cz = min(max((int)floor(z * inv_dx), 0), n - 1) - tz * kTile;
         const int key = (min(max(cz, 0), kTile - 1) * kTile + min(max(cy, 0), kTile - 1)) * kTile + min(max(cx, 0), kTile - 1);
-        s_key[j] = (short)key;
-        atomicAdd(&s_cnt[key], 1);
+        // beads within half a cell of a tile face go last: those are the ones
+        // that drift out of the tile's patch before the next re-binning and
+        // take the global-memory paths, so they share as few warps as possible
+        const T lx = x * inv_dx - (T)(tx * kTile), ly = y * inv_dx - (T)(ty * kTile), lz = z * inv_dx - (T)(tz * kTile);
+        const T dmin = min(min(min(lx, T(kTile) - lx), min(ly, T(kTile) - ly)), min(lz, T(kTile) - lz));
+        const int risk = dmin < T(0.5) ? 1 : 0;
+        s_key[j] = (short)(risk * kTileCells + key);
+        atomicAdd(&s_cnt[risk * kTileCells + key], 1);
     }
     __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan of the 512 cell counts by one warp
+    if (threadIdx.x < 32) {  // exclusive scan of the 2 x 512 (class, cell) counts by one warp
         int carry = 0;
-        for (int c0 = 0; c0 < kTileCells; c0 += 32) {
+        for (int c0 = 0; c0 < 2 * kTileCells; c0 += 32) {
             const int v = s_cnt[c0 + threadIdx.x];
             int incl = v;
             for (int o = 1; o < 32; o <<= 1) {
