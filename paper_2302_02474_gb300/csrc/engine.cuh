@@ -311,7 +311,7 @@ template <typename T> class Engine final : public EngineBase {
              })))
             return st;
         TILD_CUDA(cudaGetLastError());
-        accumulate_partials<<<1, 32, 0, stream_>>>(partials_, (int)vjp_blocks(), theta_acc);
+        accumulate_partials<<<1, 256, 0, stream_>>>(partials_, (int)vjp_blocks(), theta_acc);
         if ((st = enqueue_inverse(kInvPot))) return st;  // psi into the potential slot
         const double dV = cfg_->L * cfg_->L * cfg_->L / (double)M_;
         if ((st = dispatch_p([&](auto pp) -> tild_status {
@@ -999,8 +999,11 @@ template <typename T> class Engine final : public EngineBase {
 
     // z-pass column tile: 128 bytes of complex values, or the largest power of
     // two dividing n when that is smaller
-    // force-VJP z pass column tile: half the z pass's, at least 2
-    static constexpr int vjp_cols(int n) { return zpass_cols(n) / 2 < 2 ? 2 : zpass_cols(n) / 2; }
+    // force-VJP z pass column tile: the z pass's up to 64^3 (shared memory
+    // 8 n C elements), half of it above, at least 2
+    static constexpr int vjp_cols(int n) {
+        return n <= 64 ? zpass_cols(n) : (zpass_cols(n) / 2 < 2 ? 2 : zpass_cols(n) / 2);
+    }
     size_t vjp_smem() const { return ((size_t)n_ + 8 * (size_t)n_ * vjp_cols(n_)) * sizeof(V); }
 
     static constexpr int zpass_cols(int n) {

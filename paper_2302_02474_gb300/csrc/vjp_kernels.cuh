@@ -180,13 +180,18 @@ __global__ void __launch_bounds__(256) z_vjp(cplx_t<T>* __restrict__ H, const cp
     const int ky[2] = {(int)blockIdx.y, blockIdx.y == 0 ? 0 : N - (int)blockIdx.y};
     const int R = (ky[0] == ky[1]) ? 1 : 2;
     const size_t NN = (size_t)N * N, M = NN * N;
-    for (int i = threadIdx.x; i < 4 * R * TS; i += blockDim.x) {
+    // buffer i = (set, row, z, c): sets 0..2 from H (mu), set 3 from Zxy (rho)
+    auto src = [&](int i) {
         const int set = i / (R * TS), rem = i % (R * TS);
         const int r = rem / TS, zc = rem % TS;
-        const int z = zc / C, cc = zc % C;
-        const size_t off = z * NN + (size_t)ky[r] * N + p0 + cc;
-        buf[i] = set < 3 ? H[set * M + off] : Zxy[off];
-    }
+        const size_t off = (zc / C) * NN + (size_t)ky[r] * N + p0 + zc % C;
+        return set < 3 ? H[set * M + off] : Zxy[off];
+    };
+    auto dst = [&](int i, V v) { buf[i] = v; };
+    if (R == 1)
+        batched_load<4 * TS, 256, V>(src, dst);
+    else
+        batched_load<8 * TS, 256, V>(src, dst);
     __syncthreads();
     double acc[3] = {0.0, 0.0, 0.0};
     if (R == 1)
@@ -271,13 +276,25 @@ __global__ void __launch_bounds__(256) vjp_beads(BeadParams<T> p, BeadBuffers<T>
     out[3 * (size_t)bid + 2] = oz;
 }
 
-// acc[k] += sum_b partials[3 b + k] (k = 0..2), in a fixed order.
-static __global__ void accumulate_partials(const double* __restrict__ partials, int n_blocks, double* __restrict__ acc) {
-    if (threadIdx.x < 3) {
-        double s = 0.0;
-        for (int b = 0; b < n_blocks; ++b) s += partials[3 * b + threadIdx.x];
-        acc[threadIdx.x] += s;
+// acc[k] += sum_b partials[3 b + k] (k = 0..2), in a fixed order: strided
+// sums per thread, then a tree in shared memory. One block of 256 threads.
+static __global__ void __launch_bounds__(256) accumulate_partials(const double* __restrict__ partials, int n_blocks,
+                                                                  double* __restrict__ acc) {
+    __shared__ double s[3][256];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < n_blocks; b += 256) v += partials[3 * b + k];
+        s[k][threadIdx.x] = v;
     }
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) acc[threadIdx.x] += s[threadIdx.x][0];
 }
 
 // One reverse GJF step on the adjoint vectors (FP64, [3N] by bead id):
