@@ -270,8 +270,11 @@ tild_status tild_energy_gradient(tild_ctx* ctx, tild_energy_grad* g, void* dU_dr
  * bead j, where F is the ik particle-mesh force of Eq. PMM plus the bond
  * force of Eq. bonds (charges included) at the current positions. dtheta
  * (NULL to skip) receives d(sum_i lam_i . F_i)/d(chi, kappa, a). Chained
- * through the integrator this gives derivatives of trajectories; the
- * Python package has the GJF chain with checkpoints. Returns
+ * through the integrator this gives derivatives of trajectories
+ * (tild_gjf_trajectory_vjp). lam is spread onto the grid in 64-bit fixed
+ * point with a power-of-two scale taken from max|lam|, so the result is
+ * bitwise reproducible and exactly homogeneous under power-of-two scaling of
+ * lam; a non-finite lam makes every output NaN. Returns
  * TILD_EUNSUPPORTED with the analytic force method or for grids whose
  * planes do not fit one CTA (FP32 above 128^3, FP64 above 64^3). */
 tild_status tild_force_vjp(tild_ctx* ctx, const void* lam, void* out, int dtype, int where, double* dtheta);

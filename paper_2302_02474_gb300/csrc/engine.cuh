@@ -282,6 +282,19 @@ template <typename T> class Engine final : public EngineBase {
         return TILD_OK;
     }
     size_t vjp_blocks() const { return (size_t)(n_ / vjp_cols(n_)) * (n_ / 2 + 1); }
+    // fixed-point bits of the adjoint spread: S = min(S_max, 62 - ceil(log2 n_beads))
+    int vjp_fixed_bits() const {
+        int lg = 0;
+        while ((1ull << lg) < (unsigned long long)cfg_->n_beads) ++lg;
+        return std::min(AdjointFixed<T>::s_max, 62 - lg);
+    }
+    // the fixed-point spread [3][M] int64 pairs and the max|lam| bits
+    size_t vjp_fx_need() const { return 6 * M_ * sizeof(unsigned long long) + 16; }
+    tild_status vjp_prepare() {
+        tild_status st;
+        if ((st = vjp_supported())) return st;
+        return device_buffer(&vjp_fx_, vjp_fx_bytes_, vjp_fx_need());
+    }
 
     // J^T lam at the current positions into out_d (T, by id), and the
     // parameter sums added to theta_acc (device, 3 doubles); stream-ordered,
@@ -290,11 +303,16 @@ template <typename T> class Engine final : public EngineBase {
         const size_t N = cfg_->n_beads;
         tild_status st;
         if ((st = enqueue_fields(false, nullptr, nullptr, kInvGrad))) return st;  // D w at r; Zxy = xy(rho)
-        TILD_CUDA(cudaMemsetAsync(H_, 0, 3 * M_ * sizeof(V), stream_));
+        using Bits = typename AdjointFixed<T>::bits_t;
+        unsigned long long* fx = (unsigned long long*)vjp_fx_;
+        Bits* bits = (Bits*)(fx + 6 * M_);
+        const int S = vjp_fixed_bits();
+        TILD_CUDA(cudaMemsetAsync(fx, 0, vjp_fx_need(), stream_));
+        lam_absmax<T><<<(int)std::min<size_t>(blocks(3 * N), 2 * 152), 256, 0, stream_>>>(3 * N, lam_d, bits);
         const BeadParams<T> p = bead_params();
         const BeadBuffers<T> bf = bead_buffers();
         if ((st = dispatch_p([&](auto pp) -> tild_status {
-                 vjp_spread<decltype(pp)::value, T><<<blocks(N), 256, 0, stream_>>>(p, bf, lam_d, (T*)H_);
+                 vjp_spread<decltype(pp)::value, T><<<blocks(N), 256, 0, stream_>>>(p, bf, lam_d, fx, bits, S);
                  return TILD_OK;
              })))
             return st;
@@ -304,7 +322,7 @@ template <typename T> class Engine final : public EngineBase {
                  constexpr int NN = decltype(nn)::value;
                  if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
                      constexpr int CV = vjp_cols(NN);
-                     xy_forward_cplx<T, NN><<<dim3(NN, 3), 512, plane_smem(), stream_>>>(H_, tw_);
+                     xy_forward_cplx<T, NN><<<dim3(NN, 3), 512, plane_smem(), stream_>>>((const longlong2*)fx, bits, S, H_, tw_);
                      z_vjp<T, NN, CV><<<dim3(NN / CV, NN / 2 + 1), 256, vjp_smem(), stream_>>>(H_, Zxy_, tw_, sp, partials_, el);
                  }
                  return TILD_OK;
@@ -345,7 +363,7 @@ template <typename T> class Engine final : public EngineBase {
     // d(lam . F)/d(chi, kappa, a).
     tild_status force_vjp(const void* lam, void* out, int dtype, int where, double* dtheta) override {
         tild_status st;
-        if ((st = vjp_supported())) return st;
+        if ((st = vjp_prepare())) return st;
         const size_t N = cfg_->n_beads;
         const void* src = lam;
         if ((st = stage_in(&src, lam, 3 * N, dtype, where))) return st;
@@ -397,7 +415,7 @@ template <typename T> class Engine final : public EngineBase {
     tild_status trajectory_vjp(int64_t K, int C, const void* rbar, const void* vbar, int dtype, int where, void* r0,
                                void* v0, double* dtheta) override {
         tild_status st;
-        if ((st = vjp_supported())) return st;
+        if ((st = vjp_prepare())) return st;
         if (cfg_->scheme != kSchemeGJF) {
             err = "trajectory_vjp: implemented for the GJF scheme";
             return TILD_EUNSUPPORTED;
@@ -745,6 +763,8 @@ template <typename T> class Engine final : public EngineBase {
     size_t theta_bytes_ = 0;
     void* traj_ = nullptr;     // trajectory derivatives: checkpoints and adjoint vectors
     size_t traj_bytes_ = 0;
+    void* vjp_fx_ = nullptr;   // force VJP: fixed-point spread of lam
+    size_t vjp_fx_bytes_ = 0;
     void* stage_ = nullptr;
     size_t stage_bytes_ = 0;
     // graph cache
@@ -798,7 +818,7 @@ template <typename T> class Engine final : public EngineBase {
         invalidate_graph();
         free_beads();
         void* ptrs[] = {rho_fx_, Zxy_, H_, grad_, tw_, kernel1d_, spec_, counters_, partials_, counts_,
-                        tile_start_, cursor_, block_sums_, aux_, stage_, theta_, traj_};
+                        tile_start_, cursor_, block_sums_, aux_, stage_, theta_, traj_, vjp_fx_};
         for (void* p : ptrs) cudaFree(p);
         rho_fx_ = nullptr;
         if (own_stream_) cudaStreamDestroy(own_stream_);

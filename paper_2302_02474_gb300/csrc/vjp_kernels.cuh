@@ -9,8 +9,9 @@
 // psi_K = sum_K' eps_KK' C (D . mu_K'):
 //   (J^T lam)_j = sum_g grad W_j(g) [psi_{K_j}(g) / dV - (lam_j . D w_{K_j})(g)]
 //                 - (3/b^2) sum_{i ~ j} (lam_j - lam_i).
-// The pipeline: spread mu (three complex grids: component d of mu_A in the
-// real and of mu_B in the imaginary part), xy transforms in place, a z pass
+// The pipeline: spread mu in fixed point (three grids of int64 pairs:
+// component d of mu_A and of mu_B), xy transforms into three complex grids
+// (mu_A in the real, mu_B in the imaginary part), a z pass
 // that forms D . mu per species, psi and the parameter sums, the inverse
 // transforms of psi (the potential slot of the gradient buffer), and a
 // per-bead gather with the derivatives of the assignment weights.
@@ -21,15 +22,97 @@
 
 namespace tild {
 
-// mu_d += W_i lam_{i,d}; lam by bead id ([N][3]); mu as T pairs [3][M].
+// The spread of lam is accumulated in 64-bit fixed point, so that J^T lam is
+// independent of the order of the atomic adds (bitwise reproducible, as the
+// forward density is). Each grid sum is bounded by n_beads * max|lam| since
+// every assignment weight is at most 1; the scale is the power of two s with
+// max|lam| * s < 2^S and S = min(S_max, 62 - ceil(log2 n_beads)), so no sum
+// can overflow. S_max is 40 for FP32 (below the FP32 rounding of w * lam)
+// and 52 for FP64. A non-finite lam makes the scale 0 and the inverse scale
+// NaN: every output is then NaN.
+template <typename T> struct AdjointFixed;
+template <> struct AdjointFixed<float> {
+    using bits_t = unsigned int;
+    static constexpr int s_max = 40;
+    static __device__ __forceinline__ bits_t abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+    static __device__ __forceinline__ void scales(bits_t b, int S, float& s, float& inv) {
+        const int E = (int)(b >> 23);
+        if (E >= 255) {
+            s = 0.f;
+            inv = __int_as_float(0x7fc00000);
+            return;
+        }
+        const int e = E == 0 ? -127 : E - 127;  // max|lam| < 2^(e+1)
+        const int k = min(S - e - 1, 120);
+        s = __int_as_float((k + 127) << 23);
+        inv = __int_as_float((127 - k) << 23);
+    }
+    static __device__ __forceinline__ long long to_fixed(float x) { return __float2ll_rn(x); }
+};
+template <> struct AdjointFixed<double> {
+    using bits_t = unsigned long long;
+    static constexpr int s_max = 52;
+    static __device__ __forceinline__ bits_t abs_bits(double x) {
+        return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    }
+    static __device__ __forceinline__ void scales(bits_t b, int S, double& s, double& inv) {
+        const int E = (int)(b >> 52);
+        if (E >= 2047) {
+            s = 0.0;
+            inv = __longlong_as_double(0x7ff8000000000000ll);
+            return;
+        }
+        const int e = E == 0 ? -1023 : E - 1023;
+        const int k = min(S - e - 1, 1000);
+        s = __longlong_as_double((long long)(k + 1023) << 52);
+        inv = __longlong_as_double((long long)(1023 - k) << 52);
+    }
+    static __device__ __forceinline__ long long to_fixed(double x) { return __double2ll_rn(x); }
+};
+
+// *bits = max over the n values of lam of the bit pattern of |lam| (for
+// non-negative IEEE values the order of the bit patterns is the order of the
+// values, NaN above infinity); *bits must be 0 on entry.
+// (256 threads per block.)
+template <typename T>
+__global__ void __launch_bounds__(256) lam_absmax(size_t n, const T* __restrict__ lam,
+                                                  typename AdjointFixed<T>::bits_t* bits) {
+    using B = typename AdjointFixed<T>::bits_t;
+    B m = 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < n; i0 += 8 * stride) {
+        B v[8];  // eight independent loads in flight
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = i0 + k * stride < n ? AdjointFixed<T>::abs_bits(lam[i0 + k * stride]) : B(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m = max(m, v[k]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = max(m, (B)__shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ B s_m[8];
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 1; w < 8; ++w) m = max(m, s_m[w]);
+        if (m) atomicMax(bits, m);
+    }
+}
+
+// mu_d += W_i lam_{i,d} in fixed point; lam by bead id ([N][3]); fx as
+// int64 pairs [3][M][2] (species A, B), zero on entry.
 template <int P, typename T>
 __global__ void __launch_bounds__(256) vjp_spread(BeadParams<T> p, BeadBuffers<T> bf, const T* __restrict__ lam,
-                                                  T* __restrict__ mu) {
+                                                  unsigned long long* __restrict__ fx,
+                                                  const typename AdjointFixed<T>::bits_t* __restrict__ bits, int S) {
+    using FX = AdjointFixed<T>;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n_beads) return;
+    T sc, inv;
+    FX::scales(*bits, S, sc, inv);
     const int tag = bf.id[i];
     const int bid = slot_bead_id(tag), K = slot_species(tag);
-    const T l0 = lam[3 * (size_t)bid], l1 = lam[3 * (size_t)bid + 1], l2 = lam[3 * (size_t)bid + 2];
+    const T l0 = lam[3 * (size_t)bid] * sc, l1 = lam[3 * (size_t)bid + 1] * sc, l2 = lam[3 * (size_t)bid + 2] * sc;
     Stencil<P, T> st;
     st.set(bf.px[i], bf.py[i], bf.pz[i], p.inv_dx);
     const int n = p.n;
@@ -44,26 +127,34 @@ __global__ void __launch_bounds__(256) vjp_spread(BeadParams<T> p, BeadBuffers<T
             for (int a = 0; a < P; ++a) {
                 const size_t g = row + pwrap(st.jx + a, n);
                 const T w = st.wx[a] * wyz;
-                atomicAdd(mu + 2 * g + K, w * l0);
-                atomicAdd(mu + 2 * (M + g) + K, w * l1);
-                atomicAdd(mu + 2 * (2 * M + g) + K, w * l2);
+                atomicAdd(fx + 2 * g + K, (unsigned long long)FX::to_fixed(w * l0));
+                atomicAdd(fx + 2 * (M + g) + K, (unsigned long long)FX::to_fixed(w * l1));
+                atomicAdd(fx + 2 * (2 * M + g) + K, (unsigned long long)FX::to_fixed(w * l2));
             }
         }
 }
 
-// Forward DFT along x and y of plane blockIdx.x of field blockIdx.y of a
-// complex [3][M] array, in place, stored in mirror-paired column order.
+// Forward DFT along x and y of plane blockIdx.x of field blockIdx.y: reads
+// the fixed-point spread fx ([3][M] int64 pairs), converts it with the
+// inverse scale, and writes the complex [3][M] array `data` in mirror-paired
+// column order.
 template <typename T, int N>
-__global__ void __launch_bounds__(512) xy_forward_cplx(cplx_t<T>* __restrict__ data, const cplx_t<T>* __restrict__ tw_g) {
+__global__ void __launch_bounds__(512) xy_forward_cplx(const longlong2* __restrict__ fx,
+                                                       const typename AdjointFixed<T>::bits_t* __restrict__ bits, int S,
+                                                       cplx_t<T>* __restrict__ data, const cplx_t<T>* __restrict__ tw_g) {
     using V = cplx_t<T>;
     constexpr int PITCH = row_pitch(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tw = reinterpret_cast<V*>(smem_raw);
     V* plane = tw + N;
     load_twiddles(tw, tw_g, N);
+    T sc, inv;
+    AdjointFixed<T>::scales(*bits, S, sc, inv);
     const size_t base = (size_t)blockIdx.y * N * N * N + (size_t)blockIdx.x * N * N;
-    batched_load<N * N, 512, V>([&](int i) { return data[base + i]; },
-                                [&](int i, V v) { plane[(i / N) * PITCH + i % N] = v; });
+    batched_load<N * N, 512, longlong2>([&](int i) { return fx[base + i]; },
+                                        [&](int i, longlong2 v) {
+                                            plane[(i / N) * PITCH + i % N] = V{from_fixed(v.x, inv), from_fixed(v.y, inv)};
+                                        });
     __syncthreads();
     smem_fft_lines<N, -1, N, 512>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
     smem_fft_lines<N, -1, N, 512>(plane, StridedLines<1>{}, PITCH, tw);  // along y

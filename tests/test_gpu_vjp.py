@@ -56,6 +56,37 @@ def test_force_vjp_matches_oracle(B, prec, order, charges):
         assert th[k] == pytest.approx(ref[k], rel=tol, abs=tol * 1e-3 * abs(ref["a"])), k
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_force_vjp_is_reproducible_and_exactly_homogeneous(B, prec):
+    # lam is spread in fixed point with a power-of-two scale taken from
+    # max|lam|: repeated calls agree bitwise, and J^T (2^k lam) is exactly
+    # 2^k J^T lam (the same integers, rescaled), as is d(lam . F)/dtheta.
+    spec = I.small_system(n_chains=70, N=10, n_a=4, L=8.0, n=16, pmeorder=2, precision=prec, chi=1.1, kappa=6.0)
+    t, m, pos = _setup(B, spec)
+    dt = np.float64 if prec == "fp64" else np.float32
+    lam = np.random.default_rng(5).normal(size=pos.shape).astype(dt)
+    a, tha = t.force_vjp(lam)
+    b, thb = t.force_vjp(lam)
+    assert a.tobytes() == b.tobytes() and tha == thb
+    for k in (40, -40):
+        c, thc = t.force_vjp(lam * dt(2.0**k))
+        assert np.array_equal(c, a * dt(2.0**k)), k
+        for key in ("chi", "kappa", "a"):
+            assert thc[key] == tha[key] * 2.0**k, (k, key)
+
+
+def test_force_vjp_non_finite_lam_gives_nan(B):
+    spec = I.small_system(n_chains=70, N=10, n_a=4, L=8.0, n=16, pmeorder=2, precision="fp32", chi=1.1, kappa=6.0)
+    t, m, pos = _setup(B, spec)
+    lam = np.random.default_rng(6).normal(size=pos.shape).astype(np.float32)
+    lam[17, 1] = np.nan
+    got, th = t.force_vjp(lam)
+    assert np.isnan(got).all() and all(np.isnan(th[k]) for k in ("chi", "kappa", "a"))
+    lam[17, 1] = 0.5  # the context is still usable
+    got, th = t.force_vjp(lam)
+    assert np.isfinite(got).all()
+
+
 def test_trajectory_vjp_matches_oracle(B):
     from paper_2302_02474_gb300.trajectory import gjf_trajectory_vjp
 
