@@ -317,6 +317,14 @@ def run_diff(args):
     t.init_velocities()
     t.step(args.warmup)
     t.synchronize()
+    if args.mode == "run":  # for profilers: --steps force vector-Jacobian products, nothing else
+        lam = torch.randn(spec.n_beads * 3, dtype=torch.float32, device="cuda")
+        out = torch.empty_like(lam)
+        for _ in range(args.steps):
+            t.force_vjp(lam, out=out)
+        torch.cuda.synchronize()
+        t.close()
+        return
     K = 200
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -373,7 +381,8 @@ def main():
                     help="batch256: 256 uneven replicas stepped with tild_batch_*; diff200k: derivatives through a "
                          "200-step GJF window (extra measurements)")
     ap.add_argument("--mode", default="bench", choices=["bench", "run"],
-                    help="run: set up, warm up and take --steps steps only (for profilers)")
+                    help="run: set up, warm up and take --steps steps only (for profilers; with diff200k, --steps "
+                         "force vector-Jacobian products)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
