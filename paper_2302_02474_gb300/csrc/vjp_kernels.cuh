@@ -187,6 +187,9 @@ __device__ __forceinline__ void z_vjp_tile(cplx_t<T>* buf, const cplx_t<T>* tw, 
     const T qxB = raw_k<T, N>(kxB, tp), qyB = raw_k<T, N>(ky[rB], tp);
     const T gxA = grad_k<T, N>(kxA, tp), gyA = grad_k<T, N>(ky[0], tp);
     const T gxB = grad_k<T, N>(kxB, tp), gyB = grad_k<T, N>(ky[rB], tp);
+    // per-thread partial sums in T (a few terms each; FP64 arithmetic is slow
+    // on this part), added to the FP64 block sums after the loop
+    T a0 = T(0), a1 = T(0), a2 = T(0);
     for (int kz = threadIdx.x / C; kz < N; kz += 256 / C) {
         const int kzB = kz == 0 ? 0 : N - kz;
         if (R == 1 && kzB * C + cB < kz * C + c) continue;  // the mirror element owns this pair
@@ -235,17 +238,18 @@ __device__ __forceinline__ void z_vjp_tile(cplx_t<T>* buf, const cplx_t<T>* tw, 
                 pB.y += cq * sp.qB * sq.y;
             }
             out[s] = {-(pA.y + pB.x), pA.x - pB.y};  // i (psi~_A + i psi~_B)
-            const double sar = sA.x, sai = sA.y, sbr = sB.x, sbi = sB.y;
-            const double ar = rA.x, ai = rA.y, br = rBv.x, bi = rBv.y, u = uh;
-            acc[0] += u * ((sar * br + sai * bi) + (sbr * ar + sbi * ai));
-            acc[1] += u * ((sar + sbr) * (ar + br) + (sai + sbi) * (ai + bi));
-            const double wAr = (double)sp.eAA * ar + (double)sp.eAB * br, wAi = (double)sp.eAA * ai + (double)sp.eAB * bi;
-            const double wBr = (double)sp.eAB * ar + (double)sp.eBB * br, wBi = (double)sp.eAB * ai + (double)sp.eBB * bi;
-            acc[2] += u * (double)k2 * ((sar * wAr + sai * wAi) + (sbr * wBr + sbi * wBi));
+            a0 += uh * ((sA.x * rBv.x + sA.y * rBv.y) + (sB.x * rA.x + sB.y * rA.y));
+            a1 += uh * ((sA.x + sB.x) * (rA.x + rBv.x) + (sA.y + sB.y) * (rA.y + rBv.y));
+            const T wAr = sp.eAA * rA.x + sp.eAB * rBv.x, wAi = sp.eAA * rA.y + sp.eAB * rBv.y;
+            const T wBr = sp.eAB * rA.x + sp.eBB * rBv.x, wBi = sp.eAB * rA.y + sp.eBB * rBv.y;
+            a2 += uh * k2 * ((sA.x * wAr + sA.y * wAi) + (sB.x * wBr + sB.y * wBi));
         }
         buf[kz * C + c] = out[0];
         if (!same) buf[rB * TS + kzB * C + cB] = out[1];
     }
+    acc[0] += (double)a0;
+    acc[1] += (double)a1;
+    acc[2] += (double)a2;
     __syncthreads();
     smem_fft_lines<N, +1, R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
 }
