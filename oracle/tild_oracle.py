@@ -720,3 +720,67 @@ def gjf_trajectory_vjp(m: Model, pos0: np.ndarray, vel0: np.ndarray, n_steps: in
     for k in tb:
         tb[k] += v[k]
     return {"r0": rb + v["r"], "v0": vb, **tb}
+
+
+
+def em_trajectory_vjp(m: Model, pos0: np.ndarray, n_steps: int, r_bar: np.ndarray) -> Dict[str, object]:
+    """Reverse-mode derivative of L(r^K) through K Euler-Maruyama steps (noise
+    held fixed), given dL/dr^K = r_bar. One step is
+      r' = r + (dt/alpha) F(r) + sqrt(2 kT dt/alpha) xi,
+    so its adjoint is rb = rb' + J(r)^T ((dt/alpha) rb'), and the parameters
+    collect (dF/dtheta)(r)^T ((dt/alpha) rb') at r^0 .. r^{K-1}. There is no
+    velocity: dL/dv^0 is zero."""
+    c = m.dt / m.friction
+    st = em_initial_state(m, pos0)
+    traj = [st]
+    for _ in range(n_steps):
+        st = em_step(m, st)
+        traj.append(st)
+    rb = r_bar.copy()
+    tb = {"chi": 0.0, "kappa": 0.0, "a": 0.0}
+    for n in range(n_steps - 1, -1, -1):
+        v = force_vjp(m, traj[n].pos, c * rb)
+        for k in tb:
+            tb[k] += v[k]
+        rb = rb + v["r"]
+    return {"r0": rb, "v0": np.zeros_like(rb), **tb}
+
+
+def vv_trajectory_vjp(m: Model, pos0: np.ndarray, vel0: np.ndarray, n_steps: int, r_bar: np.ndarray,
+                      v_bar: Optional[np.ndarray] = None) -> Dict[str, object]:
+    """Reverse-mode derivative of L(r^K, v^K) through K velocity-Verlet steps
+    with the Langevin force (noise held fixed), given dL/dr^K = r_bar and
+    dL/dv^K = v_bar. One step (see vv_step) maps (r, v, F) to (r', v', F'):
+      vh = v + h F,  r' = r + dt vh,  F' = F_c(r') - alpha vh + s xi',
+      v' = vh + h F',   h = dt/2m,
+    so its adjoint is
+      Fb'_tot = Fb' + h vb',  rb'_tot = rb' + J_c(r')^T Fb'_tot,
+      vhb = vb' - alpha Fb'_tot + dt rb'_tot,  rb = rb'_tot,  vb = vhb,  Fb = h vhb.
+    The initial force (see vv_initial_state) is
+      F^0 = (F_c(r^0) - alpha v^0) / (1 - alpha h) + (terms in the noise),
+    which closes the chain at r^0 with weight q = 1/(1 - alpha h). The
+    parameters collect (dF_c/dtheta)^T of the same adjoint vectors."""
+    h = m.dt / (2.0 * m.mass)
+    al = m.friction
+    st = vv_initial_state(m, pos0, vel0)
+    traj = [st]
+    for _ in range(n_steps):
+        st = vv_step(m, st)
+        traj.append(st)
+    rb = r_bar.copy()
+    vb = np.zeros_like(rb) if v_bar is None else v_bar.copy()
+    fb = np.zeros_like(rb)
+    tb = {"chi": 0.0, "kappa": 0.0, "a": 0.0}
+    for n in range(n_steps, 0, -1):
+        ft = fb + h * vb
+        v = force_vjp(m, traj[n].pos, ft)
+        for k in tb:
+            tb[k] += v[k]
+        rt = rb + v["r"]
+        vhb = vb - al * ft + m.dt * rt
+        rb, vb, fb = rt, vhb, h * vhb
+    q = 1.0 / (1.0 - al * h)
+    v = force_vjp(m, traj[0].pos, q * fb)
+    for k in tb:
+        tb[k] += v[k]
+    return {"r0": rb + v["r"], "v0": vb - al * q * fb, **tb}

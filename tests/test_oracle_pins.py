@@ -631,3 +631,86 @@ def test_gjf_trajectory_vjp_matches_finite_differences():
         vp[i, d] += h
         vm[i, d] -= h
         assert (loss(m, pos, vp) - loss(m, pos, vm)) / (2 * h) == pytest.approx(g["v0"][i, d], rel=1e-5, abs=1e-9)
+
+
+def _fd_trajectory_pins(m, pos, vel, g, loss, check_v0=True):
+    """Central differences of `loss(model, pos, vel)` against the reverse-mode
+    derivatives g (chi, kappa, a, two initial positions and velocities)."""
+    import dataclasses
+
+    h = 1e-6
+    for name in ("chi", "kappa", "a"):
+        mp, mm_ = dataclasses.replace(m), dataclasses.replace(m)
+        if name == "chi":
+            mp.chi, mm_.chi = m.chi + h * np.array([[0, 1], [1, 0]]), m.chi - h * np.array([[0, 1], [1, 0]])
+        else:
+            setattr(mp, name, getattr(m, name) + h)
+            setattr(mm_, name, getattr(m, name) - h)
+        fd = (loss(mp, pos, vel) - loss(mm_, pos, vel)) / (2 * h)
+        assert fd == pytest.approx(g[name], rel=1e-5, abs=1e-9), name
+    for i, d in ((0, 1), (7, 2)):
+        pp, pm = pos.copy(), pos.copy()
+        pp[i, d] += h
+        pm[i, d] -= h
+        assert (loss(m, pp, vel) - loss(m, pm, vel)) / (2 * h) == pytest.approx(g["r0"][i, d], rel=1e-5, abs=1e-9)
+        if check_v0:
+            vp, vm = vel.copy(), vel.copy()
+            vp[i, d] += h
+            vm[i, d] -= h
+            assert (loss(m, pos, vp) - loss(m, pos, vm)) / (2 * h) == pytest.approx(g["v0"][i, d], rel=1e-5, abs=1e-9)
+
+
+def test_em_trajectory_vjp_matches_finite_differences():
+    """Reverse-mode derivatives of L = sum w . r^K after K Euler-Maruyama
+    steps (noise fixed) equal central differences of L with respect to chi,
+    kappa, a and initial positions; dL/dv^0 is zero (no velocity)."""
+    m, pos = _model(P=2, n_chains=4, N=4, n_a=2, L=4.0, n=8, a=0.6, dt=0.01, friction=2.0)
+    K = 6
+    w = np.random.default_rng(10).normal(size=pos.shape)
+    g = O.em_trajectory_vjp(m, pos, K, w)
+    assert not np.any(g["v0"])
+
+    def loss(mm, p, v):
+        st = O.run_with(O.em_step, mm, O.em_initial_state(mm, p), K)
+        r0 = O.wrap(pos, mm.L)
+        return float(np.sum(w * (r0 + O.minimum_image(st.pos - r0, mm.L))))
+
+    _fd_trajectory_pins(m, pos, np.zeros_like(pos), g, loss, check_v0=False)
+
+
+def test_vv_trajectory_vjp_matches_finite_differences():
+    """Reverse-mode derivatives of L = sum w . r^K + sum u . v^K after K
+    velocity-Verlet steps with the Langevin force (noise fixed) equal central
+    differences of L with respect to chi, kappa, a, initial positions and
+    initial velocities."""
+    m, pos = _model(P=2, n_chains=4, N=4, n_a=2, L=4.0, n=8, a=0.6, dt=0.02, friction=0.7)
+    vel = O.initial_state(m, pos).vel
+    K = 6
+    rng = np.random.default_rng(11)
+    w, u = rng.normal(size=pos.shape), rng.normal(size=pos.shape)
+    g = O.vv_trajectory_vjp(m, pos, vel, K, w, u)
+
+    def loss(mm, p, v):
+        st = O.run_with(O.vv_step, mm, O.vv_initial_state(mm, p, v), K)
+        r0 = O.wrap(pos, mm.L)
+        return float(np.sum(w * (r0 + O.minimum_image(st.pos - r0, mm.L))) + np.sum(u * st.vel))
+
+    _fd_trajectory_pins(m, pos, vel, g, loss)
+
+
+def test_gjf_trajectory_vjp_with_velocity_loss_matches_finite_differences():
+    """As the GJF pin above, with a velocity term in the loss:
+    L = sum w . r^K + sum u . v^K."""
+    m, pos = _model(P=2, n_chains=4, N=4, n_a=2, L=4.0, n=8, a=0.6, dt=0.02)
+    vel = O.initial_state(m, pos).vel
+    K = 5
+    rng = np.random.default_rng(12)
+    w, u = rng.normal(size=pos.shape), rng.normal(size=pos.shape)
+    g = O.gjf_trajectory_vjp(m, pos, vel, K, w, u)
+
+    def loss(mm, p, v):
+        st = O.run(mm, O.State(O.wrap(p, mm.L), v, O.forces(mm, O.wrap(p, mm.L)), 0), K)
+        r0 = O.wrap(pos, mm.L)
+        return float(np.sum(w * (r0 + O.minimum_image(st.pos - r0, mm.L))) + np.sum(u * st.vel))
+
+    _fd_trajectory_pins(m, pos, vel, g, loss)
