@@ -306,7 +306,7 @@ def run_diff(args):
 
     from paper_2302_02474_gb300 import binding as B
     from paper_2302_02474_gb300 import inputs as I
-    from paper_2302_02474_gb300.trajectory import gjf_trajectory_vjp
+    from paper_2302_02474_gb300.trajectory import trajectory_vjp
 
     torch.cuda.set_device(0)
     spec = I.config("diblock_200k_64")
@@ -333,10 +333,10 @@ def run_diff(args):
     e1.synchronize()
     plain_ms = e0.elapsed_time(e1) / K
     w = np.random.default_rng(1).normal(size=(spec.n_beads, 3))
-    gjf_trajectory_vjp(t, 20, w, checkpoint_every=20)  # warm-up of the reverse path
+    trajectory_vjp(t, 20, w, checkpoint_every=20)  # warm-up of the reverse path
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g = gjf_trajectory_vjp(t, K, w, checkpoint_every=20)
+    g = trajectory_vjp(t, K, w, checkpoint_every=20)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -271,7 +271,7 @@ tild_status tild_energy_gradient(tild_ctx* ctx, tild_energy_grad* g, void* dU_dr
  * force of Eq. bonds (charges included) at the current positions. dtheta
  * (NULL to skip) receives d(sum_i lam_i . F_i)/d(chi, kappa, a). Chained
  * through the integrator this gives derivatives of trajectories
- * (tild_gjf_trajectory_vjp). lam is spread onto the grid in 64-bit fixed
+ * (tild_trajectory_vjp). lam is spread onto the grid in 64-bit fixed
  * point with a power-of-two scale taken from max|lam|, so the result is
  * bitwise reproducible and exactly homogeneous under power-of-two scaling of
  * lam; a non-finite lam makes every output NaN. Returns
@@ -279,20 +279,25 @@ tild_status tild_energy_gradient(tild_ctx* ctx, tild_energy_grad* g, void* dU_dr
  * planes do not fit one CTA (FP32 above 128^3, FP64 above 64^3). */
 tild_status tild_force_vjp(tild_ctx* ctx, const void* lam, void* out, int dtype, int where, double* dtheta);
 
-/* Derivatives through a trajectory (differentiable form): runs n_steps GJF
- * steps (TILD_SCHEME_GJF, TILD_FORCE_IK) and returns the derivatives of a
- * loss L(r^K, v^K) with respect to r^0 (r0_bar), v^0 (v0_bar) and, in
- * dtheta (NULL to skip), chi, kappa and a, given dL/dr^K = r_bar and
- * dL/dv^K = v_bar (NULL: 0). The thermal noise is held fixed (the same
- * Philox counters). Reverse mode recomputes the states of each segment of
- * checkpoint_every steps from a device checkpoint (bit-identical) and takes
- * one force vector-Jacobian product per step; the adjoint vectors are FP64.
- * All arrays are [n_beads][3] by bead id in dtype/where. The context ends at
- * step n_steps. Allocates (n_steps/checkpoint_every + checkpoint_every + 1)
- * states of device scratch, kept with the context. */
-tild_status tild_gjf_trajectory_vjp(tild_ctx* ctx, int64_t n_steps, int checkpoint_every, const void* r_bar,
-                                   const void* v_bar, int dtype, int where, void* r0_bar, void* v0_bar,
-                                   double* dtheta);
+/* Derivatives through a trajectory (differentiable form): runs n_steps
+ * steps of the context's integrator scheme (GJF, EM or VV; TILD_FORCE_IK)
+ * and returns the derivatives of a loss L(r^K, v^K) with respect to r^0
+ * (r0_bar), v^0 (v0_bar) and, in dtheta (NULL to skip), chi, kappa and a,
+ * given dL/dr^K = r_bar and dL/dv^K = v_bar (NULL: 0). The thermal noise is
+ * held fixed (the same Philox counters). Every scheme advances the state
+ * (r, u) in one linear form,
+ *   h = su u + sf F(r) + sg xi,  r' = r + sd h + se xi,  u' = sh h + sk xi,
+ * with v = vu u + vf F + vg xi and u^0 = wu v^0 + wf F(r^0) + wg xi, so the
+ * reverse sweep is hb = sd rb' + sh ub', ub = su hb, rb = rb' + J^T(sf hb)
+ * for every scheme (EM has no velocity: v0_bar is 0). Reverse mode
+ * recomputes the states of each segment of checkpoint_every steps from a
+ * device checkpoint (bit-identical) and takes one force vector-Jacobian
+ * product per state; the adjoint vectors are FP64. All arrays are
+ * [n_beads][3] by bead id in dtype/where. The context ends at step n_steps.
+ * Allocates (n_steps/checkpoint_every + checkpoint_every + 1) states of
+ * device scratch, kept with the context. */
+tild_status tild_trajectory_vjp(tild_ctx* ctx, int64_t n_steps, int checkpoint_every, const void* r_bar,
+                                const void* v_bar, int dtype, int where, void* r0_bar, void* v0_bar, double* dtheta);
 
 /* Current positions (wrapped into [0, L)), [n_beads][3]. */
 tild_status tild_get_positions(tild_ctx* ctx, void* out, int dtype, int where);

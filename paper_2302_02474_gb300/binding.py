@@ -66,7 +66,7 @@ _SIGS = {
     "tild_set_electrostatics": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
     "tild_force_vjp": [_P, _P, _P, _I, _I, ctypes.POINTER(ctypes.c_double)],
     "tild_autotune": [_P, _I64, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
-    "tild_gjf_trajectory_vjp": [_P, _I64, _I, _P, _P, _I, _I, _P, _P, ctypes.POINTER(ctypes.c_double)],
+    "tild_trajectory_vjp": [_P, _I64, _I, _P, _P, _I, _I, _P, _P, ctypes.POINTER(ctypes.c_double)],
     "tild_set_stream": [_P, _P],
     "tild_set_positions": [_P, _P, _I, _I],
     "tild_init_velocities": [_P],

@@ -343,12 +343,12 @@ tild_status tild_profile_steps(tild_ctx* c, int n_steps, double* ms) {
     return from_engine(c, c->eng->profile(n_steps, ms));
 }
 
-tild_status tild_gjf_trajectory_vjp(tild_ctx* c, int64_t n_steps, int checkpoint_every, const void* r_bar,
-                                   const void* v_bar, int dtype, int where, void* r0_bar, void* v0_bar, double* dtheta) {
+tild_status tild_trajectory_vjp(tild_ctx* c, int64_t n_steps, int checkpoint_every, const void* r_bar,
+                                const void* v_bar, int dtype, int where, void* r0_bar, void* v0_bar, double* dtheta) {
     if (!c) return TILD_EINVAL;
     if (n_steps < 0 || checkpoint_every < 1 || !r_bar || !r0_bar || !v0_bar || !valid_io(dtype, where))
-        return fail(c, TILD_EINVAL, "gjf_trajectory_vjp: bad argument");
-    if (!c->eng->has_velocities()) return fail(c, TILD_ESTATE, "gjf_trajectory_vjp: positions and velocities must be set");
+        return fail(c, TILD_EINVAL, "trajectory_vjp: bad argument");
+    if (!c->eng->has_velocities()) return fail(c, TILD_ESTATE, "trajectory_vjp: positions and velocities must be set");
     return from_engine(c, c->eng->trajectory_vjp(n_steps, checkpoint_every, r_bar, v_bar, dtype, where, r0_bar, v0_bar,
                                                  dtheta));
 }

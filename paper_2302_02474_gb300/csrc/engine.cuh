@@ -409,17 +409,14 @@ template <typename T> class Engine final : public EngineBase {
         return TILD_OK;
     }
 
-    // Reverse-mode derivatives of L(r^K, v^K) through K GJF steps with the
-    // noise held fixed, checkpoints every C steps (see trajectory.py for the
-    // adjoint recursion); leaves the context at step K.
+    // Reverse-mode derivatives of L(r^K, v^K) through K steps of the context's
+    // scheme with the noise held fixed, checkpoints every C steps; the
+    // recursion is that of the scheme's update form (scheme_coeffs; the
+    // kernels adjoint_init and adjoint_step). Leaves the context at step K.
     tild_status trajectory_vjp(int64_t K, int C, const void* rbar, const void* vbar, int dtype, int where, void* r0,
                                void* v0, double* dtheta) override {
         tild_status st;
         if ((st = vjp_prepare())) return st;
-        if (cfg_->scheme != kSchemeGJF) {
-            err = "trajectory_vjp: implemented for the GJF scheme";
-            return TILD_EUNSUPPORTED;
-        }
         const size_t N = cfg_->n_beads, n3 = 3 * N, sb = 6 * N;  // one state: sb values of T
         const int64_t n_ckpt = K / C + 1;
         const size_t need = sizeof(T) * (sb * ((size_t)n_ckpt + (size_t)C + 1) + 2 * n3) + sizeof(double) * (3 * n3 + 3) + 8;
@@ -430,12 +427,10 @@ template <typename T> class Engine final : public EngineBase {
         T* lam = fin + sb;                          // [n3]
         T* jt = lam + n3;                           // [n3]
         double* rb = (double*)(((uintptr_t)(jt + n3) + 7) & ~(uintptr_t)7);  // 8-byte aligned
-        double* vb = rb + n3;
-        double* fb = vb + n3;
-        double* acc = fb + n3;
-        const double dt = cfg_->dt, m = cfg_->mass, al = cfg_->friction;
-        const double h = dt / (2.0 * m), ga = (1.0 - al * h) / (1.0 + al * h), gb = 1.0 / (1.0 + al * h);
-        const double c1 = gb * dt, c2 = gb * dt * dt / (2.0 * m);
+        double* ub = rb + n3;  // dL/dv^K on entry, then the adjoint of u
+        double* vout = ub + n3;
+        double* acc = vout + n3;
+        const SchemeCoeffs q = scheme_coeffs(*cfg_);
         const int64_t step0 = host_step_;
         // forward with checkpoints
         store_state(ckpt);
@@ -455,16 +450,14 @@ template <typename T> class Engine final : public EngineBase {
             src = vbar;
             if ((st = stage_in(&src, vbar, n3, dtype, where))) return st;
             if (dtype == TILD_DTYPE_F32)
-                convert_copy<float, double><<<blocks(n3), 256, 0, stream_>>>(n3, (const float*)src, vb);
+                convert_copy<float, double><<<blocks(n3), 256, 0, stream_>>>(n3, (const float*)src, ub);
             else
-                convert_copy<double, double><<<blocks(n3), 256, 0, stream_>>>(n3, (const double*)src, vb);
+                convert_copy<double, double><<<blocks(n3), 256, 0, stream_>>>(n3, (const double*)src, ub);
         } else {
-            TILD_CUDA(cudaMemsetAsync(vb, 0, n3 * sizeof(double), stream_));
+            TILD_CUDA(cudaMemsetAsync(ub, 0, n3 * sizeof(double), stream_));
         }
-        TILD_CUDA(cudaMemsetAsync(fb, 0, n3 * sizeof(double), stream_));
         TILD_CUDA(cudaMemsetAsync(acc, 0, 3 * sizeof(double), stream_));
-        // lam = fb + h vb for the last step
-        scale_copy<T><<<blocks(n3), 256, 0, stream_>>>(n3, vb, h, lam);
+        adjoint_init<T><<<blocks(n3), 256, 0, stream_>>>(n3, ub, lam, q.vu, q.vf, q.wf, K == 0 ? 1 : 0);
         TILD_CUDA(cudaGetLastError());
         for (int64_t s0 = ((K - 1) / C) * C; K > 0 && s0 >= 0; s0 -= C) {
             const int64_t s1 = std::min<int64_t>(s0 + C, K);
@@ -476,17 +469,19 @@ template <typename T> class Engine final : public EngineBase {
             for (int64_t j = s1 - 1; j >= s0; --j) {
                 if ((st = restore_state(seg + sb * (j - s0), step0 + j + 1))) return st;
                 if ((st = vjp_core(lam, jt, acc))) return st;
-                adjoint_gjf_step<T><<<blocks(n3), 256, 0, stream_>>>(n3, jt, rb, vb, fb, lam, c1, c2, h, ga, j == 0 ? 1 : 0);
+                adjoint_step<T><<<blocks(n3), 256, 0, stream_>>>(n3, jt, rb, ub, lam, q.sd, q.sh, q.su, q.sf, q.wf,
+                                                                  j == 0 ? 1 : 0);
                 TILD_CUDA(cudaGetLastError());
             }
         }
-        if (K == 0) scale_copy<T><<<blocks(n3), 256, 0, stream_>>>(n3, fb, 1.0, lam);
-        // the force at r^0
+        // the force at r^0; dL/dv^0 = wu ub
         if ((st = restore_state(ckpt, step0)) || (st = vjp_core(lam, jt, acc))) return st;
         add_into<T><<<blocks(n3), 256, 0, stream_>>>(n3, rb, jt, rb);
+        scale_copy<double><<<blocks(n3), 256, 0, stream_>>>(n3, ub, q.wu, vout);
         TILD_CUDA(cudaGetLastError());
         if ((st = restore_state(fin, step0 + K))) return st;
-        if ((st = stage_out_double(rb, n3, r0, dtype, where)) || (st = stage_out_double(vb, n3, v0, dtype, where))) return st;
+        if ((st = stage_out_double(rb, n3, r0, dtype, where)) || (st = stage_out_double(vout, n3, v0, dtype, where)))
+            return st;
         double s[3];
         TILD_CUDA(cudaMemcpyAsync(s, acc, sizeof(s), cudaMemcpyDeviceToHost, stream_));
         TILD_CUDA(cudaStreamSynchronize(stream_));
@@ -1135,43 +1130,54 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     // Constants of the integrator update (see BeadParams), from FP64.
-    static void integrator_constants(const HostConfig& c, BeadParams<T>& p) {
+    // The update of every scheme in one form (state: positions r and carried
+    // velocity u; F = F(r); xi the step's normals):
+    //   h = su u + sf F + sg xi,  r' = r + sd h + se xi,  u' = sh h + sk xi,
+    // the velocity of a state v = vu u + vf F + vg xi, and u from (r, v):
+    // u = wu v + wf F + wg xi.
+    struct SchemeCoeffs {
+        double su, sf, sg, sd, se, sh, sk, vu, vf, vg, wu, wf, wg;
+        int lag;
+    };
+    static SchemeCoeffs scheme_coeffs(const HostConfig& c) {
         const double dt = c.dt, m = c.mass, al = c.friction, kT = c.kT;
         const double hdm = dt / (2.0 * m);
-        double su = 1, sf = 2 * hdm, sg = 0, sd = dt, se = 0, sh = 1, sk = 0;
-        double vu = 1, vf = hdm, vg = 0, wu = 1, wf = -hdm, wg = 0;
-        int lag = 0;
+        SchemeCoeffs k{1, 2 * hdm, 0, dt, 0, 1, 0, 1, hdm, 0, 1, -hdm, 0, 0};
         if (c.scheme == kSchemeGJF) {
             // GJF: a = (1 - alpha dt/2m)/(1 + alpha dt/2m), b = 1/(1 + alpha dt/2m), beta = sigma xi
             const double den = 1.0 + al * hdm, ga = (1.0 - al * hdm) / den, gb = 1.0 / den;
             const double sb = std::sqrt(2.0 * al * kT * dt);
-            sd = gb * dt;
-            se = gb * dt * sb / (2.0 * m);
-            sh = ga;
-            sk = gb * sb / m;
+            k.sd = gb * dt;
+            k.se = gb * dt * sb / (2.0 * m);
+            k.sh = ga;
+            k.sk = gb * sb / m;
         } else if (c.scheme == kSchemeEM) {
             // r' = r + (dt/alpha) F + sqrt(2 kT dt/alpha) xi; no velocity
-            su = 0;
-            sf = al > 0 ? dt / al : 0;
-            sg = al > 0 ? std::sqrt(2.0 * kT * dt / al) : 0;
-            sd = 1;
-            sh = 0;
-            vu = vf = wu = wf = 0;
+            k.su = 0;
+            k.sf = al > 0 ? dt / al : 0;
+            k.sg = al > 0 ? std::sqrt(2.0 * kT * dt / al) : 0;
+            k.sd = 1;
+            k.sh = 0;
+            k.vu = k.vf = k.wu = k.wf = 0;
         } else {
             // VV: F = F_c - alpha u + s xi^n (s = sqrt(2 alpha kT/dt)), h = u + (dt/m) F
-            const double s = std::sqrt(2.0 * al * kT / dt), inv = 1.0 / (1.0 - al * hdm);
-            su = 1.0 - 2.0 * hdm * al;
-            sg = 2.0 * hdm * s;
-            lag = 1;
-            vu = 1.0 - hdm * al;
-            vg = hdm * s;
-            wu = inv;
-            wf = -inv * hdm;
-            wg = -inv * hdm * s;
+            const double sv = std::sqrt(2.0 * al * kT / dt), inv = 1.0 / (1.0 - al * hdm);
+            k.su = 1.0 - 2.0 * hdm * al;
+            k.sg = 2.0 * hdm * sv;
+            k.lag = 1;
+            k.vu = 1.0 - hdm * al;
+            k.vg = hdm * sv;
+            k.wu = inv;
+            k.wf = -inv * hdm;
+            k.wg = -inv * hdm * sv;
         }
-        p.su = (T)su; p.sf = (T)sf; p.sg = (T)sg; p.sd = (T)sd; p.se = (T)se; p.sh = (T)sh; p.sk = (T)sk;
-        p.vu = (T)vu; p.vf = (T)vf; p.vg = (T)vg; p.wu = (T)wu; p.wf = (T)wf; p.wg = (T)wg;
-        p.noise_lag = lag;
+        return k;
+    }
+    static void integrator_constants(const HostConfig& c, BeadParams<T>& p) {
+        const SchemeCoeffs k = scheme_coeffs(c);
+        p.su = (T)k.su; p.sf = (T)k.sf; p.sg = (T)k.sg; p.sd = (T)k.sd; p.se = (T)k.se; p.sh = (T)k.sh; p.sk = (T)k.sk;
+        p.vu = (T)k.vu; p.vf = (T)k.vf; p.vg = (T)k.vg; p.wu = (T)k.wu; p.wf = (T)k.wf; p.wg = (T)k.wg;
+        p.noise_lag = k.lag;
     }
 
     BeadParams<T> bead_params() const {

@@ -392,22 +392,38 @@ static __global__ void __launch_bounds__(256) accumulate_partials(const double* 
     if (threadIdx.x < 3) acc[threadIdx.x] += s[threadIdx.x][0];
 }
 
-// One reverse GJF step on the adjoint vectors (FP64, [3N] by bead id):
-//   rt = rb + J^T lam;  rb = rt;  vb <- c1 rt + ga vb;  fb <- c2 rt + h ga vb;
-// and the next adjoint vector lam = fb + h vb (or fb alone for the force at r^0).
+// Reverse sweep through K steps of the update shared by every scheme
+// (state: positions r and carried velocity u; F = F(r); xi fixed normals):
+//   h = su u + sf F + sg xi,   r' = r + sd h + se xi,   u' = sh h + sk xi,
+// with the velocity of a state v = vu u + vf F + vg xi and the initial
+// u^0 = wu v^0 + wf F(r^0) + wg xi. Adjoint vectors rb, ub (FP64) belong to
+// the state being left; lam is the adjoint of F at the next state reached.
+//
+// Start (state K): ub = vu vb (vb = dL/dv^K), lam = vf vb, plus wf ub when
+// K = 0 (then r^0 also enters through u^0).
 template <typename T>
-__global__ void adjoint_gjf_step(size_t n3, const T* __restrict__ jt, double* __restrict__ rb, double* __restrict__ vb,
-                                 double* __restrict__ fb, T* __restrict__ lam_next, double c1, double c2, double h,
-                                 double ga, int last) {
+__global__ void adjoint_init(size_t n3, double* __restrict__ ub, T* __restrict__ lam, double vu, double vf, double wf,
+                             int at_start) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n3) return;
-    const double rt = rb[i] + (double)jt[i];
-    const double v = vb[i];
-    const double vn = c1 * rt + ga * v, fn = c2 * rt + h * ga * v;
-    rb[i] = rt;
-    vb[i] = vn;
-    fb[i] = fn;
-    lam_next[i] = (T)(last ? fn : fn + h * vn);
+    const double v = ub[i], u = vu * v;
+    ub[i] = u;
+    lam[i] = (T)(vf * v + (at_start ? wf * u : 0.0));
+}
+
+// One step back, from state j+1 to state j, after the force VJP at r^{j+1}
+// (jt = J^T lam):  rb += jt;  hb = sd rb + sh ub;  ub = su hb;
+// lam = sf hb (+ wf ub when j = 0), the adjoint of F(r^j).
+template <typename T>
+__global__ void adjoint_step(size_t n3, const T* __restrict__ jt, double* __restrict__ rb, double* __restrict__ ub,
+                             T* __restrict__ lam, double sd, double sh, double su, double sf, double wf, int at_start) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const double r = rb[i] + (double)jt[i];
+    const double hb = sd * r + sh * ub[i], u = su * hb;
+    rb[i] = r;
+    ub[i] = u;
+    lam[i] = (T)(sf * hb + (at_start ? wf * u : 0.0));
 }
 
 // y = (T)(a x)

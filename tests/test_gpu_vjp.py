@@ -1,7 +1,8 @@
 """Differentiable form on the GPU: the force vector-Jacobian product
-(tild_force_vjp) and derivatives through GJF trajectories with checkpoints,
-against the oracle's force_vjp and gjf_trajectory_vjp (themselves pinned by
-finite differences)."""
+(tild_force_vjp) and derivatives through GJF, Euler-Maruyama and
+velocity-Verlet trajectories with checkpoints (tild_trajectory_vjp), against
+the oracle's force_vjp and its per-scheme trajectory adjoints (themselves
+pinned by finite differences)."""
 import numpy as np
 import pytest
 
@@ -87,25 +88,51 @@ def test_force_vjp_non_finite_lam_gives_nan(B):
     assert np.isfinite(got).all()
 
 
-def test_trajectory_vjp_matches_oracle(B):
-    from paper_2302_02474_gb300.trajectory import gjf_trajectory_vjp
+@pytest.mark.parametrize("scheme", ["gjf", "em", "vv"])
+def test_trajectory_vjp_matches_oracle(B, scheme):
+    """Derivatives through 7 steps of each scheme (checkpoints every 3)
+    against the oracle's reverse sweep for that scheme, with a velocity term
+    in the loss where the scheme has velocities; K = 0 is the identity."""
+    from paper_2302_02474_gb300.trajectory import trajectory_vjp
 
+    friction = {"gjf": 1.0, "em": 2.0, "vv": 0.7}[scheme]
     spec = I.small_system(n_chains=40, N=10, n_a=4, L=7.0, n=16, pmeorder=1, precision="fp64", chi=1.0, kappa=6.0,
-                          dt=0.01)
-    t, m, pos = _setup(B, spec)
+                          dt=0.01, friction=friction)
+    pos = I.initial_positions(spec)
+    t = B.Tild.from_spec(spec, sort_every=3)
+    t.set_scheme(scheme)
+    t.set_positions(pos)
+    m = O.model_from_spec(spec, I.species_of_beads(spec.moltypes), I.bond_pairs(spec.moltypes))
     t.init_velocities()
     vel0 = O.initial_state(m, pos).vel
     K = 7
-    w = np.random.default_rng(5).normal(size=pos.shape)
-    g = gjf_trajectory_vjp(t, K, w, checkpoint_every=3)
-    ref = O.gjf_trajectory_vjp(m, pos, vel0, K, w)
+    rng = np.random.default_rng(5)
+    w = rng.normal(size=pos.shape)
+    u = None if scheme == "em" else rng.normal(size=pos.shape)
+    g = trajectory_vjp(t, K, w, u, checkpoint_every=3)
+    if scheme == "gjf":
+        ref = O.gjf_trajectory_vjp(m, pos, vel0, K, w, u)
+        st = O.run(m, O.initial_state(m, pos), K)
+    elif scheme == "em":
+        ref = O.em_trajectory_vjp(m, pos, K, w)
+        st = O.run_with(O.em_step, m, O.em_initial_state(m, pos), K)
+    else:
+        ref = O.vv_trajectory_vjp(m, pos, vel0, K, w, u)
+        st = O.run_with(O.vv_step, m, O.vv_initial_state(m, pos, vel0), K)
     assert t.step_count() == K
-    st = O.run(m, O.initial_state(m, pos), K)
     assert np.abs(O.minimum_image(t.positions() - st.pos, m.L)).max() < 1e-10
     assert _rel(g["r0"], ref["r0"]) < 1e-9
-    assert _rel(g["v0"], ref["v0"]) < 1e-9
+    if scheme == "em":
+        assert not np.any(g["v0"])
+    else:
+        assert _rel(g["v0"], ref["v0"]) < 1e-9
     for k in ("chi", "kappa", "a"):
         assert g[k] == pytest.approx(ref[k], rel=1e-9), k
+    g0 = trajectory_vjp(t, 0, w, u)
+    assert t.step_count() == K
+    assert np.allclose(g0["r0"], w, rtol=0, atol=1e-12)
+    if u is not None:
+        assert np.allclose(g0["v0"], u, rtol=0, atol=1e-12)
 
 
 def test_force_vjp_needs_the_ik_force(B):
