@@ -291,11 +291,14 @@ tild_status tild_force_vjp(tild_ctx* ctx, const void* lam, void* out, int dtype,
  * reverse sweep is hb = sd rb' + sh ub', ub = su hb, rb = rb' + J^T(sf hb)
  * for every scheme (EM has no velocity: v0_bar is 0). Reverse mode
  * recomputes the states of each segment of checkpoint_every steps from a
- * device checkpoint (bit-identical) and takes one force vector-Jacobian
- * product per state; the adjoint vectors are FP64. All arrays are
- * [n_beads][3] by bead id in dtype/where. The context ends at step n_steps.
- * Allocates (n_steps/checkpoint_every + checkpoint_every + 1) states of
- * device scratch, kept with the context. */
+ * device checkpoint (bit-identical), keeps each recomputed state binned as
+ * it was (positions in slot order, slot arrays and the density grid, so no
+ * re-binning before its VJP) and takes one force vector-Jacobian product per
+ * state; the adjoint vectors are FP64. All arrays are [n_beads][3] by bead
+ * id in dtype/where. The context ends at step n_steps. Device scratch, kept
+ * with the context: n_steps/checkpoint_every + 2 states and
+ * checkpoint_every binned snapshots (3N values, 3N ints and 2 n^3 64-bit
+ * grid points each). */
 tild_status tild_trajectory_vjp(tild_ctx* ctx, int64_t n_steps, int checkpoint_every, const void* r_bar,
                                 const void* v_bar, int dtype, int where, void* r0_bar, void* v0_bar, double* dtheta);
 

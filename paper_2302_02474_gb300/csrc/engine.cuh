@@ -409,6 +409,42 @@ template <typename T> class Engine final : public EngineBase {
         return TILD_OK;
     }
 
+    // A binned snapshot of the current positions, what the force VJP reads:
+    // positions in slot order, slot tags, neighbour slots, tile starts and the
+    // fixed-point density of those positions (after a step it holds the
+    // spread of the new positions). Restoring one needs no re-binning.
+    static size_t snap_part(size_t b) { return (b + 255) / 256 * 256; }
+    void snapshot_parts(void* (&ptr)[5], size_t (&bytes)[5]) {
+        const size_t N = cfg_->n_beads;
+        void* p[5] = {pos_[cur_pos_], id_[cur_id_], nbr_, tile_start_, rho_fx_};
+        const size_t b[5] = {3 * N * sizeof(T), N * sizeof(int), N * sizeof(int2), (n_tiles_ + 1) * sizeof(int),
+                             2 * M_ * sizeof(unsigned long long)};
+        for (int k = 0; k < 5; ++k) {
+            ptr[k] = p[k];
+            bytes[k] = b[k];
+        }
+    }
+    size_t snapshot_bytes() {
+        void* p[5];
+        size_t b[5], total = 0;
+        snapshot_parts(p, b);
+        for (int k = 0; k < 5; ++k) total += snap_part(b[k]);
+        return total;
+    }
+    tild_status snapshot(unsigned char* s, bool store) {
+        void* p[5];
+        size_t b[5];
+        snapshot_parts(p, b);
+        for (int k = 0; k < 5; ++k) {
+            if (store)
+                TILD_CUDA(cudaMemcpyAsync(s, p[k], b[k], cudaMemcpyDeviceToDevice, stream_));
+            else
+                TILD_CUDA(cudaMemcpyAsync(p[k], s, b[k], cudaMemcpyDeviceToDevice, stream_));
+            s += snap_part(b[k]);
+        }
+        return TILD_OK;
+    }
+
     // Reverse-mode derivatives of L(r^K, v^K) through K steps of the context's
     // scheme with the noise held fixed, checkpoints every C steps; the
     // recursion is that of the scheme's update form (scheme_coeffs; the
@@ -419,14 +455,16 @@ template <typename T> class Engine final : public EngineBase {
         if ((st = vjp_prepare())) return st;
         const size_t N = cfg_->n_beads, n3 = 3 * N, sb = 6 * N;  // one state: sb values of T
         const int64_t n_ckpt = K / C + 1;
-        const size_t need = sizeof(T) * (sb * ((size_t)n_ckpt + (size_t)C + 1) + 2 * n3) + sizeof(double) * (3 * n3 + 3) + 8;
+        const size_t snap = snapshot_bytes();
+        const size_t head = snap_part(sizeof(T) * (sb * ((size_t)n_ckpt + 1) + 2 * n3));
+        const size_t need = head + snap * (size_t)C + sizeof(double) * (3 * n3 + 3);
         if ((st = device_buffer(&traj_, traj_bytes_, need))) return st;
-        T* ckpt = (T*)traj_;                        // [n_ckpt][sb]
-        T* seg = ckpt + sb * n_ckpt;                // [C][sb]
-        T* fin = seg + sb * C;                      // [sb]
+        T* ckpt = (T*)traj_;                        // [n_ckpt][sb] by id
+        T* fin = ckpt + sb * n_ckpt;                // [sb]
         T* lam = fin + sb;                          // [n3]
         T* jt = lam + n3;                           // [n3]
-        double* rb = (double*)(((uintptr_t)(jt + n3) + 7) & ~(uintptr_t)7);  // 8-byte aligned
+        unsigned char* seg = (unsigned char*)traj_ + head;  // [C] binned snapshots (256-byte aligned)
+        double* rb = (double*)(seg + snap * (size_t)C);
         double* ub = rb + n3;  // dL/dv^K on entry, then the adjoint of u
         double* vout = ub + n3;
         double* acc = vout + n3;
@@ -463,11 +501,11 @@ template <typename T> class Engine final : public EngineBase {
             const int64_t s1 = std::min<int64_t>(s0 + C, K);
             if ((st = restore_state(ckpt + sb * (s0 / C), step0 + s0))) return st;
             for (int64_t j = s0; j < s1; ++j) {
-                if ((st = step(1))) return st;
-                store_state(seg + sb * (j - s0));
+                if ((st = step(1)) || (st = snapshot(seg + snap * (size_t)(j - s0), true))) return st;
             }
             for (int64_t j = s1 - 1; j >= s0; --j) {
-                if ((st = restore_state(seg + sb * (j - s0), step0 + j + 1))) return st;
+                // r^{j+1}, binned as the recomputation left it
+                if ((st = snapshot(seg + snap * (size_t)(j - s0), false))) return st;
                 if ((st = vjp_core(lam, jt, acc))) return st;
                 adjoint_step<T><<<blocks(n3), 256, 0, stream_>>>(n3, jt, rb, ub, lam, q.sd, q.sh, q.su, q.sf, q.wf,
                                                                   j == 0 ? 1 : 0);
