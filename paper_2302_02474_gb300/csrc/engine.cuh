@@ -299,10 +299,12 @@ template <typename T> class Engine final : public EngineBase {
     // J^T lam at the current positions into out_d (T, by id), and the
     // parameter sums added to theta_acc (device, 3 doubles); stream-ordered,
     // no host synchronisation (see vjp_kernels.cuh).
-    tild_status vjp_core(const T* lam_d, T* out_d, double* theta_acc) {
+    // fields_ready: D w (grad_ fields 0..2) and Zxy of the current positions
+    // are already in place, as a step starting from them leaves them.
+    tild_status vjp_core(const T* lam_d, T* out_d, double* theta_acc, bool fields_ready = false) {
         const size_t N = cfg_->n_beads;
         tild_status st;
-        if ((st = enqueue_fields(false, nullptr, nullptr, kInvGrad))) return st;  // D w at r; Zxy = xy(rho)
+        if (!fields_ready && (st = enqueue_fields(false, nullptr, nullptr, kInvGrad))) return st;  // D w at r; Zxy = xy(rho)
         using Bits = typename AdjointFixed<T>::bits_t;
         unsigned long long* fx = (unsigned long long*)vjp_fx_;
         Bits* bits = (Bits*)(fx + 6 * M_);
@@ -445,6 +447,23 @@ template <typename T> class Engine final : public EngineBase {
         return TILD_OK;
     }
 
+    // The fields a step computes from its starting positions (D w, grad_
+    // fields 0..2, and the xy-transformed density Zxy), what the force VJP at
+    // those positions recomputes otherwise.
+    size_t field_snapshot_bytes() const { return snap_part(3 * M_ * sizeof(V)) + snap_part(M_ * sizeof(V)); }
+    tild_status field_snapshot(unsigned char* s, bool store) {
+        const size_t b0 = 3 * M_ * sizeof(V), b1 = M_ * sizeof(V);
+        unsigned char* s1 = s + snap_part(b0);
+        if (store) {
+            TILD_CUDA(cudaMemcpyAsync(s, grad_, b0, cudaMemcpyDeviceToDevice, stream_));
+            TILD_CUDA(cudaMemcpyAsync(s1, Zxy_, b1, cudaMemcpyDeviceToDevice, stream_));
+        } else {
+            TILD_CUDA(cudaMemcpyAsync(grad_, s, b0, cudaMemcpyDeviceToDevice, stream_));
+            TILD_CUDA(cudaMemcpyAsync(Zxy_, s1, b1, cudaMemcpyDeviceToDevice, stream_));
+        }
+        return TILD_OK;
+    }
+
     // Reverse-mode derivatives of L(r^K, v^K) through K steps of the context's
     // scheme with the noise held fixed, checkpoints every C steps; the
     // recursion is that of the scheme's update form (scheme_coeffs; the
@@ -455,7 +474,7 @@ template <typename T> class Engine final : public EngineBase {
         if ((st = vjp_prepare())) return st;
         const size_t N = cfg_->n_beads, n3 = 3 * N, sb = 6 * N;  // one state: sb values of T
         const int64_t n_ckpt = K / C + 1;
-        const size_t snap = snapshot_bytes();
+        const size_t bsnap = snapshot_bytes(), snap = bsnap + field_snapshot_bytes();
         const size_t head = snap_part(sizeof(T) * (sb * ((size_t)n_ckpt + 1) + 2 * n3));
         const size_t need = head + snap * (size_t)C + sizeof(double) * (3 * n3 + 3);
         if ((st = device_buffer(&traj_, traj_bytes_, need))) return st;
@@ -463,7 +482,7 @@ template <typename T> class Engine final : public EngineBase {
         T* fin = ckpt + sb * n_ckpt;                // [sb]
         T* lam = fin + sb;                          // [n3]
         T* jt = lam + n3;                           // [n3]
-        unsigned char* seg = (unsigned char*)traj_ + head;  // [C] binned snapshots (256-byte aligned)
+        unsigned char* seg = (unsigned char*)traj_ + head;  // [C] binned snapshots + fields (256-byte aligned)
         double* rb = (double*)(seg + snap * (size_t)C);
         double* ub = rb + n3;  // dL/dv^K on entry, then the adjoint of u
         double* vout = ub + n3;
@@ -501,12 +520,18 @@ template <typename T> class Engine final : public EngineBase {
             const int64_t s1 = std::min<int64_t>(s0 + C, K);
             if ((st = restore_state(ckpt + sb * (s0 / C), step0 + s0))) return st;
             for (int64_t j = s0; j < s1; ++j) {
-                if ((st = step(1)) || (st = snapshot(seg + snap * (size_t)(j - s0), true))) return st;
+                if ((st = step(1))) return st;
+                // step j started from r^j: its fields belong to state j (snapshot j - 1 - s0)
+                if (j > s0 && (st = field_snapshot(seg + snap * (size_t)(j - 1 - s0) + bsnap, true))) return st;
+                if ((st = snapshot(seg + snap * (size_t)(j - s0), true))) return st;
             }
             for (int64_t j = s1 - 1; j >= s0; --j) {
-                // r^{j+1}, binned as the recomputation left it
+                // r^{j+1}, binned as the recomputation left it, with its fields
+                // when step j+1 was recomputed
+                const bool fields = j + 1 < s1;
                 if ((st = snapshot(seg + snap * (size_t)(j - s0), false))) return st;
-                if ((st = vjp_core(lam, jt, acc))) return st;
+                if (fields && (st = field_snapshot(seg + snap * (size_t)(j - s0) + bsnap, false))) return st;
+                if ((st = vjp_core(lam, jt, acc, fields))) return st;
                 adjoint_step<T><<<blocks(n3), 256, 0, stream_>>>(n3, jt, rb, ub, lam, q.sd, q.sh, q.su, q.sf, q.wf,
                                                                   j == 0 ? 1 : 0);
                 TILD_CUDA(cudaGetLastError());
