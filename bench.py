@@ -317,11 +317,13 @@ def run_diff(args):
     t.init_velocities()
     t.step(args.warmup)
     t.synchronize()
-    if args.mode == "run":  # for profilers: --steps force vector-Jacobian products, nothing else
+    if args.mode == "run":  # for profilers: --steps force vector-Jacobian products, then one 20-step window
         lam = torch.randn(spec.n_beads * 3, dtype=torch.float32, device="cuda")
         out = torch.empty_like(lam)
         for _ in range(args.steps):
             t.force_vjp(lam, out=out)
+        torch.cuda.synchronize()
+        trajectory_vjp(t, 20, np.random.default_rng(1).normal(size=(spec.n_beads, 3)), checkpoint_every=20)
         torch.cuda.synchronize()
         t.close()
         return
@@ -382,7 +384,7 @@ def main():
                          "200-step GJF window (extra measurements)")
     ap.add_argument("--mode", default="bench", choices=["bench", "run"],
                     help="run: set up, warm up and take --steps steps only (for profilers; with diff200k, --steps "
-                         "force vector-Jacobian products)")
+                         "force vector-Jacobian products and one 20-step trajectory window)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
