@@ -296,9 +296,9 @@ tild_status tild_force_vjp(tild_ctx* ctx, const void* lam, void* out, int dtype,
  * re-binning before its VJP) and takes one force vector-Jacobian product per
  * state; the adjoint vectors are FP64. All arrays are [n_beads][3] by bead
  * id in dtype/where. The context ends at step n_steps. Device scratch, kept
- * with the context: n_steps/checkpoint_every + 2 states and
- * checkpoint_every binned snapshots (3N values, 3N ints, 2 n^3 64-bit
- * grid points and the 4 n^3 complex values of that state's fields each). */
+ * with the context: n_steps/C + 2 states and C binned snapshots (3N values,
+ * 3N ints, 2 n^3 64-bit grid points and the 4 n^3 complex values of that
+ * state's fields each), C = min(checkpoint_every, n_steps). */
 tild_status tild_trajectory_vjp(tild_ctx* ctx, int64_t n_steps, int checkpoint_every, const void* r_bar,
                                 const void* v_bar, int dtype, int where, void* r0_bar, void* v0_bar, double* dtheta);
 

@@ -473,6 +473,7 @@ template <typename T> class Engine final : public EngineBase {
         tild_status st;
         if ((st = vjp_prepare())) return st;
         const size_t N = cfg_->n_beads, n3 = 3 * N, sb = 6 * N;  // one state: sb values of T
+        if (C > K) C = K > 0 ? (int)K : 1;  // no snapshot beyond the trajectory
         const int64_t n_ckpt = K / C + 1;
         const size_t bsnap = snapshot_bytes(), snap = bsnap + field_snapshot_bytes();
         const size_t head = snap_part(sizeof(T) * (sb * ((size_t)n_ckpt + 1) + 2 * n3));

@@ -135,6 +135,22 @@ def test_trajectory_vjp_matches_oracle(B, scheme):
         assert np.allclose(g0["v0"], u, rtol=0, atol=1e-12)
 
 
+def test_trajectory_vjp_with_checkpoints_beyond_the_window(B):
+    """checkpoint_every larger than the trajectory: one segment, same result."""
+    from paper_2302_02474_gb300.trajectory import trajectory_vjp
+
+    spec = I.small_system(n_chains=30, N=10, n_a=4, L=6.0, n=16, pmeorder=1, precision="fp64", chi=1.0, kappa=6.0,
+                          dt=0.01)
+    t, m, pos = _setup(B, spec)
+    t.init_velocities()
+    vel0 = O.initial_state(m, pos).vel
+    w = np.random.default_rng(8).normal(size=pos.shape)
+    g = trajectory_vjp(t, 4, w, checkpoint_every=1000)
+    ref = O.gjf_trajectory_vjp(m, pos, vel0, 4, w)
+    assert t.step_count() == 4
+    assert _rel(g["r0"], ref["r0"]) < 1e-9 and _rel(g["v0"], ref["v0"]) < 1e-9
+
+
 def test_force_vjp_needs_the_ik_force(B):
     spec = I.small_system(n_chains=20, N=10, n_a=4, L=6.0, n=16, precision="fp64")
     t, m, pos = _setup(B, spec)
