@@ -130,6 +130,10 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
+            # sampling is live before the timed region starts (at most 5 s)
+            t_end = time.time() + 5.0
+            while time.time() < t_end and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -370,7 +374,7 @@ def run_diff(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--sort-every", type=int, default=20)
