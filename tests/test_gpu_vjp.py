@@ -151,6 +151,42 @@ def test_trajectory_vjp_with_checkpoints_beyond_the_window(B):
     assert _rel(g["r0"], ref["r0"]) < 1e-9 and _rel(g["v0"], ref["v0"]) < 1e-9
 
 
+def test_trajectory_autograd_matches_oracle(B):
+    """tild_trajectory as a torch.autograd function: r^K, v^K equal the
+    oracle's trajectory, and backward of sum w . r^K + sum u . v^K equals the
+    oracle's reverse sweep for the initial positions, velocities, chi, kappa
+    and a; the context is left where the forward left it."""
+    import torch
+
+    from paper_2302_02474_gb300.autograd import tild_trajectory
+
+    spec = I.small_system(n_chains=30, N=10, n_a=4, L=6.0, n=16, pmeorder=1, precision="fp64", chi=1.0, kappa=6.0,
+                          dt=0.01)
+    pos = I.initial_positions(spec)
+    t = B.Tild.from_spec(spec, sort_every=3)
+    m = O.model_from_spec(spec, I.species_of_beads(spec.moltypes), I.bond_pairs(spec.moltypes))
+    vel0 = O.initial_state(m, pos).vel
+    K = 5
+    rng = np.random.default_rng(13)
+    w, u = rng.normal(size=pos.shape), rng.normal(size=pos.shape)
+    f64 = dict(dtype=torch.float64)
+    r0 = torch.tensor(pos, device="cuda", requires_grad=True, **f64)
+    v0 = torch.tensor(vel0, device="cuda", requires_grad=True, **f64)
+    chi, kappa, a = (torch.tensor(float(x), requires_grad=True, **f64) for x in (spec.chi, spec.kappa, spec.a))
+    r_k, v_k = tild_trajectory(t, K, r0, v0, chi, kappa, a, checkpoint_every=2)
+    st = O.run(m, O.State(O.wrap(pos, m.L), vel0, O.forces(m, O.wrap(pos, m.L)), 0), K)
+    assert np.abs(O.minimum_image(r_k.detach().cpu().numpy() - st.pos, m.L)).max() < 1e-10
+    assert _rel(v_k.detach().cpu().numpy(), st.vel) < 1e-10
+    loss = (torch.as_tensor(w, device="cuda") * r_k).sum() + (torch.as_tensor(u, device="cuda") * v_k).sum()
+    loss.backward()
+    ref = O.gjf_trajectory_vjp(m, pos, vel0, K, w, u)
+    assert _rel(r0.grad.cpu().numpy(), ref["r0"]) < 1e-9
+    assert _rel(v0.grad.cpu().numpy(), ref["v0"]) < 1e-9
+    for name, p in (("chi", chi), ("kappa", kappa), ("a", a)):
+        assert float(p.grad) == pytest.approx(ref[name], rel=1e-9), name
+    assert t.step_count() == K
+
+
 def test_force_vjp_needs_the_ik_force(B):
     spec = I.small_system(n_chains=20, N=10, n_a=4, L=6.0, n=16, precision="fp64")
     t, m, pos = _setup(B, spec)
