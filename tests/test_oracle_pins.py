@@ -238,7 +238,7 @@ def test_translation_by_grid_vector():
         assert e1[k] == pytest.approx(e0[k], rel=1e-11, abs=1e-12)
 
 
-@pytest.mark.parametrize("P", [2, 4])
+@pytest.mark.parametrize("P", [2, 3, 4, 5])
 def test_analytic_forces_are_energy_gradient(P):
     """Central differences of E_bond + E_chi + E_kappa equal the analytic
     gradient of the gridded energy (bond force of Eq. bonds: -3/b^2 dr)."""
@@ -559,7 +559,7 @@ def test_neutral_homogeneous_melt_has_no_electrostatics():
 # ------------------------------------------------------- force vector-Jacobian
 
 
-@pytest.mark.parametrize("P", [2, 4])
+@pytest.mark.parametrize("P", [2, 3, 4, 5])
 def test_force_vjp_matches_finite_differences(P):
     """J^T lam of the ik force equals central differences of sum_i lam_i . F_i
     with respect to positions, chi, kappa and a (with charges on)."""
