@@ -66,6 +66,15 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.tild_create(None, ctypes.byref(ctx)) == B.TILD_EINVAL
     assert lib.tild_destroy(None) == B.TILD_OK
     assert lib.tild_step(None, 1) == B.TILD_EINVAL
+    # the variant, electrostatics and differentiable-form calls check their context first
+    assert lib.tild_set_integrator_scheme(None, 0) == B.TILD_EINVAL
+    assert lib.tild_set_force_method(None, 0) == B.TILD_EINVAL
+    assert lib.tild_set_electrostatics(None, 1.0, -1.0, 1.0, 0.5) == B.TILD_EINVAL
+    assert lib.tild_force_vjp(None, None, None, B.TILD_DTYPE_F64, B.TILD_HOST, None) == B.TILD_EINVAL
+    assert lib.tild_trajectory_vjp(None, 1, 1, None, None, B.TILD_DTYPE_F64, B.TILD_HOST, None, None,
+                                   None) == B.TILD_EINVAL
+    best, ms = ctypes.c_int(), ctypes.c_double()
+    assert lib.tild_autotune(None, 10, ctypes.byref(best), ctypes.byref(ms)) == B.TILD_EINVAL
 
 
 def test_library_missing_fails_loudly(monkeypatch, tmp_path):
