@@ -185,6 +185,11 @@ tild_status tild_set_integrator(tild_ctx* ctx, double dt, double friction, doubl
  * Forces reported by tild_compute are the field and bond forces only.
  * Switching keeps v^n (zero when leaving EM). Unknown schemes return
  * TILD_EINVAL. */
+#define TILD_SCHEME_GJF 0
+#define TILD_SCHEME_EM 1
+#define TILD_SCHEME_VV 2
+tild_status tild_set_integrator_scheme(tild_ctx* ctx, int scheme);
+
 /* How the particle-mesh force is taken from the potentials (Sec. "Long-range
  * interactions", Eq. PMM):
  *   TILD_FORCE_IK        the default: the field gradient by spectral (i k)
@@ -196,6 +201,10 @@ tild_status tild_set_integrator(tild_ctx* ctx, double dt, double friction, doubl
  *                        assignment weights. Not momentum conserving.
  * If velocities exist, v^n is kept. Batches (tild_batch_create) take
  * TILD_FORCE_IK contexts only. Unknown methods return TILD_EINVAL. */
+#define TILD_FORCE_IK 0
+#define TILD_FORCE_ANALYTIC 1
+tild_status tild_set_force_method(tild_ctx* ctx, int method);
+
 /* Electrostatics (Sec. "Long-range interactions": charged monomers interact
  * through Coulomb forces computed with the same particle-mesh scheme;
  * charges are spread over a unit Gaussian with a charge spreading length,
@@ -208,15 +217,6 @@ tild_status tild_set_integrator(tild_ctx* ctx, double dt, double friction, doubl
  * tild_energy_gradient. If velocities exist, v^n is kept. Non-finite values,
  * bjerrum < 0 or smear <= 0 return TILD_EINVAL. */
 tild_status tild_set_electrostatics(tild_ctx* ctx, double q_a, double q_b, double bjerrum, double smear);
-
-#define TILD_FORCE_IK 0
-#define TILD_FORCE_ANALYTIC 1
-tild_status tild_set_force_method(tild_ctx* ctx, int method);
-
-#define TILD_SCHEME_GJF 0
-#define TILD_SCHEME_EM 1
-#define TILD_SCHEME_VV 2
-tild_status tild_set_integrator_scheme(tild_ctx* ctx, int scheme);
 
 /* Order all work of this context on `stream` (a cudaStream_t; NULL = the
  * context's own stream). The stream must belong to the context's device and
