@@ -16,7 +16,16 @@
  *   5. interpolate the forces back to the beads with the same weights
  *      (caption of Fig. pmm), add harmonic bond forces (Eq. bonds);
  *   6. advance positions and velocities with the Gronbech-Jensen-Farago
- *      Langevin integrator (GJF; Sec. "Integrator Class", Listing infile).
+ *      Langevin integrator (GJF; Sec. "Integrator Class", Listing infile),
+ *      or with Euler-Maruyama or velocity-Verlet + Langevin force, the other
+ *      integrators that section lists (tild_set_integrator_scheme).
+ *
+ * Around the step: observables (tild_compute), the analytic-gradient force
+ * variant (tild_set_force_method), smeared-charge electrostatics
+ * (tild_set_electrostatics), batches of uneven replicas (tild_batch_*) and
+ * the differentiable form: the energy gradient (tild_energy_gradient), the
+ * force vector-Jacobian product (tild_force_vjp) and derivatives through
+ * trajectories (tild_trajectory_vjp).
  *
  * Units are the paper's reduced units (Sec. "Units"): energy kT, mass m of
  * a monomer, length b.
