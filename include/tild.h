@@ -420,9 +420,13 @@ const char* tild_last_error(tild_ctx* ctx);
  *   pmeorder assignment order 1..4.
  *   rho_out  device, [2][n][n][n] FP32 output (species A then B, [z][y][x]).
  *   stream   cudaStream_t to order the work on (NULL = legacy default stream).
- * Work is asynchronous on `stream`. The first call on a device looks up the
- * device address of the scratch array (with that device current), so make
- * that first call before any stream capture. Every call shares the one
+ * Work is asynchronous on `stream`. Every call looks up the device address
+ * of the scratch array on the current device (a host-side lookup). CUDA
+ * loads a library's device code lazily by default: the first call on each
+ * device then places this file's code and the 4 MiB scratch array on that
+ * device, which takes device memory once. Make that first call during
+ * set-up, before any stream capture; later calls allocate nothing. Every
+ * call shares the one
  * scratch array, which keeps the previous call's contents; each call clears
  * the part it uses first. Calls whose work overlaps on the GPU (other
  * streams, other host threads) race on the scratch and must be serialised

@@ -54,7 +54,8 @@ class TildTrajectory(torch.autograd.Function):
     that of Philox counters 1..K. Positions come back wrapped into [0, L);
     derivatives are those of the unwrapped trajectory (wrapping is a
     translation by box vectors). The backward restores the start state,
-    runs the reverse sweep and puts the context back where it was."""
+    runs the reverse sweep and puts the context back where it was: its
+    state and the interaction parameters current before the backward."""
 
     @staticmethod
     def forward(ctx, tild: Tild, n_steps: int, checkpoint_every: int, positions: torch.Tensor,
@@ -79,14 +80,26 @@ class TildTrajectory(torch.autograd.Function):
     def backward(ctx, grad_r, grad_v):
         t = ctx.tild
         here = t.get_state()
+        before = t.interactions  # the parameters current before this backward
         t.set_interactions(*ctx.params)
         t.set_state(ctx.start)
-        g = trajectory_vjp(t, ctx.n, grad_r.detach().double().cpu().numpy(),
-                           grad_v.detach().double().cpu().numpy(), ctx.every)
-        t.set_state(here)
         dt, dev = ctx.pos_meta
-        d_r0 = torch.as_tensor(g["r0"], dtype=dt, device=dev)
-        d_v0 = torch.as_tensor(g["v0"], dtype=dt, device=dev)
+        if grad_r is None:
+            grad_r = torch.zeros(t.n_beads, 3, dtype=torch.float64, device=dev)
+        if dev.type == "cuda":
+            # adjoint vectors stay on the device (no host round trip)
+            gr = grad_r.detach().to(device=dev, dtype=torch.float64)
+            gv = None if grad_v is None else grad_v.detach().to(device=dev, dtype=torch.float64)
+        else:
+            gr = grad_r.detach().double().cpu().numpy()
+            gv = None if grad_v is None else grad_v.detach().double().cpu().numpy()
+        g = trajectory_vjp(t, ctx.n, gr, gv, ctx.every)
+        # the parameters first: the saved state's carried velocity belongs to them
+        if before is not None:
+            t.set_interactions(*before)
+        t.set_state(here)
+        d_r0 = torch.as_tensor(g["r0"], device=dev).to(dt)
+        d_v0 = torch.as_tensor(g["v0"], device=dev).to(dt)
         gp = [torch.as_tensor(g[k], dtype=d, device=v) for k, (d, v) in zip(("chi", "kappa", "a"), ctx.param_meta)]
         return None, None, None, d_r0, d_v0, gp[0], gp[1], gp[2]
 

@@ -189,6 +189,7 @@ class Tild:
         self.integrator = (0.005, 1.0, 1.0, 1.0)  # dt, friction, kT, mass (the library defaults)
         self.scheme = "gjf"
         self.force_method = "ik"
+        self.interactions = None  # (chi, kappa, a) once set
 
     @classmethod
     def from_spec(cls, spec, sort_every: int = 0, precision: Optional[str] = None) -> "Tild":
@@ -229,6 +230,7 @@ class Tild:
 
     def set_interactions(self, chi: float, kappa: float, a: float) -> None:
         self._chk(self.lib.tild_set_interactions(self.ctx, chi, kappa, a))
+        self.interactions = (float(chi), float(kappa), float(a))
 
     def set_integrator(self, dt: float, friction: float, kT: float, mass: float = 1.0) -> None:
         self._chk(self.lib.tild_set_integrator(self.ctx, dt, friction, kT, mass))

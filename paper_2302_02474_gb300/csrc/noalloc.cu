@@ -6,9 +6,11 @@
 // device) is not acceptable. This entry point needs no context and allocates
 // nothing: its 64-bit fixed-point scratch grid is a file-scope __device__
 // array that every GPU loading this library holds until the process exits.
+// Under CUDA's lazy module loading (the default) that array, with this file's
+// device code, is placed on a device when the first call there looks up its
+// address; that first call should therefore run during set-up.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "bead_kernels.cuh"
@@ -23,14 +25,10 @@ constexpr size_t kNoAllocMaxPoints = (size_t)kNoAllocMaxN * kNoAllocMaxN * kNoAl
 // Two species of int64 fixed-point sums (2^22 per unit weight), 4 MiB.
 static __device__ __align__(256) unsigned long long g_noalloc_rho[2 * kNoAllocMaxPoints];
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_setup_mutex;
-
 template <int P>
-__global__ void noalloc_spread(int n_beads, const float* __restrict__ xyz, const unsigned char* __restrict__ species,
+__global__ void noalloc_spread(int64_t n_beads, const float* __restrict__ xyz, const unsigned char* __restrict__ species,
                                float L, float inv_L, float inv_dx, int n, unsigned long long* __restrict__ rho) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_beads) return;
     const float x = wrap_coord(xyz[3 * (size_t)i + 0], L, inv_L);
     const float y = wrap_coord(xyz[3 * (size_t)i + 1], L, inv_L);
@@ -79,23 +77,13 @@ tild_status tild_spread_density_noalloc(const float* xyz, const unsigned char* s
     if (n < 8 || n > kNoAllocMaxN || (n & (n - 1)) != 0)
         return fail(TILD_EINVAL, "spread_density_noalloc: n must be a power of two in [8, 64] (static scratch of 64^3 points)");
     if (pmeorder < 1 || pmeorder > 4) return fail(TILD_EINVAL, "spread_density_noalloc: pmeorder must be in 1..4");
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(TILD_EDEVICE, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fail(TILD_EUNSUPPORTED, "spread_density_noalloc: device ordinal >= 64");
-    void* scratch;
-    {
-        // one-time set-up per device, with that device current: the host-side
-        // name of a __device__ array is not a device address
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_addr[dev]) {
-            void* ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_noalloc_rho);
-            if (e != cudaSuccess) return fail(TILD_EDEVICE, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_scratch_addr[dev] = ptr;
-        }
-        scratch = g_scratch_addr[dev];
-    }
+    // the device address of the scratch array on the current device: the
+    // host-side name of a __device__ array is not a device address. Looked up
+    // on every call (a host-side table lookup once the module is loaded), so
+    // no cached address outlives a device reset.
+    void* scratch = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&scratch, g_noalloc_rho);
+    if (e != cudaSuccess) return fail(TILD_EDEVICE, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long* rho = (unsigned long long*)scratch;
     const size_t M = (size_t)n * n * n;
@@ -103,8 +91,8 @@ tild_status tild_spread_density_noalloc(const float* xyz, const unsigned char* s
     e = cudaMemsetAsync(rho, 0, 2 * M * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return fail(TILD_EDEVICE, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const float Lf = (float)L, inv_L = (float)(1.0 / L), inv_dx = (float)((double)n / L);
-    const int nb = (int)n_beads;
-    const unsigned grid = (unsigned)((nb + 255) / 256);
+    const int64_t nb = n_beads;
+    const unsigned grid = (unsigned)((nb + 255) / 256);  // nb < 2^31: at most 2^23 blocks
     if (nb > 0) {
         switch (pmeorder + 1) {
             case 2: noalloc_spread<2><<<grid, 256, 0, s>>>(nb, xyz, species, Lf, inv_L, inv_dx, n, rho); break;

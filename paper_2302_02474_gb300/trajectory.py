@@ -33,18 +33,43 @@ from typing import Dict
 
 import numpy as np
 
-from .binding import TILD_DTYPE_F64, TILD_HOST, Tild
+from .binding import TILD_DEVICE, TILD_DTYPE_F64, TILD_HOST, Tild
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
 
 
 def trajectory_vjp(t: Tild, n_steps: int, r_bar, v_bar=None, checkpoint_every: int = 20) -> Dict[str, object]:
     """Derivatives of L through `n_steps` steps of context `t` (positions and
     velocities set; any scheme, ik force). r_bar, v_bar: dL/dr^K, dL/dv^K
     (n_beads x 3, by bead id; numpy arrays or CUDA tensors). Returns
-    {"r0", "v0"} (numpy FP64) and {"chi", "kappa", "a"}; `t` is left at step
-    K. The sweep runs inside the library (tild_trajectory_vjp)."""
+    {"r0", "v0"} and {"chi", "kappa", "a"}; `t` is left at step K. The sweep
+    runs inside the library (tild_trajectory_vjp). With a CUDA tensor r_bar
+    the adjoint vectors stay on the device (FP64 CUDA tensors in and out, no
+    host copy); otherwise r0 and v0 are numpy FP64 arrays."""
     if t.force_method != "ik":
         raise ValueError("trajectory_vjp needs the ik force")
     n3 = 3 * t.n_beads
+    th = (ctypes.c_double * 3)()
+    if _is_cuda_tensor(r_bar):
+        import torch
+
+        rb = r_bar.detach().to(torch.float64).contiguous().view(-1)
+        vb = None
+        if v_bar is not None:
+            if not _is_cuda_tensor(v_bar):
+                raise ValueError("r_bar and v_bar must both be CUDA tensors or both host arrays")
+            vb = v_bar.detach().to(device=rb.device, dtype=torch.float64).contiguous().view(-1)
+        if rb.numel() != n3 or (vb is not None and vb.numel() != n3):
+            raise ValueError("r_bar and v_bar need n_beads x 3 values")
+        r0 = torch.empty(n3, dtype=torch.float64, device=rb.device)
+        v0 = torch.empty_like(r0)
+        t._chk(t.lib.tild_trajectory_vjp(t.ctx, int(n_steps), int(checkpoint_every), ctypes.c_void_p(rb.data_ptr()),
+                                         None if vb is None else ctypes.c_void_p(vb.data_ptr()), TILD_DTYPE_F64,
+                                         TILD_DEVICE, ctypes.c_void_p(r0.data_ptr()), ctypes.c_void_p(v0.data_ptr()),
+                                         th))
+        return {"r0": r0.view(-1, 3), "v0": v0.view(-1, 3), "chi": th[0], "kappa": th[1], "a": th[2]}
     rb = np.ascontiguousarray(np.asarray(r_bar.cpu() if hasattr(r_bar, "cpu") else r_bar, dtype=np.float64)).reshape(-1)
     vb = None
     if v_bar is not None:
@@ -53,7 +78,6 @@ def trajectory_vjp(t: Tild, n_steps: int, r_bar, v_bar=None, checkpoint_every: i
         raise ValueError("r_bar and v_bar need n_beads x 3 values")
     r0 = np.empty(n3, dtype=np.float64)
     v0 = np.empty(n3, dtype=np.float64)
-    th = (ctypes.c_double * 3)()
     t._chk(t.lib.tild_trajectory_vjp(t.ctx, int(n_steps), int(checkpoint_every), rb.ctypes.data,
                                      None if vb is None else vb.ctypes.data, TILD_DTYPE_F64, TILD_HOST,
                                      r0.ctypes.data, v0.ctypes.data, th))

@@ -174,9 +174,12 @@ def test_single_bead_and_wrap_at_box_edge(B):
     t = B.Tild(6.0, 8, 1, "fp64", 9)
     t.set_chains([(2, 1, 1)], 1.0)
     t.set_interactions(0.0, 3.0, 0.5)
-    # the second bead sits just inside the far faces, 0.5-0.7 away from the
-    # first through the periodic boundary
-    pos = np.array([[6.0, 0.0, 3.0], [-1e-14, 5.4999999999, 8.7]])
+    # x exactly at L (wraps to 0); the second bead 1e-14 below 0 in x (wraps to
+    # just below L) and 1e-9 below L in y, so it spreads across the x and y
+    # faces; its z = 2L + 0.7 wraps to 0.7, 2.3 from the first bead, which
+    # gives an O(1) force along z (with z = 0 the reference force is ~1e-10
+    # and a relative tolerance is meaningless)
+    pos = np.array([[6.0, 0.0, 3.0], [-1e-14, 5.999999999, 12.7]])
     t.set_positions(pos)
     r = t.positions()
     assert np.all(r >= 0) and np.all(r < 6.0)
@@ -357,6 +360,53 @@ def test_diblock_1p6M_128_sampled_forces(B):
     t.synchronize()
     r = t.positions()
     assert np.all(np.isfinite(r)) and r.min() >= 0 and r.max() < m.L
+
+
+def test_diblock_1p6M_128_steps_match_oracle(B):
+    """The benchmarked FP32 step at full size (1.6M beads, 128^3): forces of
+    all beads at t = 0, then 4 steps through tild_step with re-binning every
+    step (so the captured re-binning cycle graph runs too), positions and
+    velocities of all beads against the oracle from the same FP32-rounded
+    start."""
+    spec = I.config("diblock_1p6M_128")
+    t, m, pos = _setup(B, spec, sort_every=1)
+    t.init_velocities()
+    f, _ = t.compute(energy=False)
+    st = O.initial_state(m, pos)
+    assert _rel(f, st.force) < 1e-5
+    t.step(4)
+    r, v = t.positions(), t.velocities()
+    st = O.run(m, st, 4)
+    assert np.abs(O.minimum_image(r - st.pos, m.L)).max() < 1e-4 * m.L
+    assert _rel(v, st.vel) < 1e-4
+
+
+@pytest.mark.parametrize("n_chains", [500, 1000])
+def test_dense_tiles_match_oracle(B, n_chains):
+    """FP32 tiles denser than the bead kernel's staging chunk (512 beads) and,
+    with 1,000 chains, denser than its 32-bit shared patches allow (1,023
+    beads: those tiles spread straight into the 64-bit grid). 5,000 or
+    10,000 beads on an 8^3-cell-tile grid of 2^3 tiles: density, forces,
+    energies and a 5-step trajectory against the oracle."""
+    spec = I.small_system(n_chains=n_chains, N=10, n_a=4, L=8.0, n=16, precision="fp32", chi=0.5, kappa=2.0,
+                          seed=31)
+    t, m, pos = _setup(B, spec, sort_every=2)
+    tile = np.floor(pos / (spec.L / 2)).astype(int)
+    per_tile = np.bincount((tile[:, 2] * 2 + tile[:, 1]) * 2 + tile[:, 0], minlength=8)
+    assert per_tile.min() > (1023 if n_chains == 1000 else 512)
+    rho = t.density()
+    ref = O.spread(m, pos).transpose(0, 3, 2, 1)
+    assert np.abs(rho - ref).max() <= 2e-6 * np.abs(ref).max()
+    t.init_velocities()
+    f, e = t.compute()
+    assert _rel(f, O.forces(m, pos)) < 1e-5
+    eref = O.energies(m, pos)
+    for k in ("bond", "chi", "kappa"):
+        assert abs(e[k] - eref[k]) <= 1e-6 * abs(eref[k]), (k, e[k], eref[k])
+    t.step(5)
+    st = O.run(m, O.initial_state(m, pos), 5)
+    assert np.abs(O.minimum_image(t.positions() - st.pos, m.L)).max() < 1e-4 * m.L
+    assert _rel(t.velocities(), st.vel) < 1e-4
 
 
 def test_blend_6p4M_256_sampled_forces(B):

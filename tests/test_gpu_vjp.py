@@ -187,6 +187,37 @@ def test_trajectory_autograd_matches_oracle(B):
     assert t.step_count() == K
 
 
+def test_trajectory_autograd_backward_keeps_the_current_parameters(B):
+    """Parameters set after the forward (and before backward) are the ones
+    the context holds after backward: a step then equals the same step of a
+    context that never ran the backward."""
+    import torch
+
+    from paper_2302_02474_gb300.autograd import tild_trajectory
+
+    spec = I.small_system(n_chains=20, N=10, n_a=4, L=6.0, n=16, pmeorder=1, precision="fp64", chi=1.0, kappa=6.0)
+    pos = I.initial_positions(spec)
+    m = O.model_from_spec(spec, I.species_of_beads(spec.moltypes), I.bond_pairs(spec.moltypes))
+    vel0 = O.initial_state(m, pos).vel
+    f64 = dict(dtype=torch.float64, device="cuda")
+    t = B.Tild.from_spec(spec, sort_every=3)
+    r0 = torch.tensor(pos, requires_grad=True, **f64)
+    v0 = torch.tensor(vel0, **f64)
+    r_k, _ = tild_trajectory(t, 3, r0, v0, spec.chi, spec.kappa, spec.a, checkpoint_every=2)
+    t.set_interactions(2.0, 9.0, 0.6)
+    r_k.sum().backward()
+    assert t.interactions == (2.0, 9.0, 0.6)
+    t.step(2)
+    ref = B.Tild.from_spec(spec, sort_every=3)
+    ref.set_positions(pos)
+    ref.set_velocities(vel0)
+    ref.step(3)
+    ref.set_interactions(2.0, 9.0, 0.6)
+    ref.step(2)
+    assert np.array_equal(t.positions(), ref.positions())
+    assert r0.grad.is_cuda
+
+
 def test_force_vjp_needs_the_ik_force(B):
     spec = I.small_system(n_chains=20, N=10, n_a=4, L=6.0, n=16, precision="fp64")
     t, m, pos = _setup(B, spec)
