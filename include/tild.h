@@ -37,7 +37,8 @@
  *   - Beads are numbered 0..n_beads-1 chain by chain, in the order of the
  *     molecule types given to tild_set_chains (bead s of chain c of type t
  *     has id start_t + c*N_t + s).
- *   - Arrays of per-bead vectors are AoS, [n_beads][3], in bead-id order.
+ *   - Arrays of per-bead vectors are AoS, [n_beads][3], in bead-id order,
+ *     unless tild_set_layout selects SoA, [3][n_beads].
  *     Their element type is given by a tild_dtype; `where` says whether the
  *     pointer is host or device memory (TILD_HOST / TILD_DEVICE). The caller
  *     owns every buffer it passes; the library copies in or out and keeps no
@@ -47,8 +48,10 @@
  *     data to the caller synchronise that stream before returning; tild_step
  *     does not (use tild_synchronize).
  *   - The library owns its device state (bead arrays, grids, spectra),
- *     allocated with cudaMalloc by tild_create / tild_set_chains and freed by
- *     tild_destroy.
+ *     allocated by tild_create / tild_set_chains / tild_set_species (and
+ *     scratch by the calls that say so) and freed by tild_destroy, through
+ *     cudaMalloc/cudaFree or the allocator given to
+ *     tild_create_with_allocator.
  *   - A context is bound to the CUDA device that was current when it was
  *     created; calls on it must be made with that device current.
  *   - Not thread-safe: one host thread at a time per context.
@@ -153,15 +156,57 @@ typedef struct {
  * success *out owns device memory for the grids. */
 tild_status tild_create(const tild_params* p, tild_ctx** out);
 
+/* Device-memory allocator of a context (for instance a framework's caching
+ * allocator). alloc returns `bytes` of device memory on the context's device,
+ * aligned to at least 256 bytes, or NULL on failure (the calling tild_*
+ * function then returns TILD_ENOMEM). free releases a block that alloc
+ * returned, with its size. The library frees every block before
+ * tild_destroy returns and calls alloc/free only from the thread making the
+ * tild_* call. `user` is passed through. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, size_t bytes, void* user);
+    void* user;
+} tild_allocator;
+
+/* tild_create with every device allocation of the context (grids, bead
+ * arrays, scratch) made through *a. a == NULL or a->alloc == NULL is
+ * tild_create. Batches (tild_batch_*) and tild_autotune's checkpoint still
+ * use cudaMalloc for their own small tables. */
+tild_status tild_create_with_allocator(const tild_params* p, const tild_allocator* a, tild_ctx** out);
+
 /* Free everything the context owns. NULL is accepted. */
 tild_status tild_destroy(tild_ctx* ctx);
 
 /* Define the chains (and so the number of beads, the species and the bond
  * topology). b is the statistical segment length of Eq. bonds (bond force
  * -(3/b^2)(r_i - r_j)). At most 8 types, 1 <= N, 0 <= n_a <= N, at least one
- * bead, fewer than 2^31 beads. At most two species (A, B). Allocates the
- * bead arrays; existing positions are discarded. */
+ * bead, fewer than 2^29 beads. The chains give two species (A, B) and linear
+ * bonds; tild_set_species and tild_set_bonds replace either. Allocates the
+ * bead arrays; existing positions are discarded, as are species and bonds
+ * set before. */
 tild_status tild_set_chains(tild_ctx* ctx, int n_types, const tild_moltype* types, double b);
+
+/* Species of the beads (Sec. "Input file": each atom of the data file has a
+ * type; Eq. fh couples every pair of types through chi). n_species in 1..4.
+ * species (host, [n_beads] int32 in bead-id order, values in
+ * [0, n_species)) gives every bead's species; NULL keeps the chains' A/B
+ * pattern (then n_species must be 2). Flory parameters of the new species
+ * pairs start at 0 (tild_set_chi_matrix). Three or four species allocate a
+ * second pair of density and field grids. With more than two species,
+ * electrostatics, tild_energy_gradient, tild_force_vjp, tild_trajectory_vjp
+ * and batches return TILD_EUNSUPPORTED. Requires chains; existing positions
+ * are re-binned and velocities are kept (as for tild_set_interactions). */
+tild_status tild_set_species(tild_ctx* ctx, int n_species, const int32_t* species);
+
+/* Bond topology (Eq. bonds; Sec. "Input file": the data file lists the
+ * bonds): n_bonds >= 0 harmonic bonds between bead ids pairs[2k] and
+ * pairs[2k+1] (host int32), each pair once, no self-bonds, no repeats; any
+ * topology (rings, branches, networks) and any number of bonds per bead.
+ * Replaces the chains' linear bonds (pairs == NULL with n_bonds == 0 removes
+ * every bond). Forces and energies are independent of the order of the list.
+ * Requires chains; positions are re-binned and velocities kept. */
+tild_status tild_set_bonds(tild_ctx* ctx, int64_t n_bonds, const int32_t* pairs);
 
 /* Interactions (Eqs. fh, HelfandP; sigma^2 = 2 a^2 per Eqs. fhF, HelfandF):
  * chi_ab = Flory chi between A and B, kappa = Helfand compressibility,
@@ -171,6 +216,13 @@ tild_status tild_set_chains(tild_ctx* ctx, int n_types, const tild_moltype* type
  * velocities exist, v^n is kept and the carried state is updated to the
  * new forces. */
 tild_status tild_set_interactions(tild_ctx* ctx, double chi_ab, double kappa, double a);
+
+/* Flory matrix for more than two species (Eq. fh over every species pair):
+ * chi, host [n_species][n_species] doubles, symmetric, finite, zero
+ * diagonal. The pair potential matrix becomes eps_KK' = (chi_KK' + kappa) /
+ * rho_0. chi[0][1] is the chi_ab of tild_set_interactions (each call sets
+ * it). Velocities are kept. */
+tild_status tild_set_chi_matrix(tild_ctx* ctx, const double* chi);
 
 /* Integrator parameters (Sec. "Integrator Class"): time step dt > 0,
  * friction alpha >= 0, temperature kT >= 0, bead mass > 0. Defaults:
@@ -226,6 +278,17 @@ tild_status tild_set_force_method(tild_ctx* ctx, int method);
  * tild_energy_gradient. If velocities exist, v^n is kept. Non-finite values,
  * bjerrum < 0 or smear <= 0 return TILD_EINVAL. */
 tild_status tild_set_electrostatics(tild_ctx* ctx, double q_a, double q_b, double bjerrum, double smear);
+
+/* Layout of every per-bead vector array this context reads or writes
+ * (positions, velocities, forces, dU/dr, adjoint vectors):
+ *   TILD_LAYOUT_AOS  [n_beads][3] (the default);
+ *   TILD_LAYOUT_SOA  [3][n_beads]: all x, then all y, then all z.
+ * Device arrays in SoA pass through a context-owned device scratch of
+ * 3 n_beads doubles (allocated on first use). Unknown layouts return
+ * TILD_EINVAL. */
+#define TILD_LAYOUT_AOS 0
+#define TILD_LAYOUT_SOA 1
+tild_status tild_set_layout(tild_ctx* ctx, int layout);
 
 /* Order all work of this context on `stream` (a cudaStream_t; NULL = the
  * context's own stream). The stream must belong to the context's device and
@@ -318,18 +381,22 @@ tild_status tild_get_positions(tild_ctx* ctx, void* out, int dtype, int where);
 tild_status tild_get_velocities(tild_ctx* ctx, void* out, int dtype, int where);
 
 /* Species densities rho_K(g) on the grid (beads per unit volume) of the
- * current positions: [2][n][n][n], species A then B, [z][y][x] order. */
+ * current positions: [n_species][n][n][n] (two species: A then B),
+ * [z][y][x] order. */
 tild_status tild_get_density(tild_ctx* ctx, void* out, int dtype, int where);
 
 /* Discrete Fourier transform Z(k) = sum_g (rho_A(g) + i rho_B(g)) e^{-i k.g}
  * of the current densities, as interleaved (re, im) pairs [n][n][n][2] in
- * [kz][ky][kx] FFT index order (index m < n/2 is frequency m, else m - n). */
+ * [kz][ky][kx] FFT index order (index m < n/2 is frequency m, else m - n).
+ * Three or four species: [2][n][n][n][2], the transforms of
+ * rho_0 + i rho_1 and rho_2 + i rho_3 (rho_3 = 0 for three species). */
 tild_status tild_get_spectrum(tild_ctx* ctx, void* out, int dtype, int where);
 
 /* Gradients of the potential fields w_K = sum_K' eps_KK' u_G * rho_K' on
  * the grid, [3][n][n][n][2]: for direction d (x, y, z), point (z, y, x), the
  * pair (d w_A / d r_d, d w_B / d r_d). eps_KK = kappa/rho_0,
- * eps_AB = (chi_ab + kappa)/rho_0. */
+ * eps_AB = (chi_ab + kappa)/rho_0. Three or four species:
+ * [2][3][n][n][n][2], species pairs (0, 1) and (2, 3). */
 tild_status tild_get_field_gradient(tild_ctx* ctx, void* out, int dtype, int where);
 
 /* Number of steps taken since velocities were set. */

@@ -135,6 +135,10 @@ class Model:
     charges: Optional[np.ndarray] = None
     bjerrum: float = 0.0
     charge_smear: float = 0.5
+    # dimensionality D (Sec. "TILD Branch": two- or three-dimensional
+    # periodic boxes; Listing infile runs D = 2): positions are (N, D), grids
+    # n^D, cell volume dx^D, and u_G the unit Gaussian in D dimensions
+    dim: int = 3
 
     @property
     def n_beads(self) -> int:
@@ -146,7 +150,7 @@ class Model:
 
     @property
     def volume(self) -> float:
-        return self.L ** 3
+        return self.L ** self.dim
 
     @property
     def rho0(self) -> float:
@@ -196,13 +200,20 @@ def gradient_wavenumbers(n: int, L: float) -> np.ndarray:
     return k
 
 
-def gaussian_kernel_hat(n: int, L: float, a: float) -> np.ndarray:
-    """u_hat(k) = exp(-|k|^2 sigma^2 / 2) = exp(-|k|^2 a^2): the continuous
-    Fourier transform of the unit Gaussian u_G (Eq. fh) with sigma^2 = 2 a^2;
-    u_hat(0) = 1. Axes (x, y, z)."""
+def _k2(n: int, L: float, dim: int) -> np.ndarray:
+    """|k|^2 on the n^dim grid of wavevectors, axes (x, y[, z])."""
     k = wavenumbers(n, L)
-    k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2
-    return np.exp(-k2 * a * a)
+    if dim == 2:
+        return k[:, None] ** 2 + k[None, :] ** 2
+    return k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2
+
+
+def gaussian_kernel_hat(n: int, L: float, a: float, dim: int = 3) -> np.ndarray:
+    """u_hat(k) = exp(-|k|^2 sigma^2 / 2) = exp(-|k|^2 a^2): the continuous
+    Fourier transform of the unit Gaussian u_G (Eq. fh; normalised to unit
+    integral in D dimensions) with sigma^2 = 2 a^2; u_hat(0) = 1 in any D.
+    Axes (x, y[, z])."""
+    return np.exp(-_k2(n, L, dim) * a * a)
 
 
 def coulomb_kernel_hat(n: int, L: float, lb: float, ae: float) -> np.ndarray:
@@ -232,7 +243,9 @@ def _has_charges(m: "Model") -> bool:
 
 def spread(m: Model, pos: np.ndarray) -> np.ndarray:
     """Grid densities rho_K(g) = (1/dV) sum_{i in K} prod_d W(s_id - g_d)
-    (Eq. rhohat assigned with the spline weights). Array axes (K, x, y, z)."""
+    (Eq. rhohat assigned with the spline weights). Array axes (K, x, y[, z])."""
+    if m.dim == 2:
+        return _spread_2d(m, pos)
     n, P = m.n, m.P
     s = wrap(pos, m.L) / m.dx
     jx, wx = stencil(s[:, 0], P)
@@ -250,11 +263,39 @@ def spread(m: Model, pos: np.ndarray) -> np.ndarray:
     return rho.reshape(m.n_species, n, n, n) / m.dx ** 3
 
 
+def _spread_2d(m: Model, pos: np.ndarray) -> np.ndarray:
+    """spread for D = 2: rho_K(g) = (1/dA) sum_{i in K} W(s_ix - g_x) W(s_iy - g_y)."""
+    n, P = m.n, m.P
+    s = wrap(pos[:, :2], m.L) / m.dx
+    jx, wx = stencil(s[:, 0], P)
+    jy, wy = stencil(s[:, 1], P)
+    rho = np.zeros((m.n_species, n * n))
+    for K in range(m.n_species):
+        sel = m.species == K
+        for a in range(P):
+            for b in range(P):
+                flat = (jx[sel, a] % n) * n + (jy[sel, b] % n)
+                rho[K] += np.bincount(flat, weights=wx[sel, a] * wy[sel, b], minlength=n * n)
+    return rho.reshape(m.n_species, n, n) / m.dx ** 2
+
+
 def gather(m: Model, pos: np.ndarray, field: np.ndarray, which: Optional[np.ndarray] = None) -> np.ndarray:
     """Interpolate per-species grid vectors field[K, d, x, y, z] to the beads
     with the same weights as ``spread`` (caption of Fig. pmm). Returns (N, D)."""
     idx = np.arange(m.n_beads) if which is None else np.asarray(which)
     n, P = m.n, m.P
+    if m.dim == 2:
+        s = wrap(pos[idx, :2], m.L) / m.dx
+        jx, wx = stencil(s[:, 0], P)
+        jy, wy = stencil(s[:, 1], P)
+        K = m.species[idx]
+        out = np.zeros((len(idx), field.shape[1]))
+        for a in range(P):
+            for b in range(P):
+                w = wx[:, a] * wy[:, b]
+                for d in range(field.shape[1]):
+                    out[:, d] += w * field[K, d, jx[:, a] % n, jy[:, b] % n]
+        return out
     s = wrap(pos[idx], m.L) / m.dx
     jx, wx = stencil(s[:, 0], P)
     jy, wy = stencil(s[:, 1], P)
@@ -283,23 +324,29 @@ def potential_fields(m: Model, rho: np.ndarray) -> Dict[str, np.ndarray]:
     The continuum convolution int u(r - r') rho(r') dr' becomes this sum
     because the Fourier coefficient of rho is dV * rho_hat and V = M dV.
     """
-    n, L = m.n, m.L
-    rho_hat = np.fft.fftn(rho, axes=(1, 2, 3))
-    u_hat = gaussian_kernel_hat(n, L, m.a)
+    n, L, D = m.n, m.L, m.dim
+    axes = tuple(range(1, D + 1))
+    rho_hat = np.fft.fftn(rho, axes=axes)
+    u_hat = gaussian_kernel_hat(n, L, m.a, D)
     eps = m.eps()
     w_hat = np.einsum("kl,l...->k...", eps, rho_hat) * u_hat[None]
+    if _has_charges(m) and D != 3:
+        raise NotImplementedError("electrostatics: three dimensions only")
     if _has_charges(m):
         # electrostatic potential phi = l_B (1/r * h_e * h_e * rho_q): w_K += q_K phi
         q = np.asarray(m.charges, dtype=float)[: m.n_species]
         rho_q_hat = np.einsum("l,l...->...", q, rho_hat)
         w_hat = w_hat + q[:, None, None, None] * (coulomb_kernel_hat(n, L, m.bjerrum, m.charge_smear) * rho_q_hat)[None]
     kt = gradient_wavenumbers(n, L)
-    kvec = (kt[:, None, None], kt[None, :, None], kt[None, None, :])
-    grad = np.empty((m.n_species, 3, n, n, n))
+    if D == 2:
+        kvec = (kt[:, None], kt[None, :])
+    else:
+        kvec = (kt[:, None, None], kt[None, :, None], kt[None, None, :])
+    grad = np.empty((m.n_species, D) + (n,) * D)
     for K in range(m.n_species):
-        for d in range(3):
+        for d in range(D):
             grad[K, d] = np.fft.ifftn(1j * kvec[d] * w_hat[K]).real
-    w = np.fft.ifftn(w_hat, axes=(1, 2, 3)).real
+    w = np.fft.ifftn(w_hat, axes=axes).real
     return {"rho_hat": rho_hat, "w_hat": w_hat, "w": w, "grad_w": grad, "u_hat": u_hat}
 
 
@@ -313,7 +360,9 @@ def bond_vectors(m: Model, pos: np.ndarray) -> np.ndarray:
 
 
 def bond_energy(m: Model, pos: np.ndarray) -> float:
-    """beta U_0 = (3 / 2b^2) sum_bonds |r_i - r_j|^2  (Eq. bonds)."""
+    """beta U_0 = (3 / 2b^2) sum_bonds |r_i - r_j|^2  (Eq. bonds). Reading: the
+    equation has the factor 3/2b^2 with no dimension in it; it is kept as
+    written in two dimensions too."""
     d = bond_vectors(m, pos)
     return float(1.5 / m.b ** 2 * np.sum(d * d))
 
@@ -321,7 +370,7 @@ def bond_energy(m: Model, pos: np.ndarray) -> float:
 def bond_forces(m: Model, pos: np.ndarray) -> np.ndarray:
     """-dU_0/dr_i = -(3/b^2) sum_{j bonded to i} (r_i - r_j)."""
     d = bond_vectors(m, pos)
-    f = np.zeros((m.n_beads, 3))
+    f = np.zeros((m.n_beads, pos.shape[1]))
     k = 3.0 / m.b ** 2
     np.add.at(f, m.bonds[:, 0], -k * d)
     np.add.at(f, m.bonds[:, 1], k * d)
@@ -338,9 +387,9 @@ def field_energies(m: Model, rho_hat: np.ndarray) -> Dict[str, float]:
     The k = 0 Helfand term cancels the -rho0 shift exactly because the
     weights conserve mass (reading: E_chi keeps k = 0 as Eq. fh does).
     """
-    dV = m.dx ** 3
+    dV = m.dx ** m.dim
     V = m.volume
-    u_hat = gaussian_kernel_hat(m.n, m.L, m.a)
+    u_hat = gaussian_kernel_hat(m.n, m.L, m.a, m.dim)
     rp = dV * rho_hat
     e_chi = 0.0
     for K in range(m.n_species):
@@ -349,7 +398,7 @@ def field_energies(m: Model, rho_hat: np.ndarray) -> Dict[str, float]:
             e_chi += chi / m.rho0 / V * float(np.sum(u_hat * np.real(np.conj(rp[K]) * rp[Kp])))
     tot = rp.sum(axis=0)
     p = u_hat * np.abs(tot) ** 2
-    p[0, 0, 0] = 0.0
+    p[(0,) * m.dim] = 0.0
     e_kappa = m.kappa / (2.0 * m.rho0) / V * float(np.sum(p))
     out = {"chi": e_chi, "kappa": e_kappa, "elec": 0.0}
     if _has_charges(m):
@@ -377,6 +426,21 @@ def nonbonded_forces(m: Model, pos: np.ndarray, variant: str = "ik") -> np.ndarr
     if variant != "analytic":
         raise ValueError(variant)
     n, P, dx = m.n, m.P, m.dx
+    if m.dim == 2:
+        s = wrap(pos[:, :2], m.L) / dx
+        jx, wx = stencil(s[:, 0], P)
+        jy, wy = stencil(s[:, 1], P)
+        _, dwx = stencil_derivative(s[:, 0], P)
+        _, dwy = stencil_derivative(s[:, 1], P)
+        wf = f["w"][m.species]
+        out = np.zeros((m.n_beads, 2))
+        rows = np.arange(m.n_beads)
+        for a in range(P):
+            for b in range(P):
+                val = wf[rows, jx[:, a] % n, jy[:, b] % n]
+                out[:, 0] -= dwx[:, a] / dx * wy[:, b] * val
+                out[:, 1] -= wx[:, a] * dwy[:, b] / dx * val
+        return out
     s = wrap(pos, m.L) / dx
     js, ws, dws = [], [], []
     for d in range(3):
@@ -404,7 +468,7 @@ def forces(m: Model, pos: np.ndarray, variant: str = "ik") -> np.ndarray:
 
 def energies(m: Model, pos: np.ndarray) -> Dict[str, float]:
     rho = spread(m, pos)
-    e = field_energies(m, np.fft.fftn(rho, axes=(1, 2, 3)))
+    e = field_energies(m, np.fft.fftn(rho, axes=tuple(range(1, m.dim + 1))))
     e["bond"] = bond_energy(m, pos)
     return e
 
@@ -481,7 +545,7 @@ def initial_state(m: Model, pos: np.ndarray, force_fn=None) -> State:
     F^0 evaluated at r^0. ``force_fn(m, pos)`` defaults to ``forces``."""
     force_fn = forces if force_fn is None else force_fn
     ids = np.arange(m.n_beads)
-    vel = np.sqrt(m.kT / m.mass) * gaussian_triplets(ids, VELOCITY_INIT_STEP, m.seed)
+    vel = np.sqrt(m.kT / m.mass) * gaussian_triplets(ids, VELOCITY_INIT_STEP, m.seed)[:, : m.dim]
     p = wrap(pos, m.L)
     return State(p, vel, force_fn(m, p), 0)
 
@@ -497,7 +561,7 @@ def gjf_step(m: Model, st: State, force_fn=None) -> State:
     dt, mass, alpha = m.dt, m.mass, m.friction
     ga = (1.0 - alpha * dt / (2 * mass)) / (1.0 + alpha * dt / (2 * mass))
     gb = 1.0 / (1.0 + alpha * dt / (2 * mass))
-    beta = np.sqrt(2.0 * alpha * m.kT * dt) * gaussian_triplets(np.arange(m.n_beads), st.step + 1, m.seed)
+    beta = np.sqrt(2.0 * alpha * m.kT * dt) * gaussian_triplets(np.arange(m.n_beads), st.step + 1, m.seed)[:, : m.dim]
     r_new = st.pos + gb * dt * st.vel + gb * dt * dt / (2 * mass) * st.force + gb * dt / (2 * mass) * beta
     r_new = wrap(r_new, m.L)
     f_new = (forces if force_fn is None else force_fn)(m, r_new)
@@ -532,7 +596,7 @@ def em_step(m: Model, st: State, force_fn=None) -> State:
     velocity in this dynamics; ``vel`` stays zero.
     """
     dt, alpha = m.dt, m.friction
-    xi = gaussian_triplets(np.arange(m.n_beads), st.step + 1, m.seed)
+    xi = gaussian_triplets(np.arange(m.n_beads), st.step + 1, m.seed)[:, : m.dim]
     r_new = wrap(st.pos + dt / alpha * st.force + np.sqrt(2.0 * m.kT * dt / alpha) * xi, m.L)
     f_new = (forces if force_fn is None else force_fn)(m, r_new)
     return State(r_new, np.zeros_like(st.vel), f_new, st.step + 1)
@@ -541,7 +605,7 @@ def em_step(m: Model, st: State, force_fn=None) -> State:
 def em_initial_state(m: Model, pos: np.ndarray, force_fn=None) -> State:
     force_fn = forces if force_fn is None else force_fn
     p = wrap(pos, m.L)
-    return State(p, np.zeros((m.n_beads, 3)), force_fn(m, p), 0)
+    return State(p, np.zeros((m.n_beads, m.dim)), force_fn(m, p), 0)
 
 
 def langevin_force(m: Model, v_half: np.ndarray, step: int) -> np.ndarray:
@@ -550,7 +614,7 @@ def langevin_force(m: Model, v_half: np.ndarray, step: int) -> np.ndarray:
     acts on the half-step velocity v^{n-1/2} = v^n - (dt/2m) F^n, the
     velocity a velocity-Verlet step holds when forces are evaluated."""
     sigma = np.sqrt(2.0 * m.friction * m.kT / m.dt)
-    return -m.friction * v_half + sigma * gaussian_triplets(np.arange(m.n_beads), step, m.seed)
+    return -m.friction * v_half + sigma * gaussian_triplets(np.arange(m.n_beads), step, m.seed)[:, : m.dim]
 
 
 def vv_initial_state(m: Model, pos: np.ndarray, vel: np.ndarray, force_fn=None, step: int = 0) -> State:

@@ -28,6 +28,7 @@ TILD_FP32, TILD_FP64 = 0, 1
 TILD_DTYPE_F32, TILD_DTYPE_F64 = 0, 1
 TILD_HOST, TILD_DEVICE = 0, 1
 TILD_COMPUTE_ENERGY, TILD_COMPUTE_FORCES = 1, 2
+TILD_LAYOUT_AOS, TILD_LAYOUT_SOA = 0, 1
 
 STATUS_NAMES = {0: "TILD_OK", -1: "TILD_EINVAL", -2: "TILD_ENOMEM", -3: "TILD_EUNSUPPORTED", -4: "TILD_EDEVICE",
                 -5: "TILD_ENAN", -6: "TILD_ESTATE"}
@@ -47,6 +48,14 @@ class tild_energy_grad(ctypes.Structure):
                                                "e_elec")]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class tild_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
 class tild_energy(ctypes.Structure):
     _fields_ = [("e_bond", ctypes.c_double), ("e_chi", ctypes.c_double), ("e_kappa", ctypes.c_double),
                 ("kinetic", ctypes.c_double), ("net_force", ctypes.c_double * 3), ("e_elec", ctypes.c_double)]
@@ -57,6 +66,11 @@ _I = ctypes.c_int
 _I64 = ctypes.c_int64
 _SIGS = {
     "tild_create": [ctypes.POINTER(tild_params), ctypes.POINTER(_P)],
+    "tild_create_with_allocator": [ctypes.POINTER(tild_params), ctypes.POINTER(tild_allocator), ctypes.POINTER(_P)],
+    "tild_set_species": [_P, _I, _P],
+    "tild_set_bonds": [_P, _I64, _P],
+    "tild_set_chi_matrix": [_P, _P],
+    "tild_set_layout": [_P, _I],
     "tild_destroy": [_P],
     "tild_set_chains": [_P, _I, ctypes.POINTER(tild_moltype), ctypes.c_double],
     "tild_set_interactions": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double],
@@ -165,27 +179,71 @@ def _buffer(arr, n_elems: int):
     return ctypes.c_void_p(a.ctypes.data), code, TILD_HOST, a
 
 
+class TorchAllocator:
+    """Device memory of a context from PyTorch's caching allocator, for
+    tild_create_with_allocator. Counts live blocks and bytes (for tests)."""
+
+    def __init__(self, device: int = 0):
+        import torch
+
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self.n_alloc = 0
+        self.fail_after = None  # tests: refuse the allocation after this many
+
+        def _alloc(nbytes, _user):
+            if self.fail_after is not None and self.n_alloc >= self.fail_after:
+                return None
+            ptr = self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device)
+            self.live[ptr] = int(nbytes)
+            self.n_alloc += 1
+            return ptr
+
+        def _free(ptr, _nbytes, _user):
+            self.live.pop(ptr, None)
+            self.torch.cuda.caching_allocator_delete(ptr)
+
+        self._fns = (ALLOC_FN(_alloc), FREE_FN(_free))  # keep the callbacks alive
+        self.struct = tild_allocator(self._fns[0], self._fns[1], None)
+
+    @property
+    def live_bytes(self) -> int:
+        return sum(self.live.values())
+
+
 class Tild:
     """One TILD context (thin wrapper over the C ABI)."""
 
     def __init__(self, L: float, n: int, pmeorder: int = 1, precision: str = "fp32", seed: int = 0,
-                 sort_every: int = 0):
+                 sort_every: int = 0, allocator: Optional[TorchAllocator] = None, dim: int = 3):
+        """A context for a cubic box (dim=3) or a square box with an n x n
+        grid (dim=2; per-bead arrays keep three components, z unused)."""
         lib = load()
         p = tild_params()
         p.L[:] = [L, L, L]
-        p.n[:] = [n, n, n]
+        p.n[:] = [n, n, n] if dim == 3 else [n, n, 1]
+        self.dim = dim
+        self.nz = n if dim == 3 else 1
         p.pmeorder = pmeorder
         p.precision = TILD_FP32 if precision == "fp32" else TILD_FP64
         p.seed = seed
         p.sort_every = sort_every
         ctx = ctypes.c_void_p()
-        check(lib.tild_create(ctypes.byref(p), ctypes.byref(ctx)), None)
+        self.allocator = allocator  # must outlive the context
+        if allocator is not None:
+            check(lib.tild_create_with_allocator(ctypes.byref(p), ctypes.byref(allocator.struct), ctypes.byref(ctx)),
+                  None)
+        else:
+            check(lib.tild_create(ctypes.byref(p), ctypes.byref(ctx)), None)
         self.ctx = ctx
         self.lib = lib
         self.n = n
         self.L = L
         self.np_dtype = np.float32 if precision == "fp32" else np.float64
         self.n_beads = 0
+        self.n_species = 2
+        self.layout = "aos"
         self.integrator = (0.005, 1.0, 1.0, 1.0)  # dt, friction, kT, mass (the library defaults)
         self.scheme = "gjf"
         self.force_method = "ik"
@@ -227,6 +285,48 @@ class Tild:
             total += nc * N
         self._chk(self.lib.tild_set_chains(self.ctx, len(types), arr, b))
         self.n_beads = total
+        self.n_species = 2
+
+    def set_species(self, n_species: int, species=None) -> None:
+        """Species count (1..4) and, optionally, every bead's species (int
+        array by bead id); None keeps the chains' A/B pattern."""
+        ptr = ctypes.c_void_p()
+        keep = None
+        if species is not None:
+            keep = np.ascontiguousarray(species, dtype=np.int32)
+            if keep.size != self.n_beads:
+                raise ValueError("one species per bead")
+            ptr = ctypes.c_void_p(keep.ctypes.data)
+        self._chk(self.lib.tild_set_species(self.ctx, int(n_species), ptr))
+        self.n_species = int(n_species)
+
+    def set_bonds(self, pairs) -> None:
+        """Explicit bond list, an (n_bonds, 2) int array of bead ids."""
+        a = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        ptr = ctypes.c_void_p(a.ctypes.data) if a.size else ctypes.c_void_p()
+        self._chk(self.lib.tild_set_bonds(self.ctx, int(a.shape[0]), ptr))
+
+    def set_chi_matrix(self, chi) -> None:
+        a = np.ascontiguousarray(chi, dtype=np.float64)
+        if a.shape != (self.n_species, self.n_species):
+            raise ValueError("chi must be n_species x n_species")
+        self._chk(self.lib.tild_set_chi_matrix(self.ctx, ctypes.c_void_p(a.ctypes.data)))
+
+    LAYOUTS = {"aos": TILD_LAYOUT_AOS, "soa": TILD_LAYOUT_SOA}
+
+    def set_layout(self, layout: str) -> None:
+        """Per-bead vectors as "aos" [n][3] (default) or "soa" [3][n]."""
+        self._chk(self.lib.tild_set_layout(self.ctx, self.LAYOUTS[layout]))
+        self.layout = layout
+
+    def _vec(self, r):
+        if not isinstance(r, np.ndarray):
+            return r
+        return r.reshape(-1, 3) if self.layout == "aos" else r.reshape(3, -1)
+
+    @property
+    def n_pairs(self) -> int:
+        return 2 if self.n_species > 2 else 1
 
     def set_interactions(self, chi: float, kappa: float, a: float) -> None:
         self._chk(self.lib.tild_set_interactions(self.ctx, chi, kappa, a))
@@ -286,27 +386,35 @@ class Tild:
         return out
 
     def positions(self, out=None, dtype=np.float64):
-        r = self._out(self.lib.tild_get_positions, 3 * self.n_beads, out, dtype)
-        return r.reshape(-1, 3) if isinstance(r, np.ndarray) else r
+        return self._vec(self._out(self.lib.tild_get_positions, 3 * self.n_beads, out, dtype))
 
     def velocities(self, out=None, dtype=np.float64):
-        r = self._out(self.lib.tild_get_velocities, 3 * self.n_beads, out, dtype)
-        return r.reshape(-1, 3) if isinstance(r, np.ndarray) else r
+        return self._vec(self._out(self.lib.tild_get_velocities, 3 * self.n_beads, out, dtype))
 
     def density(self, out=None, dtype=np.float64):
-        r = self._out(self.lib.tild_get_density, 2 * self.n ** 3, out, dtype)
-        return r.reshape(2, self.n, self.n, self.n) if isinstance(r, np.ndarray) else r
+        S = self.n_species
+        r = self._out(self.lib.tild_get_density, S * self.nz * self.n ** 2, out, dtype)
+        return r.reshape(S, self.nz, self.n, self.n) if isinstance(r, np.ndarray) else r
 
     def spectrum(self, out=None, dtype=np.float64):
-        r = self._out(self.lib.tild_get_spectrum, 2 * self.n ** 3, out, dtype)
+        """DFT of rho_0 + i rho_1 [kz][ky][kx] (with more than two species,
+        [pair][kz][ky][kx])."""
+        npr = self.n_pairs
+        r = self._out(self.lib.tild_get_spectrum, 2 * npr * self.nz * self.n ** 2, out, dtype)
         if isinstance(r, np.ndarray):
-            r = r.reshape(self.n, self.n, self.n, 2)
-            return r[..., 0] + 1j * r[..., 1]
+            r = r.reshape(npr, self.nz, self.n, self.n, 2)
+            r = r[..., 0] + 1j * r[..., 1]
+            return r[0] if npr == 1 else r
         return r
 
     def field_gradient(self, out=None, dtype=np.float64):
-        r = self._out(self.lib.tild_get_field_gradient, 6 * self.n ** 3, out, dtype)
-        return r.reshape(3, self.n, self.n, self.n, 2) if isinstance(r, np.ndarray) else r
+        npr = self.n_pairs
+        D = self.dim
+        r = self._out(self.lib.tild_get_field_gradient, 2 * D * npr * self.nz * self.n ** 2, out, dtype)
+        if isinstance(r, np.ndarray):
+            r = r.reshape(npr, D, self.nz, self.n, self.n, 2)
+            return r[0] if npr == 1 else r
+        return r
 
     def compute(self, forces: bool = True, energy: bool = True, out=None, dtype=np.float64):
         e = tild_energy()
@@ -319,8 +427,8 @@ class Tild:
         self._chk(self.lib.tild_compute(self.ctx, what, ctypes.byref(e), ptr, code, where))
         en = {"bond": e.e_bond, "chi": e.e_chi, "kappa": e.e_kappa, "elec": e.e_elec, "kinetic": e.kinetic,
               "net_force": np.array(e.net_force[:])}
-        if f is not None and isinstance(f, np.ndarray):
-            f = f.reshape(-1, 3)
+        if f is not None:
+            f = self._vec(f)
         return f, en
 
     def force_vjp(self, lam, out=None):
@@ -336,9 +444,7 @@ class Tild:
             raise ValueError("force_vjp: lam and out must share dtype and memory space")
         th = (ctypes.c_double * 3)()
         self._chk(self.lib.tild_force_vjp(self.ctx, lptr, optr, lcode, lwhere, th))
-        if isinstance(out, np.ndarray):
-            out = out.reshape(-1, 3)
-        return out, {"chi": th[0], "kappa": th[1], "a": th[2]}
+        return self._vec(out), {"chi": th[0], "kappa": th[1], "a": th[2]}
 
     def energy_gradient(self, with_positions: bool = True, out=None, dtype=np.float64):
         """(dict of U, its terms and dU/dchi, dU/dkappa, dU/da; dU/dr or None)."""
@@ -349,9 +455,7 @@ class Tild:
             ptr, code, where, _keep = _buffer(buf, 3 * self.n_beads)
         self._chk(self.lib.tild_energy_gradient(self.ctx, ctypes.byref(g), ptr, code, where))
         d = {k: getattr(g, k) for k, _ in tild_energy_grad._fields_}
-        if isinstance(buf, np.ndarray):
-            buf = buf.reshape(-1, 3)
-        return d, buf
+        return d, (self._vec(buf) if buf is not None else None)
 
     def step_count(self) -> int:
         s = ctypes.c_int64()

@@ -1,7 +1,9 @@
 // extern "C" boundary of the TILD engine: argument validation, error text,
 // and dispatch to the FP32 or FP64 engine.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 #include <memory>
 #include <string>
 
@@ -13,6 +15,7 @@ struct tild_ctx {
     HostConfig cfg;
     std::unique_ptr<EngineBase> eng;
     bool have_chains = false;
+    int layout = TILD_LAYOUT_AOS;
     std::string err;
 };
 
@@ -44,24 +47,104 @@ bool valid_io(int dtype, int where) {
     return (dtype == TILD_DTYPE_F32 || dtype == TILD_DTYPE_F64) && (where == TILD_HOST || where == TILD_DEVICE);
 }
 
+template <typename TV> void host_transpose3(const TV* in, TV* out, size_t n, bool to_aos) {
+    for (size_t i = 0; i < n; ++i)
+        for (size_t d = 0; d < 3; ++d) {
+            if (to_aos)
+                out[3 * i + d] = in[d * n + i];
+            else
+                out[d * n + i] = in[3 * i + d];
+        }
+}
+
+// Per-bead vector arrays of one call in the context's layout: SoA arrays are
+// transposed to the AoS arrays the engine reads and writes (host arrays on
+// the host, device arrays through slots of the context's device scratch).
+struct LayoutIO {
+    tild_ctx* c;
+    int dtype, where;
+    size_t n;
+    std::vector<std::vector<unsigned char>> host;
+    unsigned char* dev = nullptr;
+    tild_status st = TILD_OK;
+    LayoutIO(tild_ctx* ctx, int dt, int wh, int slots)
+        : c(ctx), dtype(dt), where(wh), n((size_t)ctx->cfg.n_beads), host(slots) {
+        if (soa() && where == TILD_DEVICE) {
+            void* p = nullptr;
+            st = c->eng->io_scratch(slots * bytes(), &p);
+            dev = (unsigned char*)p;
+            if (st) c->err = c->eng->err;
+        }
+    }
+    bool soa() const { return c->layout == TILD_LAYOUT_SOA; }
+    size_t bytes() const { return 3 * n * (dtype == TILD_DTYPE_F32 ? 4 : 8); }
+    void transpose(const void* in, void* out, bool to_aos) {
+        if (where == TILD_HOST) {
+            if (dtype == TILD_DTYPE_F32)
+                host_transpose3((const float*)in, (float*)out, n, to_aos);
+            else
+                host_transpose3((const double*)in, (double*)out, n, to_aos);
+        } else if (!st) {
+            st = c->eng->transpose3(in, out, n, dtype, to_aos);
+            if (st) c->err = c->eng->err;
+        }
+    }
+    void* slot(int k) {
+        if (where == TILD_HOST) {
+            host[k].resize(bytes());
+            return host[k].data();
+        }
+        return dev + k * bytes();
+    }
+    // an input array -> the AoS pointer for the engine
+    const void* in(const void* p, int k) {
+        if (!soa() || !p || st) return p;
+        void* a = slot(k);
+        transpose(p, a, true);
+        return a;
+    }
+    // an output array -> the AoS buffer the engine writes (then done())
+    void* out(void* p, int k) { return (!soa() || !p || st) ? p : slot(k); }
+    void done(void* p, int k) {
+        if (soa() && p && !st) transpose(slot(k), p, false);
+    }
+};
+
 }  // namespace
 
 void tild::set_global_error(const std::string& msg) { g_create_error = msg; }
 
 extern "C" {
 
-tild_status tild_create(const tild_params* p, tild_ctx** out) {
+static tild_status create_ctx(const tild_params* p, const tild_allocator* a, tild_ctx** out);
+
+tild_status tild_create(const tild_params* p, tild_ctx** out) { return create_ctx(p, nullptr, out); }
+
+tild_status tild_create_with_allocator(const tild_params* p, const tild_allocator* a, tild_ctx** out) {
+    if (a && a->alloc && !a->free) {
+        g_create_error = "tild_create_with_allocator: an allocator needs both alloc and free";
+        return TILD_EINVAL;
+    }
+    return create_ctx(p, a, out);
+}
+
+static tild_status create_ctx(const tild_params* p, const tild_allocator* a, tild_ctx** out) {
     if (!p || !out) {
         g_create_error = "tild_create: NULL argument";
         return TILD_EINVAL;
     }
     *out = nullptr;
-    if (!(p->L[0] > 0) || p->L[0] != p->L[1] || p->L[0] != p->L[2] || !std::isfinite(p->L[0])) {
-        g_create_error = "tild_create: the box must be cubic with L > 0";
+    const bool two_d = p->n[2] == 1;  // Listing infile's "Dim 2": an n x n grid, z unused
+    if (!(p->L[0] > 0) || p->L[0] != p->L[1] || (!two_d && p->L[0] != p->L[2]) || !std::isfinite(p->L[0])) {
+        g_create_error = two_d ? "tild_create: a 2D box must be square with L > 0" : "tild_create: the box must be cubic with L > 0";
         return TILD_EUNSUPPORTED;
     }
-    if (p->n[0] != p->n[1] || p->n[0] != p->n[2] || !supported_n(p->n[0])) {
-        g_create_error = "tild_create: the grid must be cubic with n a power of two in [8, 256] or 24, 40, 48, 80";
+    const int n = p->n[0];
+    const bool fast = !two_d && p->n[1] == n && p->n[2] == n && supported_n(n) && (p->precision != TILD_FP64 || n <= 128);
+    const int n_max = two_d ? 2048 : (p->precision == TILD_FP64 ? 128 : 256);
+    if (p->n[1] != n || (!two_d && p->n[2] != n) || n < 4 || n > n_max) {
+        g_create_error = two_d ? "tild_create: a 2D grid is n x n x 1 with 4 <= n <= 2048"
+                               : "tild_create: the grid must be cubic with 4 <= n <= 256 (FP64: 128)";
         return TILD_EUNSUPPORTED;
     }
     if (p->pmeorder < 1 || p->pmeorder > 4) {
@@ -72,10 +155,7 @@ tild_status tild_create(const tild_params* p, tild_ctx** out) {
         g_create_error = "tild_create: precision must be TILD_FP32 or TILD_FP64";
         return TILD_EINVAL;
     }
-    if (p->precision == TILD_FP64 && p->n[0] > 128) {
-        g_create_error = "tild_create: FP64 grids are limited to 128^3";
-        return TILD_EUNSUPPORTED;
-    }
+
     if (p->sort_every < 0) {
         g_create_error = "tild_create: sort_every must be >= 0";
         return TILD_EINVAL;
@@ -83,11 +163,14 @@ tild_status tild_create(const tild_params* p, tild_ctx** out) {
     std::unique_ptr<tild_ctx> c(new tild_ctx());
     c->cfg.L = p->L[0];
     c->cfg.n = p->n[0];
+    c->cfg.dim = two_d ? 2 : 3;
+    c->cfg.generic = !fast;
     c->cfg.pmeorder = p->pmeorder;
     c->cfg.precision = p->precision;
     c->cfg.seed = p->seed;
     c->cfg.sort_every = p->sort_every == 0 ? 20 : p->sort_every;
     std::memset(&c->cfg.topo, 0, sizeof(c->cfg.topo));
+    if (a && a->alloc) c->cfg.allocator = *a;
     c->eng.reset(p->precision == TILD_FP32 ? make_engine_f32() : make_engine_f64());
     const tild_status st = c->eng->init(&c->cfg);
     if (st != TILD_OK) {
@@ -117,7 +200,7 @@ tild_status tild_set_chains(tild_ctx* c, int n_types, const tild_moltype* t, dou
         topo.N[k] = t[k].N;
         topo.n_a[k] = t[k].n_a;
         total += t[k].n_chains * (int64_t)t[k].N;
-        if (total >= (int64_t)1 << 31) return fail(c, TILD_EUNSUPPORTED, "set_chains: at most 2^31-1 beads");
+        if (total >= (int64_t)1 << 29) return fail(c, TILD_EUNSUPPORTED, "set_chains: at most 2^29-1 beads");
     }
     if (total < 1) return fail(c, TILD_EINVAL, "set_chains: no beads");
     topo.start[n_types] = (int)total;
@@ -125,6 +208,10 @@ tild_status tild_set_chains(tild_ctx* c, int n_types, const tild_moltype* t, dou
     c->cfg.topo = topo;
     c->cfg.n_beads = (int)total;
     c->cfg.b = b;
+    c->cfg.n_species = 2;  // the chains' A/B pattern and linear bonds
+    c->cfg.species_of_bead.clear();
+    c->cfg.explicit_bonds = false;
+    c->cfg.bond_pairs.clear();
     const tild_status st = c->eng->set_chains();
     if (st) return from_engine(c, st);
     c->have_chains = true;
@@ -150,12 +237,95 @@ static tild_status reparam(tild_ctx* c, const HostConfig& next) {
     return TILD_OK;
 }
 
+// Topology change (species or bonds): v^n kept across it as for parameters.
+static tild_status retopo(tild_ctx* c, const HostConfig& next) {
+    const bool keep = c->eng->has_velocities();
+    tild_status st;
+    if (keep && (st = c->eng->save_velocities())) return from_engine(c, st);
+    c->cfg = next;
+    if ((st = c->eng->set_topology())) return from_engine(c, st);
+    c->eng->params_changed();
+    if (keep && (st = c->eng->restore_velocities())) return from_engine(c, st);
+    return TILD_OK;
+}
+
+tild_status tild_set_species(tild_ctx* c, int n_species, const int32_t* species) {
+    if (!c) return TILD_EINVAL;
+    if (!c->have_chains) return fail(c, TILD_ESTATE, "set_species: call tild_set_chains first");
+    if (n_species < 1 || n_species > 4) return fail(c, TILD_EINVAL, "set_species: 1..4 species");
+    if (!species && n_species != 2)
+        return fail(c, TILD_EINVAL, "set_species: without a species array the chains' A/B pattern gives two species");
+    HostConfig next = c->cfg;
+    next.n_species = n_species;
+    next.species_of_bead.clear();
+    if (species) {
+        next.species_of_bead.resize(next.n_beads);
+        for (int i = 0; i < next.n_beads; ++i) {
+            if (species[i] < 0 || species[i] >= n_species)
+                return fail(c, TILD_EINVAL, "set_species: species values must lie in [0, n_species)");
+            next.species_of_bead[i] = (unsigned char)species[i];
+        }
+    }
+    if (n_species > 2 && next.bjerrum > 0 && (next.q_a != 0 || next.q_b != 0))
+        return fail(c, TILD_EUNSUPPORTED, "set_species: electrostatics are implemented for up to two species");
+    for (int K = n_species; K < 4; ++K)
+        for (int K2 = 0; K2 < 4; ++K2) next.chi_mat[K][K2] = next.chi_mat[K2][K] = 0.0;
+    return retopo(c, next);
+}
+
+tild_status tild_set_bonds(tild_ctx* c, int64_t n_bonds, const int32_t* pairs) {
+    if (!c) return TILD_EINVAL;
+    if (!c->have_chains) return fail(c, TILD_ESTATE, "set_bonds: call tild_set_chains first");
+    if (n_bonds < 0 || (n_bonds > 0 && !pairs)) return fail(c, TILD_EINVAL, "set_bonds: need n_bonds >= 0 and pairs");
+    const int N = c->cfg.n_beads;
+    std::vector<int64_t> keys((size_t)n_bonds);
+    for (int64_t k = 0; k < n_bonds; ++k) {
+        const int i = pairs[2 * k], j = pairs[2 * k + 1];
+        if (i < 0 || j < 0 || i >= N || j >= N || i == j)
+            return fail(c, TILD_EINVAL, "set_bonds: bead ids out of range or a self-bond");
+        keys[k] = (int64_t)std::min(i, j) * N + std::max(i, j);
+    }
+    std::sort(keys.begin(), keys.end());
+    if (std::adjacent_find(keys.begin(), keys.end()) != keys.end())
+        return fail(c, TILD_EINVAL, "set_bonds: a bond is listed twice");
+    HostConfig next = c->cfg;
+    next.explicit_bonds = true;
+    next.bond_pairs.assign(pairs, pairs + 2 * n_bonds);
+    return retopo(c, next);
+}
+
+tild_status tild_set_chi_matrix(tild_ctx* c, const double* chi) {
+    if (!c) return TILD_EINVAL;
+    if (!chi) return fail(c, TILD_EINVAL, "set_chi_matrix: NULL matrix");
+    const int S = c->cfg.n_species;
+    for (int K = 0; K < S; ++K)
+        for (int K2 = 0; K2 < S; ++K2) {
+            const double v = chi[K * S + K2];
+            if (!std::isfinite(v) || v != chi[K2 * S + K] || (K == K2 && v != 0.0))
+                return fail(c, TILD_EINVAL, "set_chi_matrix: need a finite symmetric matrix with a zero diagonal");
+        }
+    HostConfig next = c->cfg;
+    for (int K = 0; K < S; ++K)
+        for (int K2 = 0; K2 < S; ++K2) next.chi_mat[K][K2] = chi[K * S + K2];
+    next.chi = S >= 2 ? next.chi_mat[0][1] : 0.0;
+    next.have_interactions = true;
+    return reparam(c, next);
+}
+
+tild_status tild_set_layout(tild_ctx* c, int layout) {
+    if (!c) return TILD_EINVAL;
+    if (layout != TILD_LAYOUT_AOS && layout != TILD_LAYOUT_SOA) return fail(c, TILD_EINVAL, "set_layout: unknown layout");
+    c->layout = layout;
+    return TILD_OK;
+}
+
 tild_status tild_set_interactions(tild_ctx* c, double chi_ab, double kappa, double a) {
     if (!c) return TILD_EINVAL;
     if (!std::isfinite(chi_ab) || !std::isfinite(kappa) || !(kappa >= 0) || !(a > 0) || !std::isfinite(a))
         return fail(c, TILD_EINVAL, "set_interactions: need finite chi, kappa >= 0, a > 0");
     HostConfig next = c->cfg;
     next.chi = chi_ab;
+    next.chi_mat[0][1] = next.chi_mat[1][0] = chi_ab;
     next.kappa = kappa;
     next.a = a;
     next.have_interactions = true;
@@ -181,6 +351,10 @@ tild_status tild_set_electrostatics(tild_ctx* c, double q_a, double q_b, double 
     if (!std::isfinite(q_a) || !std::isfinite(q_b) || !std::isfinite(bjerrum) || !std::isfinite(smear) ||
         !(bjerrum >= 0) || !(smear > 0))
         return fail(c, TILD_EINVAL, "set_electrostatics: need finite charges, bjerrum >= 0 and smear > 0");
+    if (c->cfg.n_species > 2 && bjerrum > 0 && (q_a != 0 || q_b != 0))
+        return fail(c, TILD_EUNSUPPORTED, "set_electrostatics: implemented for up to two species");
+    if (c->cfg.generic && bjerrum > 0 && (q_a != 0 || q_b != 0))
+        return fail(c, TILD_EUNSUPPORTED, "set_electrostatics: implemented for the 3D grid sizes of the tiled kernels");
     HostConfig next = c->cfg;
     next.q_a = q_a;
     next.q_b = q_b;
@@ -193,6 +367,8 @@ tild_status tild_set_force_method(tild_ctx* c, int method) {
     if (!c) return TILD_EINVAL;
     if (method != TILD_FORCE_IK && method != TILD_FORCE_ANALYTIC)
         return fail(c, TILD_EINVAL, "set_force_method: unknown method");
+    if (method == TILD_FORCE_ANALYTIC && c->cfg.generic)
+        return fail(c, TILD_EUNSUPPORTED, "set_force_method: the analytic force is implemented for the 3D grid sizes of the tiled kernels");
     HostConfig next = c->cfg;
     next.force_method = method;
     return reparam(c, next);
@@ -217,7 +393,10 @@ tild_status tild_set_positions(tild_ctx* c, const void* xyz, int dtype, int wher
     if (!c) return TILD_EINVAL;
     if (!xyz || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "set_positions: bad pointer, dtype or where");
     if (!c->have_chains) return fail(c, TILD_ESTATE, "set_positions: call tild_set_chains first");
-    return from_engine(c, c->eng->set_positions(xyz, dtype, where));
+    LayoutIO io(c, dtype, where, 1);
+    const void* a = io.in(xyz, 0);
+    if (io.st) return io.st;
+    return from_engine(c, c->eng->set_positions(a, dtype, where));
 }
 
 tild_status tild_init_velocities(tild_ctx* c) {
@@ -230,7 +409,10 @@ tild_status tild_set_velocities(tild_ctx* c, const void* v, int dtype, int where
     if (!c) return TILD_EINVAL;
     if (!v || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "set_velocities: bad pointer, dtype or where");
     if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "set_velocities: positions not set");
-    return from_engine(c, c->eng->set_velocities(v, dtype, where));
+    LayoutIO io(c, dtype, where, 1);
+    const void* a = io.in(v, 0);
+    if (io.st) return io.st;
+    return from_engine(c, c->eng->set_velocities(a, dtype, where));
 }
 
 tild_status tild_step(tild_ctx* c, int64_t n_steps) {
@@ -252,7 +434,13 @@ tild_status tild_compute(tild_ctx* c, unsigned what, tild_energy* e, void* force
     if ((what & TILD_COMPUTE_FORCES) && (!forces_out || !valid_io(dtype, where)))
         return fail(c, TILD_EINVAL, "compute: forces requested with a bad buffer, dtype or where");
     if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "compute: positions not set");
-    return from_engine(c, c->eng->compute(what, e, (what & TILD_COMPUTE_FORCES) ? forces_out : nullptr, dtype, where));
+    void* f = (what & TILD_COMPUTE_FORCES) ? forces_out : nullptr;
+    LayoutIO io(c, dtype, where, 1);
+    if (io.st) return io.st;
+    tild_status st = c->eng->compute(what, e, io.out(f, 0), dtype, where);
+    if (st) return from_engine(c, st);
+    io.done(f, 0);
+    return io.st;
 }
 
 tild_status tild_energy_gradient(tild_ctx* c, tild_energy_grad* g, void* dU_dr, int dtype, int where) {
@@ -260,28 +448,49 @@ tild_status tild_energy_gradient(tild_ctx* c, tild_energy_grad* g, void* dU_dr, 
     if (!g) return fail(c, TILD_EINVAL, "energy_gradient: g == NULL");
     if (dU_dr && !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "energy_gradient: bad dtype or where");
     if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "energy_gradient: positions not set");
-    return from_engine(c, c->eng->energy_gradient(g, dU_dr, dtype, where));
+    LayoutIO io(c, dtype, where, 1);
+    if (io.st) return io.st;
+    tild_status st = c->eng->energy_gradient(g, io.out(dU_dr, 0), dtype, where);
+    if (st) return from_engine(c, st);
+    io.done(dU_dr, 0);
+    return io.st;
 }
 
 tild_status tild_force_vjp(tild_ctx* c, const void* lam, void* out, int dtype, int where, double* dtheta) {
     if (!c) return TILD_EINVAL;
     if (!lam || !out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "force_vjp: bad pointer, dtype or where");
     if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "force_vjp: positions not set");
-    return from_engine(c, c->eng->force_vjp(lam, out, dtype, where, dtheta));
+    LayoutIO io(c, dtype, where, 2);
+    const void* l = io.in(lam, 0);
+    if (io.st) return io.st;
+    tild_status st = c->eng->force_vjp(l, io.out(out, 1), dtype, where, dtheta);
+    if (st) return from_engine(c, st);
+    io.done(out, 1);
+    return io.st;
 }
 
 tild_status tild_get_positions(tild_ctx* c, void* out, int dtype, int where) {
     if (!c) return TILD_EINVAL;
     if (!out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "get_positions: bad pointer, dtype or where");
     if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "get_positions: positions not set");
-    return from_engine(c, c->eng->get_positions(out, dtype, where));
+    LayoutIO io(c, dtype, where, 1);
+    if (io.st) return io.st;
+    tild_status st = c->eng->get_positions(io.out(out, 0), dtype, where);
+    if (st) return from_engine(c, st);
+    io.done(out, 0);
+    return io.st;
 }
 
 tild_status tild_get_velocities(tild_ctx* c, void* out, int dtype, int where) {
     if (!c) return TILD_EINVAL;
     if (!out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "get_velocities: bad pointer, dtype or where");
     if (!c->eng->has_velocities()) return fail(c, TILD_ESTATE, "get_velocities: velocities not set");
-    return from_engine(c, c->eng->get_velocities(out, dtype, where));
+    LayoutIO io(c, dtype, where, 1);
+    if (io.st) return io.st;
+    tild_status st = c->eng->get_velocities(io.out(out, 0), dtype, where);
+    if (st) return from_engine(c, st);
+    io.done(out, 0);
+    return io.st;
 }
 
 tild_status tild_get_density(tild_ctx* c, void* out, int dtype, int where) {
@@ -349,8 +558,16 @@ tild_status tild_trajectory_vjp(tild_ctx* c, int64_t n_steps, int checkpoint_eve
     if (n_steps < 0 || checkpoint_every < 1 || !r_bar || !r0_bar || !v0_bar || !valid_io(dtype, where))
         return fail(c, TILD_EINVAL, "trajectory_vjp: bad argument");
     if (!c->eng->has_velocities()) return fail(c, TILD_ESTATE, "trajectory_vjp: positions and velocities must be set");
-    return from_engine(c, c->eng->trajectory_vjp(n_steps, checkpoint_every, r_bar, v_bar, dtype, where, r0_bar, v0_bar,
-                                                 dtheta));
+    LayoutIO io(c, dtype, where, 4);
+    const void* rb = io.in(r_bar, 0);
+    const void* vb = io.in(v_bar, 1);
+    if (io.st) return io.st;
+    tild_status st = c->eng->trajectory_vjp(n_steps, checkpoint_every, rb, vb, dtype, where, io.out(r0_bar, 2),
+                                            io.out(v0_bar, 3), dtheta);
+    if (st) return from_engine(c, st);
+    io.done(r0_bar, 2);
+    io.done(v0_bar, 3);
+    return io.st;
 }
 
 tild_status tild_autotune(tild_ctx* c, int64_t trial_steps, int* sort_every, double* ms_per_step) {

@@ -69,6 +69,14 @@ template <typename T> class BatchEngine final : public BatchBase {
                 err = "batch: replicas must share one device";
                 return TILD_EINVAL;
             }
+            if (e->generic_) {
+                err = "batch: replicas need the 3D grid sizes of the tiled kernels";
+                return TILD_EUNSUPPORTED;
+            }
+            if (e->NP_ != 1) {
+                err = "batch: replicas with more than two species are not batched";
+                return TILD_EUNSUPPORTED;
+            }
             if (!e->plane_fits_) {
                 err = "batch: replica grids must fit the single-plane xy passes";
                 return TILD_EUNSUPPORTED;

@@ -26,8 +26,13 @@
 //       u^{n+1} = v^{n+1/2} = u^n + (dt/m) F^n, r^{n+1} = r^n + dt u^{n+1}.
 //
 // Bead arrays are SoA in "slot" order: beads binned by cell (tile-major)
-// every few steps. Slot -> bead id in `id`; bonded neighbours by slot in
-// `nbr`. All results are independent of the slot order.
+// every few steps. Slot -> bead id and species in `id`; bonded neighbours by
+// slot in `nbr` (and `ext` for beads with more than two bonds). All results
+// are independent of the slot order.
+//
+// Species: up to four. The kernels carry them in pairs (species 2p and
+// 2p+1 as the real and imaginary parts of one complex field), so the density
+// has NS = 2 or 4 species slots and the gradient fields NS/2 pairs.
 #pragma once
 
 #include "common.cuh"
@@ -69,9 +74,10 @@ template <typename T> struct BeadBuffers {
     T* __restrict__ uz;
     const int* __restrict__ id;
     const int2* __restrict__ nbr;
+    const int* __restrict__ ext;  // neighbour lists of beads with more than two bonds (see for_each_extra_bond)
     const int* __restrict__ tile_start;  // [tiles^3 + 1] first slot of each tile
-    const cplx_t<T>* __restrict__ grad;  // [3][M] (A, B) pairs
-    unsigned long long* __restrict__ rho_fx;  // [2][M]
+    const cplx_t<T>* __restrict__ grad;  // [NS/2][4][M]: per species pair (d_x, d_y, d_z, potentials)
+    unsigned long long* __restrict__ rho_fx;  // [NS][M]
     const unsigned long long* step;  // device step counter: n+1 while step n -> n+1 runs
     unsigned int* err;
     T* __restrict__ f_out;        // FORCE: [n_beads][3] by id (may be null)
@@ -90,9 +96,22 @@ template <typename T> __device__ __forceinline__ T wrap_coord(T x, T L, T inv_L)
 
 template <typename T> __device__ __forceinline__ T min_image(T d, T L, T inv_L) { return d - L * rint(d * inv_L); }
 
-// Bead slots carry the bead id in bits 0..30 and the species in bit 31.
-__host__ __device__ __forceinline__ int slot_bead_id(int v) { return v & 0x7fffffff; }
-__host__ __device__ __forceinline__ int slot_species(int v) { return (int)((unsigned)v >> 31); }
+// Bead slots carry the bead id in bits 0..28 and the species in bits 29..31.
+constexpr int kSpeciesShift = 29;
+__host__ __device__ __forceinline__ int slot_bead_id(int v) { return v & 0x1fffffff; }
+__host__ __device__ __forceinline__ int slot_species(int v) { return (int)((unsigned)v >> kSpeciesShift); }
+
+// Bonded neighbours of a slot: nbr = (first, second), -1 for none. A bead
+// with more than two bonds has nbr.y = -2 - off and its neighbours after the
+// first in ext[off + 1 .. off + ext[off]] (slots, rewritten at every
+// re-binning; see bin_neighbours_explicit).
+template <class F> __device__ __forceinline__ void for_each_extra_bond(int2 nb, const int* __restrict__ ext, F&& f) {
+    if (nb.y < -1) {
+        const int off = -2 - nb.y;
+        const int cnt = ext[off];
+        for (int j = 1; j <= cnt; ++j) f(ext[off + j]);
+    }
+}
 
 // Shared-memory patch of one tile: grid points [org, org + W) per dimension
 // with W = 8 cells + stencil reach (+ an optional drift margin of kMargin
@@ -127,6 +146,7 @@ __device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_pa
                                              const typename vec4_of<T>::type* s_grad,
                                              const cplx_t<T>* __restrict__ grad, int n, int species, T& fx, T& fy,
                                              T& fz) {
+    // grad: the gradient fields of species pair species/2 (global path)
     using PT = Patch<P>;
     T gx = 0, gy = 0, gz = 0;
     if (in_patch) {
@@ -148,6 +168,8 @@ __device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_pa
             }
     } else {
         const size_t M = (size_t)n * n * n;
+        const int comp = species & 1;
+        grad += (size_t)(species >> 1) * 4 * M;
 #pragma unroll
         for (int c = 0; c < P; ++c) {
             const size_t oz = (size_t)pwrap(st.jz + c, n) * n * n;
@@ -162,9 +184,9 @@ __device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_pa
                     const cplx_t<T> vx = __ldg(grad + g);
                     const cplx_t<T> vy = __ldg(grad + M + g);
                     const cplx_t<T> vz = __ldg(grad + 2 * M + g);
-                    gx += w * (species ? vx.y : vx.x);
-                    gy += w * (species ? vy.y : vy.x);
-                    gz += w * (species ? vz.y : vz.x);
+                    gx += w * (comp ? vx.y : vx.x);
+                    gy += w * (comp ? vy.y : vy.x);
+                    gz += w * (comp ? vz.y : vz.x);
                 }
             }
         }
@@ -176,8 +198,10 @@ __device__ __forceinline__ void gather_force(const Stencil<P, T>& st, bool in_pa
 
 // Analytic-differentiation force: F_i = -sum_g grad_r W(r_i - g) w_K(g),
 // the exact gradient of the gridded energy. The potentials come from the
-// staged patch (in_patch: w_A then w_B, one value per point) or from the
-// global field pot = i (w_A + i w_B). dw*: d/ds of the weights (s = x/dx).
+// staged patch (in_patch: one value per point and species) or from the
+// global field pot = i (w_2p + i w_2p+1) of the species pair p = species/2
+// (pot points at pair 0; pairs are 4 n^3 values apart). dw*: d/ds of the
+// weights (s = x/dx).
 template <int P, typename T>
 __device__ __forceinline__ void gather_force_an(const Stencil<P, T>& st, const T (&dwx)[P], const T (&dwy)[P],
                                                 const T (&dwz)[P], bool in_patch, int3 l, const T* s_pot,
@@ -202,6 +226,8 @@ __device__ __forceinline__ void gather_force_an(const Stencil<P, T>& st, const T
                 }
             }
     } else {
+        const int comp = species & 1;
+        pot += (size_t)(species >> 1) * 4 * ((size_t)n * n * n);
 #pragma unroll
         for (int c = 0; c < P; ++c) {
             const size_t oz = (size_t)pwrap(st.jz + c, n) * n * n;
@@ -212,7 +238,7 @@ __device__ __forceinline__ void gather_force_an(const Stencil<P, T>& st, const T
 #pragma unroll
                 for (int a = 0; a < P; ++a) {
                     const cplx_t<T> v = __ldg(pot + oy + pwrap(st.jx + a, n));
-                    const T w = species ? -v.x : v.y;
+                    const T w = comp ? -v.x : v.y;
                     gx += dwx[a] * wyz * w;
                     gy += st.wx[a] * dyz * w;
                     gz += st.wx[a] * ydz * w;
@@ -270,15 +296,15 @@ template <int P, typename T> __device__ __forceinline__ bool patch_local(const S
 // Beads of a tile are staged in shared memory in chunks of up to kBeadChunk.
 constexpr int kBeadChunk = 512;
 
-template <int P, typename T, bool AN = false> struct BeadSmem {
+template <int P, typename T, bool AN = false, int NS = 2> struct BeadSmem {
     using patch_t = typename FixedPoint<T>::patch_t;
     static constexpr int W3 = Patch<P>::W3;
     // the force patch is staged when it is small (else gathered from global
-    // memory): [2 species][W3] of (gx, gy, gz, -) records, or with the
-    // analytic force [2 species][W3] potentials
-    static constexpr size_t field_bytes = AN ? 2 * W3 * sizeof(T) : 2 * W3 * sizeof(typename vec4_of<T>::type);
+    // memory): [NS species][W3] of (gx, gy, gz, -) records, or with the
+    // analytic force [NS species][W3] potentials
+    static constexpr size_t field_bytes = AN ? NS * W3 * sizeof(T) : NS * W3 * sizeof(typename vec4_of<T>::type);
     static constexpr bool stage_grad = field_bytes <= 48 * 1024;
-    static constexpr int patches = 2;
+    static constexpr int patches = NS;
     static constexpr size_t patch_off = 0;                                                       // patch_t [patches][W3]
     static constexpr size_t grad_off = (patch_off + patches * W3 * sizeof(patch_t) + 31) / 32 * 32;
     static constexpr size_t pos_off = grad_off + (stage_grad ? (field_bytes + 15) / 16 * 16 : 0);
@@ -287,7 +313,9 @@ template <int P, typename T, bool AN = false> struct BeadSmem {
     static constexpr size_t bytes = tag_off + kBeadChunk * sizeof(int);
 };
 
-template <int P, typename T, bool AN = false> constexpr size_t bead_smem_bytes() { return BeadSmem<P, T, AN>::bytes; }
+template <int P, typename T, bool AN = false, int NS = 2> constexpr size_t bead_smem_bytes() {
+    return BeadSmem<P, T, AN, NS>::bytes;
+}
 
 // Grid offset (within one field) of the first point of patch row `row`,
 // row = (plane * W + lz) * W + ly over stacked patches; sets the plane.
@@ -299,10 +327,10 @@ template <int P> __device__ __forceinline__ size_t patch_row_base(int row, int3 
     return ((size_t)pwrap(org.z + lz, n) * n + pwrap(org.y + ly, n)) * n;
 }
 
-template <int P, int MODE, typename T, bool AN = false>
+template <int P, int MODE, typename T, bool AN = false, int NS = 2>
 __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const BeadBuffers<T>& bf, int t) {
     using PT = Patch<P>;
-    using SM = BeadSmem<P, T, AN>;
+    using SM = BeadSmem<P, T, AN, NS>;
     using FP = FixedPoint<T>;
     using patch_t = typename FP::patch_t;
     using V = cplx_t<T>;
@@ -333,24 +361,28 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
         for (int i = threadIdx.x; i < SM::patches * PT::W3; i += blockDim.x) patch[i] = 0;
     }
     if (AN && kForce && row_lane) {
-        // stage w_A, w_B of the patch from pot = i (w_A + i w_B) (field 3)
+        // stage w_2p, w_2p+1 of the patch from pot = i (w_2p + i w_2p+1)
+        // (field 3 of pair p)
         constexpr int NWARP = 8;
         constexpr int ROWS_PER_LANE = (W * W + NWARP * RPW - 1) / (NWARP * RPW);
-        V v[ROWS_PER_LANE];
 #pragma unroll
-        for (int k = 0; k < ROWS_PER_LANE; ++k) {
-            const int row = row0 + k * rstride;
-            if (row < W * W) {
-                int unused;
-                v[k] = __ldg(bf.grad + 3 * M + patch_row_base<P>(row, org, p.n, unused) + gx);
+        for (int pr = 0; pr < NS / 2; ++pr) {
+            V v[ROWS_PER_LANE];
+#pragma unroll
+            for (int k = 0; k < ROWS_PER_LANE; ++k) {
+                const int row = row0 + k * rstride;
+                if (row < W * W) {
+                    int unused;
+                    v[k] = __ldg(bf.grad + (4 * pr + 3) * M + patch_row_base<P>(row, org, p.n, unused) + gx);
+                }
             }
-        }
 #pragma unroll
-        for (int k = 0; k < ROWS_PER_LANE; ++k) {
-            const int row = row0 + k * rstride;
-            if (row < W * W) {
-                s_pot[row * W + lx] = v[k].y;
-                s_pot[PT::W3 + row * W + lx] = -v[k].x;
+            for (int k = 0; k < ROWS_PER_LANE; ++k) {
+                const int row = row0 + k * rstride;
+                if (row < W * W) {
+                    s_pot[2 * pr * PT::W3 + row * W + lx] = v[k].y;
+                    s_pot[(2 * pr + 1) * PT::W3 + row * W + lx] = -v[k].x;
+                }
             }
         }
     }
@@ -359,24 +391,28 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
         // every row's loads are issued before any is used
         constexpr int NWARP = 8;  // 256 threads
         constexpr int ROWS_PER_LANE = (W * W + NWARP * RPW - 1) / (NWARP * RPW);
-        V v[ROWS_PER_LANE][3];
 #pragma unroll
-        for (int k = 0; k < ROWS_PER_LANE; ++k) {
-            const int row = row0 + k * rstride;
-            if (row < W * W) {
-                int unused;
-                const size_t g = patch_row_base<P>(row, org, p.n, unused) + gx;
-                v[k][0] = __ldg(bf.grad + g);
-                v[k][1] = __ldg(bf.grad + M + g);
-                v[k][2] = __ldg(bf.grad + 2 * M + g);
+        for (int pr = 0; pr < NS / 2; ++pr) {
+            const V* gp = bf.grad + (size_t)pr * 4 * M;
+            V v[ROWS_PER_LANE][3];
+#pragma unroll
+            for (int k = 0; k < ROWS_PER_LANE; ++k) {
+                const int row = row0 + k * rstride;
+                if (row < W * W) {
+                    int unused;
+                    const size_t g = patch_row_base<P>(row, org, p.n, unused) + gx;
+                    v[k][0] = __ldg(gp + g);
+                    v[k][1] = __ldg(gp + M + g);
+                    v[k][2] = __ldg(gp + 2 * M + g);
+                }
             }
-        }
 #pragma unroll
-        for (int k = 0; k < ROWS_PER_LANE; ++k) {
-            const int row = row0 + k * rstride;
-            if (row < W * W) {
-                s_grad[row * W + lx] = V4{v[k][0].x, v[k][1].x, v[k][2].x, T(0)};
-                s_grad[PT::W3 + row * W + lx] = V4{v[k][0].y, v[k][1].y, v[k][2].y, T(0)};
+            for (int k = 0; k < ROWS_PER_LANE; ++k) {
+                const int row = row0 + k * rstride;
+                if (row < W * W) {
+                    s_grad[2 * pr * PT::W3 + row * W + lx] = V4{v[k][0].x, v[k][1].x, v[k][2].x, T(0)};
+                    s_grad[(2 * pr + 1) * PT::W3 + row * W + lx] = V4{v[k][0].y, v[k][1].y, v[k][2].y, T(0)};
+                }
             }
         }
     }
@@ -468,19 +504,32 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
                 } else {
                     gather_force<P>(st, staged, l, s_grad, bf.grad, p.n, species, fx, fy, fz);
                 }
+                // the bond energy counts each bond once, at its end with the smaller bead id
+                auto nid_of = [&](int s) { return slot_bead_id(s >= c0 && s < c0 + cnt ? s_tag[s - c0] : bf.id[s]); };
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    if ((k == 0 ? nb.x : nb.y) >= 0) {
+                    const int s = k == 0 ? nb.x : nb.y;
+                    if (s >= 0) {
                         const T dx = min_image(x - nx[k], p.L, p.inv_L);
                         const T dy = min_image(y - ny[k], p.L, p.inv_L);
                         const T dz = min_image(z - nz[k], p.L, p.inv_L);
                         fx -= p.k_bond * dx;
                         fy -= p.k_bond * dy;
                         fz -= p.k_bond * dz;
-                        if (MODE == kModeForce && k == 1)
+                        if (MODE == kModeForce && nid_of(s) > bid)
                             acc[0] += 0.5 * (double)p.k_bond * ((double)dx * dx + (double)dy * dy + (double)dz * dz);
                     }
                 }
+                for_each_extra_bond(nb, bf.ext, [&](int s) {
+                    const T dx = min_image(x - bf.px[s], p.L, p.inv_L);
+                    const T dy = min_image(y - bf.py[s], p.L, p.inv_L);
+                    const T dz = min_image(z - bf.pz[s], p.L, p.inv_L);
+                    fx -= p.k_bond * dx;
+                    fy -= p.k_bond * dy;
+                    fz -= p.k_bond * dz;
+                    if (MODE == kModeForce && nid_of(s) > bid)
+                        acc[0] += 0.5 * (double)p.k_bond * ((double)dx * dx + (double)dy * dy + (double)dz * dz);
+                });
                 if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(bf.err, kErrNonFinite);
                 if (MODE == kModeForce) {
                     // v^n = vu u + vf F + vg xi^n (the integrator's total force enters)
@@ -573,9 +622,10 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
     }
 }
 
-template <int P, int MODE, typename T, bool AN = false>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3) ? 4 : 2) bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
-    bead_kernel_body<P, MODE, T, AN>(p, bf, blockIdx.x);
+template <int P, int MODE, typename T, bool AN = false, int NS = 2>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 3 && NS == 2) ? 4 : 2)
+    bead_kernel(BeadParams<T> p, BeadBuffers<T> bf) {
+    bead_kernel_body<P, MODE, T, AN, NS>(p, bf, blockIdx.x);
 }
 
 // Batched form: blocks [r * tiles^3, (r + 1) * tiles^3) serve replica r.
@@ -618,8 +668,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(BeadParams<T> p, BeadBuffe
 #pragma unroll
             for (int a = 0; a < P; ++a) {
                 const size_t g = ((size_t)pwrap(st.jz + c, p.n) * p.n + pwrap(st.jy + b, p.n)) * p.n + pwrap(st.jx + a, p.n);
-                const cplx_t<T> v = pot[g];
-                const T w = species ? -v.x : v.y;  // w_A = Im, w_B = -Re of i (w_A + i w_B)
+                const cplx_t<T> v = pot[(size_t)(species >> 1) * 4 * ((size_t)p.n * p.n * p.n) + g];
+                const T w = (species & 1) ? -v.x : v.y;  // w_2p = Im, w_2p+1 = -Re of i (w_2p + i w_2p+1)
                 gx += dx[a] * st.wy[b] * st.wz[c] * w;
                 gy += st.wx[a] * dy[b] * st.wz[c] * w;
                 gz += st.wx[a] * st.wy[b] * dz[c] * w;
@@ -637,6 +687,11 @@ __global__ void __launch_bounds__(256) adjoint_kernel(BeadParams<T> p, BeadBuffe
             gz += p.k_bond * min_image(z - bf.pz[s], p.L, p.inv_L);
         }
     }
+    for_each_extra_bond(nb, bf.ext, [&](int s) {
+        gx += p.k_bond * min_image(x - bf.px[s], p.L, p.inv_L);
+        gy += p.k_bond * min_image(y - bf.py[s], p.L, p.inv_L);
+        gz += p.k_bond * min_image(z - bf.pz[s], p.L, p.inv_L);
+    });
     grad_out[3 * (size_t)bid + 0] = gx;
     grad_out[3 * (size_t)bid + 1] = gy;
     grad_out[3 * (size_t)bid + 2] = gz;
@@ -676,8 +731,11 @@ __global__ void bin_count(int n_beads, const T* __restrict__ px, const T* __rest
     warp_aggregated_inc(counts, k);
 }
 
+// species_of_id (NULL: the A/B block pattern of the chains) gives each
+// bead's species.
 template <typename T>
-__global__ void bin_scatter_pos(int n_beads, Topology topo, const int* __restrict__ keys, const int* __restrict__ tile_start,
+__global__ void bin_scatter_pos(int n_beads, Topology topo, const unsigned char* __restrict__ species_of_id,
+                                const int* __restrict__ keys, const int* __restrict__ tile_start,
                                 int* __restrict__ cursor, const T* __restrict__ src /*[3][N]*/, T* __restrict__ dst,
                                 const int* __restrict__ id_src, int* __restrict__ id_dst, int* __restrict__ slot_of_id) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -687,7 +745,8 @@ __global__ void bin_scatter_pos(int n_beads, Topology topo, const int* __restric
 #pragma unroll
     for (int c = 0; c < 3; ++c) dst[(size_t)c * n_beads + s] = src[(size_t)c * n_beads + i];
     const int b = slot_bead_id(id_src[i]);
-    id_dst[s] = b | (bead_info(topo, b).species << 31);
+    const int K = species_of_id ? (int)species_of_id[b] : bead_info(topo, b).species;
+    id_dst[s] = b | (K << kSpeciesShift);
     slot_of_id[b] = s;
 }
 
@@ -783,6 +842,28 @@ static __global__ void bin_neighbours(int n_beads, Topology topo, const int* __r
     nbr[i] = make_int2(b.prev >= 0 ? slot_of_id[b.prev] : -1, b.next >= 0 ? slot_of_id[b.next] : -1);
 }
 
+// Neighbour slots from an explicit bond list: adj[b] holds the first two
+// neighbour ids of bead b in increasing order (-1: none), or for a bead with
+// more than two bonds the first neighbour and -2 - off, with the count and
+// the remaining ids in ext_ids[off], ext_ids[off + 1 ..]. ext_slots (same
+// layout) receives the slots of those ids.
+static __global__ void bin_neighbours_explicit(int n_beads, const int* __restrict__ id, const int* __restrict__ slot_of_id,
+                                               const int2* __restrict__ adj, const int* __restrict__ ext_ids,
+                                               int* __restrict__ ext_slots, int2* __restrict__ nbr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_beads) return;
+    const int2 a = adj[slot_bead_id(id[i])];
+    int2 r = make_int2(a.x >= 0 ? slot_of_id[a.x] : -1, a.y >= 0 ? slot_of_id[a.y] : -1);
+    if (a.y < -1) {
+        const int off = -2 - a.y;
+        const int cnt = ext_ids[off];
+        ext_slots[off] = cnt;
+        for (int j = 1; j <= cnt; ++j) ext_slots[off + j] = slot_of_id[ext_ids[off + j]];
+        r.y = a.y;
+    }
+    nbr[i] = r;
+}
+
 // Exclusive scan of `count` ints in blocks of 1024 (three kernels).
 static __global__ void scan_blocks(const int* __restrict__ in, int* __restrict__ out, int* __restrict__ block_sums, int count) {
     __shared__ int s[1024];
@@ -865,6 +946,18 @@ __global__ void load_by_id(int n_beads, const TI* __restrict__ in, const int* __
     const int b = slot_bead_id(id[i]);
 #pragma unroll
     for (int d = 0; d < 3; ++d) dst[(size_t)d * n_beads + i] = (T)in[3 * (size_t)b + d];
+}
+
+// [n][3] <-> [3][n] (to_aos: from SoA to AoS).
+template <typename TV>
+__global__ void transpose_vec3(size_t n, const TV* __restrict__ in, TV* __restrict__ out, bool to_aos) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    // i indexes the output
+    if (to_aos)
+        out[i] = in[(i % 3) * n + i / 3];
+    else
+        out[i] = in[3 * (i % n) + i / n];
 }
 
 template <typename TO>

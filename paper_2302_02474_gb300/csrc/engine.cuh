@@ -4,6 +4,7 @@
 #pragma once
 
 #include <algorithm>
+#include <unordered_map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -14,6 +15,7 @@
 #include "vjp_kernels.cuh"
 #include "engine_api.h"
 #include "grid_kernels.cuh"
+#include "generic_kernels.cuh"
 
 namespace tild {
 
@@ -40,8 +42,10 @@ template <typename T> class Engine final : public EngineBase {
     tild_status init(HostConfig* cfg) override {
         cfg_ = cfg;
         n_ = cfg->n;
-        M_ = (size_t)n_ * n_ * n_;
-        tiles_ = n_ / kTile;
+        generic_ = cfg->generic;
+        nz_ = cfg->dim == 2 ? 1 : n_;
+        M_ = (size_t)nz_ * n_ * n_;
+        tiles_ = (n_ + kTile - 1) / kTile;
         P_ = cfg->pmeorder + 1;
         plane_fits_ = plane_smem() <= 200 * 1024;
         C_ = std::min(n_, (int)(128 / sizeof(V)));  // y-column tiles of the split passes
@@ -49,25 +53,23 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(cudaGetDevice(&device_));
         TILD_CUDA(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking));
         stream_ = own_stream_;
-        TILD_CUDA(cudaMalloc(&rho_fx_, 2 * M_ * sizeof(unsigned long long)));
-        TILD_CUDA(cudaMalloc(&Zxy_, M_ * sizeof(V)));
-        TILD_CUDA(cudaMalloc(&H_, 3 * M_ * sizeof(V)));
-        TILD_CUDA(cudaMalloc(&grad_, 4 * M_ * sizeof(V)));  // 3 gradients + (optional) potentials
-        TILD_CUDA(cudaMalloc(&tw_, n_ * sizeof(V)));
-        TILD_CUDA(cudaMalloc(&kernel1d_, 2 * n_ * sizeof(T)));  // exp(-a^2 k_m^2), then exp(-a_e^2 k_m^2)
-        TILD_CUDA(cudaMalloc(&counters_, 4 * sizeof(unsigned long long)));
+        tild_status gst = alloc_grids(1);
+        if (gst) return gst;
+        TILD_CUDA(dev_malloc((void**)&tw_, n_ * sizeof(V)));
+        TILD_CUDA(dev_malloc((void**)&kernel1d_, 2 * n_ * sizeof(T)));  // exp(-a^2 k_m^2), then exp(-a_e^2 k_m^2)
+        TILD_CUDA(dev_malloc((void**)&counters_, 4 * sizeof(unsigned long long)));
         TILD_CUDA(cudaMemset(counters_, 0, 4 * sizeof(unsigned long long)));
-        TILD_CUDA(cudaMemset(rho_fx_, 0, 2 * M_ * sizeof(unsigned long long)));
         n_tiles_ = tiles_ * tiles_ * tiles_;
-        TILD_CUDA(cudaMalloc(&counts_, (n_tiles_ + 1) * sizeof(int)));
-        TILD_CUDA(cudaMalloc(&tile_start_, (n_tiles_ + 1) * sizeof(int)));
-        TILD_CUDA(cudaMalloc(&cursor_, (n_tiles_ + 1) * sizeof(int)));
+        TILD_CUDA(dev_malloc((void**)&counts_, (n_tiles_ + 1) * sizeof(int)));
+        TILD_CUDA(dev_malloc((void**)&tile_start_, (n_tiles_ + 1) * sizeof(int)));
+        TILD_CUDA(dev_malloc((void**)&cursor_, (n_tiles_ + 1) * sizeof(int)));
         scan_blocks_ = (int)((n_tiles_ + 1 + 1023) / 1024);
-        TILD_CUDA(cudaMalloc(&block_sums_, scan_blocks_ * sizeof(int)));
-        n_z_blocks_ = (size_t)(n_ / CZ_) * (n_ / 2 + 1);
-        n_partials_ = std::max(5 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
+        TILD_CUDA(dev_malloc((void**)&block_sums_, scan_blocks_ * sizeof(int)));
+        n_z_blocks_ = generic_ ? (size_t)blocks(M_) : (size_t)(n_ / CZ_) * (n_ / 2 + 1);  // two species pairs: twice as many (zpass_cols2)
+        n_partials_ = std::max(10 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
         n_partials_ = std::max(n_partials_, 3 * (size_t)(n_ / vjp_cols(n_)) * (n_ / 2 + 1));
-        TILD_CUDA(cudaMalloc(&partials_, n_partials_ * sizeof(double)));
+        TILD_CUDA(dev_malloc((void**)&partials_, n_partials_ * sizeof(double)));
+        partials_bytes_ = n_partials_ * sizeof(double);
         // twiddles W_n^m = exp(-2 pi i m / n) in FP64, rounded to T
         std::vector<V> tw(n_);
         for (int m = 0; m < n_; ++m) {
@@ -75,23 +77,70 @@ template <typename T> class Engine final : public EngineBase {
             tw[m] = V{(T)std::cos(ang), (T)std::sin(ang)};
         }
         TILD_CUDA(cudaMemcpy(tw_, tw.data(), n_ * sizeof(V), cudaMemcpyHostToDevice));
+        if (generic_) {
+            TILD_CUDA(cudaFuncSetAttribute(generic_axis_fft<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gaxis_smem()));
+            TILD_CUDA(cudaFuncSetAttribute(generic_axis_fft<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gaxis_smem()));
+            // the two factors of the line length: the most balanced split n = n1 n2
+            gn1_ = 1;
+            for (int f = 1; f * f <= n_; ++f)
+                if (n_ % f == 0) gn1_ = f;
+            gn2_ = n_ / gn1_;
+            return TILD_OK;
+        }
         return set_kernel_attributes();
     }
 
     tild_status set_chains() override {
         invalidate_graph();
         free_beads();
+        if (NP_ != 1) {
+            tild_status gst = alloc_grids(1);  // the chains give two species
+            if (gst) return gst;
+        }
         const size_t N = (size_t)cfg_->n_beads;
         for (int k = 0; k < 2; ++k) {
-            TILD_CUDA(cudaMalloc(&pos_[k], 3 * N * sizeof(T)));
-            TILD_CUDA(cudaMalloc(&u_[k], 3 * N * sizeof(T)));
-            TILD_CUDA(cudaMalloc(&id_[k], N * sizeof(int)));
+            TILD_CUDA(dev_malloc((void**)&pos_[k], 3 * N * sizeof(T)));
+            TILD_CUDA(dev_malloc((void**)&u_[k], 3 * N * sizeof(T)));
+            TILD_CUDA(dev_malloc((void**)&id_[k], N * sizeof(int)));
             TILD_CUDA(cudaMemset(u_[k], 0, 3 * N * sizeof(T)));
         }
-        TILD_CUDA(cudaMalloc(&nbr_, N * sizeof(int2)));
-        TILD_CUDA(cudaMalloc(&slot_of_id_, N * sizeof(int)));
-        TILD_CUDA(cudaMalloc(&keys_, N * sizeof(int)));
+        TILD_CUDA(dev_malloc((void**)&nbr_, N * sizeof(int2)));
+        TILD_CUDA(dev_malloc((void**)&slot_of_id_, N * sizeof(int)));
+        TILD_CUDA(dev_malloc((void**)&keys_, N * sizeof(int)));
         have_pos_ = have_vel_ = false;
+        return upload_topology();
+    }
+
+    // Species count, per-bead species and bond list from the HostConfig:
+    // grids for the species pairs, the device topology arrays, and (with
+    // positions) a re-binning and a fresh density.
+    tild_status set_topology() override {
+        invalidate_graph();
+        tild_status st;
+        const int np = cfg_->n_species > 2 ? 2 : 1;  // pairs of species on the grids
+        if (np != NP_ && (st = alloc_grids(np))) return st;
+        if ((st = upload_topology())) return st;
+        if (have_pos_) {
+            if ((st = enqueue_sort()) || (st = respread())) return st;
+            TILD_CUDA(cudaStreamSynchronize(stream_));
+        }
+        return TILD_OK;
+    }
+
+    tild_status io_scratch(size_t bytes, void** ptr) override {
+        tild_status st;
+        if ((st = device_buffer(&io_, io_bytes_, bytes))) return st;
+        *ptr = io_;
+        return TILD_OK;
+    }
+
+    tild_status transpose3(const void* in, void* out, size_t n, int dtype, bool to_aos) override {
+        if (dtype == TILD_DTYPE_F32)
+            transpose_vec3<float><<<blocks(3 * n), 256, 0, stream_>>>(n, (const float*)in, (float*)out, to_aos);
+        else
+            transpose_vec3<double><<<blocks(3 * n), 256, 0, stream_>>>(n, (const double*)in, (double*)out, to_aos);
+        TILD_CUDA(cudaGetLastError());
+        TILD_CUDA(cudaStreamSynchronize(stream_));
         return TILD_OK;
     }
 
@@ -114,6 +163,7 @@ template <typename T> class Engine final : public EngineBase {
         else
             load_positions<T, double><<<blocks(N), 256, 0, stream_>>>(N, (const double*)src, L, (T)(1.0 / cfg_->L), pos_[0], id_[0], err_ptr());
         TILD_CUDA(cudaGetLastError());
+        if ((st = zero_z())) return st;
         if ((st = enqueue_sort())) return st;
         if ((st = respread())) return st;
         TILD_CUDA(cudaStreamSynchronize(stream_));
@@ -180,10 +230,11 @@ template <typename T> class Engine final : public EngineBase {
     tild_status compute(unsigned what, tild_energy* e, void* f, int dtype, int where) override {
         tild_status st;
         const bool want_e = (what & TILD_COMPUTE_ENERGY) != 0;
+        if ((st = ensure_partials())) return st;
         if ((st = enqueue_fields(want_e, partials_, nullptr))) return st;
         std::vector<double> zpart;
         if (want_e) {
-            zpart.resize(5 * n_z_blocks_);
+            zpart.resize(5 * z_blocks());
             TILD_CUDA(cudaMemcpyAsync(zpart.data(), partials_, zpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
         }
         BeadBuffers<T> bf = bead_buffers();
@@ -194,22 +245,23 @@ template <typename T> class Engine final : public EngineBase {
             bf.f_out = fdev;
         }
         if ((st = launch_bead(kModeForce, bf))) return st;
-        std::vector<double> bpart(5 * (size_t)tiles_ * tiles_ * tiles_);
+        std::vector<double> bpart(5 * bead_blocks());
         TILD_CUDA(cudaMemcpyAsync(bpart.data(), partials_, bpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
         if (f && (st = stage_out_vec(fdev, (size_t)3 * cfg_->n_beads, f, dtype, where))) return st;
         TILD_CUDA(cudaStreamSynchronize(stream_));
         if ((st = check_err())) return st;
         if (want_e && e) {
             double s0 = 0, s1 = 0, s4 = 0;
-            for (size_t b = 0; b < n_z_blocks_; ++b) {
+            for (size_t b = 0; b < z_blocks(); ++b) {
                 s0 += zpart[5 * b];
                 s1 += zpart[5 * b + 1];
                 s4 += zpart[5 * b + 4];
             }
-            const double V = cfg_->L * cfg_->L * cfg_->L;
+            const double V = volume();
             const double dV = V / (double)M_;
             const double rho0 = cfg_->n_beads / V;
-            e->e_chi = cfg_->chi / rho0 * dV * dV / V * s0;
+            // one pair: the z pass sums Re[conj(rho_A) rho_B]; two pairs: chi-weighted sums
+            e->e_chi = (NP_ == 1 ? cfg_->chi : 1.0) / rho0 * dV * dV / V * s0;
             e->e_kappa = cfg_->kappa / (2.0 * rho0) * dV * dV / V * s1;
             e->e_elec = e_elec_from(s4);
         }
@@ -227,6 +279,14 @@ template <typename T> class Engine final : public EngineBase {
 
     tild_status energy_gradient(tild_energy_grad* g, void* dUdr, int dtype, int where) override {
         tild_status st;
+        if (generic_) {
+            err = "energy_gradient: implemented for the 3D grid sizes of the tiled kernels";
+            return TILD_EUNSUPPORTED;
+        }
+        if (NP_ != 1) {
+            err = "energy_gradient: implemented for one or two species";
+            return TILD_EUNSUPPORTED;
+        }
         if ((st = enqueue_fields(true, partials_, nullptr, kInvGradPot))) return st;
         std::vector<double> zpart(5 * n_z_blocks_);
         TILD_CUDA(cudaMemcpyAsync(zpart.data(), partials_, zpart.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
@@ -271,6 +331,14 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     tild_status vjp_supported() {
+        if (generic_) {
+            err = "force_vjp: implemented for the 3D grid sizes of the tiled kernels";
+            return TILD_EUNSUPPORTED;
+        }
+        if (NP_ != 1) {
+            err = "force_vjp: implemented for one or two species";
+            return TILD_EUNSUPPORTED;
+        }
         if (analytic()) {
             err = "force_vjp: implemented for the ik force";
             return TILD_EUNSUPPORTED;
@@ -353,10 +421,10 @@ template <typename T> class Engine final : public EngineBase {
     template <class P> tild_status device_buffer(P** ptr, size_t& have, size_t bytes) {
         if (have >= bytes) return TILD_OK;
         TILD_CUDA(cudaStreamSynchronize(stream_));
-        cudaFree(*ptr);
+        dev_free(*ptr);
         *ptr = nullptr;
         have = 0;
-        TILD_CUDA(cudaMalloc((void**)ptr, bytes));
+        TILD_CUDA(dev_malloc((void**)ptr, bytes));
         have = bytes;
         return TILD_OK;
     }
@@ -400,6 +468,7 @@ template <typename T> class Engine final : public EngineBase {
         invalidate_graph();
         cur_pos_ = cur_u_ = cur_id_ = 0;
         load_positions<T, T><<<blocks(N), 256, 0, stream_>>>(N, src, (T)cfg_->L, (T)(1.0 / cfg_->L), pos_[0], id_[0], err_ptr());
+        if (zero_z()) return TILD_EDEVICE;
         load_by_id<T, T><<<blocks(N), 256, 0, stream_>>>(N, src + 3 * (size_t)N, id_[0], u_[0]);
         TILD_CUDA(cudaGetLastError());
         tild_status st;
@@ -416,28 +485,30 @@ template <typename T> class Engine final : public EngineBase {
     // fixed-point density of those positions (after a step it holds the
     // spread of the new positions). Restoring one needs no re-binning.
     static size_t snap_part(size_t b) { return (b + 255) / 256 * 256; }
-    void snapshot_parts(void* (&ptr)[5], size_t (&bytes)[5]) {
+    // (with beads of more than two bonds, their neighbour slots as well)
+    void snapshot_parts(void* (&ptr)[6], size_t (&bytes)[6]) {
         const size_t N = cfg_->n_beads;
-        void* p[5] = {pos_[cur_pos_], id_[cur_id_], nbr_, tile_start_, rho_fx_};
-        const size_t b[5] = {3 * N * sizeof(T), N * sizeof(int), N * sizeof(int2), (n_tiles_ + 1) * sizeof(int),
-                             2 * M_ * sizeof(unsigned long long)};
-        for (int k = 0; k < 5; ++k) {
+        void* p[6] = {pos_[cur_pos_], id_[cur_id_], nbr_, tile_start_, rho_fx_, ext_slots_};
+        const size_t b[6] = {3 * N * sizeof(T), N * sizeof(int), N * sizeof(int2), (n_tiles_ + 1) * sizeof(int),
+                             2 * M_ * sizeof(unsigned long long), n_ext_ * sizeof(int)};
+        for (int k = 0; k < 6; ++k) {
             ptr[k] = p[k];
             bytes[k] = b[k];
         }
     }
     size_t snapshot_bytes() {
-        void* p[5];
-        size_t b[5], total = 0;
+        void* p[6];
+        size_t b[6], total = 0;
         snapshot_parts(p, b);
-        for (int k = 0; k < 5; ++k) total += snap_part(b[k]);
+        for (int k = 0; k < 6; ++k) total += snap_part(b[k]);
         return total;
     }
     tild_status snapshot(unsigned char* s, bool store) {
-        void* p[5];
-        size_t b[5];
+        void* p[6];
+        size_t b[6];
         snapshot_parts(p, b);
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < 6; ++k) {
+            if (b[k] == 0) continue;
             if (store)
                 TILD_CUDA(cudaMemcpyAsync(s, p[k], b[k], cudaMemcpyDeviceToDevice, stream_));
             else
@@ -591,8 +662,8 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     tild_status get_density(void* out, int dtype, int where) override {
-        const double scale = 1.0 / FixedPoint<T>::scale / (cfg_->L * cfg_->L * cfg_->L / (double)M_);
-        const size_t count = 2 * M_;
+        const double scale = 1.0 / FixedPoint<T>::scale / (volume() / (double)M_);
+        const size_t count = (size_t)cfg_->n_species * M_;
         tild_status st;
         void* dst = out;
         if (where == TILD_HOST) {
@@ -612,9 +683,9 @@ template <typename T> class Engine final : public EngineBase {
 
     tild_status get_spectrum(void* out, int dtype, int where) override {
         tild_status st;
-        if (!spec_) TILD_CUDA(cudaMalloc(&spec_, M_ * sizeof(V)));
+        if ((st = device_buffer(&spec_, spec_bytes_, NP_ * M_ * sizeof(V)))) return st;
         if ((st = enqueue_fields(false, nullptr, spec_))) return st;
-        if ((st = stage_out_vec((T*)spec_, 2 * M_, out, dtype, where))) return st;
+        if ((st = stage_out_vec((T*)spec_, 2 * NP_ * M_, out, dtype, where))) return st;
         TILD_CUDA(cudaStreamSynchronize(stream_));
         return TILD_OK;
     }
@@ -622,12 +693,19 @@ template <typename T> class Engine final : public EngineBase {
     tild_status get_field_gradient(void* out, int dtype, int where) override {
         tild_status st;
         if ((st = enqueue_fields(false, nullptr, nullptr, kInvGrad))) return st;
-        if ((st = stage_out_vec((T*)grad_, 6 * M_, out, dtype, where))) return st;
+        const int D = cfg_->dim;
+        for (int q = 0; q < NP_; ++q) {
+            char* o = (char*)out + (size_t)q * 2 * D * M_ * dtype_size(dtype);
+            if ((st = stage_out_vec((T*)(grad_ + 4 * q * M_), 2 * D * M_, o, dtype, where))) return st;
+            if (where == TILD_HOST) TILD_CUDA(cudaStreamSynchronize(stream_));  // the staging buffer is reused
+        }
         TILD_CUDA(cudaStreamSynchronize(stream_));
         return TILD_OK;
     }
 
     int64_t host_step() const override { return host_step_; }
+    // blocks of the z pass (energy partials): twice as many column tiles with two species pairs
+    size_t z_blocks() const { return NP_ == 2 ? (size_t)(n_ / zpass_cols2(n_)) * (n_ / 2 + 1) : n_z_blocks_; }
 
     // blob: magic, n_beads, sizeof(T), step, seed | pos[N][3] | u[N][3] (by id, T)
     size_t state_bytes() const override { return 5 * sizeof(uint64_t) + 6 * (size_t)cfg_->n_beads * sizeof(T); }
@@ -682,6 +760,7 @@ template <typename T> class Engine final : public EngineBase {
         }
         cur_pos_ = cur_u_ = cur_id_ = 0;
         load_positions<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, d, (T)cfg_->L, (T)(1.0 / cfg_->L), pos_[0], id_[0], err_ptr());
+        if ((st = zero_z())) return st;
         load_by_id<T, T><<<blocks(N), 256, 0, stream_>>>((int)N, d + 3 * N, id_[0], u_[0]);
         TILD_CUDA(cudaGetLastError());
         if ((st = enqueue_sort())) return st;
@@ -736,7 +815,8 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     int64_t launches(int64_t n) const override {
-        const int64_t per_step = (plane_fits_ ? 2 : 4) + 2;
+        const int D = cfg_->dim;
+        const int64_t per_step = generic_ ? (1 + D) + 1 + (int64_t)NP_ * D + 1 : (plane_fits_ ? 2 : 4) + 2;
         const int64_t per_sort = 8;
         const int K = cfg_->sort_every;
         int64_t since = steps_since_sort_, sorts = 0;
@@ -755,7 +835,7 @@ template <typename T> class Engine final : public EngineBase {
 
     tild_status save_velocities() override {
         const size_t N = cfg_->n_beads;
-        if (!vsave_) TILD_CUDA(cudaMalloc(&vsave_, 3 * N * sizeof(T)));
+        if (!vsave_) TILD_CUDA(dev_malloc((void**)&vsave_, 3 * N * sizeof(T)));
         tild_status st;
         if ((st = enqueue_fields(false, nullptr, nullptr))) return st;
         BeadBuffers<T> bf = bead_buffers();
@@ -781,6 +861,24 @@ template <typename T> class Engine final : public EngineBase {
    private:
     T* vsave_ = nullptr;
     HostConfig* cfg_ = nullptr;
+    // species pairs of the grids (1: up to two species, 2: three or four) and
+    // species slots of the bead kernels (2 NP)
+    int NP_ = 1, NS_ = 2;
+    // any-size / 2D kernels: grid planes along z, the two factors of n
+    bool generic_ = false;
+    int nz_ = 0, gn1_ = 1, gn2_ = 1;
+    size_t partials_bytes_ = 0;
+    // explicit topology (by bead id): species, first two neighbours, and the
+    // extra neighbour lists of beads with more than two bonds (ids and slots)
+    unsigned char* sp_of_id_ = nullptr;
+    int2* adj_ = nullptr;
+    int* ext_ids_ = nullptr;
+    int* ext_slots_ = nullptr;
+    size_t n_ext_ = 0;
+    void* io_ = nullptr;  // per-bead vectors in the other layout
+    size_t io_bytes_ = 0;
+    size_t spec_bytes_ = 0;
+    std::unordered_map<void*, size_t> live_;  // blocks from the caller's allocator
     int device_ = 0;
     int n_ = 0, tiles_ = 0, P_ = 2, C_ = 16, CZ_ = 8;
     size_t M_ = 0;
@@ -836,6 +934,38 @@ template <typename T> class Engine final : public EngineBase {
     static size_t dtype_size(int dtype) { return dtype == TILD_DTYPE_F32 ? 4 : 8; }
 
     size_t plane_smem() const { return ((size_t)n_ + (size_t)n_ * row_pitch(n_)) * sizeof(V); }
+    // two dimensions: z stays 0
+    tild_status zero_z() {
+        if (cfg_->dim == 2)
+            TILD_CUDA(cudaMemsetAsync(pos_[0] + 2 * (size_t)cfg_->n_beads, 0, (size_t)cfg_->n_beads * sizeof(T), stream_));
+        return TILD_OK;
+    }
+    double volume() const { return cfg_->dim == 2 ? cfg_->L * cfg_->L : cfg_->L * cfg_->L * cfg_->L; }
+    // lines per CTA of the any-size axis transform: about 96 KB of shared memory
+    int gaxis_lines() const {
+        const long c = ((long)(96 * 1024 / sizeof(V)) - n_) / (2L * (n_ + 1));
+        return (int)std::max(1L, std::min(32L, c));
+    }
+    size_t gaxis_smem() const { return ((size_t)n_ + 2 * (size_t)gaxis_lines() * (n_ + 1)) * sizeof(V); }
+    // blocks of the bead kernel (its FP64 partial sums)
+    size_t bead_blocks() const { return generic_ ? (size_t)blocks(cfg_->n_beads) : (size_t)tiles_ * tiles_ * tiles_; }
+    tild_status ensure_partials() {
+        const size_t need = 5 * std::max(bead_blocks(), z_blocks()) * sizeof(double);
+        return device_buffer(&partials_, partials_bytes_, need);
+    }
+    // the any-size transforms of `count` contiguous fields at f along every axis
+    tild_status generic_fft(V* f, int count, int dir) {
+        const int C = gaxis_lines();
+        const unsigned tiles = (unsigned)((M_ / n_ + C - 1) / C);
+        for (int axis = 0; axis < cfg_->dim; ++axis) {
+            if (dir < 0)
+                generic_axis_fft<T, -1><<<dim3(tiles, count), 256, gaxis_smem(), stream_>>>(f, n_, nz_, axis, C, gn1_, gn2_, tw_);
+            else
+                generic_axis_fft<T, +1><<<dim3(tiles, count), 256, gaxis_smem(), stream_>>>(f, n_, nz_, axis, C, gn1_, gn2_, tw_);
+        }
+        TILD_CUDA(cudaGetLastError());
+        return TILD_OK;
+    }
     size_t rows_smem() const { return ((size_t)n_ + (size_t)16 * row_pitch(n_)) * sizeof(V); }
     size_t ycol_smem() const { return ((size_t)n_ + 2 * (size_t)n_ * C_) * sizeof(V); }
     size_t zpass_smem() const { return ((size_t)n_ + 4 * (size_t)n_ * CZ_) * sizeof(V); }
@@ -846,28 +976,122 @@ template <typename T> class Engine final : public EngineBase {
         const double V = cfg_->L * cfg_->L * cfg_->L, dV = V / (double)M_;
         return c_el_on() ? 4.0 * 3.14159265358979323846 * cfg_->bjerrum * dV * dV / (2.0 * V) * s4 : 0.0;
     }
-    size_t bead_smem() const { return bead_smem(analytic()); }
-    size_t bead_smem(bool an) const {
+    size_t bead_smem() const { return bead_smem(analytic(), NS_); }
+    template <int P> static size_t bead_smem_p(bool an, int ns) {
+        if (ns == 4) return an ? bead_smem_bytes<P, T, true, 4>() : bead_smem_bytes<P, T, false, 4>();
+        return an ? bead_smem_bytes<P, T, true>() : bead_smem_bytes<P, T>();
+    }
+    size_t bead_smem(bool an, int ns) const {
         switch (P_) {
-            case 2: return an ? bead_smem_bytes<2, T, true>() : bead_smem_bytes<2, T>();
-            case 3: return an ? bead_smem_bytes<3, T, true>() : bead_smem_bytes<3, T>();
-            case 4: return an ? bead_smem_bytes<4, T, true>() : bead_smem_bytes<4, T>();
-            default: return an ? bead_smem_bytes<5, T, true>() : bead_smem_bytes<5, T>();
+            case 2: return bead_smem_p<2>(an, ns);
+            case 3: return bead_smem_p<3>(an, ns);
+            case 4: return bead_smem_p<4>(an, ns);
+            default: return bead_smem_p<5>(an, ns);
         }
+    }
+
+    // Device memory through the caller's allocator when one was given.
+    cudaError_t dev_malloc(void** p, size_t bytes) {
+        const tild_allocator& a = cfg_->allocator;
+        if (!a.alloc) return cudaMalloc(p, bytes);
+        *p = bytes ? a.alloc(bytes, a.user) : nullptr;
+        if (bytes && !*p) return cudaErrorMemoryAllocation;
+        if (*p) live_[*p] = bytes;
+        return cudaSuccess;
+    }
+    void dev_free(void* p) {
+        if (!p) return;
+        const tild_allocator& a = cfg_->allocator;
+        if (!a.alloc) {
+            cudaFree(p);
+            return;
+        }
+        auto it = live_.find(p);
+        const size_t bytes = it == live_.end() ? 0 : it->second;
+        if (it != live_.end()) live_.erase(it);
+        if (a.free) a.free(p, bytes, a.user);
+    }
+
+    // Density, spectrum and field grids for np species pairs.
+    tild_status alloc_grids(int np) {
+        if (stream_) TILD_CUDA(cudaStreamSynchronize(stream_));
+        void* old[] = {rho_fx_, Zxy_, H_, grad_};
+        for (void* q : old) dev_free(q);
+        rho_fx_ = nullptr;
+        Zxy_ = H_ = grad_ = nullptr;
+        NP_ = np;
+        NS_ = 2 * np;
+        TILD_CUDA(dev_malloc((void**)&rho_fx_, 2 * np * M_ * sizeof(unsigned long long)));
+        TILD_CUDA(dev_malloc((void**)&Zxy_, np * M_ * sizeof(V)));
+        TILD_CUDA(dev_malloc((void**)&H_, 3 * np * M_ * sizeof(V)));
+        TILD_CUDA(dev_malloc((void**)&grad_, 4 * np * M_ * sizeof(V)));  // per pair: 3 gradients + (optional) potentials
+        TILD_CUDA(cudaMemset(rho_fx_, 0, 2 * np * M_ * sizeof(unsigned long long)));
+        return TILD_OK;
+    }
+
+    // Device copies of the explicit species and bonds (none: the chains'
+    // pattern and linear bonds).
+    tild_status upload_topology() {
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        dev_free(sp_of_id_);
+        dev_free(adj_);
+        dev_free(ext_ids_);
+        dev_free(ext_slots_);
+        sp_of_id_ = nullptr;
+        adj_ = nullptr;
+        ext_ids_ = ext_slots_ = nullptr;
+        n_ext_ = 0;
+        const size_t N = cfg_->n_beads;
+        if (N == 0) return TILD_OK;
+        if (!cfg_->species_of_bead.empty()) {
+            TILD_CUDA(dev_malloc((void**)&sp_of_id_, N));
+            TILD_CUDA(cudaMemcpy(sp_of_id_, cfg_->species_of_bead.data(), N, cudaMemcpyHostToDevice));
+        }
+        if (cfg_->explicit_bonds) {
+            // adjacency by id, neighbours in increasing id order
+            std::vector<std::vector<int>> nb(N);
+            const std::vector<int>& bp = cfg_->bond_pairs;
+            for (size_t k = 0; k + 1 < bp.size(); k += 2) {
+                nb[bp[k]].push_back(bp[k + 1]);
+                nb[bp[k + 1]].push_back(bp[k]);
+            }
+            std::vector<int2> adj(N, make_int2(-1, -1));
+            std::vector<int> ext;
+            for (size_t b = 0; b < N; ++b) {
+                std::vector<int>& v = nb[b];
+                std::sort(v.begin(), v.end());
+                if (v.size() >= 1) adj[b].x = v[0];
+                if (v.size() == 2) adj[b].y = v[1];
+                if (v.size() > 2) {
+                    adj[b].y = -2 - (int)ext.size();
+                    ext.push_back((int)v.size() - 1);
+                    ext.insert(ext.end(), v.begin() + 1, v.end());
+                }
+            }
+            TILD_CUDA(dev_malloc((void**)&adj_, N * sizeof(int2)));
+            TILD_CUDA(cudaMemcpy(adj_, adj.data(), N * sizeof(int2), cudaMemcpyHostToDevice));
+            if (!ext.empty()) {
+                n_ext_ = ext.size();
+                TILD_CUDA(dev_malloc((void**)&ext_ids_, n_ext_ * sizeof(int)));
+                TILD_CUDA(dev_malloc((void**)&ext_slots_, n_ext_ * sizeof(int)));
+                TILD_CUDA(cudaMemcpy(ext_ids_, ext.data(), n_ext_ * sizeof(int), cudaMemcpyHostToDevice));
+            }
+        }
+        return TILD_OK;
     }
 
     void free_beads() {
         for (int k = 0; k < 2; ++k) {
-            cudaFree(pos_[k]);
-            cudaFree(u_[k]);
-            cudaFree(id_[k]);
+            dev_free(pos_[k]);
+            dev_free(u_[k]);
+            dev_free(id_[k]);
             pos_[k] = u_[k] = nullptr;
             id_[k] = nullptr;
         }
-        cudaFree(nbr_);
-        cudaFree(slot_of_id_);
-        cudaFree(keys_);
-        cudaFree(vsave_);
+        dev_free(nbr_);
+        dev_free(slot_of_id_);
+        dev_free(keys_);
+        dev_free(vsave_);
         vsave_ = nullptr;
         nbr_ = nullptr;
         slot_of_id_ = keys_ = nullptr;
@@ -875,10 +1099,12 @@ template <typename T> class Engine final : public EngineBase {
 
     void release() {
         invalidate_graph();
+        if (stream_) cudaStreamSynchronize(stream_);  // no kernel may still use a block handed back
         free_beads();
         void* ptrs[] = {rho_fx_, Zxy_, H_, grad_, tw_, kernel1d_, spec_, counters_, partials_, counts_,
-                        tile_start_, cursor_, block_sums_, aux_, stage_, theta_, traj_, vjp_fx_};
-        for (void* p : ptrs) cudaFree(p);
+                        tile_start_, cursor_, block_sums_, aux_, stage_, theta_, traj_, vjp_fx_,
+                        sp_of_id_, adj_, ext_ids_, ext_slots_, io_};
+        for (void* p : ptrs) dev_free(p);
         rho_fx_ = nullptr;
         if (own_stream_) cudaStreamDestroy(own_stream_);
         own_stream_ = nullptr;
@@ -904,10 +1130,10 @@ template <typename T> class Engine final : public EngineBase {
     tild_status ensure_aux(size_t bytes) {
         if (aux_bytes_ >= bytes) return TILD_OK;
         TILD_CUDA(cudaStreamSynchronize(stream_));
-        cudaFree(aux_);
+        dev_free(aux_);
         aux_ = nullptr;
         aux_bytes_ = 0;
-        TILD_CUDA(cudaMalloc(&aux_, bytes));
+        TILD_CUDA(dev_malloc(&aux_, bytes));
         aux_bytes_ = bytes;
         return TILD_OK;
     }
@@ -915,10 +1141,10 @@ template <typename T> class Engine final : public EngineBase {
     tild_status ensure_stage(size_t bytes) {
         if (stage_bytes_ >= bytes) return TILD_OK;
         TILD_CUDA(cudaStreamSynchronize(stream_));
-        cudaFree(stage_);
+        dev_free(stage_);
         stage_ = nullptr;
         stage_bytes_ = 0;
-        TILD_CUDA(cudaMalloc(&stage_, bytes));
+        TILD_CUDA(dev_malloc(&stage_, bytes));
         stage_bytes_ = bytes;
         return TILD_OK;
     }
@@ -990,6 +1216,9 @@ template <typename T> class Engine final : public EngineBase {
             TILD_CUDA(cudaFuncSetAttribute(y_columns<T, NN, 128 / sizeof(V), +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ycol_smem()));
         }
         constexpr int CC = zpass_cols(NN);
+        constexpr int C2 = zpass_cols2(NN);
+        TILD_CUDA(cudaFuncSetAttribute(z_spectral_pairs<T, NN, C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass2_smem()));
+        TILD_CUDA(cudaFuncSetAttribute(z_spectral_pairs<T, NN, C2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass2_smem()));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
@@ -998,12 +1227,20 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     template <int P> tild_status attrs_p() {
-        const int s = (int)bead_smem(false);
+        const int s4 = (int)bead_smem(false, 4), sa4 = (int)bead_smem(true, 4);
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSpread, T, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeForce, T, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSetVel, T, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeStep, T, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeForce, T, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa4));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSetVel, T, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa4));
+        TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeStep, T, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa4));
+        const int s = (int)bead_smem(false, 2);
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSpread, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeForce, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSetVel, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeStep, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
-        const int sa = (int)bead_smem(true);
+        const int sa = (int)bead_smem(true, 2);
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeForce, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeSetVel, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
         TILD_CUDA(cudaFuncSetAttribute(bead_kernel<P, kModeStep, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
@@ -1051,28 +1288,34 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     T density_scale() const {
-        const double dV = cfg_->L * cfg_->L * cfg_->L / (double)M_;
+        const double dV = volume() / (double)M_;
         return (T)(1.0 / FixedPoint<T>::scale / dV);
     }
 
     template <int NN> tild_status forward_n(bool zero_after) {
         if (plane_fits_) {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
-                xy_forward_plane<T, NN><<<NN, 512, plane_smem(), stream_>>>(rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0,
-                                                                            zero_after ? counters_ : nullptr);
+                xy_forward_plane<T, NN><<<dim3(NN, NP_), 512, plane_smem(), stream_>>>(
+                    rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0, zero_after ? counters_ : nullptr);
             }
         } else {
             constexpr int CC = 128 / sizeof(V);
             if constexpr (NN >= 16 && NN >= CC) {
-                x_forward_rows<T, NN, 16><<<(unsigned)((size_t)NN * NN / 16), 256, rows_smem(), stream_>>>(
+                x_forward_rows<T, NN, 16><<<dim3((unsigned)((size_t)NN * NN / 16), NP_), 256, rows_smem(), stream_>>>(
                     rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0, zero_after ? counters_ : nullptr);
-                y_columns<T, NN, CC, -1><<<dim3(NN / CC, NN, 1), 256, ycol_smem(), stream_>>>(Zxy_, tw_, two_pi_L(), 0);
+                y_columns<T, NN, CC, -1><<<dim3(NN / CC, NN, NP_), 256, ycol_smem(), stream_>>>(Zxy_, tw_, two_pi_L(), 0);
             }
         }
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
     }
     tild_status enqueue_forward(bool zero_after) {
+        if (generic_) {
+            generic_load_density<T><<<blocks((size_t)NP_ * M_), 256, 0, stream_>>>(
+                M_, NP_, rho_fx_, Zxy_, density_scale(), zero_after ? 1 : 0, zero_after ? counters_ : nullptr);
+            TILD_CUDA(cudaGetLastError());
+            return generic_fft(Zxy_, NP_, -1);
+        }
         return dispatch_n([&](auto nn) { return this->template forward_n<decltype(nn)::value>(zero_after); });
     }
 
@@ -1090,17 +1333,26 @@ template <typename T> class Engine final : public EngineBase {
         while (c > 1 && (n % c) != 0) c /= 2;
         return c < n ? c : n;
     }
+    // two species pairs: half the columns (twice the buffers), at least 2
+    static constexpr int zpass_cols2(int n) { return zpass_cols(n) / 2 < 2 ? 2 : zpass_cols(n) / 2; }
+    size_t zpass2_smem() const { return ((size_t)n_ + 8 * (size_t)n_ * zpass_cols2(n_)) * sizeof(V); }
 
     T two_pi_L() const { return (T)(2.0 * 3.14159265358979323846 / cfg_->L); }
 
     SpectralParams<T> spectral_params() const {
-        const double V = cfg_->L * cfg_->L * cfg_->L;
+        const double V = volume();
         const double rho0 = cfg_->n_beads / V;
         SpectralParams<T> sp;
         sp.two_pi_over_L = (T)(2.0 * 3.14159265358979323846 / cfg_->L);
         sp.eAA = (T)(cfg_->kappa / rho0 / (double)M_);
         sp.eBB = sp.eAA;
         sp.eAB = (T)((cfg_->chi + cfg_->kappa) / rho0 / (double)M_);
+        for (int K = 0; K < 4; ++K)
+            for (int K2 = 0; K2 < 4; ++K2) {
+                const double chi = K == K2 ? 0.0 : cfg_->chi_mat[K][K2];
+                sp.eps4[K][K2] = (T)((chi + cfg_->kappa) / rho0 / (double)M_);
+                sp.chi4[K][K2] = (T)chi;
+            }
         sp.kernel1d = kernel1d_;
         const bool charged = c_el_on();
         sp.el_scale = charged ? (T)(4.0 * 3.14159265358979323846 * cfg_->bjerrum / (double)M_) : T(0);
@@ -1115,6 +1367,23 @@ template <typename T> class Engine final : public EngineBase {
         const dim3 grid(NN / CC, NN / 2 + 1);
         const SpectralParams<T> sp = spectral_params();
         const bool el = c_el_on();
+        if (NP_ == 2) {
+            if (spec_out) {
+                // the spectra alone: each pair's forward z transform (no coupling)
+                for (int q = 0; q < 2; ++q)
+                    z_spectral<T, NN, CC><<<grid, 256, zpass_smem(), stream_>>>(Zxy_ + q * M_, H_, tw_, sp, nullptr,
+                                                                              spec_out + q * M_);
+            } else {
+                constexpr int C2 = zpass_cols2(NN);
+                const dim3 grid2(NN / C2, NN / 2 + 1);
+                if (g_only)
+                    z_spectral_pairs<T, NN, C2, true><<<grid2, 256, zpass2_smem(), stream_>>>(Zxy_, H_, tw_, sp, partials);
+                else
+                    z_spectral_pairs<T, NN, C2><<<grid2, 256, zpass2_smem(), stream_>>>(Zxy_, H_, tw_, sp, partials);
+            }
+            TILD_CUDA(cudaGetLastError());
+            return TILD_OK;
+        }
         if (g_only && el)
             z_spectral<T, NN, CC, true, true><<<grid, 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, sp, partials, spec_out);
         else if (g_only)
@@ -1134,7 +1403,7 @@ template <typename T> class Engine final : public EngineBase {
             if (cached == s) return TILD_OK;
             std::vector<T> e(n_);
             for (int i = 0; i < n_; ++i) {
-                const double m = i < n_ / 2 ? i : i - n_;
+                const double m = 2 * i < n_ ? i : i - n_;  // odd n: frequencies -(n-1)/2 .. (n-1)/2
                 const double k = 2.0 * 3.14159265358979323846 * m / cfg_->L;
                 e[i] = (T)std::exp(-s * s * k * k);
             }
@@ -1151,6 +1420,19 @@ template <typename T> class Engine final : public EngineBase {
     tild_status enqueue_zpass(double* partials, V* spec_out, bool g_only = false) {
         tild_status st;
         if ((st = refresh_tables())) return st;
+        if (generic_) {
+            if (spec_out) {  // the spectrum is complete after the forward transforms
+                TILD_CUDA(cudaMemcpyAsync(spec_out, Zxy_, NP_ * M_ * sizeof(V), cudaMemcpyDeviceToDevice, stream_));
+                return TILD_OK;
+            }
+            const SpectralParams<T> sp = spectral_params();
+            if (NP_ == 2)
+                generic_spectral<T, 2><<<blocks(M_), 256, 0, stream_>>>(Zxy_, grad_, n_, nz_, sp, partials);
+            else
+                generic_spectral<T, 1><<<blocks(M_), 256, 0, stream_>>>(Zxy_, grad_, n_, nz_, sp, partials);
+            TILD_CUDA(cudaGetLastError());
+            return TILD_OK;
+        }
         return dispatch_n([&](auto nn) { return this->template zpass_n<decltype(nn)::value>(partials, spec_out, g_only); });
     }
 
@@ -1161,14 +1443,14 @@ template <typename T> class Engine final : public EngineBase {
         const int d0 = what == kInvPot ? 3 : 0;
         if (plane_fits_) {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
-                xy_inverse_plane<T, NN><<<dim3(NN, nd), 512, plane_smem(), stream_>>>(H_, grad_, tw_, two_pi_L(), d0);
+                xy_inverse_plane<T, NN><<<dim3(NN, nd, NP_), 512, plane_smem(), stream_>>>(H_, grad_, tw_, two_pi_L(), d0);
             }
         } else {
             constexpr int CC = 128 / sizeof(V);
             if constexpr (NN >= 16 && NN >= CC) {
-                y_columns<T, NN, CC, +1><<<dim3(NN / CC, NN, what == kInvPot ? 1 : 2), 256, ycol_smem(), stream_>>>(
+                y_columns<T, NN, CC, +1><<<dim3(NN / CC, NN, (what == kInvPot ? 1 : 2) * NP_), 256, ycol_smem(), stream_>>>(
                     H_, tw_, two_pi_L(), what == kInvPot ? 1 : 0);
-                x_inverse_rows<T, NN, 16><<<dim3((unsigned)((size_t)NN * NN / 16), nd), 256, rows_smem(), stream_>>>(
+                x_inverse_rows<T, NN, 16><<<dim3((unsigned)((size_t)NN * NN / 16), nd, NP_), 256, rows_smem(), stream_>>>(
                     H_, grad_, tw_, two_pi_L(), d0);
             }
         }
@@ -1176,6 +1458,14 @@ template <typename T> class Engine final : public EngineBase {
         return TILD_OK;
     }
     tild_status enqueue_inverse(int what) {
+        if (generic_) {
+            tild_status st;
+            for (int q = 0; q < NP_; ++q) {
+                if (what != kInvPot && (st = generic_fft(grad_ + 4 * q * M_, cfg_->dim, +1))) return st;
+                if (what != kInvGrad && (st = generic_fft(grad_ + (4 * q + 3) * M_, 1, +1))) return st;
+            }
+            return TILD_OK;
+        }
         return dispatch_n([&](auto nn) { return this->template inverse_n<decltype(nn)::value>(what); });
     }
     // the fields the bead kernel's force needs: ik gradients or the potentials
@@ -1274,6 +1564,7 @@ template <typename T> class Engine final : public EngineBase {
         b.uz = b.uy + N;
         b.id = id_[cur_id_];
         b.nbr = nbr_;
+        b.ext = ext_slots_;
         b.tile_start = tile_start_;
         b.grad = grad_;
         b.rho_fx = rho_fx_;
@@ -1286,34 +1577,50 @@ template <typename T> class Engine final : public EngineBase {
         return b;
     }
 
-    template <int P> tild_status bead_p(int mode, const BeadBuffers<T>& bf) {
+    template <int P, int NS> tild_status bead_pn(int mode, const BeadBuffers<T>& bf) {
         const unsigned grid = (unsigned)tiles_ * tiles_ * tiles_;
         const BeadParams<T> p = bead_params();
         if (analytic() && mode != kModeSpread) {
-            const size_t sm = bead_smem(true);
+            const size_t sm = bead_smem(true, NS);
             switch (mode) {
-                case kModeForce: bead_kernel<P, kModeForce, T, true><<<grid, 256, sm, stream_>>>(p, bf); break;
-                case kModeSetVel: bead_kernel<P, kModeSetVel, T, true><<<grid, 256, sm, stream_>>>(p, bf); break;
-                default: bead_kernel<P, kModeStep, T, true><<<grid, 256, sm, stream_>>>(p, bf); break;
+                case kModeForce: bead_kernel<P, kModeForce, T, true, NS><<<grid, 256, sm, stream_>>>(p, bf); break;
+                case kModeSetVel: bead_kernel<P, kModeSetVel, T, true, NS><<<grid, 256, sm, stream_>>>(p, bf); break;
+                default: bead_kernel<P, kModeStep, T, true, NS><<<grid, 256, sm, stream_>>>(p, bf); break;
             }
         } else {
-            const size_t sm = bead_smem(false);
+            const size_t sm = bead_smem(false, NS);
             switch (mode) {
-                case kModeSpread: bead_kernel<P, kModeSpread, T><<<grid, 256, sm, stream_>>>(p, bf); break;
-                case kModeForce: bead_kernel<P, kModeForce, T><<<grid, 256, sm, stream_>>>(p, bf); break;
-                case kModeSetVel: bead_kernel<P, kModeSetVel, T><<<grid, 256, sm, stream_>>>(p, bf); break;
-                default: bead_kernel<P, kModeStep, T><<<grid, 256, sm, stream_>>>(p, bf); break;
+                case kModeSpread: bead_kernel<P, kModeSpread, T, false, NS><<<grid, 256, sm, stream_>>>(p, bf); break;
+                case kModeForce: bead_kernel<P, kModeForce, T, false, NS><<<grid, 256, sm, stream_>>>(p, bf); break;
+                case kModeSetVel: bead_kernel<P, kModeSetVel, T, false, NS><<<grid, 256, sm, stream_>>>(p, bf); break;
+                default: bead_kernel<P, kModeStep, T, false, NS><<<grid, 256, sm, stream_>>>(p, bf); break;
             }
         }
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
+    }
+    template <int P, int D> tild_status bead_generic(int mode, const BeadBuffers<T>& bf) {
+        const BeadParams<T> p = bead_params();
+        const unsigned g = blocks(cfg_->n_beads);
+        switch (mode) {
+            case kModeSpread: generic_bead_kernel<P, kModeSpread, T, D><<<g, 256, 0, stream_>>>(p, bf, nz_); break;
+            case kModeForce: generic_bead_kernel<P, kModeForce, T, D><<<g, 256, 0, stream_>>>(p, bf, nz_); break;
+            case kModeSetVel: generic_bead_kernel<P, kModeSetVel, T, D><<<g, 256, 0, stream_>>>(p, bf, nz_); break;
+            default: generic_bead_kernel<P, kModeStep, T, D><<<g, 256, 0, stream_>>>(p, bf, nz_); break;
+        }
+        TILD_CUDA(cudaGetLastError());
+        return TILD_OK;
+    }
+    template <int P> tild_status bead_p(int mode, const BeadBuffers<T>& bf) {
+        if (generic_) return cfg_->dim == 2 ? bead_generic<P, 2>(mode, bf) : bead_generic<P, 3>(mode, bf);
+        return NS_ == 4 ? bead_pn<P, 4>(mode, bf) : bead_pn<P, 2>(mode, bf);
     }
     tild_status launch_bead(int mode, const BeadBuffers<T>& bf) {
         return dispatch_p([&](auto pp) { return this->template bead_p<decltype(pp)::value>(mode, bf); });
     }
 
     tild_status respread() {
-        TILD_CUDA(cudaMemsetAsync(rho_fx_, 0, 2 * M_ * sizeof(unsigned long long), stream_));
+        TILD_CUDA(cudaMemsetAsync(rho_fx_, 0, 2 * NP_ * M_ * sizeof(unsigned long long), stream_));
         return launch_bead(kModeSpread, bead_buffers());
     }
 
@@ -1343,12 +1650,17 @@ template <typename T> class Engine final : public EngineBase {
         scan_blocks<<<scan_blocks_, 1024, 0, stream_>>>(counts_, tile_start_, block_sums_, n_tiles_ + 1);
         scan_top<<<1, 1024, 0, stream_>>>(block_sums_, scan_blocks_);
         scan_add<<<scan_blocks_, 1024, 0, stream_>>>(tile_start_, block_sums_, n_tiles_ + 1);
-        bin_scatter_pos<T><<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, keys_, tile_start_, cursor_, pos_[cur_pos_],
-                                                           pos_[1 - cur_pos_], id_[cur_id_], id_[1 - cur_id_], slot_of_id_);
+        bin_scatter_pos<T><<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, sp_of_id_, keys_, tile_start_, cursor_,
+                                                           pos_[cur_pos_], pos_[1 - cur_pos_], id_[cur_id_],
+                                                           id_[1 - cur_id_], slot_of_id_);
         bin_move_u<T><<<blocks(N), 256, 0, stream_>>>(N, id_[cur_id_], slot_of_id_, u_[cur_u_], u_[1 - cur_u_]);
         bin_local_sort<T><<<n_tiles_, 256, 0, stream_>>>(tile_start_, tiles_, n_, (T)((double)n_ / cfg_->L), N,
                                                           pos_[1 - cur_pos_], u_[1 - cur_u_], id_[1 - cur_id_], slot_of_id_);
-        bin_neighbours<<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, id_[1 - cur_id_], slot_of_id_, nbr_);
+        if (adj_)
+            bin_neighbours_explicit<<<blocks(N), 256, 0, stream_>>>(N, id_[1 - cur_id_], slot_of_id_, adj_, ext_ids_,
+                                                                    ext_slots_, nbr_);
+        else
+            bin_neighbours<<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, id_[1 - cur_id_], slot_of_id_, nbr_);
         TILD_CUDA(cudaGetLastError());
         cur_pos_ = 1 - cur_pos_;
         cur_u_ = 1 - cur_u_;

@@ -14,6 +14,8 @@ namespace tild {
 struct HostConfig {
     double L;
     int n;
+    int dim = 3;         // 2: a square box and n x n grid (Listing infile's "Dim 2")
+    bool generic = false;  // grid served by the any-size kernels (odd sizes, D = 2)
     int pmeorder;
     int precision;
     uint64_t seed;
@@ -22,8 +24,16 @@ struct HostConfig {
     Topology topo;
     int n_beads = 0;
     double b = 1.0;
-    // interactions
+    // species (1..4) and, when set explicitly, the species of every bead;
+    // bonds: empty = the chains' linear bonds, else an explicit list of
+    // bead-id pairs (tild_set_bonds)
+    int n_species = 2;
+    std::vector<unsigned char> species_of_bead;
+    bool explicit_bonds = false;
+    std::vector<int> bond_pairs;  // [n_bonds][2]
+    // interactions; chi_mat[K][K'] is the Flory matrix (chi = chi_mat[0][1])
     double chi = 0.0, kappa = 0.0, a = 0.5;
+    double chi_mat[4][4] = {{0}};
     bool have_interactions = false;
     // integrator
     double dt = 0.005, friction = 1.0, kT = 1.0, mass = 1.0;
@@ -31,6 +41,8 @@ struct HostConfig {
     int force_method = 0;  // TILD_FORCE_*
     // electrostatics: charge per species, Bjerrum length (0: off), charge spreading length
     double q_a = 0.0, q_b = 0.0, bjerrum = 0.0, charge_smear = 0.5;
+    // device memory: the caller's allocator (tild_create_with_allocator) or cudaMalloc
+    tild_allocator allocator = {nullptr, nullptr, nullptr};
 };
 
 class EngineBase {
@@ -39,6 +51,8 @@ class EngineBase {
     std::string err;
     virtual tild_status init(HostConfig* cfg) = 0;
     virtual tild_status set_chains() = 0;
+    // species count / per-bead species / bond list of the HostConfig changed
+    virtual tild_status set_topology() = 0;
     virtual tild_status set_stream(cudaStream_t s) = 0;
     virtual cudaStream_t stream() const = 0;
     virtual tild_status set_positions(const void* xyz, int dtype, int where) = 0;
@@ -67,6 +81,10 @@ class EngineBase {
     virtual tild_status save_velocities() = 0;
     virtual tild_status restore_velocities() = 0;
     virtual void params_changed() = 0;
+    // per-bead vector arrays in the other layout: a device scratch of the
+    // context and an [n][3] <-> [3][n] transpose on its stream (synchronised)
+    virtual tild_status io_scratch(size_t bytes, void** ptr) = 0;
+    virtual tild_status transpose3(const void* in, void* out, size_t n, int dtype, bool to_aos) = 0;
 };
 
 // Several contexts stepped together (batched form).

@@ -12,12 +12,18 @@
 // whose inverse transform is real part d w_A/dr_d, imaginary part
 // d w_B/dr_d (both gradient fields are real).
 //
-// Memory layouts (n^3 points, index g = (z n + y) n + x):
-//   rho_fx  int64 [2][M]             fixed-point densities (2^44 per bead weight)
-//   Zxy     complex [z][ky][pos(kx)]  after the forward x and y transforms
-//   H       complex [3][z][ky][pos(kx)] after the z pass (z back in real space)
+// With more than two species (up to four) the species go in pairs: pair p
+// carries species 2p and 2p+1 exactly as A and B above, and every array
+// below gains a leading pair index; only the z pass sees all pairs at once
+// (the spectral multiply couples every species).
+//
+// Memory layouts (n^3 points, index g = (z n + y) n + x; NP pairs):
+//   rho_fx  int64 [2 NP][M]           fixed-point densities (2^22 or 2^44 per bead weight)
+//   Zxy     complex [NP][z][ky][pos(kx)]  after the forward x and y transforms
+//   H       complex [NP][3][z][ky][pos(kx)] after the z pass (z back in real space)
 // (pos(kx): mirror-paired column order, see kx_of_pos)
-//   grad    complex [3][z][y][x]      (d w_A, d w_B) per point and direction
+//   grad    complex [NP][4][z][y][x]  (d w_2p, d w_2p+1) per point and direction,
+//                                     then the potentials i (w_2p + i w_2p+1)
 #pragma once
 
 #include "fft.cuh"
@@ -27,6 +33,8 @@ namespace tild {
 template <typename T> struct SpectralParams {
     T two_pi_over_L;   // 2 pi / L
     T eAA, eAB, eBB;   // eps matrix / M (the 1/M of the inverse DFT folded in)
+    T eps4[4][4];      // more than two species: eps_KK' / M
+    T chi4[4][4];      // more than two species: chi_KK' (the energy sum of the z pass weights by it)
     const T* kernel1d; // exp(-a^2 k_m^2) per 1-D frequency index m (FP64 on the host)
     // smeared-charge electrostatics: w_K += q_K c(k) (q_A rho~_A + q_B rho~_B) with
     // c(k) = el_scale exp(-a_e^2 |k|^2) / |k|^2 (0 at k = 0); el_scale = 4 pi l_B / M
@@ -172,12 +180,17 @@ template <typename T, int N> __device__ __forceinline__ void xy_forward_plane_bo
     }
 }
 
+// grid = (n, NP): species pair blockIdx.y
 template <typename T, int N>
 __global__ void __launch_bounds__(512) xy_forward_plane(unsigned long long* __restrict__ rho_fx,
                                                          cplx_t<T>* __restrict__ Zxy,
                                                          const cplx_t<T>* __restrict__ tw_g, T scale,
                                                          int zero_after, unsigned long long* step_ctr) {
-    xy_forward_plane_body<T, N>(ForwardArgs<T>{rho_fx, Zxy, tw_g, scale, zero_after, step_ctr}, blockIdx.x);
+    const size_t M = (size_t)N * N * N;
+    const int pr = blockIdx.y;
+    xy_forward_plane_body<T, N>(
+        ForwardArgs<T>{rho_fx + 2 * pr * M, Zxy + pr * M, tw_g, scale, zero_after, pr == 0 ? step_ctr : nullptr},
+        blockIdx.x);
 }
 
 // Batched form: replica blockIdx.y of a table of replicas with the same grid.
@@ -234,11 +247,15 @@ template <typename T, int N> __device__ __forceinline__ void xy_inverse_plane_bo
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) grad[dst + i] = plane[(i / N) * PITCH + i % N];
 }
 
+// grid = (n, directions, NP): species pair blockIdx.z
 template <typename T, int N>
 __global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restrict__ H,
                                                          cplx_t<T>* __restrict__ grad,
                                                          const cplx_t<T>* __restrict__ tw_g, T two_pi_over_L, int d0) {
-    xy_inverse_plane_body<T, N>(InverseArgs<T>{H, grad, tw_g, two_pi_over_L, d0}, blockIdx.x, blockIdx.y);
+    const size_t M = (size_t)N * N * N;
+    const int pr = blockIdx.z;
+    xy_inverse_plane_body<T, N>(InverseArgs<T>{H + 3 * pr * M, grad + 4 * pr * M, tw_g, two_pi_over_L, d0}, blockIdx.x,
+                                blockIdx.y);
 }
 
 // Batched form: replica blockIdx.z.
@@ -264,7 +281,10 @@ __global__ void __launch_bounds__(256) x_forward_rows(unsigned long long* __rest
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)blockIdx.x * R * N;
-    if (step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1ull;
+    const int pr = blockIdx.y;  // species pair
+    rho_fx += 2 * pr * M;
+    Zxy += pr * M;
+    if (step_ctr && blockIdx.x == 0 && pr == 0 && threadIdx.x == 0) *step_ctr += 1ull;
     load_fixed_rows<N, PITCH, R, 256>(rho_fx + base, rho_fx + M + base, rows, scale, zero_after);
     __syncthreads();
     smem_fft_lines<N, -1, R, 256>(rows, StridedLines<PITCH>{}, 1, tw);
@@ -282,6 +302,8 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
     const int d = (int)blockIdx.y + d0;
+    H += 3 * (size_t)blockIdx.z * M;  // species pair blockIdx.z
+    grad += 4 * (size_t)blockIdx.z * M;
     const size_t base = (size_t)d * M + (size_t)blockIdx.x * R * N;
     // field 3 (optional, the potentials) is the plain transform of field 0
     const size_t src = (size_t)(d == 3 ? 0 : d) * M + (size_t)blockIdx.x * R * N;
@@ -298,11 +320,11 @@ __global__ void __launch_bounds__(256) x_inverse_rows(const cplx_t<T>* __restric
 }
 
 // Column pass along y: CTA (x tile, z plane, part) handles C columns.
-// Forward (DIR = -1, part 0): Zxy in place.
+// Forward (DIR = -1): Zxy in place; blockIdx.z = species pair.
 // Inverse (DIR = +1) on H: part 0 loads a tile of G (field 0) and writes
 // the transforms of G (field 0) and of i k_y G (field 1) from the same
-// load; part 1 transforms G_z (field 2) in place. With only_g, one part
-// transforms G alone.
+// load; part 1 transforms G_z (field 2) in place; blockIdx.z = 2 pair +
+// part. With only_g, one part transforms G alone (blockIdx.z = pair).
 template <typename T, int N, int C, int DIR>
 __global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, const cplx_t<T>* __restrict__ tw_g,
                                                  T two_pi_over_L, int only_g) {
@@ -313,9 +335,12 @@ __global__ void __launch_bounds__(256) y_columns(cplx_t<T>* __restrict__ data, c
     constexpr int TS = N * C;
     load_twiddles(tw, tw_g, N);
     const size_t M = (size_t)N * N * N;
-    const bool two = DIR > 0 && blockIdx.z == 0 && !only_g;  // only_g: G alone (one part)
+    const int part = (DIR < 0 || only_g) ? 0 : (int)(blockIdx.z & 1);
+    const int pr = (DIR < 0 || only_g) ? (int)blockIdx.z : (int)(blockIdx.z >> 1);
+    data += (DIR < 0 ? 1 : 3) * (size_t)pr * M;
+    const bool two = DIR > 0 && part == 0 && !only_g;  // only_g: G alone (one part)
     const size_t off = (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * C;
-    const size_t src = (DIR > 0 && blockIdx.z == 1 ? 2 * M : 0) + off;
+    const size_t src = (DIR > 0 && part == 1 ? 2 * M : 0) + off;
     batched_load<TS, 256, V>([&](int i) { return data[src + (size_t)(i / C) * N + i % C]; },
                              [&](int i, V v) {
                                  tile[i] = v;
@@ -550,6 +575,179 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) z_spectral(const 
 template <typename T, int N, int C, bool EL = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) z_spectral_batched(const ZArgs<T>* __restrict__ args) {
     z_spectral_body<T, N, C, false, EL>(args[blockIdx.z], blockIdx.x, blockIdx.y, gridDim.x);
+}
+
+// --------------------------------------------------------------------------
+// z pass with two species pairs (three or four species): as z_spectral, on
+// both pairs' columns at once. Buffers [2 NP R][N][C]: the input (then G) of
+// pair p, row r in buffer p R + r; G_z in buffer NP R + p R + r. The
+// species spectra of pair p are rho~_2p = (Z_p(k) + conj Z_p(-k))/2 and
+// rho~_2p+1 = -i (Z_p(k) - conj Z_p(-k))/2; w~_K = u_hat sum_K' eps_KK'
+// rho~_K'; Q_p = w~_2p + i w~_2p+1. Energy partials: [0] sum_k u_hat
+// sum_{K<K'} chi_KK' Re[conj(rho~_K) rho~_K'], [1] sum_{k != 0} u_hat
+// |sum_K rho~_K|^2, [2], [3] the same weighted by |k|^2, [4] 0.
+// --------------------------------------------------------------------------
+template <typename T, int N, int C, int R, bool G_ONLY>
+__device__ __forceinline__ void z_tile_pairs(cplx_t<T>* buf, const cplx_t<T>* tw, const T* e1, const SpectralParams<T>& sp,
+                                             int p0, const int (&ky)[2], bool want_e, double (&acc)[5]) {
+    using V = cplx_t<T>;
+    constexpr int TS = N * C;
+    constexpr int NP = 2;
+    smem_fft_lines<N, -1, NP * R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+    static_assert(256 % C == 0, "a thread keeps one column");
+    constexpr int rB = R - 1;
+    const int c = threadIdx.x % C;
+    const int cB = mirror_pos(p0 + c) - p0;
+    const int kxA = kx_of_pos<N>(p0 + c), kxB = kx_of_pos<N>(p0 + cB);
+    const T exyA = e1[kxA] * e1[ky[0]], exyB = e1[kxB] * e1[ky[rB]];
+    const bool zeroA = (kxA == 0 && ky[0] == 0), zeroB = (kxB == 0 && ky[rB] == 0);
+    const T qxA = raw_k<T, N>(kxA, sp.two_pi_over_L), qyA = raw_k<T, N>(ky[0], sp.two_pi_over_L);
+    const T qxB = raw_k<T, N>(kxB, sp.two_pi_over_L), qyB = raw_k<T, N>(ky[rB], sp.two_pi_over_L);
+    const double kxy2A = (double)qxA * qxA + (double)qyA * qyA, kxy2B = (double)qxB * qxB + (double)qyB * qyB;
+    for (int kz = threadIdx.x / C; kz < N; kz += 256 / C) {
+        const int kzB = kz == 0 ? 0 : N - kz;
+        if (R == 1 && kzB * C + cB < kz * C + c) continue;  // the mirror element owns this pair
+        const bool same = (R == 1) && (kzB == kz) && (cB == c);
+        V ZA[NP], ZB[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            ZA[q] = buf[(q * R) * TS + kz * C + c];
+            ZB[q] = buf[(q * R + rB) * TS + kzB * C + cB];
+        }
+        V out[2][NP][2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (s == 1 && same) break;
+            const int kzi = s == 0 ? kz : kzB;
+            const T kzv = grad_k<T, N>(kzi, sp.two_pi_over_L);
+            const T uh = (s == 0 ? exyA : exyB) * e1[kzi];
+            V A[2 * NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const V Z = s == 0 ? ZA[q] : ZB[q];
+                const V Zm = s == 0 ? ZB[q] : ZA[q];
+                A[2 * q] = {T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y)};
+                A[2 * q + 1] = {T(0.5) * (Z.y + Zm.y), -T(0.5) * (Z.x - Zm.x)};
+            }
+            if (want_e) {
+                const double qz = (double)raw_k<T, N>(kzi, sp.two_pi_over_L);
+                const double k2 = (s == 0 ? kxy2A : kxy2B) + qz * qz;
+                double fchi = 0.0;
+#pragma unroll
+                for (int K = 0; K < 2 * NP; ++K)
+#pragma unroll
+                    for (int K2 = K + 1; K2 < 2 * NP; ++K2)
+                        fchi += (double)sp.chi4[K][K2] * ((double)A[K].x * A[K2].x + (double)A[K].y * A[K2].y);
+                fchi *= (double)uh;
+                acc[0] += fchi;
+                acc[2] += k2 * fchi;
+                if (!((s == 0 ? zeroA : zeroB) && kzi == 0)) {
+                    double tr = 0.0, ti = 0.0;
+#pragma unroll
+                    for (int K = 0; K < 2 * NP; ++K) {
+                        tr += A[K].x;
+                        ti += A[K].y;
+                    }
+                    const double fkap = (double)uh * (tr * tr + ti * ti);
+                    acc[1] += fkap;
+                    acc[3] += k2 * fkap;
+                }
+            }
+            V w[2 * NP];
+#pragma unroll
+            for (int K = 0; K < 2 * NP; ++K) {
+                T wr = 0, wi = 0;
+#pragma unroll
+                for (int K2 = 0; K2 < 2 * NP; ++K2) {
+                    wr += sp.eps4[K][K2] * A[K2].x;
+                    wi += sp.eps4[K][K2] * A[K2].y;
+                }
+                w[K] = {uh * wr, uh * wi};
+            }
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const V iQ = {-(w[2 * q].y + w[2 * q + 1].x), w[2 * q].x - w[2 * q + 1].y};  // i (w~_2q + i w~_2q+1)
+                out[s][q][0] = iQ;
+                out[s][q][1] = {kzv * iQ.x, kzv * iQ.y};
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            if (d == 1 && G_ONLY) break;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                buf[(d * NP * R + q * R) * TS + kz * C + c] = out[0][q][d];
+                if (!same) buf[(d * NP * R + q * R + rB) * TS + kzB * C + cB] = out[1][q][d];
+            }
+        }
+    }
+    __syncthreads();
+    smem_fft_lines<N, +1, (G_ONLY ? 1 : 2) * NP * R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+}
+
+template <typename T, int N, int C, bool G_ONLY = false>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) z_spectral_pairs(const cplx_t<T>* __restrict__ Zxy,
+                                                                                cplx_t<T>* __restrict__ H,
+                                                                                const cplx_t<T>* __restrict__ tw_g,
+                                                                                SpectralParams<T> sp,
+                                                                                double* __restrict__ energy_partials) {
+    using V = cplx_t<T>;
+    constexpr int NP = 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* tw = reinterpret_cast<V*>(smem_raw);
+    V* buf = tw + N;
+    constexpr int TS = N * C;
+    __shared__ double red[5][8];
+    __shared__ T e1[N];
+    load_twiddles(tw, tw_g, N);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) e1[i] = sp.kernel1d[i];
+    const int bx = blockIdx.x, by = blockIdx.y;
+    const int p0 = bx * C;
+    const int ky[2] = {by, by == 0 ? 0 : N - by};
+    const int R = (ky[0] == ky[1]) ? 1 : 2;
+    const size_t NN = (size_t)N * N, M = NN * N;
+    // buffer b = q R + r (pair q, row r)
+    auto zsrc = [&](int i) {
+        const int b = i / TS, rem = i % TS;
+        const int q = b / R, r = b % R;
+        const int z = rem / C, c = rem % C;
+        return Zxy[q * M + z * NN + (size_t)ky[r] * N + p0 + c];
+    };
+    auto zdst = [&](int i, V v) { buf[i] = v; };
+    if (R == 1)
+        batched_load<NP * TS, 256, V>(zsrc, zdst);
+    else
+        batched_load<NP * 2 * TS, 256, V>(zsrc, zdst);
+    __syncthreads();
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const bool want_e = energy_partials != nullptr;
+    if (R == 1)
+        z_tile_pairs<T, N, C, 1, G_ONLY>(buf, tw, e1, sp, p0, ky, want_e, acc);
+    else
+        z_tile_pairs<T, N, C, 2, G_ONLY>(buf, tw, e1, sp, p0, ky, want_e, acc);
+    if (want_e) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double v = acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[k][wid] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 5) {
+            double sum = 0;
+            for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) sum += red[threadIdx.x][w];
+            energy_partials[5 * ((size_t)by * gridDim.x + bx) + threadIdx.x] = sum;
+        }
+    }
+    // buffer b = (d NP + q) R + r: field 0 (G) or 2 (G_z) of pair q, row r
+    const int nbuf = (G_ONLY ? 1 : 2) * NP * R * TS;
+    for (int i = threadIdx.x; i < nbuf; i += blockDim.x) {
+        const int b = i / TS, rem = i % TS;
+        const int d = b / (NP * R), q = (b / R) % NP, r = b % R;
+        const int z = rem / C, c = rem % C;
+        H[(3 * q + 2 * d) * M + z * NN + (size_t)ky[r] * N + p0 + c] = buf[i];
+    }
 }
 
 }  // namespace tild

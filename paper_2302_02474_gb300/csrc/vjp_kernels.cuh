@@ -366,6 +366,12 @@ __global__ void __launch_bounds__(256) vjp_beads(BeadParams<T> p, BeadBuffers<T>
             oz -= p.k_bond * (l2 - lam[3 * (size_t)nid + 2]);
         }
     }
+    for_each_extra_bond(nb, bf.ext, [&](int s) {
+        const int nid = slot_bead_id(bf.id[s]);
+        ox -= p.k_bond * (l0 - lam[3 * (size_t)nid]);
+        oy -= p.k_bond * (l1 - lam[3 * (size_t)nid + 1]);
+        oz -= p.k_bond * (l2 - lam[3 * (size_t)nid + 2]);
+    });
     out[3 * (size_t)bid] = ox;
     out[3 * (size_t)bid + 1] = oy;
     out[3 * (size_t)bid + 2] = oz;

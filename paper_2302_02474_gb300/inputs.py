@@ -177,3 +177,96 @@ def batch_configs(n_replicas: int = 256, seed: int = 12345 + 5, steps: int = 500
         out.append(SystemSpec(f"batch{r}", (MolType(n_chains, 20, 10),), L, n, 1, 0.5, chi, 25.0, 0.005, 1.0, 1.0, 1.0,
                               1.0, steps, "fp32", seed * 1000 + 2 * r, seed * 1000 + 2 * r + 1))
     return out
+
+
+@dataclasses.dataclass(frozen=True)
+class Topology:
+    """Explicit species and bonds of a system (beads numbered 0..n-1):
+    ``species`` (n,) int32 in [0, n_species), ``bonds`` (n_bonds, 2) int32
+    bead-id pairs and ``positions`` (n, 3) float64 in [0, L)."""
+
+    n_species: int
+    species: np.ndarray
+    bonds: np.ndarray
+    positions: np.ndarray
+
+
+def ring_star_system(n_rings: int, ring_N: int, n_stars: int, arms: int, arm_N: int, n_linear: int, lin_N: int,
+                     L: float, b: float = 1.0, n_species: int = 3, seed: int = 9) -> Topology:
+    """A mixture of ring polymers, star polymers and linear chains with up
+    to four species, for topology tests (Sec. "Input file": a data file gives
+    each bead's type and the bond list).
+
+    Rings: ring_N beads on a closed loop, the first half species 0 and the
+    rest species 1, beads on a circle of circumference ring_N * b (so every
+    bond, the closing one included, is about b long) around a uniform centre,
+    in a uniformly oriented plane.
+    Stars: one centre bead (species 2 when n_species > 2, else 0) with
+    ``arms`` random-walk arms of arm_N beads (species 1, or 3 for the odd arms
+    when n_species == 4), each arm bonded to the centre: the centre has
+    ``arms`` bonds.
+    Linear chains: lin_N-bead random walks, species 0 then 1 (halves).
+    Molecules are numbered rings, stars, linear chains."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sp: List[int] = []
+    bonds: List[Tuple[int, int]] = []
+    pos: List[np.ndarray] = []
+    idx = 0
+    for _ in range(n_rings):
+        c = rng.uniform(0.0, L, size=3)
+        e1 = rng.normal(size=3)
+        e1 /= np.linalg.norm(e1)
+        e2 = rng.normal(size=3)
+        e2 -= e1 * np.dot(e1, e2)
+        e2 /= np.linalg.norm(e2)
+        rad = ring_N * b / (2.0 * np.pi)
+        ang = 2.0 * np.pi * np.arange(ring_N) / ring_N
+        pos.append(c + rad * (np.cos(ang)[:, None] * e1 + np.sin(ang)[:, None] * e2))
+        sp += [0] * (ring_N // 2) + [1] * (ring_N - ring_N // 2)
+        bonds += [(idx + k, idx + (k + 1) % ring_N) for k in range(ring_N)]
+        idx += ring_N
+    for _ in range(n_stars):
+        c = rng.uniform(0.0, L, size=3)
+        centre = idx
+        pos.append(c[None, :])
+        sp.append(2 if n_species > 2 else 0)
+        idx += 1
+        for a in range(arms):
+            u = rng.normal(size=(arm_N, 3))
+            u /= np.linalg.norm(u, axis=1, keepdims=True)
+            pos.append(c + np.cumsum(b * u, axis=0))
+            sp += [3 if (n_species == 4 and a % 2 == 1) else 1] * arm_N
+            bonds.append((centre, idx))
+            bonds += [(idx + k, idx + k + 1) for k in range(arm_N - 1)]
+            idx += arm_N
+    for _ in range(n_linear):
+        c = rng.uniform(0.0, L, size=3)
+        u = rng.normal(size=(lin_N - 1, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        pos.append(c + np.concatenate([np.zeros((1, 3)), np.cumsum(b * u, axis=0)]))
+        sp += [0] * (lin_N // 2) + [1] * (lin_N - lin_N // 2)
+        bonds += [(idx + k, idx + k + 1) for k in range(lin_N - 1)]
+        idx += lin_N
+    r = np.mod(np.concatenate(pos), L)
+    r[r >= L] = 0.0
+    return Topology(n_species, np.asarray(sp, np.int32), np.asarray(bonds, np.int32).reshape(-1, 2), r)
+
+
+def random_walk_positions_2d(moltypes: Sequence[MolType], L: float, b: float, seed: int) -> np.ndarray:
+    """Two-dimensional version of random_walk_positions (Listing infile's
+    "Dim 2"): (n_beads, 3) float64 with z = 0; the first bead of each chain
+    uniform in the square [0, L)^2, each following bead at distance b along a
+    uniformly random direction in the plane."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    chunks: List[np.ndarray] = []
+    for m in moltypes:
+        if m.n_chains == 0:
+            continue
+        first = rng.uniform(0.0, L, size=(m.n_chains, 1, 2))
+        ang = rng.uniform(0.0, 2.0 * np.pi, size=(m.n_chains, m.N - 1))
+        steps = np.concatenate([np.zeros((m.n_chains, 1, 2)), b * np.stack([np.cos(ang), np.sin(ang)], axis=2)], axis=1)
+        chunks.append((first + np.cumsum(steps, axis=1)).reshape(-1, 2))
+    r = np.concatenate(chunks) if chunks else np.zeros((0, 2))
+    r = np.mod(r, L)
+    r[r >= L] = 0.0
+    return np.concatenate([r, np.zeros((len(r), 1))], axis=1)

@@ -54,7 +54,13 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.tild_create(ctypes.byref(p), ctypes.byref(ctx)) == B.TILD_EUNSUPPORTED
     assert b"cubic" in lib.tild_last_error(None)
     p.L[2] = 10.0
-    p.n[:] = [20, 20, 20]
+    p.n[:] = [3, 3, 3]  # below the smallest grid
+    assert lib.tild_create(ctypes.byref(p), ctypes.byref(ctx)) == B.TILD_EUNSUPPORTED
+    p.n[:] = [300, 300, 300]  # above the largest 3D grid
+    assert lib.tild_create(ctypes.byref(p), ctypes.byref(ctx)) == B.TILD_EUNSUPPORTED
+    p.n[:] = [16, 20, 16]  # not cubic
+    assert lib.tild_create(ctypes.byref(p), ctypes.byref(ctx)) == B.TILD_EUNSUPPORTED
+    p.n[:] = [65, 64, 1]  # 2D grids are square
     assert lib.tild_create(ctypes.byref(p), ctypes.byref(ctx)) == B.TILD_EUNSUPPORTED
     p.n[:] = [16, 16, 16]
     p.pmeorder = 5
