@@ -237,11 +237,12 @@ def run_reference(args, spec, pos):
     rate, done, secs, t_init = oracle_step_rate(spec, pos, args.steps, args.reference_budget)
     sample = (f"{done} oracle GJF steps of the full {spec.n_beads}-bead / {spec.n}^3 system "
               f"(initial force evaluation {t_init:.1f} s excluded)")
-    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "steps/s", "n_gpus": args.gpus,
+    metric = METRIC if args.workload == WORKLOAD else f"TILD steps/s and bead-steps/s ({args.workload}) + % of HBM roofline"
+    out = {"impl": "reference", "metric": metric, "value": rate, "unit": "steps/s", "n_gpus": args.gpus,
            "steps": done, "warmup": warm, "ms_per_step": 1000.0 * secs / done, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "bead_steps_per_s": rate * spec.n_beads,
-           "config": {"workload": WORKLOAD, "beads": spec.n_beads, "grid": spec.n, "box": spec.L,
+           "config": {"workload": args.workload, "beads": spec.n_beads, "grid": spec.n, "box": spec.L,
                       "l2": "working set > L2"},
            "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -263,6 +264,7 @@ def run_batch(args):
         t.set_positions(I.initial_positions(s))
         t.init_velocities()
         ctxs.append(t)
+    shapes = {}
     beads = sum(s.n_beads for s in specs)
     K = args.steps
     # one context at a time (each with its own graph-replayed steps)
@@ -277,6 +279,11 @@ def run_batch(args):
         t.synchronize()
     seq_s = time.perf_counter() - t0
     batch = B.TildBatch(ctxs)
+    tuned = None
+    if not args.no_autotune:
+        # persistent kernel or per-group launch shapes, timed on the batch itself
+        choice, cand_ms = batch.autotune(trial_steps=40)
+        tuned = {"choice": choice, "ms_per_step": cand_ms}
     batch.step(args.warmup)
     batch.synchronize()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -294,7 +301,8 @@ def run_batch(args):
            "ms_per_step": 1000.0 * bat_s / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic", "bead_steps_per_s": beads * K / bat_s,
            "config": {"workload": "batch256", "replicas": len(specs), "beads": beads, "grids": sizes,
-                      "sort_every": args.sort_every},
+                      "sort_every": args.sort_every,
+                      "persistent": batch.persistent, "autotune": tuned},
            "sequential": {"value": len(specs) * K / seq_s, "unit": "replica-steps/s",
                           "note": "same replicas stepped one context at a time"},
            "speedup_vs_sequential": seq_s / bat_s, "gpu_launches": launches}
@@ -303,14 +311,16 @@ def run_batch(args):
 
 
 def run_diff(args):
-    """Differentiable form: derivatives of L = sum w . r^K through a 200-step
-    GJF window on the 200k-bead 64^3 diblock melt, checkpoints every 20 steps
-    (forward, recomputation and one force vector-Jacobian product per step)."""
+    """Differentiable form on the 200k-bead 64^3 diblock melt: the gradient of
+    L = U(r^K) + sum_z (p_A(z) - target(z))^2 (energy plus a density-profile
+    loss against a seeded sinusoidal A-density profile) with respect to chi,
+    kappa and a through a 200-step GJF window, checkpoints every 20 steps,
+    and a few gradient steps fitting chi to the target."""
     import torch
 
     from paper_2302_02474_gb300 import binding as B
     from paper_2302_02474_gb300 import inputs as I
-    from paper_2302_02474_gb300.trajectory import trajectory_vjp
+    from paper_2302_02474_gb300.trajectory import profile_loss_gradient, trajectory_vjp
 
     torch.cuda.set_device(0)
     spec = I.config("diblock_200k_64")
@@ -338,13 +348,34 @@ def run_diff(args):
     e1.record(stream)
     e1.synchronize()
     plain_ms = e0.elapsed_time(e1) / K
-    w = np.random.default_rng(1).normal(size=(spec.n_beads, 3))
-    trajectory_vjp(t, 20, w, checkpoint_every=20)  # warm-up of the reverse path
+    # seeded sinusoidal target A-density profile along z around the mean A density
+    rng = np.random.default_rng(12345 + 4)
+    phase, amp = rng.uniform(0, 2 * np.pi), rng.uniform(0.1, 0.3)
+    rho_a = 0.5 * spec.n_beads / spec.L ** 3
+    target = rho_a * (1.0 + amp * np.sin(2 * np.pi * np.arange(spec.n) / spec.n + phase))
+    start = t.get_state(torch.empty(t.state_bytes(), dtype=torch.uint8, device="cuda"))
+    profile_loss_gradient(t, 20, target, checkpoint_every=20)  # warm-up of the reverse path
+    t.set_state(start)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    g = trajectory_vjp(t, K, w, checkpoint_every=20)
-    torch.cuda.synchronize()
-    secs = time.perf_counter() - t0
+    # the backward of the energy plus the profile loss (timed), then the chi fit
+    # on the profile loss alone (the energy would only push chi down)
+    secs = []
+    for _ in range(2):
+        t.set_state(start)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g_full = profile_loss_gradient(t, K, target, checkpoint_every=20)
+        torch.cuda.synchronize()
+        secs.append(time.perf_counter() - t0)
+    chi, fit = spec.chi, []
+    for it in range(args.fit_iters):
+        t.set_interactions(spec.chi, spec.kappa, spec.a)
+        t.set_state(start)
+        t.set_interactions(chi, spec.kappa, spec.a)
+        g = profile_loss_gradient(t, K, target, checkpoint_every=20, energy_weight=0.0)
+        fit.append({"chi": chi, "profile_loss": g["profile_loss"], "dLp_dchi": g["chi"]})
+        chi -= args.fit_lr * g["chi"] / max(1e-30, abs(g["chi"]))
+    sec = min(secs)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lam = torch.randn(spec.n_beads * 3, dtype=torch.float32, device="cuda")
     out = torch.empty_like(lam)
@@ -356,17 +387,23 @@ def run_diff(args):
         t.force_vjp(lam, out=out)
     b.record(stream)
     b.synchronize()
-    out_json = {"metric": "GJF trajectory-gradient windows/s (200 steps, checkpoints every 20; 200k beads, 64^3)",
-                "value": 1.0 / secs, "unit": "windows/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
-                "ms_per_step": 1000.0 * secs / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    out_json = {"metric": "gradient windows/s of L = U + density-profile loss (200 GJF steps, checkpoints every 20; "
+                          "200k beads, 64^3)",
+                "value": 1.0 / sec, "unit": "windows/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * sec / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "diff200k", "beads": spec.n_beads, "grid": spec.n, "checkpoint_every": 20},
+                "config": {"workload": "diff200k", "beads": spec.n_beads, "grid": spec.n, "checkpoint_every": 20,
+                           "loss": "U(r^K) + sum_z (p_A - target)^2", "fit_iters": args.fit_iters},
                 "force_vjp_ms": a.elapsed_time(b) / 20,
                 "plain_step_ms": plain_ms,
-                "ratio_to_plain_step": (1000.0 * secs / K) / plain_ms,
-                "gradients": {k: g[k] for k in ("chi", "kappa", "a")},
-                "note": "wall time of forward + recomputation + reverse sweep through the public API, with "
-                        "device-memory checkpoints; one force vector-Jacobian product per reverse step"}
+                "ratio_to_plain_step": (1000.0 * sec / K) / plain_ms,
+                "gradient": {"loss": g_full["loss"], "energy": g_full["energy"], "profile_loss": g_full["profile_loss"],
+                             "dL_dchi": g_full["chi"], "dL_dkappa": g_full["kappa"], "dL_da": g_full["a"]},
+                "fit": fit,
+                "note": "wall time of one gradient of L = U + profile loss: forward to r^K, energy gradient and "
+                        "density VJP there, then forward + recomputation + reverse sweep inside tild_trajectory_vjp "
+                        "(device checkpoints, one force vector-Jacobian product per reverse step); best of 2. The "
+                        "fit steps chi by a fixed step against the sign of the profile loss's gradient"}
     print(json.dumps(out_json))
     t.close()
 
@@ -383,9 +420,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the step variants")
     ap.add_argument("--no-autotune", action="store_true", help="keep --sort-every instead of autotuning it")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "diff200k"],
-                    help="batch256: 256 uneven replicas stepped with tild_batch_*; diff200k: derivatives through a "
-                         "200-step GJF window (extra measurements)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "diblock_20k_32", "blend_6p4M_256", "batch256", "diff200k"],
+                    help="the other configurations (extra measurements): diblock_20k_32 (FP64, 20k beads, 32^3), "
+                         "blend_6p4M_256 (FP32, 6.4M beads, 256^3), batch256 (256 uneven replicas stepped with "
+                         "tild_batch_*), diff200k (gradients through a 200-step GJF window)")
+    ap.add_argument("--fit-iters", type=int, default=4, help="diff200k: gradient steps of the chi fit")
+    ap.add_argument("--fit-lr", type=float, default=0.2, help="diff200k: step of the chi fit (normalised gradient)")
     ap.add_argument("--mode", default="bench", choices=["bench", "run"],
                     help="run: set up, warm up and take --steps steps only (for profilers; with diff200k, --steps "
                          "force vector-Jacobian products and one 20-step trajectory window)")
@@ -400,7 +441,7 @@ def main():
     if args.workload == "diff200k":
         run_diff(args)
         return
-    spec = I.config(WORKLOAD)
+    spec = I.config(args.workload)
     pos = I.initial_positions(spec)
     if args.impl == "reference":
         run_reference(args, spec, pos)
@@ -512,11 +553,12 @@ def main():
     peak, peak_kind = measured_peaks()
     stage_time = {s: stage_ms[i] for i, s in enumerate(STAGES)}
     dom = max(["forward_fft", "z_spectral", "inverse_fft", "bead_step"], key=lambda s: stage_time[s])
-    dom_bytes = algorithmic_bytes(dom, n_points, spec.n_beads)
+    wide = 2 if spec.precision == "fp64" else 1  # algorithmic bytes count FP32 values; FP64 doubles them
+    dom_bytes = wide * algorithmic_bytes(dom, n_points, spec.n_beads)
     achieved = dom_bytes / (stage_time[dom] * 1e-3) / 1e9
     kernel_names = {"forward_fft": "xy_forward_plane", "z_spectral": "z_spectral",
                     "inverse_fft": "xy_inverse_plane", "bead_step": "bead_kernel"}
-    sb = step_bytes(n_points, spec.n_beads)
+    sb = wide * step_bytes(n_points, spec.n_beads)
     step_achieved = sb * (args.steps / (ms / 1000.0)) / 1e9
 
     cufft = cufft_comparison(spec.n, stage_time)
@@ -530,11 +572,14 @@ def main():
 
     if rank == 0:
         out = {
-            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "metric": METRIC if args.workload == WORKLOAD else
+            f"TILD steps/s and bead-steps/s ({args.workload}) + % of HBM roofline",
+            "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if spec.precision == "fp32" else "f64", "data": "synthetic",
             "bead_steps_per_s": value * spec.n_beads,
-            "config": {"workload": WORKLOAD, "beads": spec.n_beads, "grid": spec.n, "box": spec.L,
+            "launch_shapes": dict(zip(("plane_threads", "z_columns"), t.launch_shapes())),
+            "config": {"workload": args.workload, "beads": spec.n_beads, "grid": spec.n, "box": spec.L,
                        "pmeorder": spec.pmeorder, "sort_every": args.sort_every,
                        "l2": f"step working set {(2 * n_points * 8 + 7 * n_points * 8 + spec.n_beads * 64) / 1e6:.0f} MB > L2, no flush"},
             "roofline": {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak,

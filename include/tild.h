@@ -75,6 +75,7 @@ typedef int tild_status;
 #define TILD_EDEVICE (-4)       /* a CUDA call failed; see tild_last_error */
 #define TILD_ENAN (-5)          /* a non-finite position or force was detected on the device */
 #define TILD_ESTATE (-6)        /* call made before the state it needs exists */
+#define TILD_ETIMEOUT (-7)      /* a device-side wait ran past its time limit (batches; see tild_batch_set_wait_limit) */
 
 typedef enum { TILD_FP32 = 0, TILD_FP64 = 1 } tild_precision;
 typedef enum { TILD_DTYPE_F32 = 0, TILD_DTYPE_F64 = 1 } tild_dtype;
@@ -351,6 +352,18 @@ tild_status tild_energy_gradient(tild_ctx* ctx, tild_energy_grad* g, void* dU_dr
  * planes do not fit one CTA (FP32 above 128^3, FP64 above 64^3). */
 tild_status tild_force_vjp(tild_ctx* ctx, const void* lam, void* out, int dtype, int where, double* dtheta);
 
+/* Vector-Jacobian product of the density assignment (differentiable form;
+ * Eq. rhohat with the spline weights of Sec. "Long-range interactions"
+ * differentiated): for a grid adjoint dL_drho = dL/drho_K(g), [n_species]
+ * [n][n][n] in [z][y][x] order (dtype/where), out [n_beads][3] receives
+ * d/dr_i sum_{K,g} dL_drho_K(g) rho_K(g) = (1/dV) sum_g grad W(r_i - g)
+ * dL_drho_{K_i}(g) at the current positions: the gradient of any loss on the
+ * density grid (for example a density-profile loss) with respect to the
+ * positions. Passed as r_bar to tild_trajectory_vjp it carries the loss back
+ * through a trajectory. Three-dimensional boxes (else TILD_EUNSUPPORTED).
+ * Allocates a context scratch of n_species n^3 + 3 n_beads values. */
+tild_status tild_density_vjp(tild_ctx* ctx, const void* dL_drho, void* out, int dtype, int where);
+
 /* Derivatives through a trajectory (differentiable form): runs n_steps
  * steps of the context's integrator scheme (GJF, EM or VV; TILD_FORCE_IK)
  * and returns the derivatives of a loss L(r^K, v^K) with respect to r^0
@@ -425,23 +438,53 @@ tild_status tild_launches_per_steps(tild_ctx* ctx, int64_t n_steps, int64_t* lau
 
 /* Autotuner: times whole re-binning cycles for re-binning periods 5, 10, 20
  * and 40 (each over about trial_steps steps after one untimed cycle, from
- * the same saved state) and keeps the fastest. Trajectories are
- * bit-identical for every period, so only speed changes; the context's state
- * is restored afterwards. sort_every (may be NULL) receives the chosen
- * period, ms_per_step (may be NULL) four timings in candidate order. Needs
- * positions and velocities; allocates one state-sized device buffer for the
+ * the same saved state) and keeps the fastest; then, at that period, times
+ * the launch shapes of the step (tild_set_launch_shapes: every available
+ * plane thread count and z column tile) and keeps the fastest. Trajectories
+ * are bit-identical for every choice, so only speed changes; the context's
+ * state is restored afterwards. sort_every (may be NULL) receives the chosen
+ * period, ms_per_step (may be NULL) the four period timings in candidate
+ * order; tild_get_launch_shapes reads the chosen shapes. Needs positions and
+ * velocities; allocates one state-sized device buffer (cudaMalloc) for the
  * duration of the call. */
 tild_status tild_autotune(tild_ctx* ctx, int64_t trial_steps, int* sort_every, double* ms_per_step);
 
+/* Launch shapes of the step's FFT passes (results are bit-identical for
+ * every choice; only speed changes):
+ *   plane_threads  threads of each xy-plane CTA of the forward and inverse
+ *                  passes: 512 (default), or 256 / 128 for planes small
+ *                  enough that several CTAs share an SM (n <= 80 and n <= 64
+ *                  respectively, when stage B of the line transform keeps at
+ *                  most 32 complex values per thread);
+ *   z_columns      column tile of the z pass: the default (128 bytes of
+ *                  complex values) or the alternative of half that width
+ *                  (twice the CTAs).
+ * tild_get_launch_shapes reports the current values; tild_set_launch_shapes
+ * returns TILD_EINVAL for a value this grid does not have and
+ * TILD_EUNSUPPORTED on the any-size grids. Batches launch every grid-size
+ * group with the shapes of its first context. */
+tild_status tild_get_launch_shapes(tild_ctx* ctx, int* plane_threads, int* z_columns);
+tild_status tild_set_launch_shapes(tild_ctx* ctx, int plane_threads, int z_columns);
+
 /*
- * Batched form: step several independent systems ("replicas": contexts with
- * their own chains, box, grid, chi, kappa, a and seed; same precision and
- * device) together. Replicas with the same grid size and assignment order
- * share every kernel launch of a step (four per group), reading their
- * arguments from device tables; whole re-binning cycles of all replicas are
- * captured as one CUDA graph. Each replica's trajectory is bit-identical to
- * stepping its context alone with the same re-binning period (the batch uses
- * the first context's sort_every).
+ * Batched form (the paper's plan of several boxes per run, Sec.
+ * "Conclusions"): step several independent systems ("replicas": contexts
+ * with their own chains, box, grid, chi, kappa, a and seed; same precision
+ * and device) together. When every replica is FP32 with pmeorder 1, the ik
+ * force, no charges, two species and a grid of 24, 32, 40, 48 or 64 points
+ * per edge, the steps between two re-binnings of all replicas are ONE
+ * persistent cooperative launch: its CTAs walk a table of the work items of
+ * every replica (xy planes, z-pass tiles, bead tiles), stage by stage, and
+ * meet at grid-wide barriers whose waits are bounded (tild_batch_set_wait_
+ * limit; a wait that runs out is reported as TILD_ETIMEOUT by
+ * tild_batch_synchronize). Otherwise replicas with the same grid size and
+ * assignment order share every kernel launch of a step (four per group),
+ * reading their arguments from device tables, with each group's launch
+ * shapes taken from its first context. Either way whole re-binning cycles
+ * of all replicas are captured as one CUDA graph (re-binning and the
+ * persistent launch, or the per-group launches). Each replica's trajectory
+ * is bit-identical to stepping its context alone with the same re-binning
+ * period (the batch uses the first context's sort_every).
  *
  * tild_batch_create: every context must have positions and velocities and a
  * grid of at most 128 points (FP32) or 64 (FP64) per edge. The contexts stay
@@ -461,6 +504,34 @@ tild_status tild_batch_step(tild_batch* batch, int64_t n_steps);
 tild_status tild_batch_synchronize(tild_batch* batch);
 tild_status tild_batch_launches_per_steps(tild_batch* batch, int64_t n_steps, int64_t* launches);
 tild_status tild_batch_destroy(tild_batch* batch);
+
+/* *persistent = 1 when the batch steps through the persistent kernel. */
+tild_status tild_batch_is_persistent(tild_batch* batch, int* persistent);
+
+/* Choose the persistent kernel (persistent != 0; TILD_EUNSUPPORTED when the
+ * replicas do not allow it) or the per-group launches for the following
+ * steps. Results do not depend on the choice. */
+tild_status tild_batch_set_persistent(tild_batch* batch, int persistent);
+
+/* Batch autotuner: times whole re-binning cycles of the batch (about
+ * trial_steps steps each, after one untimed cycle, from the same saved
+ * replica states) for 7 candidates: [0] the persistent kernel (when the
+ * replicas allow it), then the per-group launches with plane threads 512,
+ * 256, 128 (each group falls back to the largest its grid allows), each with
+ * the default and the alternative z column tile; keeps the fastest. ms (may
+ * be NULL) receives the 7 timings in ms per step (-1 for an unavailable
+ * candidate), choice (may be NULL) the index kept. The replicas' states are
+ * restored afterwards (results do not depend on the choice). Allocates one
+ * state blob per replica (cudaMalloc) for the duration of the call. */
+tild_status tild_batch_autotune(tild_batch* batch, int64_t trial_steps, double* ms, int* choice);
+
+/* Time limit (wait_ns > 0; default 2 s) of one grid-barrier wait of the
+ * persistent kernel, and extra_arrivals >= 0 arrivals the barrier waits for
+ * beyond the launch's CTAs. extra_arrivals > 0 is a fault-injection hook for
+ * tests: no barrier can complete, every wait runs out, the kernel returns
+ * and tild_batch_synchronize reports TILD_ETIMEOUT (the replicas' states are
+ * then undefined). TILD_EUNSUPPORTED without the persistent path. */
+tild_status tild_batch_set_wait_limit(tild_batch* batch, int64_t wait_ns, int extra_arrivals);
 
 /* Description of the last error on this context (or, when ctx is NULL, of
  * the last failed tild_create, tild_batch_* call or

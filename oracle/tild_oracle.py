@@ -653,6 +653,37 @@ def run_with(step_fn, m: Model, st: State, n_steps: int, force_fn=None) -> State
 
 
 # ---------------------------------------------------------------------------
+# Differentiable form: vector-Jacobian product of the density assignment
+# ---------------------------------------------------------------------------
+
+
+def spread_vjp(m: Model, pos: np.ndarray, psi: np.ndarray) -> np.ndarray:
+    """d/dr_i of sum_{K,g} psi_K(g) rho_K(g) for a grid adjoint psi with the
+    axes of ``spread`` (K, x, y, z): Eq. rhohat with the spline weights
+    differentiated, (1/dV) sum_g grad_r W(r_i - g) psi_{K_i}(g). (N, 3)."""
+    n, P, dx = m.n, m.P, m.dx
+    s = wrap(pos, m.L) / dx
+    js, ws, dws = [], [], []
+    for d in range(3):
+        j, w = stencil(s[:, d], P)
+        _, dw = stencil_derivative(s[:, d], P)
+        js.append(j % n)
+        ws.append(w)
+        dws.append(dw / dx)
+    field = psi[m.species]
+    rows = np.arange(m.n_beads)
+    out = np.zeros((m.n_beads, 3))
+    for a in range(P):
+        for b in range(P):
+            for c in range(P):
+                v = field[rows, js[0][:, a], js[1][:, b], js[2][:, c]]
+                out[:, 0] += dws[0][:, a] * ws[1][:, b] * ws[2][:, c] * v
+                out[:, 1] += ws[0][:, a] * dws[1][:, b] * ws[2][:, c] * v
+                out[:, 2] += ws[0][:, a] * ws[1][:, b] * dws[2][:, c] * v
+    return out / dx ** 3
+
+
+# ---------------------------------------------------------------------------
 # Differentiable form: vector-Jacobian product of the ik force
 # ---------------------------------------------------------------------------
 

@@ -18,7 +18,9 @@ LIB_PATH = os.path.join(OUT_DIR, "libtild.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", INCLUDE]
+# -split-compile=0: the device code of each translation unit is optimised in
+# parallel jobs (one per core), which keeps the build to a few minutes
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-split-compile=0", "-I", INCLUDE]
 
 
 def _nvcc() -> str:

@@ -23,6 +23,7 @@ TILD_EUNSUPPORTED = -3
 TILD_EDEVICE = -4
 TILD_ENAN = -5
 TILD_ESTATE = -6
+TILD_ETIMEOUT = -7
 
 TILD_FP32, TILD_FP64 = 0, 1
 TILD_DTYPE_F32, TILD_DTYPE_F64 = 0, 1
@@ -31,7 +32,7 @@ TILD_COMPUTE_ENERGY, TILD_COMPUTE_FORCES = 1, 2
 TILD_LAYOUT_AOS, TILD_LAYOUT_SOA = 0, 1
 
 STATUS_NAMES = {0: "TILD_OK", -1: "TILD_EINVAL", -2: "TILD_ENOMEM", -3: "TILD_EUNSUPPORTED", -4: "TILD_EDEVICE",
-                -5: "TILD_ENAN", -6: "TILD_ESTATE"}
+                -5: "TILD_ENAN", -6: "TILD_ESTATE", -7: "TILD_ETIMEOUT"}
 
 
 class tild_params(ctypes.Structure):
@@ -79,7 +80,10 @@ _SIGS = {
     "tild_set_force_method": [_P, ctypes.c_int],
     "tild_set_electrostatics": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
     "tild_force_vjp": [_P, _P, _P, _I, _I, ctypes.POINTER(ctypes.c_double)],
+    "tild_density_vjp": [_P, _P, _P, _I, _I],
     "tild_autotune": [_P, _I64, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
+    "tild_get_launch_shapes": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "tild_set_launch_shapes": [_P, _I, _I],
     "tild_trajectory_vjp": [_P, _I64, _I, _P, _P, _I, _I, _P, _P, ctypes.POINTER(ctypes.c_double)],
     "tild_set_stream": [_P, _P],
     "tild_set_positions": [_P, _P, _I, _I],
@@ -106,6 +110,10 @@ _SIGS = {
     "tild_batch_synchronize": [_P],
     "tild_batch_launches_per_steps": [_P, _I64, ctypes.POINTER(_I64)],
     "tild_batch_destroy": [_P],
+    "tild_batch_is_persistent": [_P, ctypes.POINTER(_I)],
+    "tild_batch_set_wait_limit": [_P, _I64, _I],
+    "tild_batch_set_persistent": [_P, _I],
+    "tild_batch_autotune": [_P, _I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -446,6 +454,20 @@ class Tild:
         self._chk(self.lib.tild_force_vjp(self.ctx, lptr, optr, lcode, lwhere, th))
         return self._vec(out), {"chi": th[0], "kappa": th[1], "a": th[2]}
 
+    def density_vjp(self, dL_drho, out=None):
+        """d/dr of sum_{K,g} dL_drho[K, z, y, x] rho_K(g) by bead id, for a
+        grid adjoint of shape (n_species, n, n, n) (host array or CUDA tensor;
+        out is of the same kind and dtype)."""
+        cnt = self.n_species * self.nz * self.n ** 2
+        pptr, pcode, pwhere, _k1 = _buffer(dL_drho, cnt)
+        if out is None:
+            out = np.empty(3 * self.n_beads, dtype=np.float64 if pcode == TILD_DTYPE_F64 else np.float32)
+        optr, ocode, owhere, _k2 = _buffer(out, 3 * self.n_beads)
+        if (ocode, owhere) != (pcode, pwhere):
+            raise ValueError("density_vjp: dL_drho and out must share dtype and memory space")
+        self._chk(self.lib.tild_density_vjp(self.ctx, pptr, optr, pcode, pwhere))
+        return self._vec(out)
+
     def energy_gradient(self, with_positions: bool = True, out=None, dtype=np.float64):
         """(dict of U, its terms and dU/dchi, dU/dkappa, dU/da; dU/dr or None)."""
         g = tild_energy_grad()
@@ -498,6 +520,15 @@ class Tild:
         self._chk(self.lib.tild_autotune(self.ctx, int(trial_steps), ctypes.byref(k), ms))
         return k.value, dict(zip(self.AUTOTUNE_PERIODS, list(ms)))
 
+    def launch_shapes(self):
+        """(plane threads, z column tile) of the step's FFT passes."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._chk(self.lib.tild_get_launch_shapes(self.ctx, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set_launch_shapes(self, plane_threads: int, z_columns: int) -> None:
+        self._chk(self.lib.tild_set_launch_shapes(self.ctx, int(plane_threads), int(z_columns)))
+
     def profile_steps(self, n: int):
         ms = (ctypes.c_double * 5)()
         self._chk(self.lib.tild_profile_steps(self.ctx, int(n), ms))
@@ -531,6 +562,29 @@ class TildBatch:
         v = ctypes.c_int64()
         check(self.lib.tild_batch_launches_per_steps(self.h, int(n_steps), ctypes.byref(v)), None)
         return v.value
+
+    @property
+    def persistent(self) -> bool:
+        v = ctypes.c_int()
+        check(self.lib.tild_batch_is_persistent(self.h, ctypes.byref(v)), None)
+        return bool(v.value)
+
+    def set_persistent(self, on: bool) -> None:
+        check(self.lib.tild_batch_set_persistent(self.h, 1 if on else 0), None)
+
+    AUTOTUNE_CANDIDATES = ("persistent", "groups 512", "groups 512 alt-z", "groups 256", "groups 256 alt-z",
+                           "groups 128", "groups 128 alt-z")
+
+    def autotune(self, trial_steps: int = 40):
+        """Keep the fastest of the persistent kernel and the group launch
+        shapes; returns (chosen candidate, {candidate: ms per step})."""
+        ms = (ctypes.c_double * 7)()
+        ch = ctypes.c_int()
+        check(self.lib.tild_batch_autotune(self.h, int(trial_steps), ms, ctypes.byref(ch)), None)
+        return self.AUTOTUNE_CANDIDATES[ch.value], dict(zip(self.AUTOTUNE_CANDIDATES, list(ms)))
+
+    def set_wait_limit(self, wait_ns: int, extra_arrivals: int = 0) -> None:
+        check(self.lib.tild_batch_set_wait_limit(self.h, int(wait_ns), int(extra_arrivals)), None)
 
     def close(self) -> None:
         if getattr(self, "h", None) is not None and self.h.value:

@@ -469,6 +469,18 @@ tild_status tild_force_vjp(tild_ctx* c, const void* lam, void* out, int dtype, i
     return io.st;
 }
 
+tild_status tild_density_vjp(tild_ctx* c, const void* dL_drho, void* out, int dtype, int where) {
+    if (!c) return TILD_EINVAL;
+    if (!dL_drho || !out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "density_vjp: bad pointer, dtype or where");
+    if (!c->eng->has_positions()) return fail(c, TILD_ESTATE, "density_vjp: positions not set");
+    LayoutIO io(c, dtype, where, 1);
+    if (io.st) return io.st;
+    tild_status st = c->eng->density_vjp(dL_drho, io.out(out, 0), dtype, where);
+    if (st) return from_engine(c, st);
+    io.done(out, 0);
+    return io.st;
+}
+
 tild_status tild_get_positions(tild_ctx* c, void* out, int dtype, int where) {
     if (!c) return TILD_EINVAL;
     if (!out || !valid_io(dtype, where)) return fail(c, TILD_EINVAL, "get_positions: bad pointer, dtype or where");
@@ -570,6 +582,21 @@ tild_status tild_trajectory_vjp(tild_ctx* c, int64_t n_steps, int checkpoint_eve
     return io.st;
 }
 
+// Time n steps from the saved state after one untimed re-binning cycle;
+// ms per step in *ms.
+static tild_status time_steps(tild_ctx* c, void* saved, int64_t n, int K, cudaEvent_t e0, cudaEvent_t e1, double* ms) {
+    tild_status st;
+    if ((st = c->eng->set_state(saved, TILD_DEVICE)) || (st = c->eng->step(2 * (int64_t)K))) return st;
+    cudaStream_t s = c->eng->stream();
+    if (cudaEventRecord(e0, s) != cudaSuccess) return TILD_EDEVICE;
+    if ((st = c->eng->step(n))) return st;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return TILD_EDEVICE;
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / (double)n;
+    return TILD_OK;
+}
+
 tild_status tild_autotune(tild_ctx* c, int64_t trial_steps, int* sort_every, double* ms_per_step) {
     if (!c) return TILD_EINVAL;
     if (trial_steps < 1) return fail(c, TILD_EINVAL, "autotune: trial_steps must be >= 1");
@@ -590,22 +617,41 @@ tild_status tild_autotune(tild_ctx* c, int64_t trial_steps, int* sort_every, dou
         c->eng->params_changed();
         // whole re-binning cycles, after one untimed cycle
         const int64_t n = ((trial_steps + 2 * K - 1) / (2 * K)) * (2 * K);
-        if ((st = c->eng->set_state(saved, TILD_DEVICE)) || (st = c->eng->step(2 * K))) break;
-        cudaStream_t s = c->eng->stream();
-        if (cudaEventRecord(e0, s) != cudaSuccess) { st = TILD_EDEVICE; break; }
-        if ((st = c->eng->step(n))) break;
-        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { st = TILD_EDEVICE; break; }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms_per_step) ms_per_step[k] = ms / (double)n;
-        if (ms / (double)n < best_ms) {
-            best_ms = ms / (double)n;
+        double ms = 0;
+        if ((st = time_steps(c, saved, n, K, e0, e1, &ms))) break;
+        if (ms_per_step) ms_per_step[k] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
             best = K;
         }
     }
-    // keep the fastest period and the original state (results do not depend on the period)
     c->cfg.sort_every = st ? original : best;
     c->eng->params_changed();
+    // launch shapes (plane threads, z column tile) at the chosen period;
+    // results do not depend on them either
+    int pt0, zc0, zdef, zalt;
+    c->eng->launch_shapes(&pt0, &zc0, &zdef, &zalt);
+    if (!st && !c->cfg.generic) {
+        const int K = c->cfg.sort_every;
+        const int64_t n = ((trial_steps + 2 * K - 1) / (2 * K)) * (2 * K);
+        int best_pt = pt0, best_zc = zc0;
+        double best_sh = 1e300;
+        const int pts[3] = {512, 256, 128};
+        const int zcs[2] = {zdef, zalt};
+        for (int a = 0; a < 3 && !st; ++a)
+            for (int z = 0; z < (zalt != zdef ? 2 : 1) && !st; ++z) {
+                if (c->eng->set_launch_shapes(pts[a], zcs[z]) != TILD_OK) continue;  // not available for this grid
+                double ms = 0;
+                if ((st = time_steps(c, saved, n, K, e0, e1, &ms))) break;
+                if (ms < best_sh) {
+                    best_sh = ms;
+                    best_pt = pts[a];
+                    best_zc = zcs[z];
+                }
+            }
+        c->eng->set_launch_shapes(st ? pt0 : best_pt, st ? zc0 : best_zc);
+    }
+    // keep the fastest choices and the original state (results do not depend on them)
     if (!st) st = c->eng->set_state(saved, TILD_DEVICE);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -613,6 +659,17 @@ tild_status tild_autotune(tild_ctx* c, int64_t trial_steps, int* sort_every, dou
     if (st) return from_engine(c, st);
     if (sort_every) *sort_every = best;
     return TILD_OK;
+}
+
+tild_status tild_get_launch_shapes(tild_ctx* c, int* plane_threads, int* z_columns) {
+    if (!c || !plane_threads || !z_columns) return fail(c, TILD_EINVAL, "get_launch_shapes: NULL argument");
+    c->eng->launch_shapes(plane_threads, z_columns, nullptr, nullptr);
+    return TILD_OK;
+}
+
+tild_status tild_set_launch_shapes(tild_ctx* c, int plane_threads, int z_columns) {
+    if (!c) return TILD_EINVAL;
+    return from_engine(c, c->eng->set_launch_shapes(plane_threads, z_columns));
 }
 
 tild_status tild_launches_per_steps(tild_ctx* c, int64_t n_steps, int64_t* launches) {
@@ -681,6 +738,39 @@ tild_status tild_batch_launches_per_steps(tild_batch* b, int64_t n_steps, int64_
     if (!b || !launches || n_steps < 0) return TILD_EINVAL;
     *launches = b->b->launches(n_steps);
     return TILD_OK;
+}
+
+tild_status tild_batch_is_persistent(tild_batch* b, int* persistent) {
+    if (!b || !persistent) return TILD_EINVAL;
+    *persistent = b->b->persistent() ? 1 : 0;
+    return TILD_OK;
+}
+
+tild_status tild_batch_set_wait_limit(tild_batch* b, int64_t wait_ns, int extra_arrivals) {
+    if (!b || wait_ns < 1 || extra_arrivals < 0) {
+        g_create_error = "batch_set_wait_limit: bad argument";
+        return TILD_EINVAL;
+    }
+    const tild_status st = b->b->set_wait(wait_ns, extra_arrivals);
+    if (st) g_create_error = "batch_set_wait_limit: " + b->b->err;
+    return st;
+}
+
+tild_status tild_batch_autotune(tild_batch* b, int64_t trial_steps, double* ms, int* choice) {
+    if (!b || trial_steps < 1) {
+        g_create_error = "batch_autotune: bad argument";
+        return TILD_EINVAL;
+    }
+    const tild_status st = b->b->autotune(trial_steps, ms, choice);
+    if (st) g_create_error = "batch_autotune: " + b->b->err;
+    return st;
+}
+
+tild_status tild_batch_set_persistent(tild_batch* b, int persistent) {
+    if (!b) return TILD_EINVAL;
+    const tild_status st = b->b->set_path(persistent != 0);
+    if (st) g_create_error = "batch_set_persistent: " + b->b->err;
+    return st;
 }
 
 tild_status tild_batch_destroy(tild_batch* b) {

@@ -317,16 +317,6 @@ template <int P, typename T, bool AN = false, int NS = 2> constexpr size_t bead_
     return BeadSmem<P, T, AN, NS>::bytes;
 }
 
-// Grid offset (within one field) of the first point of patch row `row`,
-// row = (plane * W + lz) * W + ly over stacked patches; sets the plane.
-template <int P> __device__ __forceinline__ size_t patch_row_base(int row, int3 org, int n, int& plane) {
-    constexpr int W = Patch<P>::W;
-    plane = row / (W * W);
-    const int rem = row - plane * W * W;
-    const int lz = rem / W, ly = rem - lz * W;
-    return ((size_t)pwrap(org.z + lz, n) * n + pwrap(org.y + ly, n)) * n;
-}
-
 template <int P, int MODE, typename T, bool AN = false, int NS = 2>
 __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const BeadBuffers<T>& bf, int t) {
     using PT = Patch<P>;
@@ -357,9 +347,17 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
     const int row0 = (threadIdx.x >> 5) * RPW + rsub;
     const int rstride = (blockDim.x >> 5) * RPW;
     const int gx = pwrap(org.x + lx, p.n);
+    // grid offset of the first point of every patch row (lz, ly), computed
+    // once per CTA for the staging and the flush (n^3 < 2^31)
+    __shared__ int s_rowbase[W * W];
+    for (int i = threadIdx.x; i < W * W; i += blockDim.x) {
+        const int lz = i / W, ly = i - lz * W;
+        s_rowbase[i] = (pwrap(org.z + lz, p.n) * p.n + pwrap(org.y + ly, p.n)) * p.n;
+    }
     if (kSpread) {
         for (int i = threadIdx.x; i < SM::patches * PT::W3; i += blockDim.x) patch[i] = 0;
     }
+    __syncthreads();
     if (AN && kForce && row_lane) {
         // stage w_2p, w_2p+1 of the patch from pot = i (w_2p + i w_2p+1)
         // (field 3 of pair p)
@@ -372,8 +370,7 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
             for (int k = 0; k < ROWS_PER_LANE; ++k) {
                 const int row = row0 + k * rstride;
                 if (row < W * W) {
-                    int unused;
-                    v[k] = __ldg(bf.grad + (4 * pr + 3) * M + patch_row_base<P>(row, org, p.n, unused) + gx);
+                    v[k] = __ldg(bf.grad + (4 * pr + 3) * M + s_rowbase[row] + gx);
                 }
             }
 #pragma unroll
@@ -399,8 +396,7 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
             for (int k = 0; k < ROWS_PER_LANE; ++k) {
                 const int row = row0 + k * rstride;
                 if (row < W * W) {
-                    int unused;
-                    const size_t g = patch_row_base<P>(row, org, p.n, unused) + gx;
+                    const size_t g = (size_t)s_rowbase[row] + gx;
                     v[k][0] = __ldg(gp + g);
                     v[k][1] = __ldg(gp + M + g);
                     v[k][2] = __ldg(gp + 2 * M + g);
@@ -594,12 +590,12 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
     if (kSpread) {
         __syncthreads();
         if (row_lane) {
-            for (int row = row0; row < SM::patches * W * W; row += rstride) {
-                const unsigned long long v = patch[row * W + lx];
-                if (v != 0ull) {
-                    int K;
-                    const size_t base = patch_row_base<P>(row, org, p.n, K);
-                    atomicAdd(bf.rho_fx + K * M + base + gx, v);
+#pragma unroll 1
+            for (int K = 0; K < SM::patches; ++K) {
+                unsigned long long* rk = bf.rho_fx + K * M + gx;
+                for (int row = row0; row < W * W; row += rstride) {
+                    const unsigned long long v = patch[(K * W * W + row) * W + lx];
+                    if (v != 0ull) atomicAdd(rk + s_rowbase[row], v);
                 }
             }
         }

@@ -457,6 +457,39 @@ template <typename T> class Engine final : public EngineBase {
         return TILD_OK;
     }
 
+    // d/dr_i of sum_{K,g} psi_K(g) rho_K(g) for a grid adjoint psi [S][M]
+    // (dtype/where), by bead id ([N][3], dtype/where).
+    tild_status density_vjp(const void* psi, void* out, int dtype, int where) override {
+        if (cfg_->dim != 3) {
+            err = "density_vjp: three-dimensional boxes";
+            return TILD_EUNSUPPORTED;
+        }
+        tild_status st;
+        const size_t N = cfg_->n_beads, G = (size_t)cfg_->n_species * M_;
+        const void* src = psi;
+        if ((st = stage_in(&src, psi, G, dtype, where))) return st;
+        if ((st = ensure_aux((G + 3 * N) * sizeof(T)))) return st;
+        T* psi_d = (T*)aux_;
+        T* out_d = psi_d + G;
+        if (dtype == TILD_DTYPE_F32)
+            convert_copy<float, T><<<blocks(G), 256, 0, stream_>>>(G, (const float*)src, psi_d);
+        else
+            convert_copy<double, T><<<blocks(G), 256, 0, stream_>>>(G, (const double*)src, psi_d);
+        TILD_CUDA(cudaGetLastError());
+        const BeadParams<T> p = bead_params();
+        const BeadBuffers<T> bf = bead_buffers();
+        const T inv_dV = (T)((double)M_ / volume());
+        if ((st = dispatch_p([&](auto pp) -> tild_status {
+                 density_vjp_kernel<decltype(pp)::value, T><<<blocks(N), 256, 0, stream_>>>(p, bf, psi_d, inv_dV, out_d);
+                 return TILD_OK;
+             })))
+            return st;
+        TILD_CUDA(cudaGetLastError());
+        if ((st = stage_out_vec(out_d, 3 * N, out, dtype, where))) return st;
+        TILD_CUDA(cudaStreamSynchronize(stream_));
+        return check_err();
+    }
+
     // positions and carried velocities by id ([2][N][3] T) <-> the context
     void store_state(T* dst) {
         const int N = cfg_->n_beads;
@@ -858,12 +891,56 @@ template <typename T> class Engine final : public EngineBase {
 
     void params_changed() override { invalidate_graph(); }
 
+    // Launch shapes: plane threads (128, 256 or 512 where the grid allows)
+    // and the z pass's column tile (the default or the alternative).
+    void launch_shapes(int* plane_threads, int* z_cols, int* z_default, int* z_alt) const override {
+        *plane_threads = plane_nt_;
+        const int cdef = dispatch_cols(false), calt = dispatch_cols(true);
+        *z_cols = zalt_ ? calt : cdef;
+        if (z_default) *z_default = cdef;
+        if (z_alt) *z_alt = calt;
+    }
+    tild_status set_launch_shapes(int plane_threads, int z_cols) override {
+        if (generic_) {
+            err = "launch shapes: the any-size kernels have none";
+            return TILD_EUNSUPPORTED;
+        }
+        bool ok = false;
+        dispatch_n([&](auto nn) {
+            ok = plane_threads == 512 || (plane_fits_ && ((plane_threads == 256 && plane_nt_ok(decltype(nn)::value, 256)) ||
+                                                         (plane_threads == 128 && plane_nt_ok(decltype(nn)::value, 128))));
+            return TILD_OK;
+        });
+        const int cdef = dispatch_cols(false), calt = dispatch_cols(true);
+        if (!ok || (z_cols != cdef && z_cols != calt)) {
+            err = "launch shapes: plane threads must be 512 (or 128/256 where the grid allows) and the z columns the "
+                  "default or the alternative tile";
+            return TILD_EINVAL;
+        }
+        invalidate_graph();
+        plane_nt_ = plane_threads;
+        zalt_ = z_cols != cdef;
+        return TILD_OK;
+    }
+    int dispatch_cols(bool alt) const {
+        int c = 0;
+        const_cast<Engine*>(this)->dispatch_n([&](auto nn) {
+            c = alt ? zpass_cols_alt(decltype(nn)::value) : zpass_cols(decltype(nn)::value);
+            return TILD_OK;
+        });
+        return c;
+    }
+
    private:
     T* vsave_ = nullptr;
     HostConfig* cfg_ = nullptr;
     // species pairs of the grids (1: up to two species, 2: three or four) and
     // species slots of the bead kernels (2 NP)
     int NP_ = 1, NS_ = 2;
+    // launch shapes of the step (tild_set_launch_shapes, tild_autotune):
+    // threads of the xy plane CTAs and the z pass's column tile
+    int plane_nt_ = 512;
+    bool zalt_ = false;
     // any-size / 2D kernels: grid planes along z, the two factors of n
     bool generic_ = false;
     int nz_ = 0, gn1_ = 1, gn2_ = 1;
@@ -1206,6 +1283,14 @@ template <typename T> class Engine final : public EngineBase {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
                 TILD_CUDA(cudaFuncSetAttribute(xy_forward_plane<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
                 TILD_CUDA(cudaFuncSetAttribute(xy_inverse_plane<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+                if constexpr (plane_nt_ok(NN, 256)) {
+                    TILD_CUDA(cudaFuncSetAttribute(xy_forward_plane<T, NN, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+                    TILD_CUDA(cudaFuncSetAttribute(xy_inverse_plane<T, NN, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+                }
+                if constexpr (plane_nt_ok(NN, 128)) {
+                    TILD_CUDA(cudaFuncSetAttribute(xy_forward_plane<T, NN, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+                    TILD_CUDA(cudaFuncSetAttribute(xy_inverse_plane<T, NN, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+                }
                 TILD_CUDA(cudaFuncSetAttribute(xy_forward_cplx<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
                 TILD_CUDA(cudaFuncSetAttribute(z_vjp<T, NN, vjp_cols(NN)>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vjp_smem()));
             }
@@ -1220,6 +1305,9 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(cudaFuncSetAttribute(z_spectral_pairs<T, NN, C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass2_smem()));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral_pairs<T, NN, C2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass2_smem()));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
+        if constexpr (zpass_cols_alt(NN) != CC)
+            TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, zpass_cols_alt(NN)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)zpass_smem_cols(zpass_cols_alt(NN))));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
         TILD_CUDA(cudaFuncSetAttribute(z_spectral<T, NN, CC, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zpass_smem()));
@@ -1254,6 +1342,7 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     template <int V_> struct ic { static constexpr int value = V_; };
+
 
     template <class F> tild_status dispatch_n(F&& f) {
         switch (n_) {
@@ -1295,8 +1384,11 @@ template <typename T> class Engine final : public EngineBase {
     template <int NN> tild_status forward_n(bool zero_after) {
         if (plane_fits_) {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
-                xy_forward_plane<T, NN><<<dim3(NN, NP_), 512, plane_smem(), stream_>>>(
-                    rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0, zero_after ? counters_ : nullptr);
+                with_nt<NN>([&](auto nt) {
+                    constexpr int NT = decltype(nt)::value;
+                    xy_forward_plane<T, NN, NT><<<dim3(NN, NP_), NT, plane_smem(), stream_>>>(
+                        rho_fx_, Zxy_, tw_, density_scale(), zero_after ? 1 : 0, zero_after ? counters_ : nullptr);
+                });
             }
         } else {
             constexpr int CC = 128 / sizeof(V);
@@ -1335,6 +1427,30 @@ template <typename T> class Engine final : public EngineBase {
     }
     // two species pairs: half the columns (twice the buffers), at least 2
     static constexpr int zpass_cols2(int n) { return zpass_cols(n) / 2 < 2 ? 2 : zpass_cols(n) / 2; }
+    // the alternative column tile of the z pass (launch shapes): half the
+    // default, at least 2
+    static constexpr int zpass_cols_alt(int n) { return zpass_cols2(n); }
+    size_t zpass_smem_cols(int c) const { return ((size_t)n_ + 4 * (size_t)n_ * c) * sizeof(V); }
+    // plane kernels with NT threads: stage B of the line transform keeps
+    // ceil(n N1 / NT) units of N2 values per thread; at most 32 complex
+    static constexpr bool plane_nt_ok(int n, int nt) {
+        if (nt == 512) return true;
+        if (n > 80 || (nt != 128 && nt != 256)) return false;
+        const int n1 = n == 8 ? 8 : n == 16 ? 4 : (n == 48 || n == 80) ? 16 : 8;
+        const int n2 = n / n1;
+        return (n * n1 + nt - 1) / nt * n2 <= 32;
+    }
+    // runtime forms for the batch's groups
+    static bool plane_nt_allowed(int n, int nt) { return plane_nt_ok(n, nt) && n * (n + 1) * (int)sizeof(V) <= 200 * 1024; }
+    static int zpass_cols_n(int n) { return zpass_cols(n); }
+    static int zpass_cols_alt_n(int n) { return zpass_cols_alt(n); }
+    template <int NN, class F> void with_nt(F&& f) {
+        if constexpr (plane_nt_ok(NN, 128))
+            if (plane_nt_ == 128) return f(ic<128>{});
+        if constexpr (plane_nt_ok(NN, 256))
+            if (plane_nt_ == 256) return f(ic<256>{});
+        return f(ic<512>{});
+    }
     size_t zpass2_smem() const { return ((size_t)n_ + 8 * (size_t)n_ * zpass_cols2(n_)) * sizeof(V); }
 
     T two_pi_L() const { return (T)(2.0 * 3.14159265358979323846 / cfg_->L); }
@@ -1390,7 +1506,12 @@ template <typename T> class Engine final : public EngineBase {
             z_spectral<T, NN, CC, true><<<grid, 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, sp, partials, spec_out);
         else if (el)
             z_spectral<T, NN, CC, false, true><<<grid, 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, sp, partials, spec_out);
-        else
+        else if (zalt_ && !partials && !spec_out) {
+            // the step's z pass with the alternative column tile (launch shapes)
+            constexpr int CA = zpass_cols_alt(NN);
+            z_spectral<T, NN, CA><<<dim3(NN / CA, NN / 2 + 1), 256, zpass_smem_cols(CA), stream_>>>(Zxy_, H_, tw_, sp,
+                                                                                                 nullptr, nullptr);
+        } else
             z_spectral<T, NN, CC><<<grid, 256, zpass_smem(), stream_>>>(Zxy_, H_, tw_, sp, partials, spec_out);
         TILD_CUDA(cudaGetLastError());
         return TILD_OK;
@@ -1443,7 +1564,10 @@ template <typename T> class Engine final : public EngineBase {
         const int d0 = what == kInvPot ? 3 : 0;
         if (plane_fits_) {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
-                xy_inverse_plane<T, NN><<<dim3(NN, nd, NP_), 512, plane_smem(), stream_>>>(H_, grad_, tw_, two_pi_L(), d0);
+                with_nt<NN>([&](auto nt) {
+                    constexpr int NT = decltype(nt)::value;
+                    xy_inverse_plane<T, NN, NT><<<dim3(NN, nd, NP_), NT, plane_smem(), stream_>>>(H_, grad_, tw_, two_pi_L(), d0);
+                });
             }
         } else {
             constexpr int CC = 128 / sizeof(V);

@@ -76,11 +76,14 @@ class EngineBase {
     virtual bool has_velocities() const = 0;
     // Parameter changes: keep v^n while F^n changes (u = v - dt/2m F).
     virtual tild_status force_vjp(const void* lam, void* out, int dtype, int where, double* dtheta) = 0;
+    virtual tild_status density_vjp(const void* psi, void* out, int dtype, int where) = 0;
     virtual tild_status trajectory_vjp(int64_t K, int C, const void* rbar, const void* vbar, int dtype, int where,
                                        void* r0, void* v0, double* dtheta) = 0;
     virtual tild_status save_velocities() = 0;
     virtual tild_status restore_velocities() = 0;
     virtual void params_changed() = 0;
+    virtual void launch_shapes(int* plane_threads, int* z_cols, int* z_default, int* z_alt) const = 0;
+    virtual tild_status set_launch_shapes(int plane_threads, int z_cols) = 0;
     // per-bead vector arrays in the other layout: a device scratch of the
     // context and an [n][3] <-> [3][n] transpose on its stream (synchronised)
     virtual tild_status io_scratch(size_t bytes, void** ptr) = 0;
@@ -95,6 +98,10 @@ class BatchBase {
     virtual tild_status step(int64_t n) = 0;
     virtual tild_status synchronize() = 0;
     virtual int64_t launches(int64_t n) const = 0;
+    virtual tild_status set_wait(int64_t wait_ns, int extra) = 0;
+    virtual tild_status autotune(int64_t trial, double* ms, int* choice) = 0;
+    virtual tild_status set_path(bool persistent) = 0;
+    virtual bool persistent() const = 0;
 };
 
 // Error text returned by tild_last_error(NULL).

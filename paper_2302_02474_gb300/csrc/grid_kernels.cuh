@@ -78,6 +78,8 @@ template <int N, int THREADS> __host__ __device__ constexpr int upt_for(int line
 
 // Copy COUNT elements from global to shared memory with up to 16
 // independent loads in flight per thread: dst(i, value) stores element i.
+// Every access is guarded by i < COUNT (the last batch of a thread may be
+// partial when PER is not a multiple of the batch).
 template <int COUNT, int NTHR, class V, class Src, class Dst>
 __device__ __forceinline__ void batched_load(Src src, Dst dst) {
     constexpr int PER = (COUNT + NTHR - 1) / NTHR;
@@ -88,12 +90,12 @@ __device__ __forceinline__ void batched_load(Src src, Dst dst) {
 #pragma unroll
         for (int k = 0; k < B; ++k) {
             const int i = threadIdx.x + (k0 + k) * NTHR;
-            if (COUNT % NTHR == 0 || i < COUNT) v[k] = src(i);
+            if (i < COUNT) v[k] = src(i);
         }
 #pragma unroll
         for (int k = 0; k < B; ++k) {
             const int i = threadIdx.x + (k0 + k) * NTHR;
-            if (COUNT % NTHR == 0 || i < COUNT) dst(i, v[k]);
+            if (i < COUNT) dst(i, v[k]);
         }
     }
 }
@@ -139,7 +141,8 @@ __device__ __forceinline__ void load_fixed_rows(unsigned long long* __restrict__
 
 // --------------------------------------------------------------------------
 // Forward xy pass on whole z-planes (plane fits in shared memory).
-// grid = n (one CTA per z-plane), block = 512.
+// grid = n (one CTA per z-plane), block = NT (512, or 128/256 for small
+// planes, where several CTAs then share an SM).
 // --------------------------------------------------------------------------
 template <typename T> struct ForwardArgs {
     unsigned long long* rho_fx;
@@ -150,7 +153,8 @@ template <typename T> struct ForwardArgs {
     unsigned long long* step_ctr;
 };
 
-template <typename T, int N> __device__ __forceinline__ void xy_forward_plane_body(const ForwardArgs<T>& args, int bx) {
+template <typename T, int N, int NT = 512>
+__device__ __forceinline__ void xy_forward_plane_body(const ForwardArgs<T>& args, int bx) {
     using V = cplx_t<T>;
     unsigned long long* __restrict__ rho_fx = args.rho_fx;
     cplx_t<T>* __restrict__ Zxy = args.Zxy;
@@ -170,10 +174,10 @@ template <typename T, int N> __device__ __forceinline__ void xy_forward_plane_bo
     const size_t M = (size_t)N * N * N;
     const size_t base = (size_t)z * N * N;
     // load + convert: pairs of x so that global accesses are 16-byte vectors
-    load_fixed_rows<N, PITCH, N, 512>(rho_fx + base, rho_fx + M + base, plane, scale, zero_after);
+    load_fixed_rows<N, PITCH, N, NT>(rho_fx + base, rho_fx + M + base, plane, scale, zero_after);
     __syncthreads();
-    smem_fft_lines<N, -1, N, 512>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
-    smem_fft_lines<N, -1, N, 512>(plane, StridedLines<1>{}, PITCH, tw);  // along y
+    smem_fft_lines<N, -1, N, NT>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
+    smem_fft_lines<N, -1, N, NT>(plane, StridedLines<1>{}, PITCH, tw);  // along y
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
         const int y = i / N, x = i % N;
         Zxy[base + i] = plane[y * PITCH + kx_of_pos<N>(x)];  // mirror-paired column order
@@ -181,26 +185,26 @@ template <typename T, int N> __device__ __forceinline__ void xy_forward_plane_bo
 }
 
 // grid = (n, NP): species pair blockIdx.y
-template <typename T, int N>
-__global__ void __launch_bounds__(512) xy_forward_plane(unsigned long long* __restrict__ rho_fx,
+template <typename T, int N, int NT = 512>
+__global__ void __launch_bounds__(NT) xy_forward_plane(unsigned long long* __restrict__ rho_fx,
                                                          cplx_t<T>* __restrict__ Zxy,
                                                          const cplx_t<T>* __restrict__ tw_g, T scale,
                                                          int zero_after, unsigned long long* step_ctr) {
     const size_t M = (size_t)N * N * N;
     const int pr = blockIdx.y;
-    xy_forward_plane_body<T, N>(
+    xy_forward_plane_body<T, N, NT>(
         ForwardArgs<T>{rho_fx + 2 * pr * M, Zxy + pr * M, tw_g, scale, zero_after, pr == 0 ? step_ctr : nullptr},
         blockIdx.x);
 }
 
 // Batched form: replica blockIdx.y of a table of replicas with the same grid.
-template <typename T, int N>
-__global__ void __launch_bounds__(512) xy_forward_plane_batched(const ForwardArgs<T>* __restrict__ args) {
-    xy_forward_plane_body<T, N>(args[blockIdx.y], blockIdx.x);
+template <typename T, int N, int NT = 512>
+__global__ void __launch_bounds__(NT) xy_forward_plane_batched(const ForwardArgs<T>* __restrict__ args) {
+    xy_forward_plane_body<T, N, NT>(args[blockIdx.y], blockIdx.x);
 }
 
 // --------------------------------------------------------------------------
-// Inverse xy pass on whole z-planes: grid = (n, 3), block = 512.
+// Inverse xy pass on whole z-planes: grid = (n, 3), block = NT.
 // --------------------------------------------------------------------------
 template <typename T> struct InverseArgs {
     const cplx_t<T>* H;
@@ -210,7 +214,8 @@ template <typename T> struct InverseArgs {
     int d0;  // first direction (blockIdx.y + d0); 3 alone: the potentials only
 };
 
-template <typename T, int N> __device__ __forceinline__ void xy_inverse_plane_body(const InverseArgs<T>& args, int bx, int by) {
+template <typename T, int N, int NT = 512>
+__device__ __forceinline__ void xy_inverse_plane_body(const InverseArgs<T>& args, int bx, int by) {
     using V = cplx_t<T>;
     const cplx_t<T>* __restrict__ H = args.H;
     cplx_t<T>* __restrict__ grad = args.grad;
@@ -227,14 +232,14 @@ template <typename T, int N> __device__ __forceinline__ void xy_inverse_plane_bo
     const int d = by + args.d0;
     const size_t M = (size_t)N * N * N;
     const size_t src = (d == 2 ? 2 * M : 0) + (size_t)bx * N * N;
-    batched_load<N * N, 512, V>([&](int i) { return H[src + i]; },
+    batched_load<N * N, NT, V>([&](int i) { return H[src + i]; },
                                 [&](int i, V v) {
                                     const int ky = i / N;
                                     if (d == 1) v = c_scale(v, grad_k<T, N>(ky, two_pi_over_L));
                                     plane[ky * PITCH + kx_of_pos<N>(i % N)] = v;
                                 });
     __syncthreads();
-    smem_fft_lines<N, +1, N, 512>(plane, StridedLines<1>{}, PITCH, tw);  // along y
+    smem_fft_lines<N, +1, N, NT>(plane, StridedLines<1>{}, PITCH, tw);  // along y
     if (d == 0) {
         for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
             const int y = i / N, kx = i % N;
@@ -242,26 +247,26 @@ template <typename T, int N> __device__ __forceinline__ void xy_inverse_plane_bo
         }
         __syncthreads();
     }
-    smem_fft_lines<N, +1, N, 512>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
+    smem_fft_lines<N, +1, N, NT>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
     const size_t dst = (size_t)d * M + (size_t)bx * N * N;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) grad[dst + i] = plane[(i / N) * PITCH + i % N];
 }
 
 // grid = (n, directions, NP): species pair blockIdx.z
-template <typename T, int N>
-__global__ void __launch_bounds__(512) xy_inverse_plane(const cplx_t<T>* __restrict__ H,
+template <typename T, int N, int NT = 512>
+__global__ void __launch_bounds__(NT) xy_inverse_plane(const cplx_t<T>* __restrict__ H,
                                                          cplx_t<T>* __restrict__ grad,
                                                          const cplx_t<T>* __restrict__ tw_g, T two_pi_over_L, int d0) {
     const size_t M = (size_t)N * N * N;
     const int pr = blockIdx.z;
-    xy_inverse_plane_body<T, N>(InverseArgs<T>{H + 3 * pr * M, grad + 4 * pr * M, tw_g, two_pi_over_L, d0}, blockIdx.x,
-                                blockIdx.y);
+    xy_inverse_plane_body<T, N, NT>(InverseArgs<T>{H + 3 * pr * M, grad + 4 * pr * M, tw_g, two_pi_over_L, d0},
+                                    blockIdx.x, blockIdx.y);
 }
 
 // Batched form: replica blockIdx.z.
-template <typename T, int N>
-__global__ void __launch_bounds__(512) xy_inverse_plane_batched(const InverseArgs<T>* __restrict__ args) {
-    xy_inverse_plane_body<T, N>(args[blockIdx.z], blockIdx.x, blockIdx.y);
+template <typename T, int N, int NT = 512>
+__global__ void __launch_bounds__(NT) xy_inverse_plane_batched(const InverseArgs<T>* __restrict__ args) {
+    xy_inverse_plane_body<T, N, NT>(args[blockIdx.z], blockIdx.x, blockIdx.y);
 }
 
 // --------------------------------------------------------------------------

@@ -377,6 +377,49 @@ __global__ void __launch_bounds__(256) vjp_beads(BeadParams<T> p, BeadBuffers<T>
     out[3 * (size_t)bid + 2] = oz;
 }
 
+// Vector-Jacobian product of the density assignment (Eq. rhohat with the
+// weights differentiated): for per-species grid adjoints psi_K(g) =
+// dL/drho_K(g) ([S][M], real), the derivative of sum_{K,g} psi_K(g)
+// rho_K(g) with respect to bead i's position,
+//   out_i = (1/dV) sum_g grad_r W(r_i - g) psi_{K_i}(g),
+// by bead id ([N][3]).
+template <int P, typename T>
+__global__ void __launch_bounds__(256) density_vjp_kernel(BeadParams<T> p, BeadBuffers<T> bf, const T* __restrict__ psi,
+                                                          T inv_dV, T* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n_beads) return;
+    const T x = bf.px[i], y = bf.py[i], z = bf.pz[i];
+    const int tag = bf.id[i];
+    const int bid = slot_bead_id(tag), K = slot_species(tag);
+    Stencil<P, T> st;
+    st.set(x, y, z, p.inv_dx);
+    T dwx[P], dwy[P], dwz[P];
+    dh_weight_derivs<P>(x * p.inv_dx, dwx);
+    dh_weight_derivs<P>(y * p.inv_dx, dwy);
+    dh_weight_derivs<P>(z * p.inv_dx, dwz);
+    const int n = p.n;
+    const T* f = psi + (size_t)K * n * n * n;
+    T ox = 0, oy = 0, oz = 0;
+#pragma unroll
+    for (int c = 0; c < P; ++c)
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            const size_t row = ((size_t)pwrap(st.jz + c, n) * n + pwrap(st.jy + b, n)) * n;
+            const T wyz = st.wy[b] * st.wz[c], dyz = dwy[b] * st.wz[c], ydz = st.wy[b] * dwz[c];
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                const T v = f[row + pwrap(st.jx + a, n)];
+                ox += dwx[a] * wyz * v;
+                oy += st.wx[a] * dyz * v;
+                oz += st.wx[a] * ydz * v;
+            }
+        }
+    const T s = p.inv_dx * inv_dV;  // d/dr = (1/dx) d/ds
+    out[3 * (size_t)bid] = ox * s;
+    out[3 * (size_t)bid + 1] = oy * s;
+    out[3 * (size_t)bid + 2] = oz * s;
+}
+
 // acc[k] += sum_b partials[3 b + k] (k = 0..2), in a fixed order: strided
 // sums per thread, then a tree in shared memory. One block of 256 threads.
 static __global__ void __launch_bounds__(256) accumulate_partials(const double* __restrict__ partials, int n_blocks,

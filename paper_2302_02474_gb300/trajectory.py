@@ -82,3 +82,52 @@ def trajectory_vjp(t: Tild, n_steps: int, r_bar, v_bar=None, checkpoint_every: i
                                      None if vb is None else vb.ctypes.data, TILD_DTYPE_F64, TILD_HOST,
                                      r0.ctypes.data, v0.ctypes.data, th))
     return {"r0": r0.reshape(-1, 3), "v0": v0.reshape(-1, 3), "chi": th[0], "kappa": th[1], "a": th[2]}
+
+
+def profile_loss_gradient(t: Tild, n_steps: int, target, weight: float = 1.0, axis: int = 2,
+                          checkpoint_every: int = 20, energy_weight: float = 1.0) -> Dict[str, object]:
+    """The differentiable form's density-profile objective through a
+    trajectory: after `n_steps` steps from the current state,
+      L = energy_weight * U(r^K) + weight * sum_j (p_A(j) - target(j))^2,
+    U the gridded energy (E_bond + E_chi + E_kappa, Eqs. bonds, fh, HelfandP)
+    and p_A the species-0 density averaged over the two grid axes other than
+    `axis` (a length-n profile; axis 2 = z). Returns L and its derivatives
+    with respect to chi, kappa and a (the energy's explicit dependence at
+    r^K plus the trajectory's) and to r^0 and v^0.
+
+    dL/dr^K is the energy gradient (tild_energy_gradient) plus the density
+    term carried back to the positions by the assignment's vector-Jacobian
+    product (tild_density_vjp) of dL/drho_A(g) = 2 weight (p_A - target)/n^2
+    along the profile; the reverse sweep is tild_trajectory_vjp. The forward
+    is run twice (once to reach r^K, once inside the sweep); the context ends
+    at step K. Needs CUDA (the grids stay on the device)."""
+    import torch
+
+    n = t.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    start = torch.empty(t.state_bytes(), dtype=torch.uint8, device=dev)
+    t.get_state(start)
+    t.step(int(n_steps))
+    t.synchronize()
+    e, dU_dr = t.energy_gradient()
+    rho = torch.empty(t.n_species * n ** 3, dtype=torch.float64, device=dev)
+    t.density(out=rho)
+    rhoA = rho.view(t.n_species, n, n, n)[0]  # [z][y][x]
+    dims = {0: (0, 1), 1: (0, 2), 2: (1, 2)}[axis]  # axis x, y, z of the [z][y][x] grid
+    prof = rhoA.mean(dim=dims)
+    tgt = torch.as_tensor(np.asarray(target, dtype=np.float64), device=dev)
+    resid = prof - tgt
+    loss_prof = float(weight * torch.sum(resid * resid))
+    shape = [1, 1, 1]
+    shape[2 - axis] = n
+    psi = torch.zeros(t.n_species, n, n, n, dtype=torch.float64, device=dev)
+    psi[0] = (2.0 * weight / (n * n)) * resid.view(*shape).expand(n, n, n)
+    dens_bar = torch.empty(3 * t.n_beads, dtype=torch.float64, device=dev)
+    t.density_vjp(psi.view(-1), out=dens_bar)
+    ew = float(energy_weight)
+    r_bar = dens_bar.view(-1, 3) + ew * torch.as_tensor(dU_dr, device=dev)
+    t.set_state(start)
+    g = trajectory_vjp(t, int(n_steps), r_bar, None, checkpoint_every)
+    return {"loss": ew * e["energy"] + loss_prof, "energy": e["energy"], "profile_loss": loss_prof,
+            "profile": prof.cpu().numpy(), "chi": ew * e["dU_dchi"] + g["chi"], "kappa": ew * e["dU_dkappa"] + g["kappa"],
+            "a": ew * e["dU_da"] + g["a"], "r0": g["r0"], "v0": g["v0"]}

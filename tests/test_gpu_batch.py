@@ -93,3 +93,70 @@ def test_batch_rejects_bad_input(B):
     t64.init_velocities()
     with pytest.raises(B.TildError):
         B.TildBatch([t, t64])
+
+
+PERSISTENT = [r for r in REPLICAS if r[5] == 1 and r[4] in (24, 32, 40, 48, 64)] + [
+    (90, 20, 10, 20.0, 64, 1, 1.1, 17)]
+
+
+def test_persistent_batch_matches_individual_replicas_bitwise(B):
+    """Eligible replicas (FP32, pmeorder 1, grids 24..64) step through the one
+    persistent launch per re-binning run; same bits as stepping alone."""
+    specs = [_spec(r, "fp32") for r in PERSISTENT]
+    pos = [I.initial_positions(s) for s in specs]
+    batch_ctx = [_ctx(B, s, 5, p) for s, p in zip(specs, pos)]
+    alone = [_ctx(B, s, 9, p) for s, p in zip(specs, pos)]
+    with B.TildBatch(batch_ctx) as bt:
+        assert bt.persistent
+        bt.step(3)
+        bt.step(30)  # whole re-binning cycles (graph replay of sorts + persistent launches)
+        bt.step(4)
+        bt.synchronize()
+        # one launch per run of steps between re-binnings (K = 5: at most
+        # three runs in 10 steps), plus 8 per replica per re-binning (two)
+        assert bt.launches(10) <= 3 + 2 * 8 * len(specs)
+    for t in alone:
+        t.step(37)
+        t.synchronize()
+    for tb, ta in zip(batch_ctx, alone):
+        assert tb.step_count() == ta.step_count() == 37
+        assert np.array_equal(tb.positions(), ta.positions())
+        assert np.array_equal(tb.velocities(), ta.velocities())
+
+
+def test_persistent_barrier_wait_runs_out(B):
+    """Fault injection on the host side: the barrier is told to wait for one
+    CTA more than the launch has, so every wait runs out after its limit; the
+    kernel returns and the batch reports TILD_ETIMEOUT, and the device stays
+    usable."""
+    specs = [_spec(r, "fp32") for r in PERSISTENT[:2]]
+    ts = [_ctx(B, s, 5, I.initial_positions(s)) for s in specs]
+    with B.TildBatch(ts) as bt:
+        assert bt.persistent
+        bt.set_wait_limit(20_000_000, extra_arrivals=1)  # 20 ms
+        bt.step(2)
+        with pytest.raises(B.TildError) as ei:
+            bt.synchronize()
+        assert ei.value.status == B.TILD_ETIMEOUT
+    # the context and device still work
+    t = _ctx(B, specs[0], 5, I.initial_positions(specs[0]))
+    t.step(3)
+    t.synchronize()
+
+
+def test_launch_shapes_do_not_change_results(B):
+    spec = _spec(REPLICAS[3], "fp32")  # 48^3
+    pos = I.initial_positions(spec)
+    out = []
+    for pt, alt in ((512, False), (256, False), (128, True)):
+        t = _ctx(B, spec, 5, pos)
+        zdef = t.launch_shapes()[1]
+        try:
+            t.set_launch_shapes(pt, zdef if not alt else max(2, zdef // 2))
+        except B.TildError:
+            continue
+        t.step(12)
+        out.append((t.positions(), t.velocities()))
+    assert len(out) >= 2
+    for o in out[1:]:
+        assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])

@@ -368,17 +368,32 @@ def test_diblock_1p6M_128_steps_match_oracle(B):
     step (so the captured re-binning cycle graph runs too), positions and
     velocities of all beads against the oracle from the same FP32-rounded
     start."""
+    import json
+
     spec = I.config("diblock_1p6M_128")
     t, m, pos = _setup(B, spec, sort_every=1)
+    rho = t.density()
+    rref = O.spread(m, pos).transpose(0, 3, 2, 1)
     t.init_velocities()
-    f, _ = t.compute(energy=False)
+    f, e = t.compute()
     st = O.initial_state(m, pos)
+    eref = O.energies(m, pos)
     assert _rel(f, st.force) < 1e-5
     t.step(4)
     r, v = t.positions(), t.velocities()
     st = O.run(m, st, 4)
-    assert np.abs(O.minimum_image(r - st.pos, m.L)).max() < 1e-4 * m.L
+    dr = np.abs(O.minimum_image(r - st.pos, m.L)).max()
+    assert dr < 1e-4 * m.L
     assert _rel(v, st.vel) < 1e-4
+    # the FP32 path's error against the FP64 oracle on this workload
+    # (printed for the design notes; run pytest with -s to see it)
+    report = {"density_max_rel": float(np.abs(rho - rref).max() / np.abs(rref).max()),
+              "force_normwise_rel": float(_rel(f, O.forces(m, pos))),
+              "energy_rel": {k: float(abs(e[k] - eref[k]) / abs(eref[k])) for k in ("bond", "chi", "kappa")},
+              "steps": 4, "position_max_over_L": float(dr / m.L), "velocity_normwise_rel": float(_rel(v, st.vel))}
+    print("FP32_VS_ORACLE " + json.dumps(report))
+    for k in ("bond", "chi", "kappa"):
+        assert report["energy_rel"][k] < 1e-6
 
 
 @pytest.mark.parametrize("n_chains", [500, 1000])

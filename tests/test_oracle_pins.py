@@ -714,3 +714,26 @@ def test_gjf_trajectory_vjp_with_velocity_loss_matches_finite_differences():
         return float(np.sum(w * (r0 + O.minimum_image(st.pos - r0, mm.L))) + np.sum(u * st.vel))
 
     _fd_trajectory_pins(m, pos, vel, g, loss)
+
+
+@pytest.mark.parametrize("P", [2, 3, 4, 5])
+def test_spread_vjp_matches_finite_differences(P):
+    """spread_vjp is the gradient of the linear functional sum_{K,g}
+    psi_K(g) rho_K(g) of the positions: central differences of that sum
+    (computed with the spread itself) agree to O(h^2)."""
+    m, pos = _model(P=P, n_chains=5, N=4, n_a=2, L=4.0, n=8, a=0.5)
+    rng = np.random.default_rng(P)
+    psi = rng.normal(size=(2, m.n, m.n, m.n))
+    g = O.spread_vjp(m, pos, psi)
+
+    def f(p):
+        return float(np.sum(psi * O.spread(m, p)))
+
+    h = 1e-6
+    for i in (0, 7, 13):
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            fd = (f(pp) - f(pm)) / (2 * h)
+            assert abs(fd - g[i, d]) < 1e-6 * max(1.0, np.abs(g).max())
