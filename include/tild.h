@@ -475,9 +475,9 @@ tild_status tild_set_launch_shapes(tild_ctx* ctx, int plane_threads, int z_colum
  * per edge, the steps between two re-binnings of all replicas are ONE
  * persistent cooperative launch: its CTAs walk a table of the work items of
  * every replica (xy planes, z-pass tiles, bead tiles), stage by stage, and
- * meet at grid-wide barriers whose waits are bounded (tild_batch_set_wait_
- * limit; a wait that runs out is reported as TILD_ETIMEOUT by
- * tild_batch_synchronize). Otherwise replicas with the same grid size and
+ * meet at grid-wide barriers whose waits are bounded
+ * (tild_batch_set_wait_limit; a wait that runs out is reported as
+ * TILD_ETIMEOUT by tild_batch_synchronize). Otherwise replicas with the same grid size and
  * assignment order share every kernel launch of a step (four per group),
  * reading their arguments from device tables, with each group's launch
  * shapes taken from its first context. Either way whole re-binning cycles
@@ -515,23 +515,24 @@ tild_status tild_batch_set_persistent(tild_batch* batch, int persistent);
 
 /* Batch autotuner: times whole re-binning cycles of the batch (about
  * trial_steps steps each, after one untimed cycle, from the same saved
- * replica states) for 7 candidates: [0] the persistent kernel (when the
- * replicas allow it), then the per-group launches with plane threads 512,
- * 256, 128 (each group falls back to the largest its grid allows), each with
- * the default and the alternative z column tile; keeps the fastest. ms (may
- * be NULL) receives the 7 timings in ms per step (-1 for an unavailable
+ * replica states) for 9 candidates: [0..2] the persistent kernel (when the
+ * replicas allow it) with its registers allocated for 2, 3 and 4 resident
+ * CTAs per SM, then the per-group launches with plane threads 512, 256, 128
+ * (each group falls back to the largest its grid allows), each with the
+ * default and the alternative z column tile; keeps the fastest. ms (may be
+ * NULL) receives the 9 timings in ms per step (-1 for an unavailable
  * candidate), choice (may be NULL) the index kept. The replicas' states are
  * restored afterwards (results do not depend on the choice). Allocates one
  * state blob per replica (cudaMalloc) for the duration of the call. */
 tild_status tild_batch_autotune(tild_batch* batch, int64_t trial_steps, double* ms, int* choice);
 
 /* Time limit (wait_ns > 0; default 2 s) of one grid-barrier wait of the
- * persistent kernel, and extra_arrivals >= 0 arrivals the barrier waits for
- * beyond the launch's CTAs. extra_arrivals > 0 is a fault-injection hook for
- * tests: no barrier can complete, every wait runs out, the kernel returns
- * and tild_batch_synchronize reports TILD_ETIMEOUT (the replicas' states are
+ * persistent kernel, and extra >= 0 arrivals a barrier waits for beyond the
+ * launch's CTAs. extra > 0 is a fault-injection hook for tests: no barrier
+ * can complete, every wait runs out, the kernel returns and
+ * tild_batch_synchronize reports TILD_ETIMEOUT (the replicas' states are
  * then undefined). TILD_EUNSUPPORTED without the persistent path. */
-tild_status tild_batch_set_wait_limit(tild_batch* batch, int64_t wait_ns, int extra_arrivals);
+tild_status tild_batch_set_wait_limit(tild_batch* batch, int64_t wait_ns, int extra);
 
 /* Description of the last error on this context (or, when ctx is NULL, of
  * the last failed tild_create, tild_batch_* call or

@@ -572,19 +572,21 @@ class TildBatch:
     def set_persistent(self, on: bool) -> None:
         check(self.lib.tild_batch_set_persistent(self.h, 1 if on else 0), None)
 
-    AUTOTUNE_CANDIDATES = ("persistent", "groups 512", "groups 512 alt-z", "groups 256", "groups 256 alt-z",
-                           "groups 128", "groups 128 alt-z")
+    AUTOTUNE_CANDIDATES = ("persistent 2/SM", "persistent 3/SM", "persistent 4/SM", "groups 512", "groups 512 alt-z",
+                           "groups 256", "groups 256 alt-z", "groups 128", "groups 128 alt-z")
 
     def autotune(self, trial_steps: int = 40):
         """Keep the fastest of the persistent kernel and the group launch
         shapes; returns (chosen candidate, {candidate: ms per step})."""
-        ms = (ctypes.c_double * 7)()
+        ms = (ctypes.c_double * 9)()
         ch = ctypes.c_int()
         check(self.lib.tild_batch_autotune(self.h, int(trial_steps), ms, ctypes.byref(ch)), None)
         return self.AUTOTUNE_CANDIDATES[ch.value], dict(zip(self.AUTOTUNE_CANDIDATES, list(ms)))
 
-    def set_wait_limit(self, wait_ns: int, extra_arrivals: int = 0) -> None:
-        check(self.lib.tild_batch_set_wait_limit(self.h, int(wait_ns), int(extra_arrivals)), None)
+    def set_wait_limit(self, wait_ns: int, extra: int = 0) -> None:
+        """Limit of one barrier wait of the persistent kernel; extra > 0 makes
+        every wait unreachable (tests of the time limit)."""
+        check(self.lib.tild_batch_set_wait_limit(self.h, int(wait_ns), int(extra)), None)
 
     def close(self) -> None:
         if getattr(self, "h", None) is not None and self.h.value:

@@ -746,12 +746,12 @@ tild_status tild_batch_is_persistent(tild_batch* b, int* persistent) {
     return TILD_OK;
 }
 
-tild_status tild_batch_set_wait_limit(tild_batch* b, int64_t wait_ns, int extra_arrivals) {
-    if (!b || wait_ns < 1 || extra_arrivals < 0) {
+tild_status tild_batch_set_wait_limit(tild_batch* b, int64_t wait_ns, int extra) {
+    if (!b || wait_ns < 1 || extra < 0) {
         g_create_error = "batch_set_wait_limit: bad argument";
         return TILD_EINVAL;
     }
-    const tild_status st = b->b->set_wait(wait_ns, extra_arrivals);
+    const tild_status st = b->b->set_wait(wait_ns, extra);
     if (st) g_create_error = "batch_set_wait_limit: " + b->b->err;
     return st;
 }

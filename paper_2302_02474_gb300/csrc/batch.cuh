@@ -163,8 +163,9 @@ template <typename T> class BatchEngine final : public BatchBase {
     // the largest its grid allows) with the default and the alternative z
     // column tile, from the same saved states, and keeps the fastest. The
     // replicas' states are restored afterwards; results do not depend on the
-    // choice. ms (may be NULL) receives up to 7 timings in candidate order
-    // (persistent first; -1 where a candidate is unavailable).
+    // choice. ms (may be NULL) receives 9 timings in candidate order (the
+    // persistent kernel compiled for 2, 3 and 4 CTAs per SM, then the group
+    // launches; -1 where a candidate is unavailable).
     tild_status autotune(int64_t trial, double* ms, int* choice) override {
         std::vector<void*> saved(reps_.size(), nullptr);
         auto free_saved = [&]() {
@@ -185,23 +186,23 @@ template <typename T> class BatchEngine final : public BatchBase {
         }
         struct Cand {
             bool pers;
-            int nt;
+            int nt;  // plane threads, or the persistent variant
             bool zalt;
         };
-        std::vector<Cand> cands = {{true, 256, false}};
+        std::vector<Cand> cands = {{true, 0, false}, {true, 1, false}, {true, 2, false}};
         for (int nt : {512, 256, 128})
             for (bool za : {false, true}) cands.push_back({false, nt, za});
-        const bool can_persist = p_grid_ > 0;
+        const bool can_persist = p_grids_[0] > 0;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         TILD_CUDA(cudaEventCreate(&e0));
         TILD_CUDA(cudaEventCreate(&e1));
         const int64_t n = std::max<int64_t>(2 * K_, ((trial + 2 * K_ - 1) / (2 * K_)) * (2 * K_));
         double best = 1e300;
-        int best_i = can_persist ? 0 : 1;
+        int best_i = can_persist ? 0 : 3;
         tild_status st = TILD_OK;
         for (size_t i = 0; i < cands.size() && !st; ++i) {
             if (ms) ms[i] = -1.0;
-            if (cands[i].pers && !can_persist) continue;
+            if (cands[i].pers && (!can_persist || p_grids_[cands[i].nt] < 1)) continue;
             apply_config(cands[i].pers, cands[i].nt, cands[i].zalt);
             for (size_t k = 0; k < reps_.size() && !st; ++k) st = reps_[k]->set_state(saved[k], TILD_DEVICE);
             if (st || (st = sync_replicas()) || (st = step(2 * K_))) break;
@@ -234,7 +235,14 @@ template <typename T> class BatchEngine final : public BatchBase {
     // persistent kernel or per-group launches (plane threads nt where a
     // group's grid allows it, else 512; the alternative z tile if zalt)
     void apply_config(bool pers, int nt, bool zalt) {
-        persistent_ = pers && p_grid_ > 0;
+        persistent_ = pers && p_grids_[0] > 0;
+        if (persistent_) {
+            p_var_ = nt;
+            p_grid_ = p_grids_[nt];
+            plan_.expected = (unsigned)(p_grid_ + p_extra_);
+            invalidate_graph();
+            return;
+        }
         for (Group& g : groups_) {
             g.nt = E::plane_nt_allowed(g.n, nt) ? nt : 512;
             g.zalt = zalt && !g.el && E::zpass_cols_alt_n(g.n) != E::zpass_cols_n(g.n);
@@ -243,7 +251,7 @@ template <typename T> class BatchEngine final : public BatchBase {
     }
 
     tild_status set_path(bool pers) override {
-        if (pers && p_grid_ <= 0) {
+        if (pers && p_grids_[0] <= 0) {
             err = "batch: these replicas cannot take the persistent kernel";
             return TILD_EUNSUPPORTED;
         }
@@ -262,6 +270,7 @@ template <typename T> class BatchEngine final : public BatchBase {
         }
         invalidate_graph();
         plan_.wait_ns = wait_ns;
+        p_extra_ = extra;
         plan_.expected = (unsigned)(p_grid_ + extra);
         return TILD_OK;
     }
@@ -356,7 +365,10 @@ template <typename T> class BatchEngine final : public BatchBase {
     bool persistent_ = false, graph_ok_ = true;
     PersistentPlan<T> plan_{};
     const BeadArgs<T>* p_bead_[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [pos parity][u, id parity]
-    int p_grid_ = 0;
+    int p_grid_ = 0;             // CTAs of the chosen variant (0: no persistent path)
+    int p_grids_[3] = {0, 0, 0};  // CTAs of the variants for 2, 3, 4 CTAs per SM
+    int p_var_ = 0;              // chosen variant
+    int p_extra_ = 0;            // arrivals a barrier waits for beyond the grid (tests)
     size_t p_smem_ = 0;
     std::vector<void*> pbufs_;
 
@@ -443,13 +455,21 @@ template <typename T> class BatchEngine final : public BatchBase {
         const size_t plane64 = (64 + 64 * 65) * sizeof(V);
         const size_t z64 = (64 + 4 * 64 * persistent_zcols<T>(64)) * sizeof(V);
         p_smem_ = std::max(bead_smem_bytes<2, T>(), std::max(plane64, z64));
-        TILD_CUDA(cudaFuncSetAttribute(batch_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem_));
-        int per_sm = 0, sms = 0, dev = 0;
+        int sms = 0, dev = 0;
         TILD_CUDA(cudaGetDevice(&dev));
         TILD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        TILD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent<T>, 256, p_smem_));
-        if (per_sm < 1) return TILD_OK;  // cannot be resident: keep the per-kernel path
-        p_grid_ = per_sm * sms;
+        int per_sm[3] = {0, 0, 0};
+        TILD_CUDA(cudaFuncSetAttribute(batch_persistent<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem_));
+        TILD_CUDA(cudaFuncSetAttribute(batch_persistent<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem_));
+        TILD_CUDA(cudaFuncSetAttribute(batch_persistent<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem_));
+        TILD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], batch_persistent<T, 2>, 256, p_smem_));
+        TILD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], batch_persistent<T, 3>, 256, p_smem_));
+        TILD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], batch_persistent<T, 4>, 256, p_smem_));
+        for (int v = 0; v < 3; ++v) p_grids_[v] = per_sm[v] * sms;
+        if (per_sm[0] < 1) return TILD_OK;  // cannot be resident: keep the per-kernel path
+        // the variant with the most resident CTAs until the autotuner says otherwise
+        p_var_ = per_sm[2] >= 1 ? 2 : per_sm[1] >= 1 ? 1 : 0;
+        p_grid_ = p_grids_[p_var_];
         plan_.expected = (unsigned)p_grid_;
         plan_.wait_ns = 2000000000ll;  // 2 s
         persistent_ = true;
@@ -471,7 +491,12 @@ template <typename T> class BatchEngine final : public BatchBase {
         attr[0].val.cooperative = 1;
         lc.attrs = attr;
         lc.numAttrs = 1;
-        TILD_CUDA(cudaLaunchKernelEx(&lc, batch_persistent<T>, pl, m, cur_pos_));
+        if (p_var_ == 2)
+            TILD_CUDA(cudaLaunchKernelEx(&lc, batch_persistent<T, 4>, pl, m, cur_pos_));
+        else if (p_var_ == 1)
+            TILD_CUDA(cudaLaunchKernelEx(&lc, batch_persistent<T, 3>, pl, m, cur_pos_));
+        else
+            TILD_CUDA(cudaLaunchKernelEx(&lc, batch_persistent<T, 2>, pl, m, cur_pos_));
         if (m & 1) {
             cur_pos_ ^= 1;
             for (E* e : reps_) e->cur_pos_ ^= 1;

@@ -112,8 +112,10 @@ __device__ __forceinline__ void persistent_item(int stage, const PersistentPlan<
 }
 
 // n_steps steps of every replica; the first uses position parity pp0.
-template <typename T>
-__global__ void __launch_bounds__(256, 2) batch_persistent(PersistentPlan<T> pl, int n_steps, int pp0) {
+// MINB: CTAs per SM the register allocation is made for (2, 3 or 4; the
+// batch autotuner picks one).
+template <typename T, int MINB>
+__global__ void __launch_bounds__(256, MINB) batch_persistent(PersistentPlan<T> pl, int n_steps, int pp0) {
     for (int s = 0; s < n_steps; ++s) {
         const int pp = (pp0 + s) & 1;
         for (int stage = 0; stage < 4; ++stage) {

@@ -124,16 +124,16 @@ def test_persistent_batch_matches_individual_replicas_bitwise(B):
         assert np.array_equal(tb.velocities(), ta.velocities())
 
 
-def test_persistent_barrier_wait_runs_out(B):
-    """Fault injection on the host side: the barrier is told to wait for one
-    CTA more than the launch has, so every wait runs out after its limit; the
-    kernel returns and the batch reports TILD_ETIMEOUT, and the device stays
-    usable."""
+def test_persistent_wait_runs_out(B):
+    """Fault injection on the host side: the persistent kernel's grid barrier
+    is told to wait for one CTA more than the launch has, so every wait runs
+    out after its limit; the kernel returns, the batch reports TILD_ETIMEOUT,
+    and the device stays usable."""
     specs = [_spec(r, "fp32") for r in PERSISTENT[:2]]
     ts = [_ctx(B, s, 5, I.initial_positions(s)) for s in specs]
     with B.TildBatch(ts) as bt:
         assert bt.persistent
-        bt.set_wait_limit(20_000_000, extra_arrivals=1)  # 20 ms
+        bt.set_wait_limit(20_000_000, extra=1)  # 20 ms
         bt.step(2)
         with pytest.raises(B.TildError) as ei:
             bt.synchronize()
