@@ -41,19 +41,28 @@ def _stale(target: str, deps: List[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ and link libtild.so; returns its path."""
-    os.makedirs(OUT_DIR, exist_ok=True)
+DEBUG_LIB_PATH = os.path.join(OUT_DIR, "libtild_debug.so")
+
+
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile every .cu under csrc/ and link libtild.so; returns its path.
+    debug=True builds libtild_debug.so instead, with the kernels' bounds
+    checks on (-DTILD_DEBUG=1: a failed check records a flag and skips the
+    access; the next synchronising call returns TILD_EDEVICE)."""
+    out_dir = os.path.join(OUT_DIR, "debug") if debug else OUT_DIR
+    lib_path = DEBUG_LIB_PATH if debug else LIB_PATH
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "tild.h"))
     nvcc = _nvcc()
+    flags = FLAGS + (["-DTILD_DEBUG=1"] if debug else [])
     objs, procs = [], []
     for s in srcs:
-        o = os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(out_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o]
+            cmd = [nvcc, *ARCH, *flags, "-c", s, "-o", o]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((s, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
@@ -66,13 +75,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(out, file=sys.stderr)
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-    if force or procs or _stale(LIB_PATH, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB_PATH, *objs, "-cudart", "static"]
+    if force or procs or _stale(lib_path, objs):
+        cmd = [nvcc, *ARCH, "-shared", "-o", lib_path, *objs, "-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    return LIB_PATH
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

@@ -256,7 +256,8 @@ __device__ __forceinline__ void gather_force_an(const Stencil<P, T>& st, const T
 template <int P, typename T>
 __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_patch, int3 l,
                                             typename FixedPoint<T>::patch_t* patch,
-                                            unsigned long long* __restrict__ rho_fx, int n, int K) {
+                                            unsigned long long* __restrict__ rho_fx, int n, int K,
+                                            unsigned int* err = nullptr) {
     using PT = Patch<P>;
     using FP = FixedPoint<T>;
     if (in_patch) {
@@ -280,7 +281,7 @@ __device__ __forceinline__ void spread_bead(const Stencil<P, T>& st, bool in_pat
 #pragma unroll
                 for (int a = 0; a < P; ++a) {
                     const size_t g = ((size_t)pwrap(st.jz + c, n) * n + pwrap(st.jy + b, n)) * n + pwrap(st.jx + a, n);
-                    atomicAdd(rho_fx + K * M + g, FP::to_grid(st.wx[a] * wyz));
+                    if (debug_check(g < M, err)) atomicAdd(rho_fx + K * M + g, FP::to_grid(st.wx[a] * wyz));
                 }
             }
     }
@@ -481,7 +482,7 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
                         nx[k] = s_pos[s - c0];
                         ny[k] = s_pos[kBeadChunk + s - c0];
                         nz[k] = s_pos[2 * kBeadChunk + s - c0];
-                    } else if (s >= 0) {
+                    } else if (s >= 0 && debug_check(s < p.n_beads, bf.err)) {
                         nx[k] = bf.px[s];
                         ny[k] = bf.py[s];
                         nz[k] = bf.pz[s];
@@ -517,6 +518,7 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
                     }
                 }
                 for_each_extra_bond(nb, bf.ext, [&](int s) {
+                    if (!debug_check(s >= 0 && s < p.n_beads, bf.err)) return;
                     const T dx = min_image(x - bf.px[s], p.L, p.inv_L);
                     const T dy = min_image(y - bf.py[s], p.L, p.inv_L);
                     const T dz = min_image(z - bf.pz[s], p.L, p.inv_L);
@@ -583,7 +585,8 @@ __device__ __forceinline__ void bead_kernel_body(const BeadParams<T>& p, const B
                     inside = patch_local(st, org, l);
                 }
             }
-            if (kSpread) spread_bead<P>(st, inside && patch_ok, l, patch, bf.rho_fx, p.n, species);
+            if (kSpread && debug_check(species < NS, bf.err))
+                spread_bead<P>(st, inside && patch_ok, l, patch, bf.rho_fx, p.n, species, bf.err);
         }
     }
 
@@ -724,7 +727,7 @@ __global__ void bin_count(int n_beads, const T* __restrict__ px, const T* __rest
     if (i >= n_beads) return;
     const int k = tile_key(px[i], py[i], pz[i], inv_dx, n, tiles);
     keys[i] = k;
-    warp_aggregated_inc(counts, k);
+    warp_aggregated_inc(counts, k);  // k < tiles^3: cells are clamped to [0, n) in tile_key
 }
 
 // species_of_id (NULL: the A/B block pattern of the chains) gives each

@@ -246,5 +246,24 @@ __host__ __device__ __forceinline__ BeadInfo bead_info(const Topology& t, int id
 
 // Error flags raised by kernels (read by the host on demand).
 constexpr unsigned kErrNonFinite = 1u;
+constexpr unsigned kErrBounds = 2u;  // a bounds check of the debug build failed
+
+// Debug build (compiled with -DTILD_DEBUG=1, `_build.build(debug=True)`):
+// the bead kernels check slot and grid indices before they use them; a
+// failed check records kErrBounds in the context's error word and the access
+// is skipped (no trap), and the next synchronising call returns
+// TILD_EDEVICE. In the normal build every check is the constant true.
+#ifndef TILD_DEBUG
+#define TILD_DEBUG 0
+#endif
+__device__ __forceinline__ bool debug_check(bool ok, unsigned int* err) {
+#if TILD_DEBUG
+    if (!ok) atomicOr(err, kErrBounds);
+    return ok;
+#else
+    (void)err;
+    return true;
+#endif
+}
 
 }  // namespace tild

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bead_kernels.cuh"
 #include "vjp_kernels.cuh"
 #include "engine_api.h"
@@ -1196,6 +1198,11 @@ template <typename T> class Engine final : public EngineBase {
     tild_status check_err() {
         unsigned int h = 0;
         TILD_CUDA(cudaMemcpy(&h, err_ptr(), sizeof(h), cudaMemcpyDeviceToHost));
+        if (h & kErrBounds) {
+            TILD_CUDA(cudaMemset(err_ptr(), 0, sizeof(unsigned int)));
+            err = "a bounds check of the debug build failed on the device (the access was skipped)";
+            return TILD_EDEVICE;
+        }
         if (h & kErrNonFinite) {
             TILD_CUDA(cudaMemset(err_ptr(), 0, sizeof(unsigned int)));
             err = "non-finite position or force detected on the device";
@@ -1748,7 +1755,14 @@ template <typename T> class Engine final : public EngineBase {
         return launch_bead(kModeSpread, bead_buffers());
     }
 
+    // NVTX range on the host thread for profilers (no cost without one attached)
+    struct Range {
+        explicit Range(const char* name) { nvtxRangePushA(name); }
+        ~Range() { nvtxRangePop(); }
+    };
+
     tild_status enqueue_step() {
+        Range range("tild step: forward, z pass, inverse, beads");
         tild_status st;
         if ((st = enqueue_forward(true))) return st;
         if ((st = enqueue_zpass(nullptr, nullptr, analytic()))) return st;
@@ -1764,6 +1778,7 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     tild_status enqueue_sort(cudaStream_t on = nullptr) {
+        Range range("tild re-binning");
         cudaStream_t stream_ = on ? on : this->stream_;  // the batch re-bins on its own stream
         const int N = cfg_->n_beads;
         const size_t N3 = N;
@@ -1794,6 +1809,7 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     tild_status run_cycle_graph() {
+        Range range("tild re-binning cycles (graph)");
         const int key = cur_pos_ | (cur_u_ << 1) | (cur_id_ << 2);
         tild_status st;
         if (!graph_ || graph_key_ != key) {
