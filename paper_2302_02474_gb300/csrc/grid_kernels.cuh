@@ -78,24 +78,26 @@ template <int N, int THREADS> __host__ __device__ constexpr int upt_for(int line
 
 // Copy COUNT elements from global to shared memory with up to 16
 // independent loads in flight per thread: dst(i, value) stores element i.
-// Every access is guarded by i < COUNT (the last batch of a thread may be
-// partial when PER is not a multiple of the batch).
+// Accesses are guarded by i < COUNT unless every thread's batches are full
+// (COUNT a multiple of NTHR and PER a multiple of the batch); otherwise the
+// last batch of a thread may be partial.
 template <int COUNT, int NTHR, class V, class Src, class Dst>
 __device__ __forceinline__ void batched_load(Src src, Dst dst) {
     constexpr int PER = (COUNT + NTHR - 1) / NTHR;
     constexpr int B = PER < 16 ? PER : 16;
+    constexpr bool kFull = COUNT % NTHR == 0 && PER % B == 0;
 #pragma unroll 1
     for (int k0 = 0; k0 < PER; k0 += B) {
         V v[B];
 #pragma unroll
         for (int k = 0; k < B; ++k) {
             const int i = threadIdx.x + (k0 + k) * NTHR;
-            if (i < COUNT) v[k] = src(i);
+            if (kFull || i < COUNT) v[k] = src(i);
         }
 #pragma unroll
         for (int k = 0; k < B; ++k) {
             const int i = threadIdx.x + (k0 + k) * NTHR;
-            if (i < COUNT) dst(i, v[k]);
+            if (kFull || i < COUNT) dst(i, v[k]);
         }
     }
 }
@@ -110,6 +112,7 @@ __device__ __forceinline__ void load_fixed_rows(unsigned long long* __restrict__
     constexpr int PAIRS = ROWS * N / 2;
     constexpr int ITER = (PAIRS + NTHR - 1) / NTHR;
     constexpr int BATCH = ITER < 8 ? ITER : 8;
+    constexpr bool kFull = PAIRS % NTHR == 0 && ITER % BATCH == 0;  // no partial batch
     longlong2* pa = reinterpret_cast<longlong2*>(ga);
     longlong2* pb = reinterpret_cast<longlong2*>(gb);
 #pragma unroll 1
@@ -118,7 +121,7 @@ __device__ __forceinline__ void load_fixed_rows(unsigned long long* __restrict__
 #pragma unroll
         for (int k = 0; k < BATCH; ++k) {
             const int i = threadIdx.x + (k0 + k) * NTHR;
-            if (i < PAIRS) {
+            if (kFull || i < PAIRS) {
                 a[k] = __ldcs(pa + i);
                 b[k] = __ldcs(pb + i);
             }
@@ -126,7 +129,7 @@ __device__ __forceinline__ void load_fixed_rows(unsigned long long* __restrict__
 #pragma unroll
         for (int k = 0; k < BATCH; ++k) {
             const int i = threadIdx.x + (k0 + k) * NTHR;
-            if (i < PAIRS) {
+            if (kFull || i < PAIRS) {
                 if (zero_after) {
                     pa[i] = make_longlong2(0, 0);
                     pb[i] = make_longlong2(0, 0);
@@ -178,7 +181,7 @@ __device__ __forceinline__ void xy_forward_plane_body(const ForwardArgs<T>& args
     __syncthreads();
     smem_fft_lines<N, -1, N, NT>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
     smem_fft_lines<N, -1, N, NT>(plane, StridedLines<1>{}, PITCH, tw);  // along y
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    for (int i = threadIdx.x; i < N * N; i += NT) {
         const int y = i / N, x = i % N;
         Zxy[base + i] = plane[y * PITCH + kx_of_pos<N>(x)];  // mirror-paired column order
     }
@@ -241,7 +244,7 @@ __device__ __forceinline__ void xy_inverse_plane_body(const InverseArgs<T>& args
     __syncthreads();
     smem_fft_lines<N, +1, N, NT>(plane, StridedLines<1>{}, PITCH, tw);  // along y
     if (d == 0) {
-        for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        for (int i = threadIdx.x; i < N * N; i += NT) {
             const int y = i / N, kx = i % N;
             plane[y * PITCH + kx] = c_scale(plane[y * PITCH + kx], grad_k<T, N>(kx, two_pi_over_L));
         }
@@ -249,7 +252,7 @@ __device__ __forceinline__ void xy_inverse_plane_body(const InverseArgs<T>& args
     }
     smem_fft_lines<N, +1, N, NT>(plane, StridedLines<PITCH>{}, 1, tw);  // along x
     const size_t dst = (size_t)d * M + (size_t)bx * N * N;
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) grad[dst + i] = plane[(i / N) * PITCH + i % N];
+    for (int i = threadIdx.x; i < N * N; i += NT) grad[dst + i] = plane[(i / N) * PITCH + i % N];
 }
 
 // grid = (n, directions, NP): species pair blockIdx.z
