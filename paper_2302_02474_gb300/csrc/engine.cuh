@@ -851,7 +851,7 @@ template <typename T> class Engine final : public EngineBase {
 
     int64_t launches(int64_t n) const override {
         const int D = cfg_->dim;
-        const int64_t per_step = generic_ ? (1 + D) + 1 + (int64_t)NP_ * D + 1 : (plane_fits_ ? 2 : 4) + 2;
+        const int64_t per_step = generic_ ? (1 + D) + 1 + (int64_t)NP_ * D + 1 : (use_planes() ? 2 : 4) + 2;
         const int64_t per_sort = 8;
         const int K = cfg_->sort_every;
         int64_t since = steps_since_sort_, sorts = 0;
@@ -909,14 +909,16 @@ template <typename T> class Engine final : public EngineBase {
         }
         bool ok = false;
         dispatch_n([&](auto nn) {
-            ok = plane_threads == 512 || (plane_fits_ && ((plane_threads == 256 && plane_nt_ok(decltype(nn)::value, 256)) ||
-                                                         (plane_threads == 128 && plane_nt_ok(decltype(nn)::value, 128))));
+            constexpr int NN = decltype(nn)::value;
+            ok = plane_threads == 512 || (plane_fits_ && ((plane_threads == 256 && plane_nt_ok(NN, 256)) ||
+                                                         (plane_threads == 128 && plane_nt_ok(NN, 128)) ||
+                                                         (plane_threads == 0 && split_ok(NN))));
             return TILD_OK;
         });
         const int cdef = dispatch_cols(false), calt = dispatch_cols(true);
         if (!ok || (z_cols != cdef && z_cols != calt)) {
-            err = "launch shapes: plane threads must be 512 (or 128/256 where the grid allows) and the z columns the "
-                  "default or the alternative tile";
+            err = "launch shapes: plane threads must be 512 (or 128/256 where the grid allows, or 0 for the row and "
+                  "column passes) and the z columns the default or the alternative tile";
             return TILD_EINVAL;
         }
         invalidate_graph();
@@ -1301,7 +1303,8 @@ template <typename T> class Engine final : public EngineBase {
                 TILD_CUDA(cudaFuncSetAttribute(xy_forward_cplx<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
                 TILD_CUDA(cudaFuncSetAttribute(z_vjp<T, NN, vjp_cols(NN)>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vjp_smem()));
             }
-        } else {
+        }
+        if (!plane_fits_ || split_ok(NN)) {
             TILD_CUDA(cudaFuncSetAttribute(x_forward_rows<T, NN, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem()));
             TILD_CUDA(cudaFuncSetAttribute(x_inverse_rows<T, NN, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem()));
             TILD_CUDA(cudaFuncSetAttribute(y_columns<T, NN, 128 / sizeof(V), -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ycol_smem()));
@@ -1389,7 +1392,7 @@ template <typename T> class Engine final : public EngineBase {
     }
 
     template <int NN> tild_status forward_n(bool zero_after) {
-        if (plane_fits_) {
+        if (use_planes()) {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
                 with_nt<NN>([&](auto nt) {
                     constexpr int NT = decltype(nt)::value;
@@ -1447,6 +1450,13 @@ template <typename T> class Engine final : public EngineBase {
         const int n2 = n / n1;
         return (n * n1 + nt - 1) / nt * n2 <= 32;
     }
+    // The row and column passes (x rows, then y columns, through global
+    // memory) serve grids whose planes do not fit shared memory, and are the
+    // launch shape plane_threads = 0 for those that do.
+    static constexpr bool split_ok(int n) {
+        return n >= 16 && n % (int)(128 / sizeof(V)) == 0;  // whole column tiles (and rows in blocks of 16)
+    }
+    bool use_planes() const { return plane_fits_ && plane_nt_ != 0; }
     // runtime forms for the batch's groups
     static bool plane_nt_allowed(int n, int nt) { return plane_nt_ok(n, nt) && n * (n + 1) * (int)sizeof(V) <= 200 * 1024; }
     static int zpass_cols_n(int n) { return zpass_cols(n); }
@@ -1569,7 +1579,7 @@ template <typename T> class Engine final : public EngineBase {
     template <int NN> tild_status inverse_n(int what) {
         const unsigned nd = what == kInvGrad ? 3 : what == kInvGradPot ? 4 : 1;
         const int d0 = what == kInvPot ? 3 : 0;
-        if (plane_fits_) {
+        if (use_planes()) {
             if constexpr ((size_t)NN * (NN + 1) * sizeof(V) <= 200 * 1024) {
                 with_nt<NN>([&](auto nt) {
                     constexpr int NT = decltype(nt)::value;

@@ -148,7 +148,7 @@ def test_launch_shapes_do_not_change_results(B):
     spec = _spec(REPLICAS[3], "fp32")  # 48^3
     pos = I.initial_positions(spec)
     out = []
-    for pt, alt in ((512, False), (256, False), (128, True)):
+    for pt, alt in ((512, False), (256, False), (128, True), (0, False), (0, True)):
         t = _ctx(B, spec, 5, pos)
         zdef = t.launch_shapes()[1]
         try:
@@ -157,6 +157,6 @@ def test_launch_shapes_do_not_change_results(B):
             continue
         t.step(12)
         out.append((t.positions(), t.velocities()))
-    assert len(out) >= 2
+    assert len(out) >= 4  # 512, 256 and the row/column passes (0) exist for 48^3
     for o in out[1:]:
         assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])

@@ -225,6 +225,27 @@ def test_trajectory_independent_of_binning_and_graphs(B):
         assert np.array_equal(outs[0], o)
 
 
+@pytest.mark.parametrize("prec,n_chains", [("fp32", 480), ("fp32", 1000), ("fp64", 480)])
+def test_trajectory_independent_of_binning_crowded_tiles(B, prec, n_chains):
+    """Crowded tiles (600 or 1250 beads on each of 8 tiles: several staging
+    chunks, and above 1023 beads the tile spreads through global memory),
+    large steps and rare re-binning, so that more beads leave their tile's
+    patch, and more bonded neighbours lie outside the staged chunk, than the
+    per-chunk lists of the bead kernel hold: the overflow paths must give the
+    same bits as frequent re-binning."""
+    spec = I.small_system(n_chains=n_chains, N=10, n_a=4, L=8.0, n=16, precision=prec, chi=1.0, kappa=5.0)
+    spec = spec.with_(dt=0.02, kT=2.0)
+    outs = []
+    for sort_every in (2, 100000):
+        t, m, pos = _setup(B, spec, sort_every=sort_every)
+        t.init_velocities()
+        t.step(30)
+        outs.append(t.positions())
+    assert np.array_equal(outs[0], outs[1])
+    # beads moved by more than a cell (many of those near a tile face left it)
+    assert np.abs(O.minimum_image(outs[1] - pos, spec.L)).max() > spec.L / spec.n
+
+
 def test_beads_escaping_their_tile_patch(B):
     """Large steps and no re-binning: beads leave the shared-memory patch of
     their tile and are spread through the global fallback; results still
