@@ -455,7 +455,9 @@ tild_status tild_autotune(tild_ctx* ctx, int64_t trial_steps, int* sort_every, d
  *                  passes: 512 (default), or 256 / 128 for planes small
  *                  enough that several CTAs share an SM (n <= 80 and n <= 64
  *                  respectively, when stage B of the line transform keeps at
- *                  most 32 complex values per thread), or 0 for separate x-row
+ *                  most 32 complex values per thread), 1024 (FP32, n = 80 and
+ *                  128: every thread has a unit of the line transform's
+ *                  second stage), or 0 for separate x-row
  *                  and y-column passes through global memory (the passes of
  *                  grids whose planes do not fit shared memory; n a
  *                  multiple of 16 in FP32, of 8 (and at least 16) in FP64);

@@ -636,9 +636,9 @@ tild_status tild_autotune(tild_ctx* c, int64_t trial_steps, int* sort_every, dou
         const int64_t n = ((trial_steps + 2 * K - 1) / (2 * K)) * (2 * K);
         int best_pt = pt0, best_zc = zc0;
         double best_sh = 1e300;
-        const int pts[4] = {512, 256, 128, 0};  // 0: row and column passes
+        const int pts[5] = {512, 1024, 256, 128, 0};  // 0: row and column passes
         const int zcs[2] = {zdef, zalt};
-        for (int a = 0; a < 4 && !st; ++a)
+        for (int a = 0; a < 5 && !st; ++a)
             for (int z = 0; z < (zalt != zdef ? 2 : 1) && !st; ++z) {
                 if (c->eng->set_launch_shapes(pts[a], zcs[z]) != TILD_OK) continue;  // not available for this grid
                 double ms = 0;

@@ -571,7 +571,7 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
 // G_ONLY: write G alone (the potentials' path of the analytic force).
 // EL: add the smeared-charge Coulomb term (charges on).
 template <typename T, int N, int C, bool G_ONLY = false, bool EL = false>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) z_spectral(const cplx_t<T>* __restrict__ Zxy, cplx_t<T>* __restrict__ H,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (C <= 8 ? 4 : 3) : 1) z_spectral(const cplx_t<T>* __restrict__ Zxy, cplx_t<T>* __restrict__ H,
                                                   const cplx_t<T>* __restrict__ tw_g, SpectralParams<T> sp,
                                                   double* __restrict__ energy_partials,
                                                   cplx_t<T>* __restrict__ spectrum_out) {

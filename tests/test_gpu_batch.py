@@ -144,6 +144,22 @@ def test_persistent_wait_runs_out(B):
     t.synchronize()
 
 
+def test_plane_threads_1024_and_row_passes_same_bits(B):
+    """80^3 FP32: 1024-thread plane CTAs, 512 and the row/column passes give
+    the same trajectory bits."""
+    spec = I.small_system(n_chains=300, N=10, n_a=4, L=32.0, n=80, precision="fp32")
+    pos = I.initial_positions(spec)
+    out = []
+    for pt in (512, 1024, 0):
+        t = _ctx(B, spec, 5, pos)
+        t.set_launch_shapes(pt, t.launch_shapes()[1])
+        assert t.launch_shapes()[0] == pt
+        t.step(12)
+        out.append((t.positions(), t.velocities()))
+    for o in out[1:]:
+        assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
+
+
 def test_launch_shapes_do_not_change_results(B):
     spec = _spec(REPLICAS[3], "fp32")  # 48^3
     pos = I.initial_positions(spec)
