@@ -25,8 +25,9 @@
 //       F^n = F_c^n - alpha u^n + sqrt(2 alpha kT/dt) xi^n, v^n = u^n + (dt/2m) F^n,
 //       u^{n+1} = v^{n+1/2} = u^n + (dt/m) F^n, r^{n+1} = r^n + dt u^{n+1}.
 //
-// Bead arrays are SoA in "slot" order: beads binned by cell (tile-major)
-// every few steps. Slot -> bead id and species in `id`; bonded neighbours by
+// Bead arrays are SoA in "slot" order: beads binned by tile every few steps
+// (within a tile: interior beads first, each group in bank-group rounds; see
+// bin_count_fine). Slot -> bead id and species in `id`; bonded neighbours by
 // slot in `nbr` (and `ext` for beads with more than two bonds). All results
 // are independent of the slot order.
 //
@@ -720,117 +721,80 @@ __device__ __forceinline__ int warp_aggregated_inc(int* counter, int key) {
     return base + rank;
 }
 
+// Re-binning in one counting sort over fine bins: 16 per tile, (edge class,
+// bank group). Class 0 holds beads more than half a cell from every tile
+// face, class 1 the others: those drift out of the tile's patch before the
+// next re-binning and take the global-memory paths, so they go last and
+// share as few warps as possible. The bank group is the 16-byte bank group
+// of the bead's first gather record in the staged patch, (l + K W^3) mod 8
+// with l the patch record of its cell and K its species. Within a class the
+// slots go round by round: round r takes the r-th bead of every group that
+// has one, in group order, so that consecutive beads (the eight lanes of a
+// shared-memory access phase) read records in distinct bank groups.
+constexpr int kFineBins = 16;
+
 template <typename T>
-__global__ void bin_count(int n_beads, const T* __restrict__ px, const T* __restrict__ py, const T* __restrict__ pz,
-                          T inv_dx, int n, int tiles, int* __restrict__ keys, int* __restrict__ counts) {
+__global__ void bin_count_fine(int n_beads, const T* __restrict__ px, const T* __restrict__ py,
+                               const T* __restrict__ pz, T inv_dx, int n, int nz, int tiles, int patch_w, int patch_lo,
+                               Topology topo, const unsigned char* __restrict__ species_of_id,
+                               const int* __restrict__ id_src, int* __restrict__ fkey, int* __restrict__ frank,
+                               int* __restrict__ fcount) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_beads) return;
-    const int k = tile_key(px[i], py[i], pz[i], inv_dx, n, tiles);
-    keys[i] = k;
-    warp_aggregated_inc(counts, k);  // k < tiles^3: cells are clamped to [0, n) in tile_key
+    const T x = px[i], y = py[i], z = pz[i];
+    const int cx = min(max((int)floor(x * inv_dx), 0), n - 1);
+    const int cy = min(max((int)floor(y * inv_dx), 0), n - 1);
+    const int cz = min(max((int)floor(z * inv_dx), 0), nz - 1);
+    const int tx = cx / kTile, ty = cy / kTile, tz = cz / kTile;
+    const int tile = (tz * tiles + ty) * tiles + tx;
+    const T lx = x * inv_dx - (T)(tx * kTile), ly = y * inv_dx - (T)(ty * kTile), lz = z * inv_dx - (T)(tz * kTile);
+    const T dmin = min(min(min(lx, T(kTile) - lx), min(ly, T(kTile) - ly)), min(lz, T(kTile) - lz));
+    const int edge = dmin < T(0.5) ? 1 : 0;
+    const int b = slot_bead_id(id_src[i]);
+    const int K = species_of_id ? (int)species_of_id[b] : bead_info(topo, b).species;
+    const int rec = ((cz - tz * kTile - patch_lo) * patch_w + (cy - ty * kTile - patch_lo)) * patch_w +
+                    (cx - tx * kTile - patch_lo);
+    const int grp = (rec + K * patch_w * patch_w * patch_w) & 7;
+    const int f = tile * kFineBins + edge * 8 + grp;
+    fkey[i] = f;
+    frank[i] = warp_aggregated_inc(fcount, f);
 }
 
-// species_of_id (NULL: the A/B block pattern of the chains) gives each
-// bead's species.
+// tile_start[t] = fine_start[16 t] for t = 0 .. tiles^3 (the last: n_beads)
+static __global__ void bin_tile_start(const int* __restrict__ fine_start, int n_tiles, int* __restrict__ tile_start) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= n_tiles) tile_start[t] = fine_start[(size_t)t * kFineBins];
+}
+
+// Move every bead (positions, carried velocities, id with species bits) to
+// its slot: the start of its (tile, class) block, plus the beads of earlier
+// rounds, plus those of its round in lower groups.
 template <typename T>
-__global__ void bin_scatter_pos(int n_beads, Topology topo, const unsigned char* __restrict__ species_of_id,
-                                const int* __restrict__ keys, const int* __restrict__ tile_start,
-                                int* __restrict__ cursor, const T* __restrict__ src /*[3][N]*/, T* __restrict__ dst,
-                                const int* __restrict__ id_src, int* __restrict__ id_dst, int* __restrict__ slot_of_id) {
+__global__ void bin_scatter_fine(int n_beads, Topology topo, const unsigned char* __restrict__ species_of_id,
+                                 const int* __restrict__ fkey, const int* __restrict__ frank,
+                                 const int* __restrict__ fcount, const int* __restrict__ fine_start,
+                                 const T* __restrict__ pos_src /*[3][N]*/, T* __restrict__ pos_dst,
+                                 const T* __restrict__ u_src /*[3][N]*/, T* __restrict__ u_dst,
+                                 const int* __restrict__ id_src, int* __restrict__ id_dst, int* __restrict__ slot_of_id) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_beads) return;
-    const int k = keys[i];
-    const int s = tile_start[k] + warp_aggregated_inc(cursor, k);
+    const int f = fkey[i], r = frank[i];
+    const int base = f & ~7, g = f & 7;
+    int s = fine_start[base];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dst[(size_t)c * n_beads + s] = src[(size_t)c * n_beads + i];
+    for (int q = 0; q < 8; ++q) {
+        const int c = fcount[base + q];
+        s += min(c, r) + ((q < g && c > r) ? 1 : 0);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        pos_dst[(size_t)c * n_beads + s] = pos_src[(size_t)c * n_beads + i];
+        u_dst[(size_t)c * n_beads + s] = u_src[(size_t)c * n_beads + i];
+    }
     const int b = slot_bead_id(id_src[i]);
     const int K = species_of_id ? (int)species_of_id[b] : bead_info(topo, b).species;
     id_dst[s] = b | (K << kSpeciesShift);
     slot_of_id[b] = s;
-}
-
-// Within each tile, order the beads by (edge class, cell): beads more than
-// half a cell from every tile face first, then the others, each group by
-// cell (x fastest) so that neighbouring threads of the bead kernel touch
-// neighbouring shared-memory patch points. One CTA per tile; tiles with more
-// than kLocalSortMax beads keep their order.
-template <typename T>
-__global__ void __launch_bounds__(256) bin_local_sort(const int* __restrict__ tile_start, int tiles, int n, T inv_dx,
-                                                      int n_beads, T* __restrict__ pos /*[3][N]*/,
-                                                      T* __restrict__ u /*[3][N]*/, int* __restrict__ id,
-                                                      int* __restrict__ slot_of_id) {
-    constexpr int kLocalSortMax = sizeof(T) == 4 ? 1024 : 640;  // static shared memory <= 48 KB
-    __shared__ T s_v[6][kLocalSortMax];
-    __shared__ int s_id[kLocalSortMax];
-    __shared__ short s_key[kLocalSortMax];
-    __shared__ int s_cnt[2 * kTileCells];
-    const int t = blockIdx.x;
-    const int start = tile_start[t], cnt = tile_start[t + 1] - start;
-    if (cnt <= 1 || cnt > kLocalSortMax) return;
-    const int tx = t % tiles, ty = (t / tiles) % tiles, tz = t / (tiles * tiles);
-    for (int c = threadIdx.x; c < 2 * kTileCells; c += blockDim.x) s_cnt[c] = 0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-        const int i = start + j;
-        const T x = pos[i], y = pos[(size_t)n_beads + i], z = pos[2 * (size_t)n_beads + i];
-        s_v[0][j] = x;
-        s_v[1][j] = y;
-        s_v[2][j] = z;
-        s_v[3][j] = u[i];
-        s_v[4][j] = u[(size_t)n_beads + i];
-        s_v[5][j] = u[2 * (size_t)n_beads + i];
-        s_id[j] = id[i];
-        const int cx = min(max((int)floor(x * inv_dx), 0), n - 1) - tx * kTile;
-        const int cy = min(max((int)floor(y * inv_dx), 0), n - 1) - ty * kTile;
-        const int cz = min(max((int)floor(z * inv_dx), 0), n - 1) - tz * kTile;
-        const int key = (min(max(cz, 0), kTile - 1) * kTile + min(max(cy, 0), kTile - 1)) * kTile + min(max(cx, 0), kTile - 1);
-        // beads within half a cell of a tile face go last: those are the ones
-        // that drift out of the tile's patch before the next re-binning and
-        // take the global-memory paths, so they share as few warps as possible
-        const T lx = x * inv_dx - (T)(tx * kTile), ly = y * inv_dx - (T)(ty * kTile), lz = z * inv_dx - (T)(tz * kTile);
-        const T dmin = min(min(min(lx, T(kTile) - lx), min(ly, T(kTile) - ly)), min(lz, T(kTile) - lz));
-        const int risk = dmin < T(0.5) ? 1 : 0;
-        s_key[j] = (short)(risk * kTileCells + key);
-        atomicAdd(&s_cnt[risk * kTileCells + key], 1);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan of the 2 x 512 (class, cell) counts by one warp
-        int carry = 0;
-        for (int c0 = 0; c0 < 2 * kTileCells; c0 += 32) {
-            const int v = s_cnt[c0 + threadIdx.x];
-            int incl = v;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int n_ = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((int)threadIdx.x >= o) incl += n_;
-            }
-            s_cnt[c0 + threadIdx.x] = carry + incl - v;
-            carry += __shfl_sync(0xffffffffu, incl, 31);
-        }
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-        const int r = atomicAdd(&s_cnt[s_key[j]], 1);
-        const int i = start + r;
-        pos[i] = s_v[0][j];
-        pos[(size_t)n_beads + i] = s_v[1][j];
-        pos[2 * (size_t)n_beads + i] = s_v[2][j];
-        u[i] = s_v[3][j];
-        u[(size_t)n_beads + i] = s_v[4][j];
-        u[2 * (size_t)n_beads + i] = s_v[5][j];
-        id[i] = s_id[j];
-        slot_of_id[slot_bead_id(s_id[j])] = i;
-    }
-}
-
-// Move the carried velocities to the slots assigned by bin_scatter_pos.
-template <typename T>
-__global__ void bin_move_u(int n_beads, const int* __restrict__ id_src, const int* __restrict__ slot_of_id,
-                           const T* __restrict__ src /*[3][N]*/, T* __restrict__ dst) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_beads) return;
-    const int s = slot_of_id[slot_bead_id(id_src[i])];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) dst[(size_t)c * n_beads + s] = src[(size_t)c * n_beads + i];
 }
 
 static __global__ void bin_neighbours(int n_beads, Topology topo, const int* __restrict__ id, const int* __restrict__ slot_of_id,

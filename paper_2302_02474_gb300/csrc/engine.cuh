@@ -61,11 +61,13 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(dev_malloc((void**)&kernel1d_, 2 * n_ * sizeof(T)));  // exp(-a^2 k_m^2), then exp(-a_e^2 k_m^2)
         TILD_CUDA(dev_malloc((void**)&counters_, 4 * sizeof(unsigned long long)));
         TILD_CUDA(cudaMemset(counters_, 0, 4 * sizeof(unsigned long long)));
-        n_tiles_ = tiles_ * tiles_ * tiles_;
-        TILD_CUDA(dev_malloc((void**)&counts_, (n_tiles_ + 1) * sizeof(int)));
+        // tiles of 8^3 cells (one layer of tiles on a 2D grid)
+        n_tiles_ = tiles_ * tiles_ * ((nz_ + kTile - 1) / kTile);
+        n_fine_ = (size_t)kFineBins * n_tiles_ + 1;  // re-binning bins (tile, edge class, bank group)
+        TILD_CUDA(dev_malloc((void**)&counts_, n_fine_ * sizeof(int)));
         TILD_CUDA(dev_malloc((void**)&tile_start_, (n_tiles_ + 1) * sizeof(int)));
-        TILD_CUDA(dev_malloc((void**)&cursor_, (n_tiles_ + 1) * sizeof(int)));
-        scan_blocks_ = (int)((n_tiles_ + 1 + 1023) / 1024);
+        TILD_CUDA(dev_malloc((void**)&fine_start_, n_fine_ * sizeof(int)));
+        scan_blocks_ = (int)((n_fine_ + 1023) / 1024);
         TILD_CUDA(dev_malloc((void**)&block_sums_, scan_blocks_ * sizeof(int)));
         n_z_blocks_ = generic_ ? (size_t)blocks(M_) : (size_t)(n_ / CZ_) * (n_ / 2 + 1);  // two species pairs: twice as many (zpass_cols2)
         n_partials_ = std::max(10 * n_z_blocks_, 5 * (size_t)tiles_ * tiles_ * tiles_);
@@ -109,6 +111,7 @@ template <typename T> class Engine final : public EngineBase {
         TILD_CUDA(dev_malloc((void**)&nbr_, N * sizeof(int2)));
         TILD_CUDA(dev_malloc((void**)&slot_of_id_, N * sizeof(int)));
         TILD_CUDA(dev_malloc((void**)&keys_, N * sizeof(int)));
+        TILD_CUDA(dev_malloc((void**)&ranks_, N * sizeof(int)));
         have_pos_ = have_vel_ = false;
         return upload_topology();
     }
@@ -912,13 +915,14 @@ template <typename T> class Engine final : public EngineBase {
             constexpr int NN = decltype(nn)::value;
             ok = plane_threads == 512 || (plane_fits_ && ((plane_threads == 256 && plane_nt_ok(NN, 256)) ||
                                                          (plane_threads == 128 && plane_nt_ok(NN, 128)) ||
+                                                         (plane_threads == 1024 && plane_nt_ok(NN, 1024)) ||
                                                          (plane_threads == 0 && split_ok(NN))));
             return TILD_OK;
         });
         const int cdef = dispatch_cols(false), calt = dispatch_cols(true);
         if (!ok || (z_cols != cdef && z_cols != calt)) {
-            err = "launch shapes: plane threads must be 512 (or 128/256 where the grid allows, or 0 for the row and "
-                  "column passes) and the z columns the default or the alternative tile";
+            err = "launch shapes: plane threads must be 512 (or 128/256/1024 where the grid allows, or 0 for the row "
+                  "and column passes) and the z columns the default or the alternative tile";
             return TILD_EINVAL;
         }
         invalidate_graph();
@@ -983,11 +987,13 @@ template <typename T> class Engine final : public EngineBase {
     int* id_[2] = {nullptr, nullptr};
     int2* nbr_ = nullptr;
     int* slot_of_id_ = nullptr;
-    int* keys_ = nullptr;
-    int* counts_ = nullptr;
+    int* keys_ = nullptr;   // re-binning: fine bin of each bead
+    int* ranks_ = nullptr;  // and its rank in the bin
+    int* counts_ = nullptr;  // [n_fine_] bead counts of the fine bins
+    size_t n_fine_ = 0;
     int* tile_start_ = nullptr;
     int n_tiles_ = 0;
-    int* cursor_ = nullptr;
+    int* fine_start_ = nullptr;  // [n_fine_] exclusive scan of counts_
     int* block_sums_ = nullptr;
     int scan_blocks_ = 0;
     int cur_pos_ = 0, cur_u_ = 0, cur_id_ = 0;
@@ -1058,6 +1064,15 @@ template <typename T> class Engine final : public EngineBase {
         return c_el_on() ? 4.0 * 3.14159265358979323846 * cfg_->bjerrum * dV * dV / (2.0 * V) * s4 : 0.0;
     }
     size_t bead_smem() const { return bead_smem(analytic(), NS_); }
+    // width and first stencil offset of the bead kernels' shared patch
+    void patch_geometry(int* w, int* lo) const {
+        switch (P_) {
+            case 2: *w = Patch<2>::W; *lo = Patch<2>::lo; break;
+            case 3: *w = Patch<3>::W; *lo = Patch<3>::lo; break;
+            case 4: *w = Patch<4>::W; *lo = Patch<4>::lo; break;
+            default: *w = Patch<5>::W; *lo = Patch<5>::lo; break;
+        }
+    }
     template <int P> static size_t bead_smem_p(bool an, int ns) {
         if (ns == 4) return an ? bead_smem_bytes<P, T, true, 4>() : bead_smem_bytes<P, T, false, 4>();
         return an ? bead_smem_bytes<P, T, true>() : bead_smem_bytes<P, T>();
@@ -1172,10 +1187,11 @@ template <typename T> class Engine final : public EngineBase {
         dev_free(nbr_);
         dev_free(slot_of_id_);
         dev_free(keys_);
+        dev_free(ranks_);
         dev_free(vsave_);
         vsave_ = nullptr;
         nbr_ = nullptr;
-        slot_of_id_ = keys_ = nullptr;
+        slot_of_id_ = keys_ = ranks_ = nullptr;
     }
 
     void release() {
@@ -1183,7 +1199,7 @@ template <typename T> class Engine final : public EngineBase {
         if (stream_) cudaStreamSynchronize(stream_);  // no kernel may still use a block handed back
         free_beads();
         void* ptrs[] = {rho_fx_, Zxy_, H_, grad_, tw_, kernel1d_, spec_, counters_, partials_, counts_,
-                        tile_start_, cursor_, block_sums_, aux_, stage_, theta_, traj_, vjp_fx_,
+                        tile_start_, fine_start_, block_sums_, aux_, stage_, theta_, traj_, vjp_fx_,
                         sp_of_id_, adj_, ext_ids_, ext_slots_, io_};
         for (void* p : ptrs) dev_free(p);
         rho_fx_ = nullptr;
@@ -1299,6 +1315,10 @@ template <typename T> class Engine final : public EngineBase {
                 if constexpr (plane_nt_ok(NN, 128)) {
                     TILD_CUDA(cudaFuncSetAttribute(xy_forward_plane<T, NN, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
                     TILD_CUDA(cudaFuncSetAttribute(xy_inverse_plane<T, NN, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+                }
+                if constexpr (plane_nt_ok(NN, 1024)) {
+                    TILD_CUDA(cudaFuncSetAttribute(xy_forward_plane<T, NN, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
+                    TILD_CUDA(cudaFuncSetAttribute(xy_inverse_plane<T, NN, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
                 }
                 TILD_CUDA(cudaFuncSetAttribute(xy_forward_cplx<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem()));
                 TILD_CUDA(cudaFuncSetAttribute(z_vjp<T, NN, vjp_cols(NN)>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vjp_smem()));
@@ -1442,12 +1462,14 @@ template <typename T> class Engine final : public EngineBase {
     static constexpr int zpass_cols_alt(int n) { return zpass_cols2(n); }
     size_t zpass_smem_cols(int c) const { return ((size_t)n_ + 4 * (size_t)n_ * c) * sizeof(V); }
     // plane kernels with NT threads: stage B of the line transform keeps
-    // ceil(n N1 / NT) units of N2 values per thread; at most 32 complex
+    // ceil(n N1 / NT) units of N2 values per thread; at most 32 complex.
+    // 1024 threads where every thread has a stage-B unit (n N1 >= 1024).
     static constexpr bool plane_nt_ok(int n, int nt) {
         if (nt == 512) return true;
-        if (n > 80 || (nt != 128 && nt != 256)) return false;
-        const int n1 = n == 8 ? 8 : n == 16 ? 4 : (n == 48 || n == 80) ? 16 : 8;
+        const int n1 = n == 8 ? 8 : n == 16 ? 4 : (n == 48 || n == 80 || n == 128 || n == 256) ? 16 : 8;
         const int n2 = n / n1;
+        if (nt == 1024) return sizeof(V) == 8 && n * n1 >= 1024 && n <= 128;
+        if (n > 80 || (nt != 128 && nt != 256)) return false;
         return (n * n1 + nt - 1) / nt * n2 <= 32;
     }
     // The row and column passes (x rows, then y columns, through global
@@ -1462,6 +1484,8 @@ template <typename T> class Engine final : public EngineBase {
     static int zpass_cols_n(int n) { return zpass_cols(n); }
     static int zpass_cols_alt_n(int n) { return zpass_cols_alt(n); }
     template <int NN, class F> void with_nt(F&& f) {
+        if constexpr (plane_nt_ok(NN, 1024))
+            if (plane_nt_ == 1024) return f(ic<1024>{});
         if constexpr (plane_nt_ok(NN, 128))
             if (plane_nt_ == 128) return f(ic<128>{});
         if constexpr (plane_nt_ok(NN, 256))
@@ -1792,19 +1816,20 @@ template <typename T> class Engine final : public EngineBase {
         cudaStream_t stream_ = on ? on : this->stream_;  // the batch re-bins on its own stream
         const int N = cfg_->n_beads;
         const size_t N3 = N;
-        TILD_CUDA(cudaMemsetAsync(counts_, 0, (n_tiles_ + 1) * sizeof(int), stream_));
-        TILD_CUDA(cudaMemsetAsync(cursor_, 0, (n_tiles_ + 1) * sizeof(int), stream_));
+        TILD_CUDA(cudaMemsetAsync(counts_, 0, n_fine_ * sizeof(int), stream_));
         const T* p = pos_[cur_pos_];
-        bin_count<T><<<blocks(N), 256, 0, stream_>>>(N, p, p + N3, p + 2 * N3, (T)((double)n_ / cfg_->L), n_, tiles_, keys_, counts_);
-        scan_blocks<<<scan_blocks_, 1024, 0, stream_>>>(counts_, tile_start_, block_sums_, n_tiles_ + 1);
+        int pw = 0, plo = 0;
+        patch_geometry(&pw, &plo);
+        bin_count_fine<T><<<blocks(N), 256, 0, stream_>>>(N, p, p + N3, p + 2 * N3, (T)((double)n_ / cfg_->L), n_,
+                                                           nz_, tiles_, pw, plo, cfg_->topo, sp_of_id_, id_[cur_id_],
+                                                           keys_, ranks_, counts_);
+        scan_blocks<<<scan_blocks_, 1024, 0, stream_>>>(counts_, fine_start_, block_sums_, (int)n_fine_);
         scan_top<<<1, 1024, 0, stream_>>>(block_sums_, scan_blocks_);
-        scan_add<<<scan_blocks_, 1024, 0, stream_>>>(tile_start_, block_sums_, n_tiles_ + 1);
-        bin_scatter_pos<T><<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, sp_of_id_, keys_, tile_start_, cursor_,
-                                                           pos_[cur_pos_], pos_[1 - cur_pos_], id_[cur_id_],
-                                                           id_[1 - cur_id_], slot_of_id_);
-        bin_move_u<T><<<blocks(N), 256, 0, stream_>>>(N, id_[cur_id_], slot_of_id_, u_[cur_u_], u_[1 - cur_u_]);
-        bin_local_sort<T><<<n_tiles_, 256, 0, stream_>>>(tile_start_, tiles_, n_, (T)((double)n_ / cfg_->L), N,
-                                                          pos_[1 - cur_pos_], u_[1 - cur_u_], id_[1 - cur_id_], slot_of_id_);
+        scan_add<<<scan_blocks_, 1024, 0, stream_>>>(fine_start_, block_sums_, (int)n_fine_);
+        bin_tile_start<<<blocks((size_t)n_tiles_ + 1), 256, 0, stream_>>>(fine_start_, n_tiles_, tile_start_);
+        bin_scatter_fine<T><<<blocks(N), 256, 0, stream_>>>(N, cfg_->topo, sp_of_id_, keys_, ranks_, counts_,
+                                                             fine_start_, pos_[cur_pos_], pos_[1 - cur_pos_], u_[cur_u_],
+                                                             u_[1 - cur_u_], id_[cur_id_], id_[1 - cur_id_], slot_of_id_);
         if (adj_)
             bin_neighbours_explicit<<<blocks(N), 256, 0, stream_>>>(N, id_[1 - cur_id_], slot_of_id_, adj_, ext_ids_,
                                                                     ext_slots_, nbr_);

@@ -16,7 +16,8 @@ namespace tild {
 template __global__ void bead_kernel<2, kModeStep, float>(BeadParams<float>, BeadBuffers<float>);
 template __global__ void bead_kernel<2, kModeForce, float>(BeadParams<float>, BeadBuffers<float>);
 template __global__ void bead_kernel<3, kModeSpread, double>(BeadParams<double>, BeadBuffers<double>);
-template __global__ void bin_count<float>(int, const float*, const float*, const float*, float, int, int, int*, int*);
+template __global__ void bin_count_fine<float>(int, const float*, const float*, const float*, float, int, int, int, int,
+                                              int, Topology, const unsigned char*, const int*, int*, int*, int*);
 }
 '''
 
