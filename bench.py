@@ -420,6 +420,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the step variants")
     ap.add_argument("--no-autotune", action="store_true", help="keep --sort-every instead of autotuning it")
+    ap.add_argument("--launch-shapes", default=None, metavar="PT,ZC",
+                    help="plane threads and z-pass columns of the FFT passes (tild_set_launch_shapes) instead of the "
+                         "defaults; with --mode run, to profile the shapes the autotuner chose")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "diblock_20k_32", "blend_6p4M_256", "batch256", "diff200k"],
                     help="the other configurations (extra measurements): diblock_20k_32 (FP64, 20k beads, 32^3), "
@@ -467,6 +470,9 @@ def main():
     t.set_stream(stream)
     t.set_positions(pos)
     t.init_velocities()
+    if args.launch_shapes:
+        pt, zc = (int(v) for v in args.launch_shapes.split(","))
+        t.set_launch_shapes(pt, zc)
     t.step(args.warmup)
     t.synchronize()
     autotune = None
