@@ -205,6 +205,10 @@ def cufft_comparison(n: int, stage_ms):
             "ours_fwd_z_inv_ms": ours, "note": "cuFFT time excludes the spectral multiply and the fixed-point conversion"}
 
 
+ORACLE_CORES_NOTE = ("the oracle is the plain parity reference (numpy loops, np.add.at and numpy's FFT, all on one "
+                     "core), timed as it stands and reported, not scaled by the host's core count")
+
+
 def oracle_step_rate(spec, pos, n_steps: int, budget_s: float):
     """Time the FP64 oracle (single-threaded numpy) on the same system."""
     from oracle import tild_oracle as O
@@ -244,7 +248,8 @@ def run_reference(args, spec, pos):
            "bead_steps_per_s": rate * spec.n_beads,
            "config": {"workload": args.workload, "beads": spec.n_beads, "grid": spec.n, "box": spec.L,
                       "l2": "working set > L2"},
-           "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample,
+                            "why_one_core": ORACLE_CORES_NOTE},
            "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -574,7 +579,7 @@ def main():
         rate, done, secs, _ = oracle_step_rate(spec, pos, args.cpu_baseline_steps, 60.0)
         cpu = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
                "sample": f"{done} oracle GJF steps of the full {spec.n_beads}-bead system ({secs:.1f} s, "
-                         "single-threaded numpy FP64)"}
+                         "single-threaded numpy FP64)", "why_one_core": ORACLE_CORES_NOTE}
 
     if rank == 0:
         out = {
