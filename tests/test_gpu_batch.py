@@ -160,6 +160,24 @@ def test_plane_threads_1024_and_row_passes_same_bits(B):
         assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
 
 
+def test_plane_shapes_same_bits_at_128(B):
+    """128^3 FP32 (the benchmarked grid): 512- and 1024-thread planes, the
+    row/column passes and both z tiles give the same trajectory and field bits."""
+    spec = I.small_system(n_chains=1500, N=10, n_a=4, L=48.0, n=128, precision="fp32")
+    pos = I.initial_positions(spec)
+    out = []
+    for pt, alt in ((512, False), (1024, True), (1024, False), (0, True)):
+        t = _ctx(B, spec, 4, pos)
+        zdef = t.launch_shapes()[1]
+        t.set_launch_shapes(pt, zdef // 2 if alt else zdef)
+        assert t.launch_shapes()[0] == pt
+        t.step(9)
+        out.append((t.positions(), t.velocities(), t.field_gradient()))
+    for o in out[1:]:
+        for a, b in zip(o, out[0]):
+            assert np.array_equal(a, b)
+
+
 def test_launch_shapes_do_not_change_results(B):
     spec = _spec(REPLICAS[3], "fp32")  # 48^3
     pos = I.initial_positions(spec)
