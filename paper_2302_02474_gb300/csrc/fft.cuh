@@ -141,19 +141,16 @@ template <int DIR, class V> __device__ __forceinline__ V twiddle(const V* tw, in
 // line l lives at buf[addr(l) + e * es]. All NTHR threads of the CTA call
 // this; it ends with __syncthreads(). Stage B keeps all of its work units
 // in registers (UPT per thread), so one round covers every line.
+// Stage A of smem_fft_lines alone (ends with __syncthreads()): unit
+// (line, j2) transforms x[j2 + N2 j1] over j1 and applies W_N^{j2 k1}.
 template <int N, int DIR, int NLINES, int NTHR, class V, class Addr>
-__device__ __forceinline__ void smem_fft_lines(V* buf, Addr addr, int es, const V* tw) {
+__device__ __forceinline__ void smem_fft_stage_a(V* buf, Addr addr, int es, const V* tw) {
     constexpr int N1 = fft_split<N>::N1;
     constexpr int N2 = fft_split<N>::N2;
-    constexpr int nlines = NLINES;
-    constexpr int nthr = NTHR;
-    constexpr int UPT = (NLINES * N1 + NTHR - 1) / NTHR;
-    const int tid = threadIdx.x;
-
     // Stage A: unit (line, j2); reads and writes only its own positions.
-    for (int u = tid; u < nlines * N2; u += nthr) {
-        const int l = u % nlines;
-        const int j2 = u / nlines;
+    for (int u = threadIdx.x; u < NLINES * N2; u += NTHR) {
+        const int l = u % NLINES;
+        const int j2 = u / NLINES;
         V* p = buf + addr(l) + j2 * es;
         V v[N1];
 #pragma unroll
@@ -167,6 +164,17 @@ __device__ __forceinline__ void smem_fft_lines(V* buf, Addr addr, int es, const 
         for (int k1 = 0; k1 < N1; ++k1) p[k1 * N2 * es] = v[k1];
     }
     __syncthreads();
+}
+
+template <int N, int DIR, int NLINES, int NTHR, class V, class Addr>
+__device__ __forceinline__ void smem_fft_lines(V* buf, Addr addr, int es, const V* tw) {
+    constexpr int N1 = fft_split<N>::N1;
+    constexpr int N2 = fft_split<N>::N2;
+    constexpr int nthr = NTHR;
+    constexpr int UPT = (NLINES * N1 + NTHR - 1) / NTHR;
+    const int tid = threadIdx.x;
+
+    smem_fft_stage_a<N, DIR, NLINES, NTHR>(buf, addr, es, tw);
     if (N2 == 1) return;
 
     // Stage B: unit (line, k1) reads the N2 positions j2 + N2 k1 and writes

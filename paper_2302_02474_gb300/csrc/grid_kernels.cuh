@@ -401,27 +401,40 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
                                        int p0, const int (&ky)[2], bool want_e, double (&acc)[5], const T* e2) {
     using V = cplx_t<T>;
     constexpr int TS = N * C;
-    smem_fft_lines<N, -1, R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
     static_assert(256 % C == 0, "a thread keeps one column");
     constexpr int rB = R - 1;
-    // per-thread column constants (element A in row 0, its mirror B in row rB)
-    const int c = threadIdx.x % C;
-    const int cB = mirror_pos(p0 + c) - p0;
-    const int kxA = kx_of_pos<N>(p0 + c), kxB = kx_of_pos<N>(p0 + cB);
-    const T exyA = e1[kxA] * e1[ky[0]], exyB = e1[kxB] * e1[ky[rB]];
-    const bool zeroA = (kxA == 0 && ky[0] == 0), zeroB = (kxB == 0 && ky[rB] == 0);
-    // |k_x|^2 + |k_y|^2 of A and B (the Nyquist index counts as -n/2)
-    const T qxA = raw_k<T, N>(kxA, sp.two_pi_over_L), qyA = raw_k<T, N>(ky[0], sp.two_pi_over_L);
-    const T qxB = raw_k<T, N>(kxB, sp.two_pi_over_L), qyB = raw_k<T, N>(ky[rB], sp.two_pi_over_L);
-    const double kxy2A = (double)qxA * qxA + (double)qyA * qyA, kxy2B = (double)qxB * qxB + (double)qyB * qyB;
-    const T exy2A = EL ? e2[kxA] * e2[ky[0]] : T(0), exy2B = EL ? e2[kxB] * e2[ky[rB]] : T(0);
-    for (int kz = threadIdx.x / C; kz < N; kz += 256 / C) {
-        const int kzB = kz == 0 ? 0 : N - kz;
-        if (R == 1 && kzB * C + cB < kz * C + c) continue;  // the mirror element owns this pair
-        const bool same = (R == 1) && (kzB == kz) && (cB == c);
-        const V ZA = buf[kz * C + c];
-        const V ZB = buf[rB * TS + kzB * C + cB];
-        V out[2][2];
+    // column constants of element A (row 0, column c) and its mirror B (row
+    // rB, column cB)
+    struct Col {
+        int cB;
+        T exyA, exyB, exy2A, exy2B;
+        bool zeroA, zeroB;
+        double kxy2A, kxy2B;  // |k_x|^2 + |k_y|^2 (the Nyquist index counts as -n/2)
+    };
+    auto col_of = [&](int c) {
+        Col cl;
+        cl.cB = mirror_pos(p0 + c) - p0;
+        const int kxA = kx_of_pos<N>(p0 + c), kxB = kx_of_pos<N>(p0 + cl.cB);
+        cl.exyA = e1[kxA] * e1[ky[0]];
+        cl.exyB = e1[kxB] * e1[ky[rB]];
+        cl.zeroA = (kxA == 0 && ky[0] == 0);
+        cl.zeroB = (kxB == 0 && ky[rB] == 0);
+        const T qxA = raw_k<T, N>(kxA, sp.two_pi_over_L), qyA = raw_k<T, N>(ky[0], sp.two_pi_over_L);
+        const T qxB = raw_k<T, N>(kxB, sp.two_pi_over_L), qyB = raw_k<T, N>(ky[rB], sp.two_pi_over_L);
+        cl.kxy2A = (double)qxA * qxA + (double)qyA * qyA;
+        cl.kxy2B = (double)qxB * qxB + (double)qyB * qyB;
+        cl.exy2A = EL ? e2[kxA] * e2[ky[0]] : T(0);
+        cl.exy2B = EL ? e2[kxB] * e2[ky[rB]] : T(0);
+        return cl;
+    };
+    // the spectral multiply of one mirror pair: ZA = Z(k) at (row 0, c, kz),
+    // ZB = Z(-k) at (row rB, cB, kzB); out[s][d]: s = 0 for A, 1 for B,
+    // d = 0 for iQ (G), 1 for i k_z Q (G_z)
+    struct Out {
+        V g[2], gz[2];  // iQ and i k_z Q of A (0) and B (1)
+    };
+    auto mult = [&](const Col& cl, V ZA, V ZB, int kz, int kzB, bool same) {
+        Out out;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (s == 1 && same) break;
@@ -429,7 +442,7 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
             const V Zm = s == 0 ? ZB : ZA;  // Z(-k)
             const int kzi = s == 0 ? kz : kzB;
             const T kzv = grad_k<T, N>(kzi, sp.two_pi_over_L);
-            const T uh = (s == 0 ? exyA : exyB) * e1[kzi];
+            const T uh = (s == 0 ? cl.exyA : cl.exyB) * e1[kzi];
             // rho~_A = (Z + conj Zm)/2, rho~_B = -i (Z - conj Zm)/2
             const V A = {T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y)};
             const V B = {T(0.5) * (Z.y + Zm.y), -T(0.5) * (Z.x - Zm.x)};
@@ -437,11 +450,11 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
                 // energy sums and their |k|^2-weighted versions (d u_hat / d a = -2 a |k|^2 u_hat)
                 const double ar = A.x, ai = A.y, br = B.x, bi = B.y;
                 const double qz = (double)raw_k<T, N>(kzi, sp.two_pi_over_L);
-                const double k2 = (s == 0 ? kxy2A : kxy2B) + qz * qz;
+                const double k2 = (s == 0 ? cl.kxy2A : cl.kxy2B) + qz * qz;
                 const double fchi = (double)uh * (ar * br + ai * bi);
                 acc[0] += fchi;
                 acc[2] += k2 * fchi;
-                if (!((s == 0 ? zeroA : zeroB) && kzi == 0)) {
+                if (!((s == 0 ? cl.zeroA : cl.zeroB) && kzi == 0)) {
                     const double fkap = (double)uh * ((ar + br) * (ar + br) + (ai + bi) * (ai + bi));
                     acc[1] += fkap;
                     acc[3] += k2 * fkap;
@@ -452,8 +465,8 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
             if (EL) {
                 // w_K += q_K c(k) rho~_q with rho~_q = q_A rho~_A + q_B rho~_B
                 const T qzv = raw_k<T, N>(kzi, sp.two_pi_over_L);
-                const T k2 = (T)(s == 0 ? kxy2A : kxy2B) + qzv * qzv;
-                const T g = k2 > T(0) ? (s == 0 ? exy2A : exy2B) * e2[kzi] * recip(k2) : T(0);
+                const T k2 = (T)(s == 0 ? cl.kxy2A : cl.kxy2B) + qzv * qzv;
+                const T g = k2 > T(0) ? (s == 0 ? cl.exy2A : cl.exy2B) * e2[kzi] * recip(k2) : T(0);
                 const V rq = {sp.qA * A.x + sp.qB * B.x, sp.qA * A.y + sp.qB * B.y};
                 const T c = sp.el_scale * g;
                 wA.x += c * sp.qA * rq.x;
@@ -463,14 +476,70 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
                 if (want_e) acc[4] += (double)g * ((double)rq.x * rq.x + (double)rq.y * rq.y);
             }
             const V iQ = {-(wA.y + wB.x), wA.x - wB.y};  // i (w~_A + i w~_B)
-            out[s][0] = iQ;                               // x, y: k_x, k_y applied in the xy pass
-            out[s][1] = {kzv * iQ.x, kzv * iQ.y};         // z
+            out.g[s] = iQ;                                // x, y: k_x, k_y applied in the xy pass
+            out.gz[s] = {kzv * iQ.x, kzv * iQ.y};         // z
         }
+        return out;
+    };
+    auto store = [&](const Out& out, int c, int cB, int kz, int kzB, bool same) {
+        buf[kz * C + c] = out.g[0];
+        if (!same) buf[rB * TS + kzB * C + cB] = out.g[1];
+        if (!G_ONLY) {
+            buf[R * TS + kz * C + c] = out.gz[0];
+            if (!same) buf[(R + rB) * TS + kzB * C + cB] = out.gz[1];
+        }
+    };
+    constexpr int N1 = fft_split<N>::N1, N2 = fft_split<N>::N2;
+    if constexpr (R == 2 && !EL && N2 > 1 && C * N1 == 256) {
+        // two rows: the forward transform's second stage and the multiply in
+        // registers (tiles where every thread has one pair of units). Thread q
+        // takes stage-B unit (row 0, column c, k1)
+        // and the unit holding the mirrors of its outputs, (row 1, column cB,
+        // (N1 - k1) mod N1); the outputs X[k1 + N1 k2] of the first meet
+        // their mirrors X[-(k1 + N1 k2)] in the second, so each pair is
+        // multiplied where the transform left it (same operations as the
+        // transform followed by the loop below).
+        smem_fft_stage_a<N, -1, R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+        const int q = threadIdx.x;
+        const bool active = q < C * N1;
+        const int c = q % C, k1 = q / C;
+        const int k1B = (N1 - k1) % N1;
+        const Col cl = col_of(c);
+        V va[N2], vb[N2];
+        if (active) {
+            const V* pa = buf + c + k1 * N2 * C;             // line c of row 0: positions k1 N2 + j2
+            const V* pb = buf + TS + cl.cB + k1B * N2 * C;   // line cB of row 1
 #pragma unroll
-        for (int d = 0; d < 2; ++d) {
-            if (d == 1 && G_ONLY) break;
-            buf[(d * R) * TS + kz * C + c] = out[0][d];
-            if (!same) buf[(d * R + rB) * TS + kzB * C + cB] = out[1][d];
+            for (int j2 = 0; j2 < N2; ++j2) {
+                va[j2] = pa[j2 * C];
+                vb[j2] = pb[j2 * C];
+            }
+        }
+        __syncthreads();  // every stage-B input is read before any output is written
+        if (active) {
+            reg_dft<N2, -1, V>::run(va);
+            reg_dft<N2, -1, V>::run(vb);
+            // the mirror of output k2: (N2 - k2) mod N2 when k1 = 0, else N2 - 1 - k2
+            // (selected with constant indices, so the arrays stay in registers)
+            V vm[N2];
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) vm[k2] = k1 == 0 ? vb[(N2 - k2) % N2] : vb[N2 - 1 - k2];
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int kz = k1 + N1 * k2;
+                const int kzB = kz == 0 ? 0 : N - kz;
+                store(mult(cl, va[k2], vm[k2], kz, kzB, false), c, cl.cB, kz, kzB, false);
+            }
+        }
+    } else {
+        smem_fft_lines<N, -1, R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+        const int c = threadIdx.x % C;
+        const Col cl = col_of(c);
+        for (int kz = threadIdx.x / C; kz < N; kz += 256 / C) {
+            const int kzB = kz == 0 ? 0 : N - kz;
+            if (R == 1 && kzB * C + cl.cB < kz * C + c) continue;  // the mirror element owns this pair
+            const bool same = (R == 1) && (kzB == kz) && (cl.cB == c);
+            store(mult(cl, buf[kz * C + c], buf[rB * TS + kzB * C + cl.cB], kz, kzB, same), c, cl.cB, kz, kzB, same);
         }
     }
     __syncthreads();
