@@ -217,3 +217,40 @@ template <int LS> struct StridedLines {
 };
 
 }  // namespace tild
+
+namespace tild {
+
+// smem_fft_lines whose second stage hands each output to out(l, k, X_l[k])
+// instead of writing it back to shared memory (the caller's last use of the
+// lines, e.g. a store to global memory); no barrier at the end. N2 > 1.
+template <int N, int DIR, int NLINES, int NTHR, class V, class Addr, class Out>
+__device__ __forceinline__ void smem_fft_lines_out(V* buf, Addr addr, int es, const V* tw, Out out) {
+    constexpr int N1 = fft_split<N>::N1;
+    constexpr int N2 = fft_split<N>::N2;
+    static_assert(N2 > 1, "two-stage lengths only");
+    constexpr int UPT = (NLINES * N1 + NTHR - 1) / NTHR;
+    smem_fft_stage_a<N, DIR, NLINES, NTHR>(buf, addr, es, tw);
+    V v[UPT][N2];
+#pragma unroll
+    for (int r = 0; r < UPT; ++r) {
+        const int u = threadIdx.x + r * NTHR;
+        if (u < NLINES * N1) {
+            const int l = u % NLINES, k1 = u / NLINES;
+            const V* p = buf + addr(l) + k1 * N2 * es;
+#pragma unroll
+            for (int j2 = 0; j2 < N2; ++j2) v[r][j2] = p[j2 * es];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < UPT; ++r) {
+        const int u = threadIdx.x + r * NTHR;
+        if (u < NLINES * N1) {
+            const int l = u % NLINES, k1 = u / NLINES;
+            reg_dft<N2, DIR, V>::run(v[r]);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) out(l, k1 + N1 * k2, v[r][k2]);
+        }
+    }
+}
+
+}  // namespace tild

@@ -396,9 +396,11 @@ template <typename T> __device__ __forceinline__ int freq_index(int i, int n) { 
 // with Q = w~_A + i w~_B. Buffers [2R][N][C]: G of row r in buffer r
 // (overwriting the input), G_z in buffer R + r.
 // --------------------------------------------------------------------------
-template <typename T, int N, int C, int R, bool G_ONLY, bool EL>
+// out(b, c, z, v): output element z of column c of buffer b (the inverse
+// transforms' results, handed over as their last stage produces them).
+template <typename T, int N, int C, int R, bool G_ONLY, bool EL, class Out>
 __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, const T* e1, const SpectralParams<T>& sp,
-                                       int p0, const int (&ky)[2], bool want_e, double (&acc)[5], const T* e2) {
+                                       int p0, const int (&ky)[2], bool want_e, double (&acc)[5], const T* e2, Out out) {
     using V = cplx_t<T>;
     constexpr int TS = N * C;
     static_assert(256 % C == 0, "a thread keeps one column");
@@ -430,11 +432,11 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
     // the spectral multiply of one mirror pair: ZA = Z(k) at (row 0, c, kz),
     // ZB = Z(-k) at (row rB, cB, kzB); out[s][d]: s = 0 for A, 1 for B,
     // d = 0 for iQ (G), 1 for i k_z Q (G_z)
-    struct Out {
+    struct Mult {
         V g[2], gz[2];  // iQ and i k_z Q of A (0) and B (1)
     };
     auto mult = [&](const Col& cl, V ZA, V ZB, int kz, int kzB, bool same) {
-        Out out;
+        Mult out;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (s == 1 && same) break;
@@ -481,7 +483,7 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
         }
         return out;
     };
-    auto store = [&](const Out& out, int c, int cB, int kz, int kzB, bool same) {
+    auto store = [&](const Mult& out, int c, int cB, int kz, int kzB, bool same) {
         buf[kz * C + c] = out.g[0];
         if (!same) buf[rB * TS + kzB * C + cB] = out.g[1];
         if (!G_ONLY) {
@@ -543,7 +545,14 @@ __device__ __forceinline__ void z_tile(cplx_t<T>* buf, const cplx_t<T>* tw, cons
         }
     }
     __syncthreads();
-    smem_fft_lines<N, +1, (G_ONLY ? 1 : 2) * R * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+    constexpr int NB = (G_ONLY ? 1 : 2) * R;  // output buffers
+    if constexpr (N2 > 1) {
+        smem_fft_lines_out<N, +1, NB * C, 256>(buf, TileAddr<C, TS>{}, C, tw,
+                                                [&](int l, int z, V v) { out(l / C, l % C, z, v); });
+    } else {
+        smem_fft_lines<N, +1, NB * C, 256>(buf, TileAddr<C, TS>{}, C, tw);
+        for (int i = threadIdx.x; i < NB * TS; i += blockDim.x) out(i / TS, i % C, (i % TS) / C, buf[i]);
+    }
 }
 
 template <typename T> struct ZArgs {
@@ -606,10 +615,18 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
         }
         return;
     }
+    const size_t M = NN * N;
+    // G of row r to field 0, G_z to field 2, at (z, ky[r], p0 + c)
+    auto store_h = [&](int rr, int b, int c, int z, V v) {
+        const int f = (b / rr) * 2, r = b % rr;
+        H[f * M + z * NN + (size_t)ky[r] * N + p0 + c] = v;
+    };
     if (R == 1)
-        z_tile<T, N, C, 1, G_ONLY, EL>(buf, tw, e1, sp, p0, ky, want_e, acc, e2);
+        z_tile<T, N, C, 1, G_ONLY, EL>(buf, tw, e1, sp, p0, ky, want_e, acc, e2,
+                                       [&](int b, int c, int z, V v) { store_h(1, b, c, z, v); });
     else
-        z_tile<T, N, C, 2, G_ONLY, EL>(buf, tw, e1, sp, p0, ky, want_e, acc, e2);
+        z_tile<T, N, C, 2, G_ONLY, EL>(buf, tw, e1, sp, p0, ky, want_e, acc, e2,
+                                       [&](int b, int c, int z, V v) { store_h(2, b, c, z, v); });
     if (want_e) {
         // block reduction in a fixed order (deterministic)
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -626,14 +643,6 @@ __device__ __forceinline__ void z_spectral_body(const ZArgs<T>& args, int bx, in
             const size_t b = (size_t)by * gdx + bx;
             energy_partials[5 * b + threadIdx.x] = sum;
         }
-    }
-    const size_t M = NN * N;
-    const int nbuf = (G_ONLY ? 1 : 2) * R * TS;
-    for (int i = threadIdx.x; i < nbuf; i += blockDim.x) {
-        const int b = i / TS, rem = i % TS;
-        const int f = (b / R) * 2, r = b % R;  // fields 0 (G) and 2 (G_z)
-        const int z = rem / C, c = rem % C;
-        H[f * M + z * NN + (size_t)ky[r] * N + p0 + c] = buf[i];
     }
 }
 
